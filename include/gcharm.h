@@ -1,0 +1,313 @@
+/*
+ * gcharm.h -- C ABI of libgcharm, a GB300 (sm_103a) engine for batches of
+ * many small, irregular pair-interaction work requests, after the G-Charm
+ * runtime strategies of Rengasamy & Vadhiyar (arXiv 2008.05712).
+ *
+ * Model (Section 2.2, Section 3.1, Section 3.2 of the paper):
+ *   - Application objects create work requests ("tasks"), each naming the
+ *     data items it reads by index (Section 2.2, Section 3.2: a workRequest
+ *     carries the buffer indices of its data).
+ *   - Pending tasks are combined into one batch and executed by one set of
+ *     kernel launches instead of one launch per task (Section 3.1).
+ *   - A chare table maps data ids to device-memory slots so that data
+ *     already resident is reused and only missing data is transferred
+ *     (Section 3.2); the data each task reads is then gathered in sorted
+ *     slot order into contiguous staging so the interaction kernel reads it
+ *     coalesced (Section 3.2, Fig. 1d).
+ *
+ * Two interaction kinds are provided, from the paper's two applications:
+ *   GC_GRAVITY  (Section 4.1, ChaNGa buckets): for every target i of the
+ *               task and every source j of its interaction list,
+ *               a_i += m_j r_ij / (|r_ij|^2 + eps2)^(3/2),
+ *               phi_i -= m_j / (|r_ij|^2 + eps2)^(1/2),  r_ij = x_j - x_i.
+ *   GC_LJ_PAIR / GC_LJ_SELF (Section 4.2, interact() of a compute object
+ *               on two patches, updating the forces of both): truncated
+ *               Lennard-Jones forces between the atoms of cell A (targets)
+ *               and cell B (sources, shifted by the task's cell offset);
+ *               a self task uses the pairs i < j of cell A.
+ *
+ * Conventions for every function:
+ *   - Return GC_OK (0) or a negative GC_ERR_* code; on any error the pool
+ *     stays valid and the pending batch is unchanged unless stated.
+ *   - Host pointers are caller-owned and only read (or written, for
+ *     outputs) during the call.  "Device" pointers are CUDA device
+ *     addresses on the pool's device; they are read in stream order on the
+ *     pool's stream and must stay valid until the operation completes.
+ *   - A pool is not thread-safe: one host thread at a time.
+ *   - Data values are float4 records (x, y, z, w): for gravity w is the
+ *     mass; for LJ atoms xyz is the atom's offset from its cell's origin (an
+ *     exact multiple of 2^-21) and w is ignored.
+ */
+#ifndef GCHARM_H
+#define GCHARM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque pool handle (library-owned). */
+typedef struct gc_pool gc_pool_t;
+
+/* ---- status codes ------------------------------------------------------ */
+#define GC_OK 0
+#define GC_ERR_ARG (-1)         /* bad argument or configuration           */
+#define GC_ERR_OOM (-2)         /* device or pinned host allocation failed */
+#define GC_ERR_POOL_FULL (-3)   /* batch references more distinct ids than
+                                   the pool can hold at once               */
+#define GC_ERR_UNKNOWN_ID (-4)  /* a task references an id >= id_capacity or
+                                   never uploaded; the batch is dropped    */
+#define GC_ERR_BUDGET (-5)      /* one task alone exceeds the staging budget */
+#define GC_ERR_NOT_READY (-6)   /* results requested before completion     */
+#define GC_ERR_TIMEOUT (-7)     /* wait or device-side poll ran out        */
+#define GC_ERR_CUDA (-8)        /* a CUDA runtime call failed              */
+#define GC_ERR_STATE (-9)       /* call not valid in the pool's state      */
+
+/* ---- task kinds -------------------------------------------------------- */
+#define GC_GRAVITY 0u
+#define GC_LJ_PAIR 1u
+#define GC_LJ_SELF 2u
+
+/* ---- configuration (gc_pool_create) ------------------------------------ */
+typedef struct {
+    float eps2;                   /* gravity softening squared, > 0        */
+    float lj_eps, lj_sigma;       /* LJ well depth and diameter, > 0       */
+    float lj_rc2;                 /* LJ cutoff squared; rc2 * 2^42 must be
+                                     an integer (cutoff decided exactly on
+                                     the 2^-21 grid)                       */
+    float md_edge;                /* MD cell edge, a multiple of 2^-21     */
+    uint64_t id_capacity;         /* data ids must be < id_capacity        */
+    uint64_t pool_capacity;       /* device slots (resident data items)   */
+    uint64_t staging_budget_bytes;/* max staging bytes per flush wave; 0 =
+                                     no limit                              */
+    int deterministic;            /* 1: per-id totals summed in admission
+                                     order (always on in this version)     */
+    void *cuda_stream;            /* cudaStream_t the pool issues on; NULL =
+                                     the legacy default stream             */
+} gc_config;
+
+/* ---- one task (gc_submit) ---------------------------------------------- */
+typedef struct {
+    uint64_t task_id;             /* caller's tag, returned with results   */
+    uint32_t kind;                /* GC_GRAVITY | GC_LJ_PAIR | GC_LJ_SELF   */
+    uint32_t n_targets, n_sources;
+    const uint32_t *target_ids;   /* host, n_targets ids                   */
+    const uint32_t *source_ids;   /* host, n_sources ids (LJ_SELF: none)   */
+    int8_t shift[3];              /* LJ: cell offset of B from A, in cells  */
+} gc_task;
+
+/* ---- statistics -------------------------------------------------------- */
+typedef struct {
+    uint64_t flushes;             /* batches executed                       */
+    uint64_t tasks;               /* tasks executed                         */
+    uint64_t entries;             /* id references (targets + sources)      */
+    uint64_t unique;              /* distinct ids referenced, summed/flush  */
+    uint64_t hits;                /* distinct ids found resident            */
+    uint64_t misses;              /* distinct ids fetched from host memory  */
+    uint64_t updates;             /* uploads that overwrote a resident slot */
+    uint64_t evictions;           /* resident ids evicted                   */
+    uint64_t h2d_bytes;           /* bytes moved host -> device             */
+    uint64_t interactions;        /* pair interactions evaluated            */
+    uint64_t lj_pairs_in_cutoff;  /* LJ pairs inside the cutoff (last flush) */
+    uint64_t last_unique, last_hits, last_misses, last_evictions;
+    uint64_t last_staging_bytes;  /* staging bytes of the last flush        */
+    uint64_t last_waves;          /* waves the last flush was split into    */
+    uint64_t reuse_hist[8];       /* last flush: distinct ids referenced
+                                     1, 2, 3-4, 5-8, 9-16, 17-32, 33-64,
+                                     >64 times                             */
+} gc_stats_t;
+
+/* ---- pool lifetime and data -------------------------------------------- */
+
+/* Create a pool: device slots, the chare table (id -> slot), a pinned host
+ * mirror of every id's value, and per-id FP64 totals.  *out receives the
+ * handle.  Errors: GC_ERR_ARG (zero capacities, eps2 <= 0, bad LJ values),
+ * GC_ERR_OOM, GC_ERR_CUDA. */
+int gc_pool_create(const gc_config *cfg, gc_pool_t **out);
+
+/* Release everything the pool owns.  Waits for its stream first. */
+int gc_pool_destroy(gc_pool_t *pool);
+
+/* Store values for ids (host arrays, n ids and 4n floats).  A resident id is
+ * overwritten in its slot (an update, not a miss); a non-resident id is
+ * stored in the host mirror and fetched at the next flush that references
+ * it.  Duplicate ids in one call: one of the values wins.  Waits for the
+ * pool's stream before writing the mirror.  Errors: GC_ERR_ARG (id >=
+ * id_capacity), GC_ERR_CUDA. */
+int gc_pool_upload(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
+                   uint64_t n);
+
+/* As gc_pool_upload, with device arrays, in stream order (no host wait).
+ * Ids are not checked on the host; an id >= id_capacity sets the pool's
+ * device error flag and is skipped (reported by the next flush). */
+int gc_pool_upload_device(gc_pool_t *pool, const uint32_t *ids_dev,
+                          const float *xyzm_dev, uint64_t n);
+
+/* ---- batching ---------------------------------------------------------- */
+
+/* Append tasks to the pending batch (host descriptors; ids are copied).
+ * *batch_out (may be NULL) receives the index the next gc_flush will give
+ * this batch.  Errors: GC_ERR_ARG (unknown kind, LJ_SELF with sources),
+ * GC_ERR_BUDGET (one task's staging exceeds the budget), GC_ERR_OOM. */
+int gc_submit(gc_pool_t *pool, const gc_task *tasks, uint64_t n,
+              uint64_t *batch_out);
+
+/* Append n_tasks tasks given as CSR arrays: task t has targets
+ * tgt_ids[tgt_off[t] .. tgt_off[t+1]) and sources src_ids[src_off[t] ..
+ * src_off[t+1]), kind kinds[t], shift shifts[3t..3t+2] (may be NULL: all
+ * zero), tag task_ids[t] (NULL: running task counter).  on_device = 0:
+ * all arrays are host arrays.  on_device = 1: all arrays are device arrays
+ * and n_tgt_total / n_src_total must equal tgt_off[n_tasks] /
+ * src_off[n_tasks] (the offsets are not read on the host).  Offsets must
+ * start at 0 and not decrease. */
+int gc_submit_csr(gc_pool_t *pool, uint64_t n_tasks, const uint64_t *task_ids,
+                  const uint32_t *kinds, const int8_t *shifts,
+                  const uint64_t *tgt_off, const uint32_t *tgt_ids,
+                  const uint64_t *src_off, const uint32_t *src_ids,
+                  uint64_t n_tgt_total, uint64_t n_src_total, int on_device,
+                  uint64_t *batch_out);
+
+/* Run the pending batch: residency (chare-table lookup, slot allocation in
+ * ascending id order, eviction of the least recently used unreferenced ids
+ * when the pool is full, fetch of misses from the host mirror), pack
+ * (per list, entries in ascending (slot, list position) order gathered into
+ * contiguous float4 staging), interaction (FP32 pair arithmetic with
+ * compensated accumulation), and the FP64 per-id accumulation of totals.
+ * Reads a few counters back to the host after the residency step; the rest
+ * is queued on the pool's stream.  Errors: GC_ERR_UNKNOWN_ID (batch
+ * dropped), GC_ERR_POOL_FULL (batch dropped, pool unchanged),
+ * GC_ERR_CUDA.  Flushing an empty batch is a no-op. */
+int gc_flush(gc_pool_t *pool);
+
+/* Wait until batch `batch` (as returned by the submit calls) has completed,
+ * for at most timeout_ns (0 = forever).  GC_ERR_TIMEOUT if it has not. */
+int gc_wait(gc_pool_t *pool, uint64_t batch, uint64_t timeout_ns);
+
+/* ---- results ----------------------------------------------------------- */
+
+/* Number of result rows of the last completed batch: one per target, plus
+ * one per source for GC_LJ_PAIR tasks (targets first), in admission order. */
+int gc_result_rows(gc_pool_t *pool, uint64_t *rows_out);
+
+/* Copy the per-row results of the last batch, 8 floats per row: the
+ * compensated partial (s0..s3, c0..c3) whose value is s - c; for gravity
+ * (ax, ay, az, phi), for LJ (fx, fy, fz, U/2).  first_row / n_rows select a
+ * range.  Errors: GC_ERR_ARG (range outside the batch). */
+int gc_read_batch_results(gc_pool_t *pool, uint64_t first_row, uint64_t n_rows,
+                          float *out);
+
+/* Copy the result rows of the tasks with the given tags (each from the last
+ * batch), task after task, 8 floats per row.  Errors: GC_ERR_ARG (tag not in
+ * the last batch). */
+int gc_read_results(gc_pool_t *pool, const uint64_t *task_ids, uint64_t n,
+                    float *partial_sum_comp);
+
+/* Per-id FP64 totals accumulated by every batch since the last reset:
+ * 4 doubles per id (sum over the id's result rows of s - c). */
+int gc_read_totals(gc_pool_t *pool, const uint32_t *ids, uint64_t n,
+                   double *acc4);
+
+/* Device address of the totals array (double4 per id, id_capacity rows). */
+int gc_totals_device(gc_pool_t *pool, const double **totals_dev);
+
+/* Zero all per-id totals (stream-ordered). */
+int gc_reset_totals(gc_pool_t *pool);
+
+/* Counters since creation plus details of the last flush. */
+int gc_stats(gc_pool_t *pool, gc_stats_t *out);
+
+/* Human-readable text for a status code (static string). */
+const char *gc_strerror(int status);
+
+/* ---- introspection of the last batch (integer work, for checking) ----- */
+
+/* Slot of every entry of the last batch: n_tgt target entries then n_src
+ * source entries, in admission order. */
+int gc_read_entry_slots(gc_pool_t *pool, uint32_t *tgt_slots, uint32_t *src_slots);
+
+/* Pack permutation of the last batch: for each list, perm[k] = list
+ * position of the k-th staged entry (ascending (slot, position)). */
+int gc_read_pack_perm(gc_pool_t *pool, uint32_t *tgt_perm, uint32_t *src_perm);
+
+/* Sizes of the last batch. */
+int gc_batch_sizes(gc_pool_t *pool, uint64_t *n_tasks, uint64_t *n_tgt,
+                   uint64_t *n_src);
+
+/* Copy the chare table: slot_of_id (id_capacity), id_of_slot and last_use
+ * (pool_capacity each); NONE = 0xFFFFFFFF.  Any pointer may be NULL. */
+int gc_read_residency(gc_pool_t *pool, uint32_t *slot_of_id, uint32_t *id_of_slot,
+                      uint32_t *last_use);
+
+/* Ids evicted by the last flush, in the order they were chosen. */
+int gc_read_evicted(gc_pool_t *pool, uint32_t *ids, uint64_t cap, uint64_t *n_out);
+
+/* ---- task builders on the device --------------------------------------- */
+
+/* N-body tasks (Section 4.1): build the Barnes-Hut octree of the n
+ * particles xyzm_dev (device, 4 floats per particle; particle p has data id
+ * p) and append one GC_GRAVITY task per bucket to the pending batch:
+ * targets = the bucket's particles in Morton order, sources = its
+ * interaction list.  Tree: 21-bit grid per axis over the bounding cube
+ * (power-of-two edge), Morton keys with x in bit 0, stable sort by key;
+ * cells with more than bucket_max particles split into their non-empty
+ * octants (octant order), a finest-level leaf with more is cut into chunks
+ * of bucket_max; nodes numbered in depth-first preorder, node k has data id
+ * n + k and value (centre of mass, mass), uploaded to the pool by this
+ * call.  Walk: nodes containing the bucket are opened; any other node is
+ * accepted iff theta_den^2 s^2 < theta_num^2 d^2 (s node edge, d distance
+ * from the node centre to the bucket's box, integer doubled grid units);
+ * opened leaves contribute their particles.  theta_num, theta_den in
+ * [0, 255], theta_den >= 1.  Requires id_capacity >= n + node count.
+ * task_id of bucket b = task_id_base + b.  info_out (may be NULL) receives
+ * {n_nodes, n_buckets, list entries, max list length}.  Errors: GC_ERR_ARG,
+ * GC_ERR_POOL_FULL (ids would exceed id_capacity), GC_ERR_OOM. */
+int gc_build_nbody_tasks(gc_pool_t *pool, const float *xyzm_dev, uint64_t n,
+                         int bucket_max, int theta_num, int theta_den,
+                         uint64_t task_id_base, uint64_t info_out[4]);
+
+/* Copy the last N-body tree: sorted ids (n) and keys (n); per node (nn):
+ * level, cell[3], first, count, leaf, subtree size; per bucket (nb): first,
+ * count, leaf node; and the list CSR (nb+1 offsets, entries).  Any pointer
+ * may be NULL. */
+int gc_read_nbody_tree(gc_pool_t *pool, uint32_t *sorted_ids, uint64_t *sorted_keys,
+                       uint8_t *level, uint32_t *cell3, uint32_t *first,
+                       uint32_t *count, uint8_t *leaf, uint32_t *size,
+                       float *node_xyzm, uint32_t *bucket_first,
+                       uint32_t *bucket_count, uint32_t *bucket_node,
+                       uint64_t *list_off, uint32_t *list_ids);
+
+/* MD tasks (Section 4.2): group the n atoms by cell (cell_dev: linear cell
+ * index x + m (y + m z) per atom, device) into an m^3 periodic grid, atoms
+ * of a cell in ascending atom id (atom a has data id a), and append, for
+ * every cell in ascending index, its GC_LJ_SELF task and one GC_LJ_PAIR
+ * task per neighbour offset (dx, dy, dz) lexicographically above (0,0,0)
+ * (13 offsets), cell B = A + offset wrapped, shift = offset.  Requires
+ * m >= 3.  task_id of task t = task_id_base + t.  info_out (may be NULL)
+ * receives {tasks, target entries, source entries, max atoms in a cell}. */
+int gc_build_md_tasks(gc_pool_t *pool, const uint32_t *cell_dev, uint64_t n, int m,
+                      uint64_t task_id_base, uint64_t info_out[4]);
+
+/* Copy the last MD cell grouping: cell_start (m^3 + 1), cell_atoms (n). */
+int gc_read_md_cells(gc_pool_t *pool, uint32_t *cell_start, uint32_t *cell_atoms);
+
+/* ---- single-task launches (the one-launch-per-task baseline) ----------- */
+
+/* Execute the pending batch like gc_flush, but launch the interaction
+ * kernel once per task (same kernel body, one task per launch), as a
+ * runtime without kernel combining would (Section 3.1).  Same results. */
+int gc_flush_per_task(gc_pool_t *pool);
+
+/* ---- timing of the last flush ------------------------------------------ */
+
+/* Device time in milliseconds of each stage of the last flush, measured
+ * with CUDA events on the pool's stream: {residency, pack, interaction,
+ * scatter, total}.  Valid after gc_wait. */
+int gc_last_timings(gc_pool_t *pool, float ms_out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCHARM_H */

@@ -1,0 +1,798 @@
+// gc_api.cu -- C ABI of libgcharm: pool lifetime, uploads, batching
+// (submit/flush/wait), result read-back and introspection.  The batched
+// step itself is split across gc_residency.cu (chare table), gc_kernels.cu
+// (pack, interaction, scatter) and the task builders.
+#include <cmath>
+#include <cstring>
+#include <ctime>
+#include <unordered_map>
+#include <vector>
+
+#include "gc_common.cuh"
+
+// ---- helpers declared in other translation units ----------------------------
+int gc_prepare(gc_pool *p, TaskRec *tasks, uint64_t n, uint64_t info[5]);
+int gc_read_wu_offsets(gc_pool *p, uint64_t n, std::vector<uint32_t> &wu_off,
+                       std::vector<uint32_t> &lj_off);
+int gc_pack(gc_pool *p, const TaskRec *tasks, uint64_t t0, uint64_t t1, uint64_t tgt_base,
+            uint64_t src_base, uint64_t msrc);
+int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
+                      const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
+                      uint64_t l1, uint64_t tgt_base, uint64_t src_base);
+int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
+                         const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
+                         uint64_t l1, uint64_t tgt_base, uint64_t src_base);
+
+// ---- DBuf ---------------------------------------------------------------------
+int DBuf::reserve(size_t bytes)
+{
+    if (bytes <= cap) return GC_OK;
+    release();
+    size_t want = bytes + bytes / 4 + 256;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        cap = 0;
+        return GC_ERR_OOM;
+    }
+    cap = want;
+    return GC_OK;
+}
+
+void DBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+}
+
+// Grow keeping the first `used` bytes.
+static int grow_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s)
+{
+    if (bytes <= b.cap) return GC_OK;
+    size_t want = bytes + bytes / 2 + 256;
+    void *np = nullptr;
+    if (cudaMalloc(&np, want) != cudaSuccess) {
+        cudaGetLastError();
+        return GC_ERR_OOM;
+    }
+    if (used && b.p) {
+        if (cudaMemcpyAsync(np, b.p, used, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaFree(np);
+            return GC_ERR_CUDA;
+        }
+        cudaStreamSynchronize(s);
+    }
+    b.release();
+    b.p = np;
+    b.cap = want;
+    return GC_OK;
+}
+
+int gc_reserve_batch(gc_pool *p, uint64_t add_tasks, uint64_t add_tgt, uint64_t add_src)
+{
+    GC_TRY(grow_keep(p->tasks, (p->nb_tasks + add_tasks + 1) * sizeof(TaskRec),
+                     p->nb_tasks * sizeof(TaskRec), p->s));
+    GC_TRY(grow_keep(p->tgt_ids, (p->nb_tgt + add_tgt + 1) * sizeof(uint32_t),
+                     p->nb_tgt * sizeof(uint32_t), p->s));
+    GC_TRY(grow_keep(p->src_ids, (p->nb_src + add_src + 1) * sizeof(uint32_t),
+                     p->nb_src * sizeof(uint32_t), p->s));
+    return GC_OK;
+}
+
+namespace {
+
+__global__ void k_gather_totals(const gcd4 *totals, const uint32_t *ids, uint64_t n,
+                                uint64_t id_cap, gcd4 *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t id = ids[i];
+        out[i] = (id < id_cap) ? totals[id] : gcd4{0, 0, 0, 0};
+    }
+}
+
+void free_pool(gc_pool *p)
+{
+    if (!p) return;
+    cudaFree(p->d_pool);
+    cudaFree(p->d_slot_of_id);
+    cudaFree(p->d_id_of_slot);
+    cudaFree(p->d_last_use);
+    cudaFree(p->d_ref_epoch);
+    cudaFree(p->d_ref_count);
+    cudaFree(p->d_known);
+    cudaFree(p->d_totals);
+    cudaFree(p->d_ctr);
+    if (p->h_mirror) cudaFreeHost(p->h_mirror);
+    if (p->h_ctr) cudaFreeHost(p->h_ctr);
+    DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->last_tasks_buf, &p->last_tgt_ids,
+                    &p->last_src_ids, &p->tgt_slot, &p->src_slot, &p->tgt_perm, &p->src_perm,
+                    &p->stg_tgt, &p->stg_src, &p->uniq, &p->miss, &p->freel, &p->tiles,
+                    &p->ekeys, &p->ekeys2, &p->evicted, &p->wu, &p->wu_cnt, &p->wu_off,
+                    &p->rowcnt, &p->res, &p->row_id, &p->rid_sorted, &p->row_sorted,
+                    &p->rows_tmp, &p->runs, &p->merge_a, &p->merge_b, &p->cub_tmp, &p->small,
+                    &p->nb.keys, &p->nb.keys2, &p->nb.ids, &p->nb.ids2, &p->nb.lcp, &p->nb.win,
+                    &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a, &p->nb.node_b,
+                    &p->nb.node_val, &p->nb.bucket, &p->nb.bbox, &p->nb.list_off,
+                    &p->nb.list_len, &p->nb.list, &p->nb.bounds, &p->nb.cub_tmp, &p->nb.mono, &p->md.keys,
+                    &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
+                    &p->md.cnt_s, &p->md.cub_tmp};
+    for (DBuf *b : bufs) b->release();
+    for (int i = 0; i < 6; ++i)
+        if (p->ev_stage[i]) cudaEventDestroy(p->ev_stage[i]);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
+    if (p->owns_stream && p->s) cudaStreamDestroy(p->s);
+    delete p;
+}
+
+template <class T>
+int dmalloc(T **ptr, uint64_t count)
+{
+    if (cudaMalloc((void **)ptr, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return GC_ERR_OOM;
+    }
+    return GC_OK;
+}
+
+bool on_grid(double v, double scale, int64_t *out)
+{
+    double g = v * scale;
+    if (!(g >= 0) || g > 9.0e18 || std::floor(g) != g) return false;
+    *out = (int64_t)g;
+    return true;
+}
+
+void clear_last_stats(gc_pool *p)
+{
+    gc_stats_t &s = p->stats;
+    s.last_unique = s.last_hits = s.last_misses = s.last_evictions = 0;
+    s.last_staging_bytes = s.last_waves = 0;
+    s.lj_pairs_in_cutoff = 0;
+    for (int b = 0; b < 8; ++b) s.reuse_hist[b] = 0;
+}
+
+void drop_pending(gc_pool *p)
+{
+    p->nb_tasks = p->nb_tgt = p->nb_src = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gc_strerror(int status)
+{
+    switch (status) {
+    case GC_OK: return "ok";
+    case GC_ERR_ARG: return "invalid argument";
+    case GC_ERR_OOM: return "out of memory";
+    case GC_ERR_POOL_FULL: return "pool full: batch references more ids than fit";
+    case GC_ERR_UNKNOWN_ID: return "unknown id: a task references an id never uploaded";
+    case GC_ERR_BUDGET: return "one task exceeds the staging budget";
+    case GC_ERR_NOT_READY: return "not ready";
+    case GC_ERR_TIMEOUT: return "timeout";
+    case GC_ERR_CUDA: return "CUDA error";
+    case GC_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
+{
+    if (!cfg || !out) return GC_ERR_ARG;
+    *out = nullptr;
+    if (cfg->id_capacity == 0 || cfg->pool_capacity == 0 || !(cfg->eps2 > 0.0f) ||
+        cfg->id_capacity > 0xFFFFFFFEull || cfg->pool_capacity > 0xFFFFFFFEull)
+        return GC_ERR_ARG;
+    gc_pool *p = new gc_pool();
+    std::memset(&p->stats, 0, sizeof p->stats);
+    for (int i = 0; i < 6; ++i) p->ev_stage[i] = nullptr;
+    p->cfg = *cfg;
+    int64_t rc2g = 0, eg = 0;
+    if (cfg->lj_rc2 > 0.0f) {
+        if (!on_grid((double)cfg->lj_rc2, 4398046511104.0, &rc2g)) { delete p; return GC_ERR_ARG; }
+    }
+    if (cfg->md_edge > 0.0f) {
+        if (!on_grid((double)cfg->md_edge, 2097152.0, &eg) || eg >= (1 << 23)) {
+            delete p;
+            return GC_ERR_ARG;
+        }
+    }
+    p->rc2_grid = rc2g;
+    p->md_edge_grid = (int32_t)eg;
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return GC_ERR_CUDA;
+    }
+    if (cfg->cuda_stream) {
+        p->s = (cudaStream_t)cfg->cuda_stream;
+        p->owns_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking) != cudaSuccess) {
+            delete p;
+            return GC_ERR_CUDA;
+        }
+        p->owns_stream = true;
+    }
+    const uint64_t idc = cfg->id_capacity, cap = cfg->pool_capacity;
+    int rc = GC_OK;
+    if (rc == GC_OK) rc = dmalloc(&p->d_pool, cap);
+    if (rc == GC_OK) rc = dmalloc(&p->d_slot_of_id, idc);
+    if (rc == GC_OK) rc = dmalloc(&p->d_id_of_slot, cap);
+    if (rc == GC_OK) rc = dmalloc(&p->d_last_use, cap);
+    if (rc == GC_OK) rc = dmalloc(&p->d_ref_epoch, idc);
+    if (rc == GC_OK) rc = dmalloc(&p->d_ref_count, idc);
+    if (rc == GC_OK) rc = dmalloc(&p->d_known, idc);
+    if (rc == GC_OK) rc = dmalloc(&p->d_totals, idc);
+    if (rc == GC_OK) rc = dmalloc(&p->d_ctr, (uint64_t)CTR_COUNT);
+    if (rc == GC_OK) {
+        if (cudaHostAlloc((void **)&p->h_mirror, sizeof(float4) * idc, cudaHostAllocMapped) !=
+                cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&p->d_mirror, p->h_mirror, 0) != cudaSuccess ||
+            cudaHostAlloc((void **)&p->h_ctr, sizeof(unsigned long long) * CTR_COUNT,
+                          cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            rc = GC_ERR_OOM;
+        }
+    }
+    if (rc == GC_OK) {
+        cudaMemsetAsync(p->d_slot_of_id, 0xFF, sizeof(uint32_t) * idc, p->s);
+        cudaMemsetAsync(p->d_id_of_slot, 0xFF, sizeof(uint32_t) * cap, p->s);
+        cudaMemsetAsync(p->d_last_use, 0, sizeof(uint32_t) * cap, p->s);
+        cudaMemsetAsync(p->d_ref_epoch, 0, sizeof(uint32_t) * idc, p->s);
+        cudaMemsetAsync(p->d_ref_count, 0, sizeof(uint32_t) * idc, p->s);
+        cudaMemsetAsync(p->d_known, 0, idc, p->s);
+        cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * idc, p->s);
+        cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned long long) * CTR_COUNT, p->s);
+        std::memset(p->h_mirror, 0, sizeof(float4) * idc);
+        for (int i = 0; i < 6 && rc == GC_OK; ++i)
+            if (cudaEventCreate(&p->ev_stage[i]) != cudaSuccess) rc = GC_ERR_CUDA;
+        if (rc == GC_OK && cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) !=
+                               cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (rc == GC_OK && cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
+    }
+    if (rc != GC_OK) {
+        free_pool(p);
+        return rc;
+    }
+    *out = p;
+    return GC_OK;
+}
+
+int gc_pool_destroy(gc_pool_t *p)
+{
+    if (!p) return GC_ERR_ARG;
+    cudaStreamSynchronize(p->s);
+    free_pool(p);
+    return GC_OK;
+}
+
+int gc_pool_upload(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_t n)
+{
+    if (!p || (n && (!ids || !xyzm))) return GC_ERR_ARG;
+    if (n == 0) return GC_OK;
+    for (uint64_t i = 0; i < n; ++i)
+        if (ids[i] >= p->cfg.id_capacity) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));   // no flush may be reading the mirror
+    for (uint64_t i = 0; i < n; ++i)
+        std::memcpy(&p->h_mirror[ids[i]], xyzm + 4 * i, sizeof(float4));
+    DBuf tmp_ids, tmp_vals;
+    GC_TRY(tmp_ids.reserve(n * sizeof(uint32_t)));
+    if (tmp_vals.reserve(n * sizeof(float4)) != GC_OK) {
+        tmp_ids.release();
+        return GC_ERR_OOM;
+    }
+    int rc = GC_OK;
+    if (cudaMemcpyAsync(tmp_ids.p, ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice, p->s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(tmp_vals.p, xyzm, n * sizeof(float4), cudaMemcpyHostToDevice, p->s) !=
+            cudaSuccess)
+        rc = GC_ERR_CUDA;
+    if (rc == GC_OK)
+        rc = gc_launch_upload(p, tmp_ids.as<uint32_t>(), tmp_vals.as<float4>(), n, 0);
+    if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
+    tmp_ids.release();
+    tmp_vals.release();
+    p->stats.h2d_bytes += n * (sizeof(uint32_t) + sizeof(float4));
+    return rc;
+}
+
+int gc_pool_upload_device(gc_pool_t *p, const uint32_t *ids_dev, const float *xyzm_dev,
+                          uint64_t n)
+{
+    if (!p || (n && (!ids_dev || !xyzm_dev))) return GC_ERR_ARG;
+    if (((uintptr_t)xyzm_dev) % 16) return GC_ERR_ARG;
+    return gc_launch_upload(p, ids_dev, (const float4 *)xyzm_dev, n, 1);
+}
+
+// ---- submission ---------------------------------------------------------------
+
+static int gc_submit_csr_impl(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
+                       const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
+                       const uint32_t *tgt_ids, const uint64_t *src_off,
+                       const uint32_t *src_ids, uint64_t n_tgt_total, uint64_t n_src_total,
+                       int on_device, uint64_t *batch_out)
+{
+    if (!p || (n_tasks && (!kinds || !tgt_off || !src_off))) return GC_ERR_ARG;
+    if (batch_out) *batch_out = p->submitted_batches;
+    if (n_tasks == 0) return GC_OK;
+    const uint64_t budget = p->cfg.staging_budget_bytes;
+    if (!on_device) {
+        if (tgt_off[0] != 0 || src_off[0] != 0) return GC_ERR_ARG;
+        for (uint64_t t = 0; t < n_tasks; ++t) {
+            if (tgt_off[t + 1] < tgt_off[t] || src_off[t + 1] < src_off[t]) return GC_ERR_ARG;
+            uint64_t nt = tgt_off[t + 1] - tgt_off[t], ns = src_off[t + 1] - src_off[t];
+            if (nt > 0xFFFFFFFFull || ns > 0xFFFFFFFFull) return GC_ERR_ARG;
+            if (kinds[t] > GC_LJ_SELF || (kinds[t] == GC_LJ_SELF && ns)) return GC_ERR_ARG;
+            if (budget && (nt + ns) * sizeof(float4) > budget) return GC_ERR_BUDGET;
+        }
+        n_tgt_total = tgt_off[n_tasks];
+        n_src_total = src_off[n_tasks];
+        if (n_tgt_total && !tgt_ids) return GC_ERR_ARG;
+        if (n_src_total && !src_ids) return GC_ERR_ARG;
+    }
+    GC_TRY(gc_reserve_batch(p, n_tasks, n_tgt_total, n_src_total));
+    TaskRec *recs = p->tasks.as<TaskRec>() + p->nb_tasks;
+    uint32_t *dt = p->tgt_ids.as<uint32_t>() + p->nb_tgt;
+    uint32_t *ds = p->src_ids.as<uint32_t>() + p->nb_src;
+    const uint64_t id_base = p->stats.tasks + p->nb_tasks;
+    if (on_device) {
+        if (n_tgt_total)
+            GC_CUDA_TRY(cudaMemcpyAsync(dt, tgt_ids, n_tgt_total * sizeof(uint32_t),
+                                        cudaMemcpyDeviceToDevice, p->s));
+        if (n_src_total)
+            GC_CUDA_TRY(cudaMemcpyAsync(ds, src_ids, n_src_total * sizeof(uint32_t),
+                                        cudaMemcpyDeviceToDevice, p->s));
+        GC_TRY(gc_make_task_recs(p, n_tasks, task_ids, kinds, shifts, tgt_off, src_off,
+                                 p->nb_tgt, p->nb_src, id_base, recs));
+    } else {
+        // stage the descriptor arrays on the device
+        size_t b_ids = task_ids ? n_tasks * 8 : 0, b_k = n_tasks * 4,
+               b_sh = shifts ? n_tasks * 3 : 0, b_off = (n_tasks + 1) * 8;
+        size_t o_ids = 0, o_k = (o_ids + b_ids + 15) & ~15ull, o_sh = (o_k + b_k + 15) & ~15ull,
+               o_to = (o_sh + b_sh + 15) & ~15ull, o_so = (o_to + b_off + 15) & ~15ull,
+               total = o_so + b_off;
+        DBuf tmp;
+        GC_TRY(tmp.reserve(total));
+        char *base = (char *)tmp.p;
+        int rc = GC_OK;
+        if (task_ids && cudaMemcpyAsync(base + o_ids, task_ids, b_ids, cudaMemcpyHostToDevice,
+                                        p->s) != cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (cudaMemcpyAsync(base + o_k, kinds, b_k, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (shifts && cudaMemcpyAsync(base + o_sh, shifts, b_sh, cudaMemcpyHostToDevice, p->s) !=
+                          cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (cudaMemcpyAsync(base + o_to, tgt_off, b_off, cudaMemcpyHostToDevice, p->s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(base + o_so, src_off, b_off, cudaMemcpyHostToDevice, p->s) !=
+                cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (rc == GC_OK && n_tgt_total &&
+            cudaMemcpyAsync(dt, tgt_ids, n_tgt_total * 4, cudaMemcpyHostToDevice, p->s) !=
+                cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (rc == GC_OK && n_src_total &&
+            cudaMemcpyAsync(ds, src_ids, n_src_total * 4, cudaMemcpyHostToDevice, p->s) !=
+                cudaSuccess)
+            rc = GC_ERR_CUDA;
+        if (rc == GC_OK)
+            rc = gc_make_task_recs(p, n_tasks, task_ids ? (uint64_t *)(base + o_ids) : nullptr,
+                                   (uint32_t *)(base + o_k),
+                                   shifts ? (int8_t *)(base + o_sh) : nullptr,
+                                   (uint64_t *)(base + o_to), (uint64_t *)(base + o_so),
+                                   p->nb_tgt, p->nb_src, id_base, recs);
+        if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
+        tmp.release();
+        if (rc != GC_OK) return rc;
+        p->stats.h2d_bytes += total + 4 * (n_tgt_total + n_src_total);
+    }
+    p->nb_tasks += n_tasks;
+    p->nb_tgt += n_tgt_total;
+    p->nb_src += n_src_total;
+    return GC_OK;
+}
+
+int gc_submit_csr(gc_pool_t *p, uint64_t n_tasks, const uint64_t *task_ids,
+                  const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
+                  const uint32_t *tgt_ids, const uint64_t *src_off, const uint32_t *src_ids,
+                  uint64_t n_tgt_total, uint64_t n_src_total, int on_device,
+                  uint64_t *batch_out)
+{
+    return gc_submit_csr_impl(p, n_tasks, task_ids, kinds, shifts, tgt_off, tgt_ids, src_off,
+                              src_ids, n_tgt_total, n_src_total, on_device, batch_out);
+}
+
+int gc_submit(gc_pool_t *p, const gc_task *tasks, uint64_t n, uint64_t *batch_out)
+{
+    if (!p || (n && !tasks)) return GC_ERR_ARG;
+    std::vector<uint64_t> ids(n), to(n + 1), so(n + 1);
+    std::vector<uint32_t> kinds(n), tg, sr;
+    std::vector<int8_t> sh(3 * n);
+    to[0] = so[0] = 0;
+    for (uint64_t t = 0; t < n; ++t) {
+        const gc_task &k = tasks[t];
+        if ((k.n_targets && !k.target_ids) || (k.n_sources && !k.source_ids)) return GC_ERR_ARG;
+        ids[t] = k.task_id;
+        kinds[t] = k.kind;
+        for (int a = 0; a < 3; ++a) sh[3 * t + a] = k.shift[a];
+        tg.insert(tg.end(), k.target_ids, k.target_ids + k.n_targets);
+        sr.insert(sr.end(), k.source_ids, k.source_ids + k.n_sources);
+        to[t + 1] = to[t] + k.n_targets;
+        so[t + 1] = so[t] + k.n_sources;
+    }
+    return gc_submit_csr_impl(p, n, ids.data(), kinds.data(), sh.data(), to.data(), tg.data(),
+                              so.data(), sr.data(), 0, 0, 0, batch_out);
+}
+
+// ---- flush ----------------------------------------------------------------------
+
+static int flush_impl(gc_pool *p, int per_task)
+{
+    if (!p) return GC_ERR_ARG;
+    if (p->nb_tasks == 0) return GC_OK;
+    const uint64_t T = p->nb_tasks, NT = p->nb_tgt, NS = p->nb_src;
+    TaskRec *tasks = p->tasks.as<TaskRec>();
+    const uint32_t *tgt_ids = p->tgt_ids.as<uint32_t>();
+    const uint32_t *src_ids = p->src_ids.as<uint32_t>();
+    clear_last_stats(p);
+    p->timing_valid = false;
+
+    uint64_t info[5];
+    int rc = gc_prepare(p, tasks, T, info);
+    if (rc != GC_OK) return rc;
+    GC_CUDA_TRY(cudaMemcpy(p->h_ctr, p->d_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (p->h_ctr[CTR_FLAGS] & GC_FLAG_BAD_TASK) {
+        cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, sizeof(unsigned long long), p->s);
+        drop_pending(p);
+        return GC_ERR_ARG;
+    }
+    const uint64_t R = info[0], W = info[1], L = info[2], inter = info[3], max_list = info[4];
+
+    GC_TRY(p->tgt_slot.reserve((NT + 1) * 4));
+    GC_TRY(p->src_slot.reserve((NS + 1) * 4));
+    GC_TRY(p->tgt_perm.reserve((NT + 1) * 4));
+    GC_TRY(p->src_perm.reserve((NS + 1) * 4));
+    GC_TRY(p->res.reserve((R + 1) * 2 * sizeof(float4)));
+    GC_TRY(p->row_id.reserve((R + 1) * 4));
+
+    // waves under the staging budget
+    struct Wave { uint64_t t0, t1, tg0, tg1, s0, s1; };
+    std::vector<Wave> waves;
+    const uint64_t budget = p->cfg.staging_budget_bytes;
+    std::vector<uint32_t> wu_off, lj_off;
+    bool need_offsets = per_task != 0;
+    if (budget && (NT + NS) * sizeof(float4) > budget) {
+        std::vector<TaskRec> h(T);
+        GC_CUDA_TRY(cudaMemcpy(h.data(), tasks, T * sizeof(TaskRec), cudaMemcpyDeviceToHost));
+        uint64_t t0 = 0;
+        while (t0 < T) {
+            uint64_t t1 = t0, bytes = 0;
+            while (t1 < T && bytes + (uint64_t)(h[t1].nt + h[t1].ns) * sizeof(float4) <= budget) {
+                bytes += (uint64_t)(h[t1].nt + h[t1].ns) * sizeof(float4);
+                ++t1;
+            }
+            if (t1 == t0) {
+                drop_pending(p);
+                return GC_ERR_BUDGET;
+            }
+            Wave w;
+            w.t0 = t0; w.t1 = t1;
+            w.tg0 = h[t0].tgt_off; w.tg1 = (t1 < T) ? h[t1].tgt_off : NT;
+            w.s0 = h[t0].src_off; w.s1 = (t1 < T) ? h[t1].src_off : NS;
+            waves.push_back(w);
+            t0 = t1;
+        }
+        need_offsets = true;
+    } else {
+        waves.push_back(Wave{0, T, 0, NT, 0, NS});
+    }
+    if (need_offsets) GC_TRY(gc_read_wu_offsets(p, T, wu_off, lj_off));
+
+    uint64_t max_wt = 0, max_ws = 0;
+    for (const Wave &w : waves) {
+        if (w.tg1 - w.tg0 > max_wt) max_wt = w.tg1 - w.tg0;
+        if (w.s1 - w.s0 > max_ws) max_ws = w.s1 - w.s0;
+    }
+    GC_TRY(p->stg_tgt.reserve((max_wt + 1) * sizeof(float4)));
+    GC_TRY(p->stg_src.reserve((max_ws + 1) * sizeof(float4)));
+    if (max_list > 4096) {
+        GC_TRY(p->merge_a.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
+        GC_TRY(p->merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
+    }
+
+    float ms_res = 0, ms_pack = 0, ms_int = 0;
+    GC_CUDA_TRY(cudaMemsetAsync(p->d_ctr + CTR_LJ_IN, 0, sizeof(unsigned long long), p->s));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_stage[0], p->s));
+    for (size_t k = 0; k < waves.size(); ++k) {
+        const Wave &w = waves[k];
+        cudaEvent_t e0 = p->ev_stage[0];
+        if (k > 0) GC_CUDA_TRY(cudaEventRecord(e0, p->s));
+        rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0,
+                          p->tgt_slot.as<uint32_t>() + w.tg0, p->src_slot.as<uint32_t>() + w.s0);
+        if (rc != GC_OK) {
+            drop_pending(p);
+            return rc;
+        }
+        GC_CUDA_TRY(cudaEventRecord(p->ev_stage[1], p->s));
+        GC_TRY(gc_pack(p, tasks, w.t0, w.t1, w.tg0, w.s0, max_wt + 1));
+        GC_CUDA_TRY(cudaEventRecord(p->ev_stage[2], p->s));
+        uint64_t w0 = 0, w1 = W, l0 = 0, l1 = L;
+        if (need_offsets) {
+            w0 = wu_off[w.t0]; w1 = wu_off[w.t1];
+            l0 = lj_off[w.t0]; l1 = lj_off[w.t1];
+        }
+        if (!per_task) {
+            GC_TRY(gc_interact_range(p, tasks, tgt_ids, src_ids, w0, w1, l0, l1, w.tg0, w.s0));
+        } else {
+            for (uint64_t t = w.t0; t < w.t1; ++t)
+                GC_TRY(gc_interact_one_task(p, tasks, tgt_ids, src_ids, wu_off[t],
+                                            wu_off[t + 1], lj_off[t], lj_off[t + 1], w.tg0,
+                                            w.s0));
+        }
+        GC_CUDA_TRY(cudaEventRecord(p->ev_stage[3], p->s));
+        if (waves.size() > 1) {
+            float a = 0, b = 0, c = 0;
+            GC_CUDA_TRY(cudaEventSynchronize(p->ev_stage[3]));
+            cudaEventElapsedTime(&a, p->ev_stage[0], p->ev_stage[1]);
+            cudaEventElapsedTime(&b, p->ev_stage[1], p->ev_stage[2]);
+            cudaEventElapsedTime(&c, p->ev_stage[2], p->ev_stage[3]);
+            ms_res += a; ms_pack += b; ms_int += c;
+        }
+    }
+    GC_TRY(gc_scatter(p, R));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_stage[4], p->s));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_done, p->s));
+    p->multiwave_ms[0] = ms_res;
+    p->multiwave_ms[1] = ms_pack;
+    p->multiwave_ms[2] = ms_int;
+    p->n_waves_last = waves.size();
+    p->timing_valid = true;
+
+    gc_stats_t &st = p->stats;
+    st.flushes += 1;
+    st.tasks += T;
+    st.interactions += inter;
+    st.last_waves = waves.size();
+    st.last_staging_bytes = (NT + NS) * sizeof(float4);
+
+    // the executed batch becomes the "last" batch; its buffers are kept for
+    // result mapping and introspection
+    std::swap(p->tasks, p->last_tasks_buf);
+    std::swap(p->tgt_ids, p->last_tgt_ids);
+    std::swap(p->src_ids, p->last_src_ids);
+    p->last_tasks = T;
+    p->last_tgt = NT;
+    p->last_src = NS;
+    p->last_rows = R;
+    p->last_batch = p->submitted_batches;
+    p->have_last = true;
+    p->submitted_batches += 1;
+    drop_pending(p);
+    p->host_tasks_valid = false;
+    return GC_OK;
+}
+
+int gc_flush(gc_pool_t *p) { return flush_impl(p, 0); }
+
+int gc_flush_per_task(gc_pool_t *p) { return flush_impl(p, 1); }
+
+int gc_wait(gc_pool_t *p, uint64_t batch, uint64_t timeout_ns)
+{
+    if (!p) return GC_ERR_ARG;
+    if (!p->have_last || batch > p->last_batch) return GC_ERR_NOT_READY;
+    if (timeout_ns == 0) {
+        GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
+        return GC_OK;
+    }
+    struct timespec t0, t1;
+    clock_gettime(CLOCK_MONOTONIC, &t0);
+    for (;;) {
+        cudaError_t e = cudaEventQuery(p->ev_done);
+        if (e == cudaSuccess) return GC_OK;
+        if (e != cudaErrorNotReady) return GC_ERR_CUDA;
+        clock_gettime(CLOCK_MONOTONIC, &t1);
+        uint64_t el = (uint64_t)(t1.tv_sec - t0.tv_sec) * 1000000000ull +
+                      (uint64_t)(t1.tv_nsec - t0.tv_nsec);
+        if (el >= timeout_ns) return GC_ERR_TIMEOUT;
+    }
+}
+
+// ---- results -----------------------------------------------------------------------
+
+int gc_result_rows(gc_pool_t *p, uint64_t *rows_out)
+{
+    if (!p || !rows_out) return GC_ERR_ARG;
+    *rows_out = p->have_last ? p->last_rows : 0;
+    return GC_OK;
+}
+
+int gc_read_batch_results(gc_pool_t *p, uint64_t first_row, uint64_t n_rows, float *out)
+{
+    if (!p || (n_rows && !out)) return GC_ERR_ARG;
+    if (!p->have_last || first_row + n_rows > p->last_rows) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
+    GC_CUDA_TRY(cudaMemcpy(out, p->res.as<float4>() + 2 * first_row, n_rows * 2 * sizeof(float4),
+                           cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
+static int ensure_host_tasks(gc_pool *p)
+{
+    if (p->host_tasks_valid) return GC_OK;
+    p->host_tasks.resize(p->last_tasks);
+    GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
+    GC_CUDA_TRY(cudaMemcpy(p->host_tasks.data(), p->last_tasks_buf.p,
+                           p->last_tasks * sizeof(TaskRec), cudaMemcpyDeviceToHost));
+    p->task_index.clear();
+    p->task_index.reserve(p->last_tasks * 2);
+    for (uint64_t t = 0; t < p->last_tasks; ++t) p->task_index[p->host_tasks[t].task_id] = t;
+    p->host_tasks_valid = true;
+    return GC_OK;
+}
+
+int gc_read_results(gc_pool_t *p, const uint64_t *task_ids, uint64_t n, float *out)
+{
+    if (!p || (n && (!task_ids || !out))) return GC_ERR_ARG;
+    if (!p->have_last) return GC_ERR_NOT_READY;
+    GC_TRY(ensure_host_tasks(p));
+    std::vector<float4> all(2 * p->last_rows + 2);
+    if (p->last_rows)
+        GC_CUDA_TRY(cudaMemcpy(all.data(), p->res.p, p->last_rows * 2 * sizeof(float4),
+                               cudaMemcpyDeviceToHost));
+    uint64_t w = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        auto it = p->task_index.find(task_ids[i]);
+        if (it == p->task_index.end()) return GC_ERR_ARG;
+        const TaskRec &r = p->host_tasks[it->second];
+        uint64_t rows = r.nt + (r.kind == GC_LJ_PAIR ? r.ns : 0u);
+        std::memcpy(out + 8 * w, &all[2 * r.row_off], rows * 2 * sizeof(float4));
+        w += rows;
+    }
+    return GC_OK;
+}
+
+int gc_read_totals(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
+{
+    if (!p || (n && (!ids || !acc4))) return GC_ERR_ARG;
+    if (n == 0) return GC_OK;
+    DBuf di, dout;
+    GC_TRY(di.reserve(n * 4));
+    if (dout.reserve(n * sizeof(gcd4)) != GC_OK) {
+        di.release();
+        return GC_ERR_OOM;
+    }
+    int rc = GC_OK;
+    if (cudaMemcpyAsync(di.p, ids, n * 4, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
+        rc = GC_ERR_CUDA;
+    if (rc == GC_OK) {
+        unsigned g = (unsigned)((n + 255) / 256);
+        if (g > 65535u * 8) g = 65535u * 8;
+        k_gather_totals<<<g, 256, 0, p->s>>>(p->d_totals, di.as<uint32_t>(), n,
+                                             p->cfg.id_capacity, dout.as<gcd4>());
+        if (cudaMemcpyAsync(acc4, dout.p, n * sizeof(gcd4), cudaMemcpyDeviceToHost, p->s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(p->s) != cudaSuccess)
+            rc = GC_ERR_CUDA;
+    }
+    di.release();
+    dout.release();
+    return rc;
+}
+
+int gc_totals_device(gc_pool_t *p, const double **totals_dev)
+{
+    if (!p || !totals_dev) return GC_ERR_ARG;
+    *totals_dev = (const double *)p->d_totals;
+    return GC_OK;
+}
+
+int gc_reset_totals(gc_pool_t *p)
+{
+    if (!p) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * p->cfg.id_capacity, p->s));
+    return GC_OK;
+}
+
+int gc_stats(gc_pool_t *p, gc_stats_t *out)
+{
+    if (!p || !out) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    unsigned long long c[CTR_COUNT];
+    GC_CUDA_TRY(cudaMemcpy(c, p->d_ctr, sizeof c, cudaMemcpyDeviceToHost));
+    *out = p->stats;
+    out->updates = c[CTR_UPDATES];
+    out->lj_pairs_in_cutoff = c[CTR_LJ_IN];
+    return GC_OK;
+}
+
+int gc_last_timings(gc_pool_t *p, float ms[5])
+{
+    if (!p || !ms) return GC_ERR_ARG;
+    if (!p->timing_valid) return GC_ERR_NOT_READY;
+    GC_CUDA_TRY(cudaEventSynchronize(p->ev_stage[4]));
+    if (p->n_waves_last > 1) {
+        ms[0] = p->multiwave_ms[0];
+        ms[1] = p->multiwave_ms[1];
+        ms[2] = p->multiwave_ms[2];
+        cudaEventElapsedTime(&ms[3], p->ev_stage[3], p->ev_stage[4]);
+        ms[4] = ms[0] + ms[1] + ms[2] + ms[3];
+        return GC_OK;
+    }
+    cudaEventElapsedTime(&ms[0], p->ev_stage[0], p->ev_stage[1]);
+    cudaEventElapsedTime(&ms[1], p->ev_stage[1], p->ev_stage[2]);
+    cudaEventElapsedTime(&ms[2], p->ev_stage[2], p->ev_stage[3]);
+    cudaEventElapsedTime(&ms[3], p->ev_stage[3], p->ev_stage[4]);
+    cudaEventElapsedTime(&ms[4], p->ev_stage[0], p->ev_stage[4]);
+    return GC_OK;
+}
+
+// ---- introspection -----------------------------------------------------------------
+
+int gc_batch_sizes(gc_pool_t *p, uint64_t *n_tasks, uint64_t *n_tgt, uint64_t *n_src)
+{
+    if (!p) return GC_ERR_ARG;
+    if (n_tasks) *n_tasks = p->have_last ? p->last_tasks : 0;
+    if (n_tgt) *n_tgt = p->have_last ? p->last_tgt : 0;
+    if (n_src) *n_src = p->have_last ? p->last_src : 0;
+    return GC_OK;
+}
+
+int gc_read_entry_slots(gc_pool_t *p, uint32_t *tgt_slots, uint32_t *src_slots)
+{
+    if (!p || !p->have_last) return GC_ERR_STATE;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    if (tgt_slots && p->last_tgt)
+        GC_CUDA_TRY(cudaMemcpy(tgt_slots, p->tgt_slot.p, p->last_tgt * 4, cudaMemcpyDeviceToHost));
+    if (src_slots && p->last_src)
+        GC_CUDA_TRY(cudaMemcpy(src_slots, p->src_slot.p, p->last_src * 4, cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
+int gc_read_pack_perm(gc_pool_t *p, uint32_t *tgt_perm, uint32_t *src_perm)
+{
+    if (!p || !p->have_last) return GC_ERR_STATE;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    if (tgt_perm && p->last_tgt)
+        GC_CUDA_TRY(cudaMemcpy(tgt_perm, p->tgt_perm.p, p->last_tgt * 4, cudaMemcpyDeviceToHost));
+    if (src_perm && p->last_src)
+        GC_CUDA_TRY(cudaMemcpy(src_perm, p->src_perm.p, p->last_src * 4, cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
+int gc_read_residency(gc_pool_t *p, uint32_t *slot_of_id, uint32_t *id_of_slot,
+                      uint32_t *last_use)
+{
+    if (!p) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    if (slot_of_id)
+        GC_CUDA_TRY(cudaMemcpy(slot_of_id, p->d_slot_of_id, p->cfg.id_capacity * 4,
+                               cudaMemcpyDeviceToHost));
+    if (id_of_slot)
+        GC_CUDA_TRY(cudaMemcpy(id_of_slot, p->d_id_of_slot, p->cfg.pool_capacity * 4,
+                               cudaMemcpyDeviceToHost));
+    if (last_use)
+        GC_CUDA_TRY(cudaMemcpy(last_use, p->d_last_use, p->cfg.pool_capacity * 4,
+                               cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
+int gc_read_evicted(gc_pool_t *p, uint32_t *ids, uint64_t cap, uint64_t *n_out)
+{
+    if (!p || !n_out) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    *n_out = p->n_evicted_last;
+    uint64_t k = p->n_evicted_last < cap ? p->n_evicted_last : cap;
+    if (k && ids) GC_CUDA_TRY(cudaMemcpy(ids, p->evicted.p, k * 4, cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// gc_common.cuh -- internal declarations shared by the libgcharm translation
+// units (not part of the public ABI; see include/gcharm.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <unordered_map>
+#include <vector>
+
+#include "gcharm.h"
+
+#define GC_NONE 0xFFFFFFFFu
+
+// Four doubles, 32-byte aligned (one per-id FP64 total).
+struct __align__(32) gcd4 {
+    double x, y, z, w;
+};
+
+// Device error-flag bits (pool->d_ctr[CTR_FLAGS]).
+#define GC_FLAG_UNKNOWN_ID 1u     // a batch entry names an id never uploaded
+#define GC_FLAG_ID_RANGE 2u       // an id >= id_capacity (device upload/build)
+#define GC_FLAG_BAD_TASK 4u       // unknown kind, or LJ_SELF with sources
+
+// Indices into the device counter block (pool->d_ctr, uint64 each).  The
+// residency counters (CTR_UNIQUE .. end) are cleared at every wave.
+enum {
+    CTR_FLAGS = 0,      // error bits
+    CTR_UPDATES,        // uploads that hit a resident slot
+    CTR_LJ_IN,          // LJ pairs inside the cutoff
+    CTR_QUEUE,          // work-queue head of the persistent interaction kernel
+    CTR_INTER,          // pair interactions of the batch
+    CTR_NGRAV_WU,       // gravity work units of the batch
+    CTR_NLJ,            // LJ tasks of the batch
+    CTR_MAXLIST,        // longest list of the batch
+    CTR_RUNS,           // distinct ids among result rows
+    CTR_UNIQUE,         // distinct ids in the current wave
+    CTR_HITS,
+    CTR_MISSES,
+    CTR_FREE,
+    CTR_HIST0,          // 8 reuse-histogram bins
+    CTR_COUNT = CTR_HIST0 + 8
+};
+
+// One task as the kernels see it (48 bytes).
+struct TaskRec {
+    uint64_t task_id;
+    uint64_t tgt_off;   // first target entry (batch-global)
+    uint64_t src_off;   // first source entry (batch-global)
+    uint64_t row_off;   // first result row (batch-global)
+    uint32_t kind;
+    uint32_t nt, ns;
+    int8_t shift[4];
+};
+static_assert(sizeof(TaskRec) == 48, "TaskRec layout");
+
+// Growable device buffer.  Growing frees the old storage (contents lost).
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    int reserve(size_t bytes);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Work unit of the gravity kernel: one task and a block of <= 32 targets.
+struct GravWU {
+    uint32_t task;
+    uint32_t t0;
+};
+
+struct NBodyState {
+    uint64_t n = 0, n_nodes = 0, n_buckets = 0, n_list = 0, max_list = 0;
+    DBuf keys, keys2, ids, ids2, lcp, win, dmax, nnode, node_off;
+    DBuf node_a, node_b, node_val, bucket, bbox, list_off, list_len, list;
+    DBuf bounds, cub_tmp, mono;
+};
+
+struct MDState {
+    uint64_t n = 0;
+    int m = 0;
+    DBuf keys, keys2, ids, ids2, cell_start, cnt_t, cnt_s, cub_tmp;
+};
+
+struct gc_pool {
+    gc_config cfg;
+    cudaStream_t s = nullptr;
+    bool owns_stream = false;
+    int device = 0;
+    int num_sms = 0;
+    int64_t rc2_grid = 0;       // cutoff^2 in (2^-21)^2 units
+    int32_t md_edge_grid = 0;   // cell edge in 2^-21 units
+
+    // chare table and data
+    float4 *d_pool = nullptr;          // [pool_capacity]
+    uint32_t *d_slot_of_id = nullptr;  // [id_capacity]
+    uint32_t *d_id_of_slot = nullptr;  // [pool_capacity]
+    uint32_t *d_last_use = nullptr;    // [pool_capacity]
+    uint32_t *d_ref_epoch = nullptr;   // [id_capacity]
+    uint32_t *d_ref_count = nullptr;   // [id_capacity]
+    uint8_t *d_known = nullptr;        // [id_capacity]
+    float4 *h_mirror = nullptr;        // pinned, mapped [id_capacity]
+    float4 *d_mirror = nullptr;        // device alias of h_mirror
+    gcd4 *d_totals = nullptr;       // [id_capacity]
+    unsigned long long *d_ctr = nullptr;   // [CTR_COUNT]
+    unsigned long long *h_ctr = nullptr;   // pinned copy
+
+    // pending batch (device-resident)
+    uint64_t nb_tasks = 0, nb_tgt = 0, nb_src = 0;
+    DBuf tasks, tgt_ids, src_ids;
+    uint64_t submitted_batches = 0;   // index of the pending batch
+
+    // last executed batch
+    uint64_t last_tasks = 0, last_tgt = 0, last_src = 0, last_rows = 0;
+    uint64_t last_batch = 0;          // index of the last flushed batch
+    bool have_last = false;
+    DBuf last_tasks_buf, last_tgt_ids, last_src_ids;   // swapped with pending
+
+    // per-flush work buffers
+    DBuf tgt_slot, src_slot, tgt_perm, src_perm, stg_tgt, stg_src;
+    DBuf uniq, miss, freel, tiles, ekeys, ekeys2, evicted;
+    DBuf wu, wu_cnt, wu_off, rowcnt, res, row_id, rid_sorted, row_sorted, rows_tmp;
+    DBuf runs, merge_a, merge_b, cub_tmp, small;
+    uint64_t n_evicted_last = 0;
+    uint32_t epoch = 0;
+
+    // completion
+    cudaEvent_t ev_stage[6];
+    cudaEvent_t ev_done = nullptr;
+    bool timing_valid = false;
+    float multiwave_ms[3] = {0, 0, 0};
+    uint64_t n_waves_last = 0;
+
+    // host copy of the last batch's task records (for gc_read_results)
+    std::vector<TaskRec> host_tasks;
+    std::unordered_map<uint64_t, uint64_t> task_index;
+    bool host_tasks_valid = false;
+
+    gc_stats_t stats;
+    NBodyState nb;
+    MDState md;
+};
+
+// ---- error helper ----------------------------------------------------------
+#define GC_CUDA_TRY(expr)                                    \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return GC_ERR_CUDA;           \
+    } while (0)
+
+#define GC_TRY(expr)                                         \
+    do {                                                     \
+        int _r = (expr);                                     \
+        if (_r != GC_OK) return _r;                          \
+    } while (0)
+
+// ---- CUB-backed primitives (gc_sort.cu) -------------------------------------
+int gc_sort_pairs_u64(DBuf &tmp, const uint64_t *kin, uint64_t *kout, const uint32_t *vin,
+                      uint32_t *vout, uint64_t n, int end_bit, cudaStream_t s);
+int gc_sort_pairs_u32(DBuf &tmp, const uint32_t *kin, uint32_t *kout, const uint32_t *vin,
+                      uint32_t *vout, uint64_t n, int end_bit, cudaStream_t s);
+int gc_sort_keys_u64(DBuf &tmp, const uint64_t *kin, uint64_t *kout, uint64_t n,
+                     cudaStream_t s);
+int gc_exclusive_scan_u64(DBuf &tmp, const uint64_t *in, uint64_t *out, uint64_t n,
+                          cudaStream_t s);
+int gc_exclusive_scan_u32(DBuf &tmp, const uint32_t *in, uint32_t *out, uint64_t n,
+                          cudaStream_t s);
+
+// ---- residency (gc_residency.cu) -----------------------------------------------
+// Runs the chare-table step for the entries tgt[0..nt) and src[0..ns); fills
+// tgt_slot / src_slot.  Returns GC_OK, GC_ERR_UNKNOWN_ID or GC_ERR_POOL_FULL.
+int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
+                 uint64_t ns, uint32_t *tgt_slot, uint32_t *src_slot);
+int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64_t n,
+                     int write_mirror);
+
+// ---- pack / interaction / scatter (gc_kernels.cu) -----------------------------
+int gc_scatter(gc_pool *p, uint64_t n_rows);
+int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
+                      const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
+                      const uint64_t *src_off, uint64_t tgt_base, uint64_t src_base,
+                      uint64_t task_id_base, TaskRec *out);
+
+// ---- compaction helper (gc_residency.cu) ---------------------------------------
+// Writes, in ascending order, every i in [0, n) with flags-kind predicate.
+enum CompactKind {
+    CK_REF_EPOCH = 0,   // i: ref_epoch[i] == epoch           (id space)
+    CK_MISS,            // k < count: slot_of_id[uniq[k]] == NONE   (value uniq[k])
+    CK_FREE,            // s: id_of_slot[s] == NONE           (slot space)
+    CK_RUN_START        // i < count: i == 0 || key[i] != key[i-1]
+};
+int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev,
+               const uint32_t *arr, uint32_t *out, unsigned long long *count_out);
+
+// ---- builders --------------------------------------------------------------------
+int gc_reserve_batch(gc_pool *p, uint64_t add_tasks, uint64_t add_tgt, uint64_t add_src);

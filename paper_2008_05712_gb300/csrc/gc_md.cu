@@ -1,0 +1,203 @@
+// gc_md.cu -- MD task builder on the device (Section 4.2: the space is
+// split into patches (here cubic periodic cells of edge >= cutoff) that own
+// their atoms; a compute object per pair of neighbouring patches calls
+// interact() on the two atom vectors and updates the forces of both).
+//
+// Cells: a stable sort of the atoms by cell index gives each cell's atoms in
+// ascending atom id; cell_start comes from the sorted keys.  Tasks: for
+// every cell in ascending index, its self task, then one task per
+// neighbour offset in the upper half-shell (13 offsets lexicographically
+// above (0,0,0), dx most significant), so every pair of neighbouring cells
+// is visited exactly once.
+#include "gc_common.cuh"
+
+namespace {
+
+#define GRID_STRIDE(i, n)                                                       \
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); \
+         i += (uint64_t)gridDim.x * blockDim.x)
+
+inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
+{
+    uint64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (uint64_t)max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+// task slot o = 1..13 -> neighbour offset; slot 0 is the self task
+__constant__ int8_t c_half_shell[13][3] = {
+    {0, 0, 1},  {0, 1, -1},  {0, 1, 0},  {0, 1, 1},  {1, -1, -1}, {1, -1, 0}, {1, -1, 1},
+    {1, 0, -1}, {1, 0, 0},   {1, 0, 1},  {1, 1, -1}, {1, 1, 0},   {1, 1, 1}};
+
+__global__ void k_cell_keys(const uint32_t *cell, uint64_t n, uint32_t n_cells, uint32_t *keys,
+                            uint32_t *ids, unsigned long long *ctr)
+{
+    GRID_STRIDE(i, n) {
+        uint32_t c = cell[i];
+        if (c >= n_cells) {
+            atomicOr(&ctr[CTR_FLAGS], (unsigned long long)GC_FLAG_ID_RANGE);
+            c = n_cells - 1;
+        }
+        keys[i] = c;
+        ids[i] = (uint32_t)i;
+    }
+}
+
+// cell_start[c] = first sorted index with key >= c, for c = 0 .. n_cells
+__global__ void k_cell_start(const uint32_t *keys, uint64_t n, uint32_t n_cells,
+                             uint32_t *start)
+{
+    GRID_STRIDE(i, n + 1) {
+        // cells c with keys[i-1] < c <= keys[i] start at i (keys[-1] = -1,
+        // keys[n] = n_cells)
+        uint32_t lo = (i == 0) ? 0u : keys[i - 1] + 1u;
+        uint32_t hi = (i == n) ? n_cells : keys[i];
+        for (uint32_t c = lo; c <= hi; ++c) start[c] = (uint32_t)i;
+    }
+}
+
+__device__ __forceinline__ void task_cells(uint64_t t, int m, uint32_t &ca, uint32_t &cb,
+                                           int8_t d[3], bool &self)
+{
+    uint64_t c = t / 14;
+    int o = (int)(t % 14);
+    ca = (uint32_t)c;
+    self = (o == 0);
+    if (self) {
+        cb = ca;
+        d[0] = d[1] = d[2] = 0;
+        return;
+    }
+    int x = (int)(c % m), y = (int)((c / m) % m), z = (int)(c / ((uint64_t)m * m));
+    d[0] = c_half_shell[o - 1][0];
+    d[1] = c_half_shell[o - 1][1];
+    d[2] = c_half_shell[o - 1][2];
+    int bx = (x + d[0] + m) % m, by = (y + d[1] + m) % m, bz = (z + d[2] + m) % m;
+    cb = (uint32_t)(bx + m * (by + m * bz));
+}
+
+__global__ void k_md_counts(uint64_t nt, int m, const uint32_t *start, uint64_t *cnt_t,
+                            uint64_t *cnt_s)
+{
+    GRID_STRIDE(t, nt + 1) {
+        if (t == nt) {
+            cnt_t[t] = 0;
+            cnt_s[t] = 0;
+            continue;
+        }
+        uint32_t ca, cb;
+        int8_t d[3];
+        bool self;
+        task_cells(t, m, ca, cb, d, self);
+        cnt_t[t] = start[ca + 1] - start[ca];
+        cnt_s[t] = self ? 0 : (start[cb + 1] - start[cb]);
+    }
+}
+
+__global__ void k_md_fill(uint64_t nt, int m, const uint32_t *start, const uint32_t *atoms,
+                          const uint64_t *off_t, const uint64_t *off_s, uint64_t tgt_base,
+                          uint64_t src_base, uint64_t id_base, uint32_t *tgt, uint32_t *src,
+                          TaskRec *recs)
+{
+    GRID_STRIDE(t, nt) {
+        uint32_t ca, cb;
+        int8_t d[3];
+        bool self;
+        task_cells(t, m, ca, cb, d, self);
+        uint32_t a0 = start[ca], a1 = start[ca + 1];
+        uint32_t b0 = start[cb], b1 = self ? start[cb] : start[cb + 1];
+        uint64_t ot = off_t[t], os = off_s[t];
+        for (uint32_t q = a0; q < a1; ++q) tgt[ot + (q - a0)] = atoms[q];
+        for (uint32_t q = b0; q < b1; ++q) src[os + (q - b0)] = atoms[q];
+        TaskRec r;
+        r.task_id = id_base + t;
+        r.tgt_off = tgt_base + ot;
+        r.src_off = src_base + os;
+        r.row_off = 0;
+        r.kind = self ? GC_LJ_SELF : GC_LJ_PAIR;
+        r.nt = a1 - a0;
+        r.ns = b1 - b0;
+        r.shift[0] = d[0];
+        r.shift[1] = d[1];
+        r.shift[2] = d[2];
+        r.shift[3] = 0;
+        recs[t] = r;
+    }
+}
+
+}  // namespace
+
+extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m,
+                                 uint64_t task_id_base, uint64_t info_out[4])
+{
+    if (!p || !cell_dev || n == 0 || n > 0x7FFFFFFFull || m < 3 || m > 1024) return GC_ERR_ARG;
+    if (n > p->cfg.id_capacity) return GC_ERR_POOL_FULL;
+    MDState &S = p->md;
+    cudaStream_t s = p->s;
+    const uint32_t n_cells = (uint32_t)m * m * m;
+    const uint64_t nt = 14ull * n_cells;
+    const int maxb = p->num_sms * 16;
+    GC_TRY(S.keys.reserve(n * 4));
+    GC_TRY(S.keys2.reserve(n * 4));
+    GC_TRY(S.ids.reserve(n * 4));
+    GC_TRY(S.ids2.reserve(n * 4));
+    GC_TRY(S.cell_start.reserve(((uint64_t)n_cells + 1) * 4));
+    GC_TRY(S.cnt_t.reserve((nt + 1) * 8 * 2));
+    GC_TRY(S.cnt_s.reserve((nt + 1) * 8 * 2));
+    k_cell_keys<<<grid_for(n, 256, maxb), 256, 0, s>>>(cell_dev, n, n_cells, S.keys.as<uint32_t>(),
+                                                       S.ids.as<uint32_t>(), p->d_ctr);
+    int bits = 1;
+    while (bits < 32 && (1ull << bits) < n_cells) ++bits;
+    GC_TRY(gc_sort_pairs_u32(S.cub_tmp, S.keys.as<uint32_t>(), S.keys2.as<uint32_t>(),
+                             S.ids.as<uint32_t>(), S.ids2.as<uint32_t>(), n, bits, s));
+    uint32_t *start = S.cell_start.as<uint32_t>();
+    k_cell_start<<<grid_for(n + 1, 256, maxb), 256, 0, s>>>(S.keys2.as<uint32_t>(), n, n_cells,
+                                                            start);
+    uint64_t *ct = S.cnt_t.as<uint64_t>(), *ot = ct + (nt + 1);
+    uint64_t *cs = S.cnt_s.as<uint64_t>(), *os = cs + (nt + 1);
+    k_md_counts<<<grid_for(nt + 1, 256, maxb), 256, 0, s>>>(nt, m, start, ct, cs);
+    GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, ct, ot, nt + 1, s));
+    GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, cs, os, nt + 1, s));
+    uint64_t tot_t = 0, tot_s = 0;
+    unsigned long long flags = 0;
+    GC_CUDA_TRY(cudaMemcpyAsync(&tot_t, ot + nt, 8, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaMemcpyAsync(&tot_s, os + nt, 8, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaMemcpyAsync(&flags, p->d_ctr + CTR_FLAGS, 8, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (flags & GC_FLAG_ID_RANGE) {
+        GC_CUDA_TRY(cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, 8, s));
+        return GC_ERR_ARG;
+    }
+    GC_TRY(gc_reserve_batch(p, nt, tot_t, tot_s));
+    k_md_fill<<<grid_for(nt, 256, maxb), 256, 0, s>>>(
+        nt, m, start, S.ids2.as<uint32_t>(), ot, os, p->nb_tgt, p->nb_src, task_id_base,
+        p->tgt_ids.as<uint32_t>() + p->nb_tgt, p->src_ids.as<uint32_t>() + p->nb_src,
+        p->tasks.as<TaskRec>() + p->nb_tasks);
+    GC_CUDA_TRY(cudaGetLastError());
+    p->nb_tasks += nt;
+    p->nb_tgt += tot_t;
+    p->nb_src += tot_s;
+    S.n = n;
+    S.m = m;
+    if (info_out) {
+        info_out[0] = nt;
+        info_out[1] = tot_t;
+        info_out[2] = tot_s;
+        info_out[3] = 0;
+    }
+    return GC_OK;
+}
+
+extern "C" int gc_read_md_cells(gc_pool_t *p, uint32_t *cell_start, uint32_t *cell_atoms)
+{
+    if (!p || p->md.n == 0) return GC_ERR_STATE;
+    MDState &S = p->md;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    uint64_t nc = (uint64_t)S.m * S.m * S.m;
+    if (cell_start)
+        GC_CUDA_TRY(cudaMemcpy(cell_start, S.cell_start.p, (nc + 1) * 4, cudaMemcpyDeviceToHost));
+    if (cell_atoms)
+        GC_CUDA_TRY(cudaMemcpy(cell_atoms, S.ids2.p, S.n * 4, cudaMemcpyDeviceToHost));
+    return GC_OK;
+}

@@ -1,0 +1,548 @@
+// gc_nbody.cu -- N-body task builder on the device (Section 4.1: particles
+// grouped into buckets of a Barnes-Hut tree; each bucket's tree walk yields
+// one interaction list of tree nodes and particles; one work request per
+// bucket).
+//
+// Construction without recursion or per-level launches.  After a stable
+// sort of the Morton keys, every tree node is the cell at some level l that
+// starts at some sorted particle i, so a node is named by (i, l):
+//   - i starts a level-l cell iff l > lcp(i), the common-prefix level of
+//     keys i-1 and i;
+//   - the level-l cell of i has more than B particles iff some window of
+//     B+1 consecutive sorted particles containing i shares its level-l
+//     prefix, i.e. l <= D(i) = max over windows [j, j+B] containing i of the
+//     common-prefix level of keys j and j+B;
+//   - a cell is a node iff its parent has more than B particles, and a node
+//     is a leaf iff it has at most B particles or l = 21.
+// So particle i starts the nodes at levels lcp(i)+1 .. min(D(i)+1, 21).
+// Ordering the pairs (i, l) by i, then l, is exactly depth-first preorder
+// with children in octant order (a node precedes its descendants, which
+// share or follow its first particle; siblings are ordered by first
+// particle).  A prefix sum over the per-particle node counts numbers the
+// nodes; a node's particle range end comes from a binary search on the
+// sorted keys and its subtree size from the same prefix sum.
+//
+// The walk visits nodes in preorder with skips (no stack): an accepted or
+// leaf node continues at k + size(k), an opened internal node at k + 1.
+#include <cub/device/device_scan.cuh>
+
+#include "gc_common.cuh"
+
+int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint64_t n);
+
+namespace {
+
+#define GRID_STRIDE(i, n)                                                       \
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); \
+         i += (uint64_t)gridDim.x * blockDim.x)
+
+inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
+{
+    uint64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (uint64_t)max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+struct GridParams {
+    double lo[3];
+    double scale;   // 2^21 / L, L = smallest power of two >= largest extent
+};
+
+__device__ __forceinline__ uint32_t ord_key(float f)
+{
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float ord_val(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// bounds[0..2] = ordered-int min, bounds[3..5] = ordered-int max
+__global__ void k_bbox(const float4 *x, uint64_t n, uint32_t *bounds)
+{
+    uint32_t mn[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, mx[3] = {0, 0, 0};
+    GRID_STRIDE(i, n) {
+        float4 v = x[i];
+        uint32_t k[3] = {ord_key(v.x), ord_key(v.y), ord_key(v.z)};
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = min(mn[a], k[a]);
+            mx[a] = max(mx[a], k[a]);
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o; o >>= 1) {
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(&bounds[a], mn[a]);
+            atomicMax(&bounds[3 + a], mx[a]);
+        }
+}
+
+__global__ void k_grid_params(const uint32_t *bounds, GridParams *gp)
+{
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double lo = (double)ord_val(bounds[a]);
+        double hi = (double)ord_val(bounds[3 + a]);
+        gp->lo[a] = lo;
+        if (hi - lo > ext) ext = hi - lo;
+    }
+    double L = 1.0;
+    if (ext > 0.0) {
+        while (L < ext) L *= 2.0;
+        while (L * 0.5 >= ext) L *= 0.5;
+    }
+    gp->scale = 2097152.0 / L;
+}
+
+__device__ __forceinline__ uint32_t quant(float x, double lo, double scale)
+{
+    double t = __dmul_rn(__dsub_rn((double)x, lo), scale);
+    double f = floor(t);
+    f = fmax(f, 0.0);
+    f = fmin(f, 2097151.0);
+    return (uint32_t)f;
+}
+
+// spread the 21 low bits of v to every third bit
+__device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1FFFFFu;
+    x = (x | (x << 32)) & 0x001F00000000FFFFull;
+    x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+    x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+    x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t compact3(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x | (x >> 2)) & 0x10C30C30C30C30C3ull;
+    x = (x | (x >> 4)) & 0x100F00F00F00F00Full;
+    x = (x | (x >> 8)) & 0x001F0000FF0000FFull;
+    x = (x | (x >> 16)) & 0x001F00000000FFFFull;
+    x = (x | (x >> 32)) & 0x00000000001FFFFFull;
+    return (uint32_t)x;
+}
+
+__global__ void k_keys(const float4 *x, uint64_t n, const GridParams *gp, uint64_t *keys,
+                       uint32_t *ids)
+{
+    const GridParams g = *gp;
+    GRID_STRIDE(i, n) {
+        float4 v = x[i];
+        uint32_t qx = quant(v.x, g.lo[0], g.scale);
+        uint32_t qy = quant(v.y, g.lo[1], g.scale);
+        uint32_t qz = quant(v.z, g.lo[2], g.scale);
+        keys[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+        ids[i] = (uint32_t)i;
+    }
+}
+
+// deepest level l (0..21) at which keys a and b share the level-l cell
+__device__ __forceinline__ int common_level(uint64_t a, uint64_t b)
+{
+    uint64_t x = a ^ b;
+    if (x == 0) return 21;
+    int hb = 63 - __clzll((long long)x);
+    return 20 - hb / 3;
+}
+
+__global__ void k_lcp_win(const uint64_t *K, uint64_t n, int B, int8_t *lcp, int8_t *win)
+{
+    GRID_STRIDE(i, n) {
+        lcp[i] = (int8_t)((i == 0) ? -1 : common_level(K[i - 1], K[i]));
+        if (i + (uint64_t)B < n) win[i] = (int8_t)common_level(K[i], K[i + B]);
+    }
+}
+
+__global__ void k_dmax(const int8_t *lcp, const int8_t *win, uint64_t n, int B, int8_t *dmax,
+                       uint32_t *nnode)
+{
+    GRID_STRIDE(i, n) {
+        int d = -1;
+        if (n > (uint64_t)B) {
+            int64_t j0 = (int64_t)i - B;
+            if (j0 < 0) j0 = 0;
+            int64_t j1 = (int64_t)i;
+            if (j1 > (int64_t)(n - B - 1)) j1 = (int64_t)(n - B - 1);
+            for (int64_t j = j0; j <= j1; ++j) d = max(d, (int)win[j]);
+        }
+        dmax[i] = (int8_t)d;
+        int lo = (i == 0) ? 0 : lcp[i] + 1;
+        int hi = min(d + 1, 21);
+        nnode[i] = (hi >= lo) ? (uint32_t)(hi - lo + 1) : 0u;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) nnode[n] = 0;
+}
+
+// node_a = {first, count, subtree size, level | leaf << 8}; node_b = {cell x, y, z, 0}
+__global__ void k_emit_nodes(const uint64_t *K, uint64_t n, const int8_t *lcp,
+                             const int8_t *dmax, const uint32_t *node_off, uint4 *node_a,
+                             uint4 *node_b, uint32_t *bcnt, int B)
+{
+    GRID_STRIDE(i, n) {
+        int lo = (i == 0) ? 0 : lcp[i] + 1;
+        int d = dmax[i];
+        int hi = min(d + 1, 21);
+        for (int l = lo; l <= hi; ++l) {
+            uint32_t k = node_off[i] + (uint32_t)(l - lo);
+            int sh = 3 * (21 - l);
+            uint64_t pre = (sh >= 64) ? 0 : (K[i] >> sh);
+            // end of the cell: first e > i whose key prefix differs
+            uint64_t a = i + 1, b = n;
+            while (a < b) {
+                uint64_t mid = (a + b) >> 1;
+                uint64_t pm = (sh >= 64) ? 0 : (K[mid] >> sh);
+                if (pm == pre) a = mid + 1; else b = mid;
+            }
+            uint32_t e = (uint32_t)a;
+            bool leaf = (l > d) || (l == 21);
+            uint32_t cnt = e - (uint32_t)i;
+            uint32_t size = node_off[e] - node_off[i] - (uint32_t)(l - lo);
+            node_a[k] = make_uint4((uint32_t)i, cnt, size, (uint32_t)l | (leaf ? 256u : 0u));
+            node_b[k] = make_uint4(compact3(pre), compact3(pre >> 1), compact3(pre >> 2), 0u);
+            bcnt[k] = leaf ? (cnt + (uint32_t)B - 1) / (uint32_t)B : 0u;
+        }
+    }
+}
+
+// FP64 monopoles from prefix sums over the sorted particles: a node's
+// (mass, mass-weighted position) is P[first + count] - P[first].
+struct M4 {
+    double m, mx, my, mz;
+};
+
+struct M4Add {
+    __device__ __forceinline__ M4 operator()(const M4 &a, const M4 &b) const
+    {
+        return M4{a.m + b.m, a.mx + b.mx, a.my + b.my, a.mz + b.mz};
+    }
+};
+
+__global__ void k_mono_input(const uint32_t *sorted_ids, const float4 *x, uint64_t n, M4 *out)
+{
+    GRID_STRIDE(i, n + 1) {
+        M4 v{0, 0, 0, 0};
+        if (i < n) {
+            float4 p = x[sorted_ids[i]];
+            double w = (double)p.w;
+            v = M4{w, w * (double)p.x, w * (double)p.y, w * (double)p.z};
+        }
+        out[i] = v;
+    }
+}
+
+__global__ void k_mono_nodes(const uint4 *node_a, uint64_t nn, const M4 *P, float4 *node_val)
+{
+    GRID_STRIDE(k, nn) {
+        uint4 A = node_a[k];
+        M4 e = P[A.x + A.y], f = P[A.x];
+        double m = e.m - f.m;
+        float4 v;
+        v.x = (float)(m != 0.0 ? (e.mx - f.mx) / m : 0.0);
+        v.y = (float)(m != 0.0 ? (e.my - f.my) / m : 0.0);
+        v.z = (float)(m != 0.0 ? (e.mz - f.mz) / m : 0.0);
+        v.w = (float)m;
+        node_val[k] = v;
+    }
+}
+
+// bucket = {first, count, leaf node, 0}; box in doubled grid units
+__global__ void k_emit_buckets(const uint4 *node_a, uint64_t nn, const uint32_t *boff,
+                               const uint64_t *K, int B, uint4 *bucket, int4 *blo, int4 *bhi)
+{
+    GRID_STRIDE(k, nn) {
+        uint4 A = node_a[k];
+        if (!(A.w & 256u)) continue;
+        uint32_t nb = (A.y + (uint32_t)B - 1) / (uint32_t)B;
+        for (uint32_t c = 0; c < nb; ++c) {
+            uint32_t f = A.x + c * (uint32_t)B;
+            uint32_t cnt = min((uint32_t)B, A.y - c * (uint32_t)B);
+            uint32_t b = boff[k] + c;
+            bucket[b] = make_uint4(f, cnt, (uint32_t)k, 0u);
+            int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
+            for (uint32_t q = f; q < f + cnt; ++q) {
+                uint64_t key = K[q];
+                int v[3] = {(int)compact3(key), (int)compact3(key >> 1), (int)compact3(key >> 2)};
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = min(lo[a], v[a]);
+                    hi[a] = max(hi[a], v[a]);
+                }
+            }
+            blo[b] = make_int4(2 * lo[0], 2 * lo[1], 2 * lo[2], 0);
+            bhi[b] = make_int4(2 * hi[0] + 2, 2 * hi[1] + 2, 2 * hi[2] + 2, 0);
+        }
+    }
+}
+
+// Stackless preorder walk.  FILL = false: count list entries; true: write them.
+template <bool FILL>
+__global__ void k_walk(const uint4 *node_a, const uint4 *node_b, uint32_t nn,
+                       const uint4 *bucket, const int4 *blo, const int4 *bhi, uint64_t nb,
+                       const uint32_t *sorted_ids, uint32_t n_part, int64_t tn2, int64_t td2,
+                       uint32_t *len, const uint64_t *off, uint32_t *out)
+{
+    GRID_STRIDE(b, nb) {
+        uint32_t bf = bucket[b].x;
+        int4 lo = blo[b], hi = bhi[b];
+        uint32_t cnt = 0;
+        uint32_t *o = FILL ? out + off[b] : nullptr;
+        uint32_t k = 0;
+        while (k < nn) {
+            uint4 A = node_a[k];
+            bool contains = (A.x <= bf) && (bf < A.x + A.y);
+            if (!contains) {
+                uint4 C = node_b[k];
+                int lvl = (int)(A.w & 255u);
+                int64_t s = (int64_t)1 << (22 - lvl);
+                int64_t h = s >> 1;
+                int64_t cx = (int64_t)C.x * s + h, cy = (int64_t)C.y * s + h,
+                        cz = (int64_t)C.z * s + h;
+                int64_t dx = max((int64_t)0, max((int64_t)lo.x - cx, cx - (int64_t)hi.x));
+                int64_t dy = max((int64_t)0, max((int64_t)lo.y - cy, cy - (int64_t)hi.y));
+                int64_t dz = max((int64_t)0, max((int64_t)lo.z - cz, cz - (int64_t)hi.z));
+                int64_t d2 = dx * dx + dy * dy + dz * dz;
+                if (td2 * s * s < tn2 * d2) {
+                    if (FILL) o[cnt] = n_part + k;
+                    ++cnt;
+                    k += A.z;
+                    continue;
+                }
+            }
+            if (A.w & 256u) {
+                if (FILL)
+                    for (uint32_t q = 0; q < A.y; ++q) o[cnt + q] = sorted_ids[A.x + q];
+                cnt += A.y;
+            }
+            k += 1;
+        }
+        if (!FILL) len[b] = cnt;
+    }
+}
+
+__global__ void k_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n)
+{
+    GRID_STRIDE(i, n) out[i] = in[i];
+}
+
+__global__ void k_nbody_tasks(const uint4 *bucket, uint64_t nb, const uint64_t *list_off,
+                              const uint32_t *list_len, uint64_t tgt_base, uint64_t src_base,
+                              uint64_t id_base, TaskRec *out)
+{
+    GRID_STRIDE(b, nb) {
+        TaskRec r;
+        uint4 B = bucket[b];
+        r.task_id = id_base + b;
+        r.tgt_off = tgt_base + B.x;
+        r.src_off = src_base + list_off[b];
+        r.row_off = 0;
+        r.kind = GC_GRAVITY;
+        r.nt = B.y;
+        r.ns = list_len[b];
+        r.shift[0] = r.shift[1] = r.shift[2] = r.shift[3] = 0;
+        out[b] = r;
+    }
+}
+
+}  // namespace
+
+extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_t n,
+                                    int bucket_max, int theta_num, int theta_den,
+                                    uint64_t task_id_base, uint64_t info_out[4])
+{
+    if (!p || !xyzm_dev || n == 0 || n > 0x7FFFFFFFull || bucket_max < 1 || bucket_max > 4096 ||
+        theta_num < 0 || theta_num > 255 || theta_den < 1 || theta_den > 255)
+        return GC_ERR_ARG;
+    if (((uintptr_t)xyzm_dev) % 16) return GC_ERR_ARG;
+    if (n >= p->cfg.id_capacity) return GC_ERR_POOL_FULL;
+    NBodyState &S = p->nb;
+    cudaStream_t s = p->s;
+    const int B = bucket_max;
+    const int maxb = p->num_sms * 16;
+    const float4 *x = (const float4 *)xyzm_dev;
+
+    GC_TRY(S.bounds.reserve(64 + sizeof(GridParams)));
+    GC_TRY(S.keys.reserve(n * 8));
+    GC_TRY(S.keys2.reserve(n * 8));
+    GC_TRY(S.ids.reserve(n * 4));
+    GC_TRY(S.ids2.reserve(n * 4));
+    GC_TRY(S.lcp.reserve(n + 1));
+    GC_TRY(S.win.reserve(n + 1));
+    GC_TRY(S.dmax.reserve(n + 1));
+    GC_TRY(S.nnode.reserve((n + 1) * 4));
+    GC_TRY(S.node_off.reserve((n + 1) * 4));
+
+    uint32_t *bounds = S.bounds.as<uint32_t>();
+    GridParams *gp = (GridParams *)(S.bounds.as<char>() + 64);
+    uint32_t init[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0, 0, 0};
+    GC_CUDA_TRY(cudaMemcpyAsync(bounds, init, sizeof init, cudaMemcpyHostToDevice, s));
+    k_bbox<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, bounds);
+    k_grid_params<<<1, 1, 0, s>>>(bounds, gp);
+    k_keys<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, gp, S.keys.as<uint64_t>(),
+                                                  S.ids.as<uint32_t>());
+    GC_TRY(gc_sort_pairs_u64(S.cub_tmp, S.keys.as<uint64_t>(), S.keys2.as<uint64_t>(),
+                             S.ids.as<uint32_t>(), S.ids2.as<uint32_t>(), n, 63, s));
+    const uint64_t *K = S.keys2.as<uint64_t>();
+    const uint32_t *sid = S.ids2.as<uint32_t>();
+    k_lcp_win<<<grid_for(n, 256, maxb), 256, 0, s>>>(K, n, B, S.lcp.as<int8_t>(),
+                                                     S.win.as<int8_t>());
+    k_dmax<<<grid_for(n, 256, maxb), 256, 0, s>>>(S.lcp.as<int8_t>(), S.win.as<int8_t>(), n, B,
+                                                  S.dmax.as<int8_t>(), S.nnode.as<uint32_t>());
+    GC_TRY(gc_exclusive_scan_u32(S.cub_tmp, S.nnode.as<uint32_t>(), S.node_off.as<uint32_t>(),
+                                 n + 1, s));
+    uint32_t NN = 0;
+    GC_CUDA_TRY(cudaMemcpyAsync(&NN, S.node_off.as<uint32_t>() + n, 4, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaStreamSynchronize(s));
+    if ((uint64_t)n + NN > p->cfg.id_capacity) return GC_ERR_POOL_FULL;
+
+    GC_TRY(S.node_a.reserve((uint64_t)NN * 16 + 16));
+    GC_TRY(S.node_b.reserve((uint64_t)NN * 16 + 16));
+    GC_TRY(S.node_val.reserve((uint64_t)NN * 16 + 16));
+    GC_TRY(S.list_len.reserve(((uint64_t)NN + 1) * 4 * 2));   // bucket counts, then offsets
+    uint32_t *bcnt = S.list_len.as<uint32_t>();
+    uint32_t *boff = bcnt + (NN + 1);
+    GC_CUDA_TRY(cudaMemsetAsync(bcnt + NN, 0, 4, s));
+    k_emit_nodes<<<grid_for(n, 256, maxb), 256, 0, s>>>(
+        K, n, S.lcp.as<int8_t>(), S.dmax.as<int8_t>(), S.node_off.as<uint32_t>(),
+        S.node_a.as<uint4>(), S.node_b.as<uint4>(), bcnt, B);
+    GC_TRY(S.mono.reserve((n + 1) * sizeof(M4) * 2));
+    M4 *mono_in = S.mono.as<M4>(), *mono_pre = mono_in + (n + 1);
+    k_mono_input<<<grid_for(n + 1, 256, maxb), 256, 0, s>>>(sid, x, n, mono_in);
+    {
+        size_t bytes = 0;
+        if (cub::DeviceScan::ExclusiveScan(nullptr, bytes, mono_in, mono_pre, M4Add(),
+                                           M4{0, 0, 0, 0}, (int64_t)(n + 1), s) != cudaSuccess)
+            return GC_ERR_CUDA;
+        GC_TRY(S.cub_tmp.reserve(bytes + 16));
+        size_t have = S.cub_tmp.cap;
+        if (cub::DeviceScan::ExclusiveScan(S.cub_tmp.p, have, mono_in, mono_pre, M4Add(),
+                                           M4{0, 0, 0, 0}, (int64_t)(n + 1), s) != cudaSuccess)
+            return GC_ERR_CUDA;
+    }
+    k_mono_nodes<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, mono_pre,
+                                                         S.node_val.as<float4>());
+    GC_TRY(gc_launch_upload_seq(p, (uint32_t)n, S.node_val.as<float4>(), NN));
+    GC_TRY(gc_exclusive_scan_u32(S.cub_tmp, bcnt, boff, (uint64_t)NN + 1, s));
+    uint32_t NB = 0;
+    GC_CUDA_TRY(cudaMemcpyAsync(&NB, boff + NN, 4, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaStreamSynchronize(s));
+
+    GC_TRY(S.bucket.reserve((uint64_t)NB * 16 + 16));
+    GC_TRY(S.bbox.reserve((uint64_t)NB * 32 + 32));
+    int4 *blo = S.bbox.as<int4>(), *bhi = blo + NB;
+    k_emit_buckets<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, boff, K, B,
+                                                           S.bucket.as<uint4>(), blo, bhi);
+    GC_TRY(S.list_off.reserve(((uint64_t)NB + 1) * 8 * 2));
+    GC_TRY(S.win.reserve(((uint64_t)NB + 1) * 4));   // reused for list lengths
+    uint32_t *llen = S.win.as<uint32_t>();
+    uint64_t *llen64 = S.list_off.as<uint64_t>();
+    uint64_t *loff = llen64 + (NB + 1);
+    const int64_t tn2 = (int64_t)theta_num * theta_num, td2 = (int64_t)theta_den * theta_den;
+    k_walk<false><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
+        S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
+        (uint32_t)n, tn2, td2, llen, nullptr, nullptr);
+    GC_CUDA_TRY(cudaMemsetAsync(llen + NB, 0, 4, s));
+    k_u32_to_u64<<<grid_for(NB + 1, 256, maxb), 256, 0, s>>>(llen, llen64, (uint64_t)NB + 1);
+    GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, llen64, loff, (uint64_t)NB + 1, s));
+    uint64_t NL = 0;
+    uint32_t maxlen = 0;
+    GC_CUDA_TRY(cudaMemcpyAsync(&NL, loff + NB, 8, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaStreamSynchronize(s));
+
+    // append the tasks to the pending batch
+    GC_TRY(gc_reserve_batch(p, NB, n, NL));
+    uint32_t *dt = p->tgt_ids.as<uint32_t>() + p->nb_tgt;
+    uint32_t *ds = p->src_ids.as<uint32_t>() + p->nb_src;
+    TaskRec *recs = p->tasks.as<TaskRec>() + p->nb_tasks;
+    k_walk<true><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
+        S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
+        (uint32_t)n, tn2, td2, nullptr, loff, ds);
+    GC_CUDA_TRY(cudaMemcpyAsync(dt, sid, n * 4, cudaMemcpyDeviceToDevice, s));
+    k_nbody_tasks<<<grid_for(NB, 256, maxb), 256, 0, s>>>(S.bucket.as<uint4>(), NB, loff, llen,
+                                                          p->nb_tgt, p->nb_src, task_id_base,
+                                                          recs);
+    GC_CUDA_TRY(cudaGetLastError());
+    p->nb_tasks += NB;
+    p->nb_tgt += n;
+    p->nb_src += NL;
+    S.n = n;
+    S.n_nodes = NN;
+    S.n_buckets = NB;
+    S.n_list = NL;
+    (void)maxlen;
+    if (info_out) {
+        info_out[0] = NN;
+        info_out[1] = NB;
+        info_out[2] = NL;
+        info_out[3] = 0;
+    }
+    return GC_OK;
+}
+
+extern "C" int gc_read_nbody_tree(gc_pool_t *p, uint32_t *sorted_ids, uint64_t *sorted_keys,
+                                  uint8_t *level, uint32_t *cell3, uint32_t *first,
+                                  uint32_t *count, uint8_t *leaf, uint32_t *size,
+                                  float *node_xyzm, uint32_t *bucket_first,
+                                  uint32_t *bucket_count, uint32_t *bucket_node,
+                                  uint64_t *list_off, uint32_t *list_ids)
+{
+    if (!p || p->nb.n == 0) return GC_ERR_STATE;
+    NBodyState &S = p->nb;
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    const uint64_t n = S.n, NN = S.n_nodes, NB = S.n_buckets;
+    if (sorted_ids) GC_CUDA_TRY(cudaMemcpy(sorted_ids, S.ids2.p, n * 4, cudaMemcpyDeviceToHost));
+    if (sorted_keys) GC_CUDA_TRY(cudaMemcpy(sorted_keys, S.keys2.p, n * 8, cudaMemcpyDeviceToHost));
+    if (level || first || count || leaf || size || cell3) {
+        std::vector<uint4> a(NN), b(NN);
+        GC_CUDA_TRY(cudaMemcpy(a.data(), S.node_a.p, NN * 16, cudaMemcpyDeviceToHost));
+        GC_CUDA_TRY(cudaMemcpy(b.data(), S.node_b.p, NN * 16, cudaMemcpyDeviceToHost));
+        for (uint64_t k = 0; k < NN; ++k) {
+            if (first) first[k] = a[k].x;
+            if (count) count[k] = a[k].y;
+            if (size) size[k] = a[k].z;
+            if (level) level[k] = (uint8_t)(a[k].w & 255u);
+            if (leaf) leaf[k] = (uint8_t)((a[k].w >> 8) & 1u);
+            if (cell3) {
+                cell3[3 * k] = b[k].x;
+                cell3[3 * k + 1] = b[k].y;
+                cell3[3 * k + 2] = b[k].z;
+            }
+        }
+    }
+    if (node_xyzm) GC_CUDA_TRY(cudaMemcpy(node_xyzm, S.node_val.p, NN * 16, cudaMemcpyDeviceToHost));
+    if (bucket_first || bucket_count || bucket_node) {
+        std::vector<uint4> bk(NB);
+        GC_CUDA_TRY(cudaMemcpy(bk.data(), S.bucket.p, NB * 16, cudaMemcpyDeviceToHost));
+        for (uint64_t b = 0; b < NB; ++b) {
+            if (bucket_first) bucket_first[b] = bk[b].x;
+            if (bucket_count) bucket_count[b] = bk[b].y;
+            if (bucket_node) bucket_node[b] = bk[b].z;
+        }
+    }
+    const uint64_t *loff = S.list_off.as<uint64_t>() + (NB + 1);
+    if (list_off) GC_CUDA_TRY(cudaMemcpy(list_off, loff, (NB + 1) * 8, cudaMemcpyDeviceToHost));
+    if (list_ids) {
+        // the lists live in the batch source array (pending, or last flushed)
+        const uint32_t *src = nullptr;
+        uint64_t base = 0;
+        if (p->nb_src >= S.n_list && p->nb_tasks >= NB) {
+            src = p->src_ids.as<uint32_t>();
+            base = p->nb_src - S.n_list;
+        } else if (p->have_last && p->last_src >= S.n_list) {
+            src = p->last_src_ids.as<uint32_t>();
+            base = p->last_src - S.n_list;
+        }
+        if (!src) return GC_ERR_STATE;
+        GC_CUDA_TRY(cudaMemcpy(list_ids, src + base, S.n_list * 4, cudaMemcpyDeviceToHost));
+    }
+    return GC_OK;
+}

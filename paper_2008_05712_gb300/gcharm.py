@@ -1,0 +1,362 @@
+"""Thin Python binding of libgcharm (include/gcharm.h).
+
+Argument marshalling only: every step of the batched path runs in the CUDA
+library.  Host arrays are numpy; device arrays are torch CUDA tensors, used
+purely as device memory (their ``data_ptr()`` is handed to the library).
+The library must have been built (``paper_2008_05712_gb300.build.build()``);
+there is no fallback: importing the binding without the library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libgcharm.so")
+
+GC_OK = 0
+GC_ERR_ARG = -1
+GC_ERR_OOM = -2
+GC_ERR_POOL_FULL = -3
+GC_ERR_UNKNOWN_ID = -4
+GC_ERR_BUDGET = -5
+GC_ERR_NOT_READY = -6
+GC_ERR_TIMEOUT = -7
+GC_ERR_CUDA = -8
+GC_ERR_STATE = -9
+
+GC_GRAVITY = 0
+GC_LJ_PAIR = 1
+GC_LJ_SELF = 2
+
+NONE32 = 0xFFFFFFFF
+
+
+class GcConfig(C.Structure):
+    _fields_ = [("eps2", C.c_float), ("lj_eps", C.c_float), ("lj_sigma", C.c_float),
+                ("lj_rc2", C.c_float), ("md_edge", C.c_float),
+                ("id_capacity", C.c_uint64), ("pool_capacity", C.c_uint64),
+                ("staging_budget_bytes", C.c_uint64), ("deterministic", C.c_int),
+                ("cuda_stream", C.c_void_p)]
+
+
+class GcTask(C.Structure):
+    _fields_ = [("task_id", C.c_uint64), ("kind", C.c_uint32), ("n_targets", C.c_uint32),
+                ("n_sources", C.c_uint32), ("target_ids", C.POINTER(C.c_uint32)),
+                ("source_ids", C.POINTER(C.c_uint32)), ("shift", C.c_int8 * 3)]
+
+
+_STAT_FIELDS = ["flushes", "tasks", "entries", "unique", "hits", "misses", "updates",
+                "evictions", "h2d_bytes", "interactions", "lj_pairs_in_cutoff", "last_unique",
+                "last_hits", "last_misses", "last_evictions", "last_staging_bytes",
+                "last_waves"]
+
+
+class GcStats(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in _STAT_FIELDS] + [("reuse_hist", C.c_uint64 * 8)]
+
+
+class GcError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = _lib.gc_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+_lib = None
+
+P = C.c_void_p
+U64 = C.c_uint64
+U64P = C.POINTER(C.c_uint64)
+
+# name -> argtypes (all return int unless noted)
+_SIGS = {
+    "gc_pool_create": [C.POINTER(GcConfig), C.POINTER(P)],
+    "gc_pool_destroy": [P],
+    "gc_pool_upload": [P, P, P, U64],
+    "gc_pool_upload_device": [P, P, P, U64],
+    "gc_submit": [P, P, U64, U64P],
+    "gc_submit_csr": [P, U64, P, P, P, P, P, P, P, U64, U64, C.c_int, U64P],
+    "gc_flush": [P],
+    "gc_flush_per_task": [P],
+    "gc_wait": [P, U64, U64],
+    "gc_result_rows": [P, U64P],
+    "gc_read_batch_results": [P, U64, U64, P],
+    "gc_read_results": [P, P, U64, P],
+    "gc_read_totals": [P, P, U64, P],
+    "gc_totals_device": [P, C.POINTER(P)],
+    "gc_reset_totals": [P],
+    "gc_stats": [P, C.POINTER(GcStats)],
+    "gc_strerror": [C.c_int],
+    "gc_read_entry_slots": [P, P, P],
+    "gc_read_pack_perm": [P, P, P],
+    "gc_batch_sizes": [P, U64P, U64P, U64P],
+    "gc_read_residency": [P, P, P, P],
+    "gc_read_evicted": [P, P, U64, U64P],
+    "gc_build_nbody_tasks": [P, P, U64, C.c_int, C.c_int, C.c_int, U64, P],
+    "gc_read_nbody_tree": [P] + [P] * 14,
+    "gc_build_md_tasks": [P, P, U64, C.c_int, U64, P],
+    "gc_read_md_cells": [P, P, P],
+    "gc_last_timings": [P, P],
+}
+
+
+def exported_symbols():
+    """Names the header declares (used by the ABI test)."""
+    return sorted(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load libgcharm.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_2008_05712_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name == "gc_strerror" else C.c_int
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _check(rc, what):
+    if rc != GC_OK:
+        raise GcError(rc, what)
+
+
+def _dptr(t):
+    """Device pointer of a torch CUDA tensor (contiguous)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Pool:
+    """One device pool (chare table + slots + batch + totals)."""
+
+    def __init__(self, id_capacity, pool_capacity, eps2=1e-4, lj_eps=1.0, lj_sigma=1.0,
+                 lj_rc2=0.0, md_edge=0.0, staging_budget_bytes=0, stream=None):
+        lib = load()
+        cfg = GcConfig()
+        cfg.eps2 = eps2
+        cfg.lj_eps, cfg.lj_sigma, cfg.lj_rc2, cfg.md_edge = lj_eps, lj_sigma, lj_rc2, md_edge
+        cfg.id_capacity, cfg.pool_capacity = int(id_capacity), int(pool_capacity)
+        cfg.staging_budget_bytes = int(staging_budget_bytes)
+        cfg.deterministic = 1
+        cfg.cuda_stream = stream
+        h = C.c_void_p()
+        _check(lib.gc_pool_create(C.byref(cfg), C.byref(h)), "gc_pool_create")
+        self.h = h
+        self.cfg = cfg
+        self.lib = lib
+
+    def close(self):
+        if self.h:
+            _check(self.lib.gc_pool_destroy(self.h), "gc_pool_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- data -----------------------------------------------------------------
+    def upload(self, ids, xyzm):
+        ids = np.ascontiguousarray(ids, np.uint32)
+        x = np.ascontiguousarray(xyzm, np.float32)
+        assert x.shape == (ids.shape[0], 4)
+        _check(self.lib.gc_pool_upload(self.h, _p(ids), _p(x), ids.shape[0]), "gc_pool_upload")
+
+    def upload_device(self, ids_t, xyzm_t):
+        _check(self.lib.gc_pool_upload_device(self.h, _dptr(ids_t), _dptr(xyzm_t),
+                                              ids_t.numel()), "gc_pool_upload_device")
+
+    # ---- batching ---------------------------------------------------------------
+    def submit_csr(self, kinds, tgt_off, tgt_ids, src_off, src_ids, shifts=None, task_ids=None):
+        kinds = np.ascontiguousarray(kinds, np.uint32)
+        to = np.ascontiguousarray(tgt_off, np.uint64)
+        so = np.ascontiguousarray(src_off, np.uint64)
+        tg = np.ascontiguousarray(tgt_ids, np.uint32)
+        sr = np.ascontiguousarray(src_ids, np.uint32)
+        sh = None if shifts is None else np.ascontiguousarray(shifts, np.int8)
+        ti = None if task_ids is None else np.ascontiguousarray(task_ids, np.uint64)
+        b = C.c_uint64()
+        _check(self.lib.gc_submit_csr(self.h, kinds.shape[0], _p(ti), _p(kinds), _p(sh), _p(to),
+                                      _p(tg), _p(so), _p(sr), 0, 0, 0, C.byref(b)),
+               "gc_submit_csr")
+        return b.value
+
+    def submit_csr_device(self, kinds, tgt_off, tgt_ids, src_off, src_ids, n_tgt, n_src,
+                          shifts=None, task_ids=None):
+        b = C.c_uint64()
+        _check(self.lib.gc_submit_csr(self.h, kinds.numel(), _dptr(task_ids), _dptr(kinds),
+                                      _dptr(shifts), _dptr(tgt_off), _dptr(tgt_ids),
+                                      _dptr(src_off), _dptr(src_ids), int(n_tgt), int(n_src),
+                                      1, C.byref(b)), "gc_submit_csr(device)")
+        return b.value
+
+    def submit_tasks(self, tasks):
+        """tasks: list of dicts {task_id, kind, targets, sources, shift}."""
+        arr = (GcTask * len(tasks))()
+        keep = []
+        for t, d in zip(arr, tasks):
+            tg = np.ascontiguousarray(d["targets"], np.uint32)
+            sr = np.ascontiguousarray(d.get("sources", []), np.uint32)
+            keep += [tg, sr]
+            t.task_id = int(d.get("task_id", 0))
+            t.kind = int(d["kind"])
+            t.n_targets, t.n_sources = tg.shape[0], sr.shape[0]
+            t.target_ids = tg.ctypes.data_as(C.POINTER(C.c_uint32))
+            t.source_ids = sr.ctypes.data_as(C.POINTER(C.c_uint32))
+            for a, v in enumerate(d.get("shift", (0, 0, 0))):
+                t.shift[a] = int(v)
+        b = C.c_uint64()
+        _check(self.lib.gc_submit(self.h, C.cast(arr, C.c_void_p), len(tasks), C.byref(b)),
+               "gc_submit")
+        return b.value
+
+    def flush(self):
+        _check(self.lib.gc_flush(self.h), "gc_flush")
+
+    def flush_per_task(self):
+        _check(self.lib.gc_flush_per_task(self.h), "gc_flush_per_task")
+
+    def wait(self, batch, timeout_ns=0):
+        _check(self.lib.gc_wait(self.h, int(batch), int(timeout_ns)), "gc_wait")
+
+    # ---- results ----------------------------------------------------------------
+    def result_rows(self):
+        r = C.c_uint64()
+        _check(self.lib.gc_result_rows(self.h, C.byref(r)), "gc_result_rows")
+        return r.value
+
+    def results(self, first=0, n=None):
+        """(rows, 8) float32: sum (4) then compensation (4); value = s - c."""
+        if n is None:
+            n = self.result_rows() - first
+        out = np.empty((n, 8), np.float32)
+        _check(self.lib.gc_read_batch_results(self.h, first, n, _p(out)),
+               "gc_read_batch_results")
+        return out
+
+    def read_results(self, task_ids, n_rows):
+        ti = np.ascontiguousarray(task_ids, np.uint64)
+        out = np.empty((n_rows, 8), np.float32)
+        _check(self.lib.gc_read_results(self.h, _p(ti), ti.shape[0], _p(out)), "gc_read_results")
+        return out
+
+    def totals(self, ids):
+        ids = np.ascontiguousarray(ids, np.uint32)
+        out = np.empty((ids.shape[0], 4), np.float64)
+        _check(self.lib.gc_read_totals(self.h, _p(ids), ids.shape[0], _p(out)), "gc_read_totals")
+        return out
+
+    def totals_device_ptr(self):
+        p = C.c_void_p()
+        _check(self.lib.gc_totals_device(self.h, C.byref(p)), "gc_totals_device")
+        return p.value
+
+    def reset_totals(self):
+        _check(self.lib.gc_reset_totals(self.h), "gc_reset_totals")
+
+    def stats(self):
+        s = GcStats()
+        _check(self.lib.gc_stats(self.h, C.byref(s)), "gc_stats")
+        d = {f: getattr(s, f) for f in _STAT_FIELDS}
+        d["reuse_hist"] = list(s.reuse_hist)
+        return d
+
+    def timings(self):
+        ms = np.zeros(5, np.float32)
+        _check(self.lib.gc_last_timings(self.h, _p(ms)), "gc_last_timings")
+        return dict(zip(["residency", "pack", "interact", "scatter", "total"], ms.tolist()))
+
+    # ---- introspection ----------------------------------------------------------
+    def batch_sizes(self):
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(self.lib.gc_batch_sizes(self.h, C.byref(a), C.byref(b), C.byref(c)),
+               "gc_batch_sizes")
+        return a.value, b.value, c.value
+
+    def entry_slots(self):
+        _, nt, ns = self.batch_sizes()
+        t = np.empty(nt, np.uint32)
+        s = np.empty(ns, np.uint32)
+        _check(self.lib.gc_read_entry_slots(self.h, _p(t), _p(s)), "gc_read_entry_slots")
+        return t, s
+
+    def pack_perm(self):
+        _, nt, ns = self.batch_sizes()
+        t = np.empty(nt, np.uint32)
+        s = np.empty(ns, np.uint32)
+        _check(self.lib.gc_read_pack_perm(self.h, _p(t), _p(s)), "gc_read_pack_perm")
+        return t, s
+
+    def residency(self):
+        a = np.empty(self.cfg.id_capacity, np.uint32)
+        b = np.empty(self.cfg.pool_capacity, np.uint32)
+        c = np.empty(self.cfg.pool_capacity, np.uint32)
+        _check(self.lib.gc_read_residency(self.h, _p(a), _p(b), _p(c)), "gc_read_residency")
+        return a, b, c
+
+    def evicted(self):
+        n = C.c_uint64()
+        buf = np.empty(self.cfg.pool_capacity, np.uint32)
+        _check(self.lib.gc_read_evicted(self.h, _p(buf), buf.shape[0], C.byref(n)),
+               "gc_read_evicted")
+        return buf[:n.value].copy()
+
+    # ---- task builders ----------------------------------------------------------
+    def build_nbody(self, xyzm_t, bucket_max=32, theta_num=7, theta_den=10, task_id_base=0):
+        info = np.zeros(4, np.uint64)
+        _check(self.lib.gc_build_nbody_tasks(self.h, _dptr(xyzm_t), xyzm_t.shape[0], bucket_max,
+                                             theta_num, theta_den, task_id_base, _p(info)),
+               "gc_build_nbody_tasks")
+        return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]))
+
+    def nbody_tree(self, n, n_nodes, n_buckets, n_list):
+        out = dict(sorted_ids=np.empty(n, np.uint32), sorted_keys=np.empty(n, np.uint64),
+                   level=np.empty(n_nodes, np.uint8), cell=np.empty((n_nodes, 3), np.uint32),
+                   first=np.empty(n_nodes, np.uint32), count=np.empty(n_nodes, np.uint32),
+                   leaf=np.empty(n_nodes, np.uint8), size=np.empty(n_nodes, np.uint32),
+                   node_xyzm=np.empty((n_nodes, 4), np.float32),
+                   bucket_first=np.empty(n_buckets, np.uint32),
+                   bucket_count=np.empty(n_buckets, np.uint32),
+                   bucket_node=np.empty(n_buckets, np.uint32),
+                   list_off=np.empty(n_buckets + 1, np.uint64),
+                   list_ids=np.empty(n_list, np.uint32))
+        keys = ["sorted_ids", "sorted_keys", "level", "cell", "first", "count", "leaf", "size",
+                "node_xyzm", "bucket_first", "bucket_count", "bucket_node", "list_off",
+                "list_ids"]
+        _check(self.lib.gc_read_nbody_tree(self.h, *[_p(out[k]) for k in keys]),
+               "gc_read_nbody_tree")
+        return out
+
+    def build_md(self, cell_t, m, task_id_base=0):
+        info = np.zeros(4, np.uint64)
+        _check(self.lib.gc_build_md_tasks(self.h, _dptr(cell_t), cell_t.numel(), m, task_id_base,
+                                          _p(info)), "gc_build_md_tasks")
+        return dict(tasks=int(info[0]), tgt_entries=int(info[1]), src_entries=int(info[2]))
+
+    def md_cells(self, n, m):
+        start = np.empty(m ** 3 + 1, np.uint32)
+        atoms = np.empty(n, np.uint32)
+        _check(self.lib.gc_read_md_cells(self.h, _p(start), _p(atoms)), "gc_read_md_cells")
+        return start, atoms
+
+
+def value(res):
+    """FP64 value s - c of result rows (rows, 8) -> (rows, 4)."""
+    return res[:, :4].astype(np.float64) - res[:, 4:].astype(np.float64)

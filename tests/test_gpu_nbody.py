@@ -1,0 +1,147 @@
+"""GPU parity of the N-body path (Section 4.1 buckets and Barnes-Hut
+interaction lists) against the FP64 oracle: tree, buckets, lists and the
+chare-table / pack integers bit-exact; forces within 1e-5 relative L2 per
+task."""
+import numpy as np
+import pytest
+
+from paper_2008_05712_gb300 import inputs
+from gpu_util import EPS2, TOL, make_pool, per_task_errors, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_2008_05712_gb300 import gcharm
+    gcharm.load()
+    return gcharm
+
+
+def build_and_flush(gc, x, theta=(7, 10), bucket=32, per_task=False):
+    n = x.shape[0]
+    pool = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    xd = torch.from_numpy(x).cuda()
+    info = pool.build_nbody(xd, bucket, theta[0], theta[1])
+    tree = pool.nbody_tree(n, info["n_nodes"], info["n_buckets"], info["list_entries"])
+    if per_task:
+        pool.flush_per_task()
+    else:
+        pool.flush()
+    pool.wait(0)
+    return pool, info, tree
+
+
+@pytest.mark.parametrize("n,theta,bucket", [(4096, (7, 10), 32), (3000, (0, 1), 32),
+                                            (5000, (255, 1), 16), (33, (7, 10), 32),
+                                            (1, (7, 10), 32)])
+def test_tree_and_lists_bit_exact(gc, orc, n, theta, bucket):
+    x = inputs.plummer(n, inputs.SEED_BASE + 1)
+    pool, info, g = build_and_flush(gc, x, theta, bucket)
+    tr = orc.Tree(x, bucket_max=bucket)
+    assert info["n_nodes"] == tr.n_nodes and info["n_buckets"] == tr.n_buckets
+    assert np.array_equal(g["sorted_ids"], tr.sorted_ids)
+    assert np.array_equal(g["sorted_keys"], tr.sorted_keys)
+    for k in ["level", "first", "count", "leaf", "size"]:
+        assert np.array_equal(g[k], getattr(tr, k)), k
+    assert np.array_equal(g["cell"], tr.cell)
+    assert np.array_equal(g["bucket_first"], tr.bucket_first)
+    assert np.array_equal(g["bucket_count"], tr.bucket_count)
+    assert np.array_equal(g["bucket_node"], tr.bucket_node)
+    off, ids = tr.lists(*theta)
+    assert np.array_equal(g["list_off"], off)
+    assert np.array_equal(g["list_ids"], ids)
+    # node values: FP64 monopoles rounded to float32 (independent sums)
+    np.testing.assert_allclose(g["node_xyzm"], tr.node_table(), rtol=2e-7, atol=1e-12)
+    pool.close()
+
+
+@pytest.mark.parametrize("n", [4096, 20000])
+def test_forces_vs_oracle(gc, orc, n):
+    x = inputs.plummer(n, inputs.SEED_BASE + 1)
+    pool, info, g = build_and_flush(gc, x)
+    tr = orc.Tree(x)
+    tab = np.concatenate([x, tr.node_table()])
+    to, tg = tr.bucket_targets()
+    lo, li = tr.lists(7, 10)
+    ref = orc.gravity_batch(tab, to, tg, lo, li, EPS2)
+    got = gc.value(pool.results())
+    errs = per_task_errors(got, ref, to)
+    assert errs.max() <= TOL, (errs.max(), np.argmax(errs))
+    # per-id FP64 totals: each particle is the target of exactly one bucket
+    tot = pool.totals(tg)
+    assert rel_l2(tot[:, :3], ref[:, :3]) <= TOL
+    per = np.linalg.norm(tot[:, :3] - ref[:, :3], axis=1) / np.linalg.norm(ref[:, :3], axis=1)
+    assert np.percentile(per, 99) <= TOL
+    pool.close()
+
+
+def test_residency_and_pack_bit_exact(gc, orc):
+    n = 4096
+    x = inputs.plummer(n, inputs.SEED_BASE + 1)
+    pool, info, g = build_and_flush(gc, x)
+    id_cap = pool.cfg.id_capacity
+    cap = pool.cfg.pool_capacity
+    # the oracle's chare table sees the upload, then this batch's entries
+    tr = orc.Tree(x)
+    to, tg = tr.bucket_targets()
+    lo, li = tr.lists(7, 10)
+    R = orc.Residency(id_cap, cap)
+    rc, r = R.flush(np.concatenate([tg, li]), epoch=1)
+    assert rc == 0
+    st, ss = pool.entry_slots()
+    assert np.array_equal(st, r["slots"][:len(tg)])
+    assert np.array_equal(ss, r["slots"][len(tg):])
+    s2o, o2s, lu = pool.residency()
+    assert np.array_equal(s2o, R.slot_of_id)
+    assert np.array_equal(o2s, R.id_of_slot)
+    pt, ps = pool.pack_perm()
+    assert np.array_equal(pt, orc.pack_perm_batch(to, st))
+    assert np.array_equal(ps, orc.pack_perm_batch(lo, ss))
+    s = pool.stats()
+    assert s["last_unique"] == r["unique"] and s["last_misses"] == r["misses"]
+    assert s["last_hits"] == 0
+    pool.close()
+
+
+def test_per_task_launches_match_batched(gc):
+    x = inputs.plummer(3000, 5)
+    p1, _, _ = build_and_flush(gc, x)
+    a = p1.results()
+    p1.close()
+    p2, _, _ = build_and_flush(gc, x, per_task=True)
+    b = p2.results()
+    p2.close()
+    assert np.array_equal(a, b)
+
+
+def test_drift_step_reuses_slots(gc, orc):
+    # a second step after a small drift: particles are updated in place
+    # (hits), node ids whose value changed are updates too
+    n = 6000
+    x0 = inputs.plummer(n, 21)
+    pool = make_pool(gc, torch, 3 * n, 3 * n)
+    ids = np.arange(n, dtype=np.uint32)
+    pool.upload(ids, x0)
+    pool.build_nbody(torch.from_numpy(x0).cuda())
+    pool.flush()
+    s0 = pool.stats()
+    x1 = inputs.drift(x0, 22)
+    pool.upload_device(torch.from_numpy(ids).cuda(), torch.from_numpy(x1).cuda())
+    pool.reset_totals()
+    pool.build_nbody(torch.from_numpy(x1).cuda())
+    pool.flush()
+    pool.wait(1)
+    s1 = pool.stats()
+    assert s1["last_hits"] > 0.9 * s1["last_unique"]
+    assert s1["updates"] - s0["updates"] >= n
+    tr = orc.Tree(x1)
+    tab = np.concatenate([x1, tr.node_table()])
+    to, tg = tr.bucket_targets()
+    lo, li = tr.lists(7, 10)
+    ref = orc.gravity_batch(tab, to, tg, lo, li, EPS2)
+    errs = per_task_errors(gc.value(pool.results()), ref, to)
+    assert errs.max() <= TOL
+    pool.close()
