@@ -1,0 +1,363 @@
+"""Benchmark: pair interactions/s of the batched G-Charm hot path on GB300.
+
+Workload (one "step"): N-body at scale -- 1,048,576 Plummer-sphere particles
+(float4 xyzm, FP32), softening 0.01, buckets <= 32, opening angle 0.7.  Each
+step drifts every particle by N(0, 1e-3) per axis (positions pre-generated
+and resident in HBM before timing), uploads them in place into the pool,
+rebuilds the octree and interaction lists on the GPU, and runs one batched
+flush: chare-table residency, sorted pack, persistent interaction kernel,
+FP64 per-id scatter.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun with N > 1, every rank runs an independent replica problem
+(its own seed) on its own GPU; there is no data-path collective.  Rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2008_05712_gb300 import inputs  # noqa: E402
+
+N_PART = 1 << 20
+THETA = (7, 10)
+BUCKET = 32
+EPS2 = float(np.float32(1e-4))
+METRIC = "pair interactions/sec, batched vs per-task launch on 1 GB300; p50/p99 task latency"
+WORKLOAD = ("nbody_plummer_1M: 1,048,576 Plummer particles, theta=0.7, buckets<=32, "
+            "eps=0.01, drift N(0,1e-3) + rebuild + batched flush per step")
+# FP32 flops of one gravity interaction in the plain formula (no compensation):
+# 3 sub, 3 FMA for r^2 + eps^2, 3 mul, 3 FMA accumulate, 1 add for phi.
+FLOPS_PER_INTERACTION = 19
+SM_COUNT = 152
+FP32_LANES = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(sm_mhz):
+    return SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
+                   samples=len(rows))
+        return out
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(x, n_tasks, seed, budget_s=None):
+    """Oracle (plain FP64 C, one thread) on a seeded sample of this step's
+    tasks: tree build, interaction-list walk and gravity of the sampled
+    buckets.  Returns (interactions, seconds of per-task work, n_tasks)."""
+    from oracle import oracle as O
+    tr = O.Tree(x, bucket_max=BUCKET)
+    g = inputs.rng(seed)
+    pick = np.sort(g.choice(tr.n_buckets, size=min(n_tasks, tr.n_buckets), replace=False))
+    t0 = time.perf_counter()
+    off, ids = tr.lists(THETA[0], THETA[1], buckets=pick)
+    to, tg = tr.bucket_targets(pick)
+    tab = np.concatenate([x, tr.node_table()])
+    O.gravity_batch(tab, to, tg, off, ids, EPS2)
+    dt = time.perf_counter() - t0
+    inter = int(np.sum(np.diff(to.astype(np.int64)) * np.diff(off.astype(np.int64))))
+    return inter, dt, len(pick)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    x = inputs.plummer(N_PART, inputs.SEED_BASE + 2)
+    per_step = 600
+    for k in range(args.warmup):
+        oracle_sample(x, 50, 100 + k)
+    tot_i, tot_t = 0, 0.0
+    for k in range(args.steps):
+        i, t, _ = oracle_sample(x, per_step, 1000 + k)
+        tot_i += i
+        tot_t += t
+    v = tot_i / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "interactions/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{per_step} seeded-random buckets per step"},
+        "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} random buckets of the 1M-particle step per "
+                                   "step (walk + FP64 gravity; tree build untimed)"},
+        "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-task", action="store_true")
+    ap.add_argument("--n", type=int, default=N_PART)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2008_05712_gb300 import gcharm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gcharm.load()
+    n = args.n
+    K, W = args.steps, max(args.warmup, 3)
+    seed = inputs.SEED_BASE + 2 + 1000 * rank
+
+    # pre-generate all steps' positions (a drift walk), resident in HBM
+    xs = [inputs.plummer(n, seed)]
+    for k in range(K + W + 1):
+        xs.append(inputs.drift(xs[-1], seed + 1 + k))
+    X = torch.from_numpy(np.stack(xs[1:])).cuda()        # (K+W+1, n, 4)
+    ids_np = np.arange(n, dtype=np.uint32)
+    ids_d = torch.from_numpy(ids_np).cuda()
+    stream = torch.cuda.Stream()
+    id_cap = 2 * n + 1024
+    pool = gcharm.Pool(id_capacity=id_cap, pool_capacity=id_cap, eps2=EPS2,
+                       stream=stream.cuda_stream)
+    pool.upload(ids_np, xs[0])
+    torch.cuda.synchronize()
+
+    def step(k):
+        pool.upload_device(ids_d, X[k])
+        pool.reset_totals()
+        pool.build_nbody(X[k], BUCKET, *THETA)
+        pool.flush()
+
+    for k in range(W):
+        step(k)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    s0 = pool.stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    inter_ms, inter_n = [], []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(W, W + K):
+        before = pool.stats()["interactions"]
+        step(k)
+        t = pool.timings()                 # stage times of this flush (events)
+        inter_ms.append(t["interact"])
+        inter_n.append(pool.stats()["interactions"] - before)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    s1 = pool.stats()
+    interactions = s1["interactions"] - s0["interactions"]
+    launches = s1["kernel_launches"] - s0["kernel_launches"]
+    prims = s1["primitive_calls"] - s0["primitive_calls"]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        c = torch.tensor([float(interactions)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        interactions_all = int(c.item())
+    else:
+        interactions_all = interactions
+    value = interactions_all / (ms / 1e3)
+    last_timing = pool.timings()
+    hits, uniq = s1["last_hits"], s1["last_unique"]
+
+    # roofline of the dominant kernel (the interaction kernel)
+    avg_int_ms = float(np.mean(inter_ms))
+    avg_int_n = float(np.mean(inter_n))
+    achieved = FLOPS_PER_INTERACTION * avg_int_n / (avg_int_ms / 1e3) / 1e12
+    pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_max)
+
+    # end-to-end through the C ABI with host buffers (pinned), copies timed
+    pinned = torch.empty((K, n, 4), dtype=torch.float32, pin_memory=True)
+    pinned.copy_(X[W:W + K].cpu())
+    hx = pinned.numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        pool.upload(ids_np, hx[k])               # ids + values H2D
+        pool.reset_totals()
+        pool.build_nbody(hx[k], BUCKET, *THETA)  # values H2D again
+        pool.flush()
+        tot = pool.totals(ids_np)                # ids H2D, totals D2H
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": interactions / K * K / e2e_s if K else 0.0, "unit": "interactions/s",
+           "h2d_bytes_per_step": int(n * (4 + 16 + 16 + 4)),
+           "d2h_bytes_per_step": int(tot.nbytes)}
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e["value"] = interactions_all / float(t.item())
+
+    # the same step with one interaction launch per task (no combining)
+    per_task = None
+    if not args.no_per_task:
+        step_k = W + K
+        pool.upload_device(ids_d, X[step_k])
+        pool.reset_totals()
+        pool.build_nbody(X[step_k], BUCKET, *THETA)
+        i0 = pool.stats()["interactions"]
+        pool.flush_per_task()
+        torch.cuda.synchronize()
+        tp = pool.timings()
+        pn = pool.stats()["interactions"] - i0
+        pool.upload_device(ids_d, X[step_k])
+        pool.reset_totals()
+        pool.build_nbody(X[step_k], BUCKET, *THETA)
+        pool.flush()
+        torch.cuda.synchronize()
+        tb = pool.timings()
+        per_task = {
+            "interact_ms_per_task_launch": tp["interact"],
+            "interact_ms_batched": tb["interact"],
+            "interactions": pn,
+            "value_per_task_launch": pn / (tp["interact"] / 1e3),
+            "value_batched": pn / (tb["interact"] / 1e3),
+            "speedup_interaction_stage": tp["interact"] / tb["interact"],
+            "flush_ms_per_task_launch": tp["total"],
+            "flush_ms_batched": tb["total"],
+            "speedup_flush": tp["total"] / tb["total"],
+        }
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ci, ct, cn = oracle_sample(xs[W], 60000, 77)
+        cpu = {"value": ci / ct, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cn} seeded-random buckets of the first timed step "
+                         f"({ci} interactions): oracle walk + FP64 gravity, one thread; "
+                         "tree build untimed"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": ws,
+            "steps": K, "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": n, "tasks_per_step": None,
+                       "l2": "inputs larger than L2 (staging ~4 GB per step)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_gravity",
+                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x "
+                                       f"{sm_max:.0f} MHz (fallback derivation, no FP32 "
+                                       "figure measured)",
+                         "flops_per_interaction": FLOPS_PER_INTERACTION},
+            "stage_ms_last_step": last_timing,
+            "reuse": {"last_hits": hits, "last_unique": uniq},
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "primitive_calls": prims,
+            "per_task_launch": per_task,
+            "cpu_baseline": cpu,
+        }
+        line["config"]["tasks_per_step"] = int(s1["tasks"] - s0["tasks"]) // max(K, 1)
+        print(json.dumps(line), flush=True)
+    pool.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,9 @@ typedef struct {
     uint64_t reuse_hist[8];       /* last flush: distinct ids referenced
                                      1, 2, 3-4, 5-8, 9-16, 17-32, 33-64,
                                      >64 times                             */
+    uint64_t kernel_launches;     /* kernels of this library launched      */
+    uint64_t primitive_calls;     /* device-wide sort/scan calls (CUB), each
+                                     a few launches of its own              */
 } gc_stats_t;
 
 /* ---- pool lifetime and data -------------------------------------------- */
@@ -246,8 +249,8 @@ int gc_read_evicted(gc_pool_t *pool, uint32_t *ids, uint64_t cap, uint64_t *n_ou
 /* ---- task builders on the device --------------------------------------- */
 
 /* N-body tasks (Section 4.1): build the Barnes-Hut octree of the n
- * particles xyzm_dev (device, 4 floats per particle; particle p has data id
- * p) and append one GC_GRAVITY task per bucket to the pending batch:
+ * particles xyzm (4 floats per particle, a device or a host pointer -- host
+ * data is first copied to the device; particle p has data id p) and append one GC_GRAVITY task per bucket to the pending batch:
  * targets = the bucket's particles in Morton order, sources = its
  * interaction list.  Tree: 21-bit grid per axis over the bounding cube
  * (power-of-two edge), Morton keys with x in bit 0, stable sort by key;
@@ -279,7 +282,7 @@ int gc_read_nbody_tree(gc_pool_t *pool, uint32_t *sorted_ids, uint64_t *sorted_k
                        uint64_t *list_off, uint32_t *list_ids);
 
 /* MD tasks (Section 4.2): group the n atoms by cell (cell_dev: linear cell
- * index x + m (y + m z) per atom, device) into an m^3 periodic grid, atoms
+ * index x + m (y + m z) per atom, a device or a host pointer) into an m^3 periodic grid, atoms
  * of a cell in ascending atom id (atom a has data id a), and append, for
  * every cell in ascending index, its GC_LJ_SELF task and one GC_LJ_PAIR
  * task per neighbour offset (dx, dy, dz) lexicographically above (0,0,0)

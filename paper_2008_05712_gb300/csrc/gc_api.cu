@@ -69,6 +69,25 @@ static int grow_keep(DBuf &b, size_t bytes, size_t used, cudaStream_t s)
     return GC_OK;
 }
 
+const void *gc_device_view(gc_pool *p, const void *ptr, size_t bytes, DBuf &buf, int *rc)
+{
+    *rc = GC_OK;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return ptr;
+    if ((*rc = buf.reserve(bytes)) != GC_OK) return nullptr;
+    if (cudaMemcpyAsync(buf.p, ptr, bytes, cudaMemcpyHostToDevice, p->s) != cudaSuccess ||
+        cudaStreamSynchronize(p->s) != cudaSuccess) {
+        *rc = GC_ERR_CUDA;
+        return nullptr;
+    }
+    p->stats.h2d_bytes += bytes;
+    return buf.p;
+}
+
 int gc_reserve_batch(gc_pool *p, uint64_t add_tasks, uint64_t add_tgt, uint64_t add_src)
 {
     GC_TRY(grow_keep(p->tasks, (p->nb_tasks + add_tasks + 1) * sizeof(TaskRec),
@@ -115,7 +134,7 @@ void free_pool(gc_pool *p)
                     &p->nb.keys, &p->nb.keys2, &p->nb.ids, &p->nb.ids2, &p->nb.lcp, &p->nb.win,
                     &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a, &p->nb.node_b,
                     &p->nb.node_val, &p->nb.bucket, &p->nb.bbox, &p->nb.list_off,
-                    &p->nb.list_len, &p->nb.list, &p->nb.bounds, &p->nb.cub_tmp, &p->nb.mono, &p->md.keys,
+                    &p->nb.list_len, &p->nb.list, &p->nb.bounds, &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->md.hostcopy, &p->md.keys,
                     &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
                     &p->md.cnt_s, &p->md.cub_tmp};
     for (DBuf *b : bufs) b->release();
@@ -676,6 +695,7 @@ int gc_read_totals(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
     if (rc == GC_OK) {
         unsigned g = (unsigned)((n + 255) / 256);
         if (g > 65535u * 8) g = 65535u * 8;
+        ++p->stats.kernel_launches;
         k_gather_totals<<<g, 256, 0, p->s>>>(p->d_totals, di.as<uint32_t>(), n,
                                              p->cfg.id_capacity, dout.as<gcd4>());
         if (cudaMemcpyAsync(acc4, dout.p, n * sizeof(gcd4), cudaMemcpyDeviceToHost, p->s) !=

@@ -74,13 +74,13 @@ struct NBodyState {
     uint64_t n = 0, n_nodes = 0, n_buckets = 0, n_list = 0, max_list = 0;
     DBuf keys, keys2, ids, ids2, lcp, win, dmax, nnode, node_off;
     DBuf node_a, node_b, node_val, bucket, bbox, list_off, list_len, list;
-    DBuf bounds, cub_tmp, mono;
+    DBuf bounds, cub_tmp, mono, hostcopy;
 };
 
 struct MDState {
     uint64_t n = 0;
     int m = 0;
-    DBuf keys, keys2, ids, ids2, cell_start, cnt_t, cnt_s, cub_tmp;
+    DBuf keys, keys2, ids, ids2, cell_start, cnt_t, cnt_s, cub_tmp, hostcopy;
 };
 
 struct gc_pool {
@@ -194,4 +194,7 @@ int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev
                const uint32_t *arr, uint32_t *out, unsigned long long *count_out);
 
 // ---- builders --------------------------------------------------------------------
+// If ptr is host memory, copy bytes of it into buf (stream-ordered, then
+// synchronised) and return the device copy; device pointers pass through.
+const void *gc_device_view(gc_pool *p, const void *ptr, size_t bytes, DBuf &buf, int *rc);
 int gc_reserve_batch(gc_pool *p, uint64_t add_tasks, uint64_t add_tgt, uint64_t add_src);

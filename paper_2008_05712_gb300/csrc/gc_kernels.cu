@@ -533,6 +533,7 @@ int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
                       uint64_t task_id_base, TaskRec *out)
 {
     if (n_tasks == 0) return GC_OK;
+    ++p->stats.kernel_launches;
     k_task_recs<<<grid_for(n_tasks, 256, p->num_sms * 16), 256, 0, p->s>>>(
         n_tasks, task_ids, kinds, shifts, tgt_off, src_off, tgt_base, src_base, task_id_base,
         out, p->d_ctr);
@@ -557,10 +558,14 @@ int gc_prepare(gc_pool *p, TaskRec *tasks, uint64_t n, uint64_t info[5])
     GC_CUDA_TRY(cudaMemsetAsync(rows + n, 0, sizeof(uint64_t), p->s));
     GC_CUDA_TRY(cudaMemsetAsync(wu_g + n, 0, sizeof(uint32_t), p->s));
     GC_CUDA_TRY(cudaMemsetAsync(lj + n, 0, sizeof(uint32_t), p->s));
+    ++p->stats.kernel_launches;
     k_prep_counts<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(tasks, n, rows, wu_g, lj,
                                                                        p->d_ctr);
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(p->cub_tmp, rows, row_off, n + 1, p->s));
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u32(p->cub_tmp, wu_g, wu_off, n + 1, p->s));
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u32(p->cub_tmp, lj, lj_off, n + 1, p->s));
     // totals at index n
     uint64_t h_rows = 0;
@@ -573,6 +578,7 @@ int gc_prepare(gc_pool *p, TaskRec *tasks, uint64_t n, uint64_t info[5])
     GC_CUDA_TRY(cudaStreamSynchronize(p->s));
     GC_TRY(p->wu.reserve(((uint64_t)h_wu + 1) * sizeof(GravWU)));
     GC_TRY(p->small.reserve(((uint64_t)h_lj + 1) * sizeof(uint32_t)));
+    ++p->stats.kernel_launches;
     k_prep_fill<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
         tasks, n, row_off, wu_off, lj_off, p->wu.as<GravWU>(), p->small.as<uint32_t>());
     GC_CUDA_TRY(cudaGetLastError());
@@ -620,7 +626,9 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, uint64_t t0, uint64_t t1, uint64_t
     a.ma = p->merge_a.as<uint64_t>();
     a.mb = p->merge_b.as<uint64_t>();
     a.msrc = msrc;
+    ++p->stats.kernel_launches;
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, p->s>>>(a);
+    ++p->stats.kernel_launches;
     k_pack_large<<<grid_for(a.n_lists, 1, p->num_sms * 8), PACK_THREADS, 0, p->s>>>(a);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
@@ -678,6 +686,7 @@ int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
         GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), p->s));
         uint64_t need = (a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS;
         unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
+        ++p->stats.kernel_launches;
         k_gravity<<<g, GRAV_THREADS, 0, p->s>>>(a);
     }
     if (l1 > l0) {
@@ -688,6 +697,7 @@ int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
         GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), p->s));
         uint64_t need = (a.n_lj + GRAV_WARPS - 1) / GRAV_WARPS;
         unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
+        ++p->stats.kernel_launches;
         k_lj<<<g, GRAV_THREADS, 0, p->s>>>(a);
     }
     GC_CUDA_TRY(cudaGetLastError());
@@ -709,6 +719,7 @@ int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_i
         a.lj_list = nullptr;
         a.n_lj = 0;
         unsigned g = (unsigned)((a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS);
+        ++p->stats.kernel_launches;
         k_gravity<<<g, GRAV_THREADS, 0, p->s>>>(a);
     }
     if (l1 > l0) {
@@ -716,6 +727,7 @@ int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_i
         a.n_wu = 0;
         a.lj_list = p->small.as<uint32_t>() + l0;
         a.n_lj = l1 - l0;
+        ++p->stats.kernel_launches;
         k_lj<<<1, 32, 0, p->s>>>(a);
     }
     GC_CUDA_TRY(cudaGetLastError());
@@ -730,14 +742,17 @@ int gc_scatter(gc_pool *p, uint64_t n_rows)
     GC_TRY(p->row_sorted.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(p->runs.reserve((n_rows + 1) * sizeof(uint32_t)));
     const int maxb = p->num_sms * 16;
+    ++p->stats.kernel_launches;
     k_iota<<<grid_for(n_rows, 256, maxb), 256, 0, p->s>>>(p->rows_tmp.as<uint32_t>(), n_rows);
     int bits = 1;
     while (bits < 32 && ((uint64_t)1 << bits) < p->cfg.id_capacity) ++bits;
+    ++p->stats.primitive_calls;
     GC_TRY(gc_sort_pairs_u32(p->cub_tmp, p->row_id.as<uint32_t>(), p->rid_sorted.as<uint32_t>(),
                              p->rows_tmp.as<uint32_t>(), p->row_sorted.as<uint32_t>(), n_rows,
                              bits, p->s));
     GC_TRY(gc_compact(p, CK_RUN_START, n_rows, nullptr, p->rid_sorted.as<uint32_t>(),
                       p->runs.as<uint32_t>(), p->d_ctr + CTR_RUNS));
+    ++p->stats.kernel_launches;
     k_reduce_runs<<<grid_for(n_rows, 256, maxb), 256, 0, p->s>>>(
         p->runs.as<uint32_t>(), p->d_ctr + CTR_RUNS, n_rows, p->rid_sorted.as<uint32_t>(),
         p->row_sorted.as<uint32_t>(), p->res.as<float4>(), p->d_totals);

@@ -134,6 +134,10 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
     if (!p || !cell_dev || n == 0 || n > 0x7FFFFFFFull || m < 3 || m > 1024) return GC_ERR_ARG;
     if (n > p->cfg.id_capacity) return GC_ERR_POOL_FULL;
     MDState &S = p->md;
+    int vrc = GC_OK;
+    cell_dev = (const uint32_t *)gc_device_view(p, cell_dev, n * sizeof(uint32_t), S.hostcopy,
+                                                &vrc);
+    if (vrc != GC_OK) return vrc;
     cudaStream_t s = p->s;
     const uint32_t n_cells = (uint32_t)m * m * m;
     const uint64_t nt = 14ull * n_cells;
@@ -145,19 +149,25 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
     GC_TRY(S.cell_start.reserve(((uint64_t)n_cells + 1) * 4));
     GC_TRY(S.cnt_t.reserve((nt + 1) * 8 * 2));
     GC_TRY(S.cnt_s.reserve((nt + 1) * 8 * 2));
+    ++p->stats.kernel_launches;
     k_cell_keys<<<grid_for(n, 256, maxb), 256, 0, s>>>(cell_dev, n, n_cells, S.keys.as<uint32_t>(),
                                                        S.ids.as<uint32_t>(), p->d_ctr);
     int bits = 1;
     while (bits < 32 && (1ull << bits) < n_cells) ++bits;
+    ++p->stats.primitive_calls;
     GC_TRY(gc_sort_pairs_u32(S.cub_tmp, S.keys.as<uint32_t>(), S.keys2.as<uint32_t>(),
                              S.ids.as<uint32_t>(), S.ids2.as<uint32_t>(), n, bits, s));
     uint32_t *start = S.cell_start.as<uint32_t>();
+    ++p->stats.kernel_launches;
     k_cell_start<<<grid_for(n + 1, 256, maxb), 256, 0, s>>>(S.keys2.as<uint32_t>(), n, n_cells,
                                                             start);
     uint64_t *ct = S.cnt_t.as<uint64_t>(), *ot = ct + (nt + 1);
     uint64_t *cs = S.cnt_s.as<uint64_t>(), *os = cs + (nt + 1);
+    ++p->stats.kernel_launches;
     k_md_counts<<<grid_for(nt + 1, 256, maxb), 256, 0, s>>>(nt, m, start, ct, cs);
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, ct, ot, nt + 1, s));
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, cs, os, nt + 1, s));
     uint64_t tot_t = 0, tot_s = 0;
     unsigned long long flags = 0;
@@ -170,6 +180,7 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
         return GC_ERR_ARG;
     }
     GC_TRY(gc_reserve_batch(p, nt, tot_t, tot_s));
+    ++p->stats.kernel_launches;
     k_md_fill<<<grid_for(nt, 256, maxb), 256, 0, s>>>(
         nt, m, start, S.ids2.as<uint32_t>(), ot, os, p->nb_tgt, p->nb_src, task_id_base,
         p->tgt_ids.as<uint32_t>() + p->nb_tgt, p->src_ids.as<uint32_t>() + p->nb_src,

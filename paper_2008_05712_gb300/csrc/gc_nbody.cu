@@ -365,6 +365,9 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     if (((uintptr_t)xyzm_dev) % 16) return GC_ERR_ARG;
     if (n >= p->cfg.id_capacity) return GC_ERR_POOL_FULL;
     NBodyState &S = p->nb;
+    int vrc = GC_OK;
+    xyzm_dev = (const float *)gc_device_view(p, xyzm_dev, n * sizeof(float4), S.hostcopy, &vrc);
+    if (vrc != GC_OK) return vrc;
     cudaStream_t s = p->s;
     const int B = bucket_max;
     const int maxb = p->num_sms * 16;
@@ -385,18 +388,25 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     GridParams *gp = (GridParams *)(S.bounds.as<char>() + 64);
     uint32_t init[6] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0, 0, 0};
     GC_CUDA_TRY(cudaMemcpyAsync(bounds, init, sizeof init, cudaMemcpyHostToDevice, s));
+    ++p->stats.kernel_launches;
     k_bbox<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, bounds);
+    ++p->stats.kernel_launches;
     k_grid_params<<<1, 1, 0, s>>>(bounds, gp);
+    ++p->stats.kernel_launches;
     k_keys<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, gp, S.keys.as<uint64_t>(),
                                                   S.ids.as<uint32_t>());
+    ++p->stats.primitive_calls;
     GC_TRY(gc_sort_pairs_u64(S.cub_tmp, S.keys.as<uint64_t>(), S.keys2.as<uint64_t>(),
                              S.ids.as<uint32_t>(), S.ids2.as<uint32_t>(), n, 63, s));
     const uint64_t *K = S.keys2.as<uint64_t>();
     const uint32_t *sid = S.ids2.as<uint32_t>();
+    ++p->stats.kernel_launches;
     k_lcp_win<<<grid_for(n, 256, maxb), 256, 0, s>>>(K, n, B, S.lcp.as<int8_t>(),
                                                      S.win.as<int8_t>());
+    ++p->stats.kernel_launches;
     k_dmax<<<grid_for(n, 256, maxb), 256, 0, s>>>(S.lcp.as<int8_t>(), S.win.as<int8_t>(), n, B,
                                                   S.dmax.as<int8_t>(), S.nnode.as<uint32_t>());
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u32(S.cub_tmp, S.nnode.as<uint32_t>(), S.node_off.as<uint32_t>(),
                                  n + 1, s));
     uint32_t NN = 0;
@@ -411,11 +421,13 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     uint32_t *bcnt = S.list_len.as<uint32_t>();
     uint32_t *boff = bcnt + (NN + 1);
     GC_CUDA_TRY(cudaMemsetAsync(bcnt + NN, 0, 4, s));
+    ++p->stats.kernel_launches;
     k_emit_nodes<<<grid_for(n, 256, maxb), 256, 0, s>>>(
         K, n, S.lcp.as<int8_t>(), S.dmax.as<int8_t>(), S.node_off.as<uint32_t>(),
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), bcnt, B);
     GC_TRY(S.mono.reserve((n + 1) * sizeof(M4) * 2));
     M4 *mono_in = S.mono.as<M4>(), *mono_pre = mono_in + (n + 1);
+    ++p->stats.kernel_launches;
     k_mono_input<<<grid_for(n + 1, 256, maxb), 256, 0, s>>>(sid, x, n, mono_in);
     {
         size_t bytes = 0;
@@ -424,13 +436,16 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
             return GC_ERR_CUDA;
         GC_TRY(S.cub_tmp.reserve(bytes + 16));
         size_t have = S.cub_tmp.cap;
+        ++p->stats.primitive_calls;
         if (cub::DeviceScan::ExclusiveScan(S.cub_tmp.p, have, mono_in, mono_pre, M4Add(),
                                            M4{0, 0, 0, 0}, (int64_t)(n + 1), s) != cudaSuccess)
             return GC_ERR_CUDA;
     }
+    ++p->stats.kernel_launches;
     k_mono_nodes<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, mono_pre,
                                                          S.node_val.as<float4>());
     GC_TRY(gc_launch_upload_seq(p, (uint32_t)n, S.node_val.as<float4>(), NN));
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u32(S.cub_tmp, bcnt, boff, (uint64_t)NN + 1, s));
     uint32_t NB = 0;
     GC_CUDA_TRY(cudaMemcpyAsync(&NB, boff + NN, 4, cudaMemcpyDeviceToHost, s));
@@ -439,6 +454,7 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     GC_TRY(S.bucket.reserve((uint64_t)NB * 16 + 16));
     GC_TRY(S.bbox.reserve((uint64_t)NB * 32 + 32));
     int4 *blo = S.bbox.as<int4>(), *bhi = blo + NB;
+    ++p->stats.kernel_launches;
     k_emit_buckets<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, boff, K, B,
                                                            S.bucket.as<uint4>(), blo, bhi);
     GC_TRY(S.list_off.reserve(((uint64_t)NB + 1) * 8 * 2));
@@ -447,11 +463,14 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     uint64_t *llen64 = S.list_off.as<uint64_t>();
     uint64_t *loff = llen64 + (NB + 1);
     const int64_t tn2 = (int64_t)theta_num * theta_num, td2 = (int64_t)theta_den * theta_den;
+    ++p->stats.kernel_launches;
     k_walk<false><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
         (uint32_t)n, tn2, td2, llen, nullptr, nullptr);
     GC_CUDA_TRY(cudaMemsetAsync(llen + NB, 0, 4, s));
+    ++p->stats.kernel_launches;
     k_u32_to_u64<<<grid_for(NB + 1, 256, maxb), 256, 0, s>>>(llen, llen64, (uint64_t)NB + 1);
+    ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, llen64, loff, (uint64_t)NB + 1, s));
     uint64_t NL = 0;
     uint32_t maxlen = 0;
@@ -463,10 +482,12 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     uint32_t *dt = p->tgt_ids.as<uint32_t>() + p->nb_tgt;
     uint32_t *ds = p->src_ids.as<uint32_t>() + p->nb_src;
     TaskRec *recs = p->tasks.as<TaskRec>() + p->nb_tasks;
+    ++p->stats.kernel_launches;
     k_walk<true><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
         (uint32_t)n, tn2, td2, nullptr, loff, ds);
     GC_CUDA_TRY(cudaMemcpyAsync(dt, sid, n * 4, cudaMemcpyDeviceToDevice, s));
+    ++p->stats.kernel_launches;
     k_nbody_tasks<<<grid_for(NB, 256, maxb), 256, 0, s>>>(S.bucket.as<uint4>(), NB, loff, llen,
                                                           p->nb_tgt, p->nb_src, task_id_base,
                                                           recs);

@@ -305,8 +305,11 @@ int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev
     a.slot_of_id = p->d_slot_of_id;
     a.id_of_slot = p->d_id_of_slot;
     a.epoch = p->epoch;
+    ++p->stats.kernel_launches;
     k_compact_count<<<(unsigned)n_tiles, CT_THREADS, 0, p->s>>>(a, p->tiles.as<uint32_t>());
+    ++p->stats.kernel_launches;
     k_compact_scan<<<1, CT_THREADS, 0, p->s>>>(p->tiles.as<uint32_t>(), n_tiles, count_out);
+    ++p->stats.kernel_launches;
     k_compact_write<<<(unsigned)n_tiles, CT_THREADS, 0, p->s>>>(a, p->tiles.as<uint32_t>(), out);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
@@ -316,6 +319,7 @@ int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64
                      int write_mirror)
 {
     if (n == 0) return GC_OK;
+    ++p->stats.kernel_launches;
     k_upload<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
         ids, 0, vals, n, p->cfg.id_capacity, p->d_slot_of_id, p->d_pool, p->d_mirror,
         p->d_known, write_mirror, p->d_ctr);
@@ -328,6 +332,7 @@ int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64
 int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint64_t n)
 {
     if (n == 0) return GC_OK;
+    ++p->stats.kernel_launches;
     k_upload<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
         nullptr, id_base, vals, n, p->cfg.id_capacity, p->d_slot_of_id, p->d_pool,
         p->d_mirror, p->d_known, 1, p->d_ctr);
@@ -347,16 +352,19 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
 
     GC_CUDA_TRY(cudaMemsetAsync(ctr + CTR_UNIQUE, 0,
                                 sizeof(unsigned long long) * (CTR_COUNT - CTR_UNIQUE), p->s));
-    if (n > 0)
+    if (n > 0) {
+        ++p->stats.kernel_launches;
         k_mark<<<grid_for(n, 256, maxb), 256, 0, p->s>>>(tgt, nt, src, ns, id_cap, p->d_known,
                                                          p->d_ref_epoch, p->d_ref_count,
                                                          p->epoch, ctr);
+    }
     uint64_t ubound = n < id_cap ? n : id_cap;
     GC_TRY(p->uniq.reserve((ubound + 1) * sizeof(uint32_t)));
     GC_TRY(p->miss.reserve((ubound + 1) * sizeof(uint32_t)));
     GC_TRY(p->freel.reserve((cap + 1) * sizeof(uint32_t)));
     GC_TRY(gc_compact(p, CK_REF_EPOCH, id_cap, nullptr, nullptr, p->uniq.as<uint32_t>(),
                       ctr + CTR_UNIQUE));
+    ++p->stats.kernel_launches;
     k_classify<<<grid_for(ubound, 256, maxb), 256, 0, p->s>>>(
         p->uniq.as<uint32_t>(), ctr + CTR_UNIQUE, p->d_slot_of_id, p->d_ref_count, ctr);
     GC_TRY(gc_compact(p, CK_MISS, ubound, (const uint64_t *)(ctr + CTR_UNIQUE),
@@ -384,11 +392,14 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         GC_TRY(p->ekeys.reserve(cap * sizeof(uint64_t)));
         GC_TRY(p->ekeys2.reserve(cap * sizeof(uint64_t)));
         GC_TRY(p->evicted.reserve(need * sizeof(uint32_t)));
+        ++p->stats.kernel_launches;
         k_evict_keys<<<grid_for(cap, 256, maxb), 256, 0, p->s>>>(
             cap, p->d_id_of_slot, p->d_ref_epoch, p->d_last_use, p->epoch,
             p->ekeys.as<uint64_t>());
+        ++p->stats.primitive_calls;
         GC_TRY(gc_sort_keys_u64(p->cub_tmp, p->ekeys.as<uint64_t>(), p->ekeys2.as<uint64_t>(),
                                 cap, p->s));
+        ++p->stats.kernel_launches;
         k_evict_apply<<<grid_for(need, 256, maxb), 256, 0, p->s>>>(
             p->ekeys2.as<uint64_t>(), need, p->d_id_of_slot, p->d_slot_of_id, p->d_pool,
             p->d_mirror, p->evicted.as<uint32_t>());
@@ -396,20 +407,28 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
                           ctr + CTR_FREE));
         p->n_evicted_last = need;
     }
-    if (M)
+    if (M) {
+        ++p->stats.kernel_launches;
         k_assign<<<grid_for(M, 256, maxb), 256, 0, p->s>>>(
             p->miss.as<uint32_t>(), M, p->freel.as<uint32_t>(), p->d_slot_of_id,
             p->d_id_of_slot, p->d_pool, p->d_mirror);
-    if (U)
+    }
+    if (U) {
+        ++p->stats.kernel_launches;
         k_touch<<<grid_for(U, 256, maxb), 256, 0, p->s>>>(p->uniq.as<uint32_t>(), U,
                                                           p->d_slot_of_id, p->d_last_use,
                                                           p->epoch);
-    if (nt)
+    }
+    if (nt) {
+        ++p->stats.kernel_launches;
         k_entry_slots<<<grid_for(nt, 256, maxb), 256, 0, p->s>>>(tgt, nt, p->d_slot_of_id,
                                                                  tgt_slot);
-    if (ns)
+    }
+    if (ns) {
+        ++p->stats.kernel_launches;
         k_entry_slots<<<grid_for(ns, 256, maxb), 256, 0, p->s>>>(src, ns, p->d_slot_of_id,
                                                                  src_slot);
+    }
     GC_CUDA_TRY(cudaGetLastError());
 
     gc_stats_t &st = p->stats;

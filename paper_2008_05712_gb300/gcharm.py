@@ -55,7 +55,8 @@ _STAT_FIELDS = ["flushes", "tasks", "entries", "unique", "hits", "misses", "upda
 
 
 class GcStats(C.Structure):
-    _fields_ = [(f, C.c_uint64) for f in _STAT_FIELDS] + [("reuse_hist", C.c_uint64 * 8)]
+    _fields_ = ([(f, C.c_uint64) for f in _STAT_FIELDS] + [("reuse_hist", C.c_uint64 * 8)]
+                + [("kernel_launches", C.c_uint64), ("primitive_calls", C.c_uint64)])
 
 
 class GcError(RuntimeError):
@@ -276,6 +277,8 @@ class Pool:
         _check(self.lib.gc_stats(self.h, C.byref(s)), "gc_stats")
         d = {f: getattr(s, f) for f in _STAT_FIELDS}
         d["reuse_hist"] = list(s.reuse_hist)
+        d["kernel_launches"] = s.kernel_launches
+        d["primitive_calls"] = s.primitive_calls
         return d
 
     def timings(self):
@@ -319,9 +322,15 @@ class Pool:
         return buf[:n.value].copy()
 
     # ---- task builders ----------------------------------------------------------
-    def build_nbody(self, xyzm_t, bucket_max=32, theta_num=7, theta_den=10, task_id_base=0):
+    def build_nbody(self, xyzm, bucket_max=32, theta_num=7, theta_den=10, task_id_base=0):
+        """xyzm: CUDA tensor (n, 4) or a host numpy float32 (n, 4) array."""
         info = np.zeros(4, np.uint64)
-        _check(self.lib.gc_build_nbody_tasks(self.h, _dptr(xyzm_t), xyzm_t.shape[0], bucket_max,
+        if isinstance(xyzm, np.ndarray):
+            xyzm = np.ascontiguousarray(xyzm, np.float32)
+            ptr = _p(xyzm)
+        else:
+            ptr = _dptr(xyzm)
+        _check(self.lib.gc_build_nbody_tasks(self.h, ptr, xyzm.shape[0], bucket_max,
                                              theta_num, theta_den, task_id_base, _p(info)),
                "gc_build_nbody_tasks")
         return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]))
@@ -344,10 +353,16 @@ class Pool:
                "gc_read_nbody_tree")
         return out
 
-    def build_md(self, cell_t, m, task_id_base=0):
+    def build_md(self, cell, m, task_id_base=0):
+        """cell: CUDA tensor or host numpy array of uint32/int32 cell indices."""
         info = np.zeros(4, np.uint64)
-        _check(self.lib.gc_build_md_tasks(self.h, _dptr(cell_t), cell_t.numel(), m, task_id_base,
-                                          _p(info)), "gc_build_md_tasks")
+        if isinstance(cell, np.ndarray):
+            cell = np.ascontiguousarray(cell, np.uint32)
+            ptr, n = _p(cell), cell.shape[0]
+        else:
+            ptr, n = _dptr(cell), cell.numel()
+        _check(self.lib.gc_build_md_tasks(self.h, ptr, n, m, task_id_base, _p(info)),
+               "gc_build_md_tasks")
         return dict(tasks=int(info[0]), tgt_entries=int(info[1]), src_entries=int(info[2]))
 
     def md_cells(self, n, m):
