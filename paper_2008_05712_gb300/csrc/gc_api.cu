@@ -14,14 +14,15 @@
 int gc_prepare(gc_pool *p, TaskRec *tasks, uint64_t n, uint64_t info[5]);
 int gc_read_wu_offsets(gc_pool *p, uint64_t n, std::vector<uint32_t> &wu_off,
                        std::vector<uint32_t> &lj_off);
-int gc_pack(gc_pool *p, const TaskRec *tasks, uint64_t t0, uint64_t t1, uint64_t tgt_base,
-            uint64_t src_base, uint64_t msrc);
+int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uint32_t *src_ids,
+            uint64_t t0, uint64_t t1, uint64_t tgt_base, uint64_t src_base, uint64_t msrc);
 int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
                       const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
-                      uint64_t l1, uint64_t tgt_base, uint64_t src_base);
+                      uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
 int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
                          const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
-                         uint64_t l1, uint64_t tgt_base, uint64_t src_base);
+                         uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
+int gc_entry_slots(gc_pool *p, const uint32_t *ids, uint64_t n, uint32_t *out);
 
 // ---- DBuf ---------------------------------------------------------------------
 int DBuf::reserve(size_t bytes)
@@ -126,7 +127,7 @@ void free_pool(gc_pool *p)
     if (p->h_mirror) cudaFreeHost(p->h_mirror);
     if (p->h_ctr) cudaFreeHost(p->h_ctr);
     DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->last_tasks_buf, &p->last_tgt_ids,
-                    &p->last_src_ids, &p->tgt_slot, &p->src_slot, &p->tgt_perm, &p->src_perm,
+                    &p->last_src_ids, &p->tgt_perm, &p->src_perm,
                     &p->stg_tgt, &p->stg_src, &p->uniq, &p->miss, &p->freel, &p->tiles,
                     &p->ekeys, &p->ekeys2, &p->evicted, &p->wu, &p->wu_cnt, &p->wu_off,
                     &p->rowcnt, &p->res, &p->row_id, &p->rid_sorted, &p->row_sorted,
@@ -476,8 +477,6 @@ static int flush_impl(gc_pool *p, int per_task)
     }
     const uint64_t R = info[0], W = info[1], L = info[2], inter = info[3], max_list = info[4];
 
-    GC_TRY(p->tgt_slot.reserve((NT + 1) * 4));
-    GC_TRY(p->src_slot.reserve((NS + 1) * 4));
     GC_TRY(p->tgt_perm.reserve((NT + 1) * 4));
     GC_TRY(p->src_perm.reserve((NS + 1) * 4));
     GC_TRY(p->res.reserve((R + 1) * 2 * sizeof(float4)));
@@ -516,10 +515,11 @@ static int flush_impl(gc_pool *p, int per_task)
     }
     if (need_offsets) GC_TRY(gc_read_wu_offsets(p, T, wu_off, lj_off));
 
+    // source staging holds one extra float4 per task (pad of odd gravity lists)
     uint64_t max_wt = 0, max_ws = 0;
     for (const Wave &w : waves) {
         if (w.tg1 - w.tg0 > max_wt) max_wt = w.tg1 - w.tg0;
-        if (w.s1 - w.s0 > max_ws) max_ws = w.s1 - w.s0;
+        if (w.s1 - w.s0 + (w.t1 - w.t0) > max_ws) max_ws = w.s1 - w.s0 + (w.t1 - w.t0);
     }
     GC_TRY(p->stg_tgt.reserve((max_wt + 1) * sizeof(float4)));
     GC_TRY(p->stg_src.reserve((max_ws + 1) * sizeof(float4)));
@@ -535,14 +535,13 @@ static int flush_impl(gc_pool *p, int per_task)
         const Wave &w = waves[k];
         cudaEvent_t e0 = p->ev_stage[0];
         if (k > 0) GC_CUDA_TRY(cudaEventRecord(e0, p->s));
-        rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0,
-                          p->tgt_slot.as<uint32_t>() + w.tg0, p->src_slot.as<uint32_t>() + w.s0);
+        rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0);
         if (rc != GC_OK) {
             drop_pending(p);
             return rc;
         }
         GC_CUDA_TRY(cudaEventRecord(p->ev_stage[1], p->s));
-        GC_TRY(gc_pack(p, tasks, w.t0, w.t1, w.tg0, w.s0, max_wt + 1));
+        GC_TRY(gc_pack(p, tasks, tgt_ids, src_ids, w.t0, w.t1, w.tg0, w.s0, max_wt + 1));
         GC_CUDA_TRY(cudaEventRecord(p->ev_stage[2], p->s));
         uint64_t w0 = 0, w1 = W, l0 = 0, l1 = L;
         if (need_offsets) {
@@ -550,12 +549,13 @@ static int flush_impl(gc_pool *p, int per_task)
             l0 = lj_off[w.t0]; l1 = lj_off[w.t1];
         }
         if (!per_task) {
-            GC_TRY(gc_interact_range(p, tasks, tgt_ids, src_ids, w0, w1, l0, l1, w.tg0, w.s0));
+            GC_TRY(gc_interact_range(p, tasks, tgt_ids, src_ids, w0, w1, l0, l1, w.tg0, w.s0,
+                                     w.t0));
         } else {
             for (uint64_t t = w.t0; t < w.t1; ++t)
                 GC_TRY(gc_interact_one_task(p, tasks, tgt_ids, src_ids, wu_off[t],
                                             wu_off[t + 1], lj_off[t], lj_off[t + 1], w.tg0,
-                                            w.s0));
+                                            w.s0, w.t0));
         }
         GC_CUDA_TRY(cudaEventRecord(p->ev_stage[3], p->s));
         if (waves.size() > 1) {
@@ -769,12 +769,23 @@ int gc_batch_sizes(gc_pool_t *p, uint64_t *n_tasks, uint64_t *n_tgt, uint64_t *n
 int gc_read_entry_slots(gc_pool_t *p, uint32_t *tgt_slots, uint32_t *src_slots)
 {
     if (!p || !p->have_last) return GC_ERR_STATE;
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
-    if (tgt_slots && p->last_tgt)
-        GC_CUDA_TRY(cudaMemcpy(tgt_slots, p->tgt_slot.p, p->last_tgt * 4, cudaMemcpyDeviceToHost));
-    if (src_slots && p->last_src)
-        GC_CUDA_TRY(cudaMemcpy(src_slots, p->src_slot.p, p->last_src * 4, cudaMemcpyDeviceToHost));
-    return GC_OK;
+    // looked up in the chare table now (the pack reads the table directly)
+    DBuf tmp;
+    GC_TRY(tmp.reserve((p->last_tgt + p->last_src + 1) * 4));
+    uint32_t *d = tmp.as<uint32_t>();
+    int rc = gc_entry_slots(p, p->last_tgt_ids.as<uint32_t>(), p->last_tgt, d);
+    if (rc == GC_OK)
+        rc = gc_entry_slots(p, p->last_src_ids.as<uint32_t>(), p->last_src, d + p->last_tgt);
+    if (rc == GC_OK && cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
+    if (rc == GC_OK && tgt_slots && p->last_tgt &&
+        cudaMemcpy(tgt_slots, d, p->last_tgt * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = GC_ERR_CUDA;
+    if (rc == GC_OK && src_slots && p->last_src &&
+        cudaMemcpy(src_slots, d + p->last_tgt, p->last_src * 4, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        rc = GC_ERR_CUDA;
+    tmp.release();
+    return rc;
 }
 
 int gc_read_pack_perm(gc_pool_t *p, uint32_t *tgt_perm, uint32_t *src_perm)

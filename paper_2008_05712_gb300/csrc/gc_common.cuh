@@ -64,10 +64,12 @@ struct DBuf {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
-// Work unit of the gravity kernel: one task and a block of <= 32 targets.
+// Work unit of the gravity kernel: one task and a block of <= 16 targets.
 struct GravWU {
     uint32_t task;
-    uint32_t t0;
+    uint32_t t0;     // first target (staged order)
+    uint32_t tn;     // targets in the block
+    uint32_t pad;
 };
 
 struct NBodyState {
@@ -118,7 +120,7 @@ struct gc_pool {
     DBuf last_tasks_buf, last_tgt_ids, last_src_ids;   // swapped with pending
 
     // per-flush work buffers
-    DBuf tgt_slot, src_slot, tgt_perm, src_perm, stg_tgt, stg_src;
+    DBuf tgt_perm, src_perm, stg_tgt, stg_src;
     DBuf uniq, miss, freel, tiles, ekeys, ekeys2, evicted;
     DBuf wu, wu_cnt, wu_off, rowcnt, res, row_id, rid_sorted, row_sorted, rows_tmp;
     DBuf runs, merge_a, merge_b, cub_tmp, small;
@@ -168,10 +170,11 @@ int gc_exclusive_scan_u32(DBuf &tmp, const uint32_t *in, uint32_t *out, uint64_t
                           cudaStream_t s);
 
 // ---- residency (gc_residency.cu) -----------------------------------------------
-// Runs the chare-table step for the entries tgt[0..nt) and src[0..ns); fills
-// tgt_slot / src_slot.  Returns GC_OK, GC_ERR_UNKNOWN_ID or GC_ERR_POOL_FULL.
+// Runs the chare-table step for the entries tgt[0..nt) and src[0..ns): after
+// it every referenced id is resident.  Returns GC_OK, GC_ERR_UNKNOWN_ID or
+// GC_ERR_POOL_FULL.
 int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
-                 uint64_t ns, uint32_t *tgt_slot, uint32_t *src_slot);
+                 uint64_t ns);
 int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64_t n,
                      int write_mirror);
 

@@ -60,7 +60,7 @@ __global__ void k_prep_counts(const TaskRec *tasks, uint64_t n, uint64_t *rows,
         TaskRec r = tasks[t];
         uint64_t rw = r.nt + (r.kind == GC_LJ_PAIR ? r.ns : 0u);
         rows[t] = rw;
-        wu_g[t] = (r.kind == GC_GRAVITY) ? (r.nt + 31u) / 32u : 0u;
+        wu_g[t] = (r.kind == GC_GRAVITY) ? (r.nt + 15u) / 16u : 0u;
         lj[t] = (r.kind != GC_GRAVITY) ? 1u : 0u;
         if (r.kind == GC_GRAVITY) inter += (unsigned long long)r.nt * r.ns;
         else if (r.kind == GC_LJ_PAIR) inter += (unsigned long long)r.nt * r.ns;
@@ -86,11 +86,16 @@ __global__ void k_prep_fill(TaskRec *tasks, uint64_t n, const uint64_t *row_off,
         TaskRec &r = tasks[t];
         r.row_off = row_off[t];
         if (r.kind == GC_GRAVITY) {
-            uint32_t nb = (r.nt + 31u) / 32u;
+            // blocks of at most 16 targets, sizes as equal as possible, so
+            // that a warp keeps >= 2 source lanes per target
+            uint32_t nb = (r.nt + 15u) / 16u;
+            uint32_t bs = nb ? (r.nt + nb - 1u) / nb : 0u;
             for (uint32_t b = 0; b < nb; ++b) {
                 GravWU w;
                 w.task = (uint32_t)t;
-                w.t0 = b * 32u;
+                w.t0 = b * bs;
+                w.tn = min(bs, r.nt - b * bs);
+                w.pad = 0;
                 wu[wu_off[t] + b] = w;
             }
         } else {
@@ -102,60 +107,100 @@ __global__ void k_prep_fill(TaskRec *tasks, uint64_t n, const uint64_t *row_off,
 // ---------------------------------------------------------------------------
 // pack: sort each list by (slot, position), gather into staging
 // ---------------------------------------------------------------------------
+//
+// Staging layouts (wave-local, float4 units):
+//   targets           : AoS, entry k of a list at (tgt_off - tgt_base) + k.
+//   gravity sources   : paired SoA, for the list of task t starting at
+//                       S_t = (src_off - src_base) + (t - task_base):
+//                       float4 S_t + 2q     = (x_2q, x_2q+1, y_2q, y_2q+1)
+//                       float4 S_t + 2q + 1 = (z_2q, z_2q+1, m_2q, m_2q+1)
+//                       an odd list is padded with a zero-mass source;
+//                       two sources then sit in register pairs ready for
+//                       the paired FP32 instructions of the kernel.
+//   LJ sources        : AoS at S_t + k.
+// The extra float4 per task keeps every padded segment inside its own range.
 
-constexpr int PACK_CAP = 4096;       // keys sorted in shared memory at once
-constexpr int PACK_THREADS = 256;
+constexpr int PK_CAP = 4096;          // entries sorted in shared memory at once
+constexpr int PK_THREADS = 256;
+constexpr int PK_WARPS = PK_THREADS / 32;
 
 struct PackArgs {
     const TaskRec *tasks;
     uint64_t t0, n_lists;
-    const uint32_t *slot_t, *slot_s;     // batch-global entry index
+    const uint32_t *tgt_ids, *src_ids;   // batch-global entry index
+    const uint32_t *slot_of_id;
     uint32_t *perm_t, *perm_s;           // batch-global entry index
-    float4 *stg_t, *stg_s;               // wave-local entry index
-    uint64_t tgt_base, src_base;
+    float4 *stg_t, *stg_s;               // wave-local staging
+    uint64_t tgt_base, src_base, task_base;
     const float4 *pool;
     uint64_t *ma, *mb;                   // merge scratch: targets at the wave-local
     uint64_t msrc;                       // target index, sources at msrc + local index
+    int passes;                          // radix passes of 8 bits over the slot
 };
 
-__device__ __forceinline__ void list_of(const PackArgs &a, uint64_t L, uint32_t &n,
-                                        uint64_t &off, bool &src)
+struct PackList {
+    uint32_t n;
+    uint64_t off;     // batch-global first entry
+    bool src;
+    bool paired;      // gravity source list
+    uint64_t stg;     // first staging float4 (wave-local)
+};
+
+__device__ __forceinline__ PackList list_of(const PackArgs &a, uint64_t L)
 {
-    const TaskRec *r = a.tasks + a.t0 + (L >> 1);
-    src = (L & 1) != 0;
-    n = src ? r->ns : r->nt;
-    off = src ? r->src_off : r->tgt_off;
+    const uint64_t t = a.t0 + (L >> 1);
+    const TaskRec *r = a.tasks + t;
+    PackList l;
+    l.src = (L & 1) != 0;
+    l.n = l.src ? r->ns : r->nt;
+    l.off = l.src ? r->src_off : r->tgt_off;
+    l.paired = l.src && r->kind == GC_GRAVITY;
+    l.stg = l.src ? (l.off - a.src_base) + (t - a.task_base) : l.off - a.tgt_base;
+    return l;
 }
 
-__device__ __forceinline__ void emit_sorted(const PackArgs &a, bool src, uint64_t off,
-                                            uint32_t k, uint64_t key)
+// write staged entry k (list position pos, pool slot) of list l
+__device__ __forceinline__ void emit(const PackArgs &a, const PackList &l, uint32_t k,
+                                     uint32_t slot, uint32_t pos)
 {
-    uint32_t pos = (uint32_t)(key & 0xFFFFFFFFu);
-    uint32_t slot = (uint32_t)(key >> 32);
-    if (src) {
-        a.perm_s[off + k] = pos;
-        a.stg_s[off - a.src_base + k] = a.pool[slot];
-    } else {
-        a.perm_t[off + k] = pos;
-        a.stg_t[off - a.tgt_base + k] = a.pool[slot];
+    float4 v = a.pool[slot];
+    if (!l.src) {
+        a.perm_t[l.off + k] = pos;
+        a.stg_t[l.stg + k] = v;
+        return;
+    }
+    a.perm_s[l.off + k] = pos;
+    if (!l.paired) {
+        a.stg_s[l.stg + k] = v;
+        return;
+    }
+    float *f = reinterpret_cast<float *>(a.stg_s + l.stg + 2 * (k >> 1));
+    const uint32_t h = k & 1u;
+    f[h] = v.x;
+    f[2 + h] = v.y;
+    f[4 + h] = v.z;
+    f[6 + h] = v.w;
+    if (h == 0 && k + 1 == l.n) {   // odd list: zero-mass pad source
+        f[1] = 0.f;
+        f[3] = 0.f;
+        f[5] = 0.f;
+        f[7] = 0.f;
     }
 }
 
-// Lists of at most 32 entries: one warp, bitonic sort in registers.
+// Lists of at most 32 entries: one warp, bitonic sort of (slot, pos) keys
+// in registers.
 __global__ void k_pack_small(PackArgs a)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t L = warp; L < a.n_lists; L += nwarps) {
-        uint32_t n;
-        uint64_t off;
-        bool src;
-        list_of(a, L, n, off, src);
-        if (n == 0 || n > 32) continue;
-        const uint32_t *slots = src ? a.slot_s : a.slot_t;
+        PackList l = list_of(a, L);
+        if (l.n == 0 || l.n > 32) continue;
+        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
         uint64_t key = ~0ull;
-        if ((uint32_t)lane < n) key = ((uint64_t)slots[off + lane] << 32) | (uint64_t)lane;
+        if ((uint32_t)lane < l.n) key = ((uint64_t)a.slot_of_id[ids[lane]] << 32) | (uint64_t)lane;
 #pragma unroll
         for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
@@ -168,101 +213,171 @@ __global__ void k_pack_small(PackArgs a)
                 key = (lower == up) ? lo : hi;
             }
         }
-        if ((uint32_t)lane < n) emit_sorted(a, src, off, lane, key);
+        if ((uint32_t)lane < l.n)
+            emit(a, l, lane, (uint32_t)(key >> 32), (uint32_t)(key & 0xFFFFFFFFu));
     }
 }
 
-__device__ void block_bitonic(uint64_t *s, int np)
+struct PackSmem {
+    uint32_t ka[PK_CAP], kb[PK_CAP];     // slots
+    uint16_t pa[PK_CAP], pb[PK_CAP];     // list positions (within a chunk)
+    uint32_t hist[256][PK_WARPS];        // per (digit, warp) counts, then offsets
+    uint32_t wsum[PK_WARPS];
+    int skip;
+};
+
+__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *wsum)
 {
-    for (int k = 2; k <= np; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int q = threadIdx.x; q < (np >> 1); q += blockDim.x) {
-                int i = 2 * j * (q / j) + (q % j);
-                int l = i + j;
-                uint64_t x = s[i], y = s[l];
-                bool up = (i & k) == 0;
-                if ((x > y) == up) {
-                    s[i] = y;
-                    s[l] = x;
-                }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int q = 0; q < w; ++q) before += wsum[q];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Stable LSD radix sort of n <= PK_CAP (slot, pos) entries held in ka/pa,
+// 8-bit digits, `passes` passes.  Warp w owns a contiguous range of the
+// items; inside a warp, 32 items at a time are ranked among equal digits
+// with __match_any_sync, so equal digits keep their order (warp by warp,
+// chunk by chunk, lane by lane).  Returns 0 if the result is in ka/pa, 1 if
+// in kb/pb.
+__device__ int block_radix_sort(PackSmem &sm, int n, int passes)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int per = (((n + PK_WARPS - 1) / PK_WARPS) + 31) & ~31;
+    const int b0 = min(n, w * per), b1 = min(n, b0 + per);
+    uint32_t *ka = sm.ka, *kb = sm.kb;
+    uint16_t *pa = sm.pa, *pb = sm.pb;
+    int flip = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int sh = 8 * pass;
+        for (int i = threadIdx.x; i < 256 * PK_WARPS; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
+        if (threadIdx.x == 0) sm.skip = 0;
+        __syncthreads();
+        for (int c = b0; c < b1; c += 32) {
+            const int k = c + lane;
+            const bool v = k < b1;
+            const uint32_t d = v ? ((ka[k] >> sh) & 255u) : 256u + (uint32_t)lane;
+            const uint32_t m = __match_any_sync(0xffffffffu, d);
+            if (v && (m & lt) == 0) sm.hist[d][w] += (uint32_t)__popc(m);
+        }
+        __syncthreads();
+        uint32_t s = 0;
+        for (int q = 0; q < PK_WARPS; ++q) s += sm.hist[threadIdx.x][q];
+        if (s == (uint32_t)n) sm.skip = 1;       // one digit value: pass is the identity
+        uint32_t run = block_excl_scan256(s, sm.wsum);
+        for (int q = 0; q < PK_WARPS; ++q) {
+            uint32_t c = sm.hist[threadIdx.x][q];
+            sm.hist[threadIdx.x][q] = run;
+            run += c;
+        }
+        __syncthreads();
+        if (sm.skip) continue;
+        for (int c = b0; c < b1; c += 32) {
+            const int k = c + lane;
+            const bool v = k < b1;
+            const uint32_t key = v ? ka[k] : 0u;
+            const uint32_t d = v ? ((key >> sh) & 255u) : 256u + (uint32_t)lane;
+            const uint32_t m = __match_any_sync(0xffffffffu, d);
+            if (v) {
+                const uint32_t dst = sm.hist[d][w] + (uint32_t)__popc(m & lt);
+                kb[dst] = key;
+                pb[dst] = pa[k];
+            }
+            __syncwarp();
+            if (v && (m & lt) == 0) sm.hist[d][w] += (uint32_t)__popc(m);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t *tk = ka; ka = kb; kb = tk;
+        uint16_t *tp = pa; pa = pb; pb = tp;
+        flip ^= 1;
+    }
+    return flip;
+}
+
+// Lists of more than 32 entries: one block.  Up to PK_CAP entries are
+// radix-sorted in shared memory; longer lists are sorted in chunks of PK_CAP
+// and merged pairwise in global scratch (keys (slot << 32 | pos) are
+// unique, so an element's output index is its rank in its own run plus its
+// rank in the other run).
+__global__ void __launch_bounds__(PK_THREADS) k_pack_large(PackArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PackSmem &sm = *reinterpret_cast<PackSmem *>(smem_raw);
+    for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
+        PackList l = list_of(a, L);
+        if (l.n <= 32) continue;
+        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
+        if (l.n <= (uint32_t)PK_CAP) {
+            for (int k = threadIdx.x; k < (int)l.n; k += blockDim.x) {
+                sm.ka[k] = a.slot_of_id[ids[k]];
+                sm.pa[k] = (uint16_t)k;
             }
             __syncthreads();
-        }
-    }
-}
-
-// Lists of more than 32 entries: one block.  Up to PACK_CAP entries are
-// sorted in shared memory; longer lists are sorted in chunks of PACK_CAP and
-// merged pairwise in global scratch (keys are unique, so each element's
-// output position is its rank in its own run plus its rank in the other).
-__global__ void __launch_bounds__(PACK_THREADS) k_pack_large(PackArgs a)
-{
-    __shared__ uint64_t sk[PACK_CAP];
-    for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
-        uint32_t n;
-        uint64_t off;
-        bool src;
-        list_of(a, L, n, off, src);
-        if (n <= 32) continue;
-        const uint32_t *slots = (src ? a.slot_s : a.slot_t) + off;
-        if (n <= (uint32_t)PACK_CAP) {
-            int np = 64;
-            while (np < (int)n) np <<= 1;
-            for (int k = threadIdx.x; k < np; k += blockDim.x)
-                sk[k] = (k < (int)n) ? (((uint64_t)slots[k] << 32) | (uint64_t)k) : ~0ull;
-            __syncthreads();
-            block_bitonic(sk, np);
-            for (int k = threadIdx.x; k < (int)n; k += blockDim.x)
-                emit_sorted(a, src, off, (uint32_t)k, sk[k]);
+            int f = block_radix_sort(sm, (int)l.n, a.passes);
+            const uint32_t *kk = f ? sm.kb : sm.ka;
+            const uint16_t *pp = f ? sm.pb : sm.pa;
+            for (int k = threadIdx.x; k < (int)l.n; k += blockDim.x) emit(a, l, k, kk[k], pp[k]);
             __syncthreads();
             continue;
         }
-        uint64_t loc = src ? a.msrc + (off - a.src_base) : off - a.tgt_base;
+        const uint64_t loc = l.src ? a.msrc + (l.off - a.src_base) : l.off - a.tgt_base;
         uint64_t *A = a.ma + loc;
         uint64_t *B = a.mb + loc;
-        for (uint32_t c0 = 0; c0 < n; c0 += PACK_CAP) {
-            uint32_t cn = min((uint32_t)PACK_CAP, n - c0);
-            int np = 64;
-            while (np < (int)cn) np <<= 1;
-            for (int k = threadIdx.x; k < np; k += blockDim.x)
-                sk[k] = (k < (int)cn) ? (((uint64_t)slots[c0 + k] << 32) | (uint64_t)(c0 + k))
-                                      : ~0ull;
+        const uint32_t n = l.n;
+        for (uint32_t c0 = 0; c0 < n; c0 += PK_CAP) {
+            const int cn = (int)min((uint32_t)PK_CAP, n - c0);
+            for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+                sm.ka[k] = a.slot_of_id[ids[c0 + k]];
+                sm.pa[k] = (uint16_t)k;
+            }
             __syncthreads();
-            block_bitonic(sk, np);
-            for (int k = threadIdx.x; k < (int)cn; k += blockDim.x) A[c0 + k] = sk[k];
+            int f = block_radix_sort(sm, cn, a.passes);
+            const uint32_t *kk = f ? sm.kb : sm.ka;
+            const uint16_t *pp = f ? sm.pb : sm.pa;
+            for (int k = threadIdx.x; k < cn; k += blockDim.x)
+                A[c0 + k] = ((uint64_t)kk[k] << 32) | (uint64_t)(c0 + pp[k]);
             __syncthreads();
         }
-        for (uint32_t w = PACK_CAP; w < n; w <<= 1) {
+        for (uint32_t w = PK_CAP; w < n; w <<= 1) {
             for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
-                uint32_t r = e / w;
-                uint32_t ls = (r & ~1u) * w;            // left run start
-                uint32_t rs = ls + w;                   // right run start
-                uint64_t key = A[e];
+                const uint32_t r = e / w;
+                const uint32_t ls = (r & ~1u) * w;
+                const uint32_t rs = ls + w;
+                const uint64_t key = A[e];
                 if (rs >= n) {
                     B[e] = key;
                     continue;
                 }
-                uint32_t re = min(rs + w, n);
-                uint32_t lo, hi, rank_other, own;
-                if (e < rs) {   // in the left run: count right-run keys < key
-                    lo = rs; hi = re;
-                    own = e - ls;
-                } else {        // in the right run: count left-run keys < key
-                    lo = ls; hi = rs;
-                    own = e - rs;
+                const uint32_t re = min(rs + w, n);
+                uint32_t lo, hi, own;
+                if (e < rs) {
+                    lo = rs; hi = re; own = e - ls;
+                } else {
+                    lo = ls; hi = rs; own = e - rs;
                 }
-                uint32_t base = lo;
+                const uint32_t base = lo;
                 while (lo < hi) {
                     uint32_t mid = (lo + hi) >> 1;
                     if (A[mid] < key) lo = mid + 1; else hi = mid;
                 }
-                rank_other = lo - base;
-                B[ls + own + rank_other] = key;
+                B[ls + own + (lo - base)] = key;
             }
             __syncthreads();
             uint64_t *t = A; A = B; B = t;
         }
-        for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) emit_sorted(a, src, off, k, A[k]);
+        for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
+            emit(a, l, k, (uint32_t)(A[k] >> 32), (uint32_t)(A[k] & 0xFFFFFFFFu));
         __syncthreads();
     }
 }
@@ -273,7 +388,7 @@ __global__ void __launch_bounds__(PACK_THREADS) k_pack_large(PackArgs a)
 
 constexpr int GRAV_THREADS = 256;
 constexpr int GRAV_WARPS = GRAV_THREADS / 32;
-constexpr int KAHAN_BLOCK = 8;   // plain FP32 partial over <= 8 sources, then compensated add
+constexpr int KB = 8;   // source pairs per plain FP32 partial before the compensated add
 
 struct InterArgs {
     const TaskRec *tasks;
@@ -282,7 +397,7 @@ struct InterArgs {
     const uint32_t *lj_list;
     uint64_t n_lj;
     const float4 *stg_t, *stg_s;
-    uint64_t tgt_base, src_base;
+    uint64_t tgt_base, src_base, task_base;
     const uint32_t *perm_t, *perm_s;
     const uint32_t *tgt_ids, *src_ids;
     float eps2;
@@ -303,6 +418,17 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
     s = t;
 }
 
+// Paired compensated add: (s, c) += b on both halves, with FMA-by-(-1)
+// standing in for subtraction (exact: one rounding, as a subtraction).
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 b, float2 m1)
+{
+    float2 y = __ffma2_rn(c, m1, b);      // b - c
+    float2 t = __fadd2_rn(s, y);
+    float2 d = __ffma2_rn(s, m1, t);      // t - s
+    c = __ffma2_rn(y, m1, d);             // (t - s) - y
+    s = t;
+}
+
 // Store the FP64 value v as the float pair (s, c) with s - c ~= v.
 __device__ __forceinline__ void split_store(float4 *dst, double v0, double v1, double v2,
                                             double v3)
@@ -316,11 +442,32 @@ __device__ __forceinline__ void split_store(float4 *dst, double v0, double v1, d
     dst[1] = c;
 }
 
-// One warp per work unit (task, block of <= 32 targets).  With T targets in
+// One source pair against one target, paired FP32 arithmetic.
+#define GRAV_PAIR(A, B)                                                   \
+    do {                                                                  \
+        float2 dx = __fadd2_rn(make_float2((A).x, (A).y), nx);            \
+        float2 dy = __fadd2_rn(make_float2((A).z, (A).w), ny);            \
+        float2 dz = __fadd2_rn(make_float2((B).x, (B).y), nz);            \
+        float2 r2 = __ffma2_rn(dx, dx, e2);                               \
+        r2 = __ffma2_rn(dy, dy, r2);                                      \
+        r2 = __ffma2_rn(dz, dz, r2);                                      \
+        float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));              \
+        float2 mr = __fmul2_rn(make_float2((B).z, (B).w), ri);            \
+        float2 mr3 = __fmul2_rn(mr, __fmul2_rn(ri, ri));                  \
+        bx = __ffma2_rn(mr3, dx, bx);                                     \
+        by = __ffma2_rn(mr3, dy, by);                                     \
+        bz = __ffma2_rn(mr3, dz, bz);                                     \
+        bp = __ffma2_rn(mr, m1, bp);                                      \
+    } while (0)
+
+// One warp per work unit (task, block of <= 16 targets).  With T targets in
 // the block, the warp splits into S = 32 / T source lanes per target: lane
-// (t, s) accumulates target t over sources s, s + S, ...; the S partial
-// results of a target are combined in FP64 in lane order.  Work units are
-// pulled from a device queue (persistent kernel).
+// (t, s) accumulates target t over source pairs s, s + S, ...; every source
+// pair is evaluated with paired FP32 instructions (two interactions per
+// instruction), partial sums of KB pairs are added with compensation, and
+// the S lane results of a target are combined in FP64 in lane order.  Work
+// units are pulled from a device queue (persistent kernel); with a null
+// queue each warp takes a fixed share (one-launch-per-task mode).
 __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
 {
     __shared__ double red[GRAV_WARPS][32][4];
@@ -328,6 +475,8 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
     const int wib = threadIdx.x >> 5;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 e2 = make_float2(a.eps2, a.eps2);
     for (uint64_t it = 0;; ++it) {
         unsigned long long w = gwarp + it * nwarps;
         if (a.queue) {
@@ -335,63 +484,68 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
             w = __shfl_sync(0xffffffffu, w, 0);
         }
         if (w >= a.n_wu) break;
-        GravWU u = a.wu[w];
+        const GravWU u = a.wu[w];
         const TaskRec r = a.tasks[u.task];
-        const int T = (int)min(32u, r.nt - u.t0);
+        const int T = (int)u.tn;
         const int S = 32 / T;
         const int t = lane % T;
         const int sl = lane / T;
-        const bool active = sl < S;
-        const float4 *src = a.stg_s + (r.src_off - a.src_base);
-        const uint32_t ns = r.ns;
-        float4 xi = a.stg_t[r.tgt_off - a.tgt_base + u.t0 + t];
-        float sx = 0.f, sy = 0.f, sz = 0.f, sp = 0.f;
-        float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f;
-        if (active) {
-            uint32_t j = (uint32_t)sl;
-            while (j < ns) {
-                float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+        const float4 *P = a.stg_s + (r.src_off - a.src_base) + (u.task - a.task_base);
+        const uint32_t np = (r.ns + 1u) >> 1;
+        const float4 xi = a.stg_t[r.tgt_off - a.tgt_base + u.t0 + t];
+        const float2 nx = make_float2(-xi.x, -xi.x);
+        const float2 ny = make_float2(-xi.y, -xi.y);
+        const float2 nz = make_float2(-xi.z, -xi.z);
+        float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
+        float2 cx = sx, cy = sx, cz = sx, cp = sx;
+        const uint32_t nq = (sl < S && (uint32_t)sl < np) ? (np - (uint32_t)sl + S - 1) / S : 0u;
+        const float4 *q = P + 2 * sl;
+        const uint32_t stride = 2u * (uint32_t)S;
+        uint32_t i = 0;
+        for (; i + KB <= nq; i += KB) {
+            float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
 #pragma unroll
-                for (int q = 0; q < KAHAN_BLOCK; ++q) {
-                    if (j < ns) {
-                        float4 pj = __ldg(src + j);
-                        float dx = pj.x - xi.x;
-                        float dy = pj.y - xi.y;
-                        float dz = pj.z - xi.z;
-                        float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, a.eps2)));
-                        float rinv = rsqrtf(r2);
-                        float mr = pj.w * rinv;
-                        float mr3 = mr * rinv * rinv;
-                        bx = fmaf(mr3, dx, bx);
-                        by = fmaf(mr3, dy, by);
-                        bz = fmaf(mr3, dz, bz);
-                        bp -= mr;
-                    }
-                    j += (uint32_t)S;
-                }
-                kahan_add(sx, cx, bx);
-                kahan_add(sy, cy, by);
-                kahan_add(sz, cz, bz);
-                kahan_add(sp, cp, bp);
+            for (int k = 0; k < KB; ++k) {
+                const float4 A = __ldg(q);
+                const float4 B = __ldg(q + 1);
+                q += stride;
+                GRAV_PAIR(A, B);
             }
+            kahan_add2(sx, cx, bx, m1);
+            kahan_add2(sy, cy, by, m1);
+            kahan_add2(sz, cz, bz, m1);
+            kahan_add2(sp, cp, bp, m1);
         }
-        red[wib][lane][0] = (double)sx - (double)cx;
-        red[wib][lane][1] = (double)sy - (double)cy;
-        red[wib][lane][2] = (double)sz - (double)cz;
-        red[wib][lane][3] = (double)sp - (double)cp;
+        if (i < nq) {
+            float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
+            for (; i < nq; ++i) {
+                const float4 A = __ldg(q);
+                const float4 B = __ldg(q + 1);
+                q += stride;
+                GRAV_PAIR(A, B);
+            }
+            kahan_add2(sx, cx, bx, m1);
+            kahan_add2(sy, cy, by, m1);
+            kahan_add2(sz, cz, bz, m1);
+            kahan_add2(sp, cp, bp, m1);
+        }
+        red[wib][lane][0] = ((double)sx.x - (double)cx.x) + ((double)sx.y - (double)cx.y);
+        red[wib][lane][1] = ((double)sy.x - (double)cy.x) + ((double)sy.y - (double)cy.y);
+        red[wib][lane][2] = ((double)sz.x - (double)cz.x) + ((double)sz.y - (double)cz.y);
+        red[wib][lane][3] = ((double)sp.x - (double)cp.x) + ((double)sp.y - (double)cp.y);
         __syncwarp();
         if (sl == 0) {
             double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-            for (int q = 0; q < S; ++q) {
-                int l = q * T + t;
+            for (int s = 0; s < S; ++s) {
+                const int l = s * T + t;
                 v0 += red[wib][l][0];
                 v1 += red[wib][l][1];
                 v2 += red[wib][l][2];
                 v3 += red[wib][l][3];
             }
-            uint64_t e = r.tgt_off + u.t0 + t;
-            uint32_t pos = a.perm_t[e];
-            uint64_t row = r.row_off + pos;
+            const uint64_t e = r.tgt_off + u.t0 + t;
+            const uint32_t pos = a.perm_t[e];
+            const uint64_t row = r.row_off + pos;
             split_store(a.res + 2 * row, v0, v1, v2, v3);
             a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
         }
@@ -426,7 +580,7 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
         const bool self = r.kind == GC_LJ_SELF;
         const uint32_t nA = r.nt, nB = self ? 0u : r.ns;
         const float4 *As = a.stg_t + (r.tgt_off - a.tgt_base);
-        const float4 *Bs = a.stg_s + (r.src_off - a.src_base);
+        const float4 *Bs = a.stg_s + (r.src_off - a.src_base) + (ti - a.task_base);
         const int32_t shx = (int32_t)r.shift[0] * a.edge_grid;
         const int32_t shy = (int32_t)r.shift[1] * a.edge_grid;
         const int32_t shz = (int32_t)r.shift[2] * a.edge_grid;
@@ -606,16 +760,27 @@ int gc_read_wu_offsets(gc_pool *p, uint64_t n, std::vector<uint32_t> &wu_off,
     return GC_OK;
 }
 
-int gc_pack(gc_pool *p, const TaskRec *tasks, uint64_t t0, uint64_t t1, uint64_t tgt_base,
-            uint64_t src_base, uint64_t msrc)
+int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uint32_t *src_ids,
+            uint64_t t0, uint64_t t1, uint64_t tgt_base, uint64_t src_base, uint64_t msrc)
 {
     if (t1 <= t0) return GC_OK;
+    static bool attr_set = false;
+    if (!attr_set) {
+        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PackSmem)));
+        attr_set = true;
+    }
     PackArgs a;
     a.tasks = tasks;
     a.t0 = t0;
     a.n_lists = 2 * (t1 - t0);
-    a.slot_t = p->tgt_slot.as<uint32_t>();
-    a.slot_s = p->src_slot.as<uint32_t>();
+    a.tgt_ids = tgt_ids;
+    a.src_ids = src_ids;
+    a.slot_of_id = p->d_slot_of_id;
+    a.task_base = t0;
+    int bits = 1;
+    while (bits < 32 && ((uint64_t)1 << bits) < p->cfg.pool_capacity) ++bits;
+    a.passes = (bits + 7) / 8;
     a.perm_t = p->tgt_perm.as<uint32_t>();
     a.perm_s = p->src_perm.as<uint32_t>();
     a.stg_t = p->stg_tgt.as<float4>();
@@ -629,16 +794,18 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, uint64_t t0, uint64_t t1, uint64_t
     ++p->stats.kernel_launches;
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, p->s>>>(a);
     ++p->stats.kernel_launches;
-    k_pack_large<<<grid_for(a.n_lists, 1, p->num_sms * 8), PACK_THREADS, 0, p->s>>>(a);
+    k_pack_large<<<grid_for(a.n_lists, 1, p->num_sms * 4), PK_THREADS, sizeof(PackSmem),
+                   p->s>>>(a);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
 
 static int fill_inter_args(gc_pool *p, const TaskRec *tasks, uint64_t tgt_base,
-                           uint64_t src_base, const uint32_t *tgt_ids, const uint32_t *src_ids,
-                           InterArgs &a)
+                           uint64_t src_base, uint64_t task_base, const uint32_t *tgt_ids,
+                           const uint32_t *src_ids, InterArgs &a)
 {
     a.tasks = tasks;
+    a.task_base = task_base;
     a.stg_t = p->stg_tgt.as<float4>();
     a.stg_s = p->stg_src.as<float4>();
     a.tgt_base = tgt_base;
@@ -673,10 +840,10 @@ int gc_grav_blocks(gc_pool *p)
 // tasks [l0, l1) of the prepared batch.
 int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
                       const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
-                      uint64_t l1, uint64_t tgt_base, uint64_t src_base)
+                      uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base)
 {
     InterArgs a;
-    fill_inter_args(p, tasks, tgt_base, src_base, tgt_ids, src_ids, a);
+    fill_inter_args(p, tasks, tgt_base, src_base, task_base, tgt_ids, src_ids, a);
     int full = gc_grav_blocks(p);
     if (w1 > w0) {
         a.wu = p->wu.as<GravWU>() + w0;
@@ -708,10 +875,10 @@ int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
 // work assignment, grid sized to the task.
 int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
                          const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
-                         uint64_t l1, uint64_t tgt_base, uint64_t src_base)
+                         uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base)
 {
     InterArgs a;
-    fill_inter_args(p, tasks, tgt_base, src_base, tgt_ids, src_ids, a);
+    fill_inter_args(p, tasks, tgt_base, src_base, task_base, tgt_ids, src_ids, a);
     a.queue = nullptr;
     if (w1 > w0) {
         a.wu = p->wu.as<GravWU>() + w0;

@@ -141,21 +141,54 @@ __global__ void k_compact_write(CompactArgs a, const uint32_t *tile_off, uint32_
 
 // ---- residency kernels ------------------------------------------------------
 
+// Reference marking and counting.  Each block takes a contiguous chunk of
+// entries (neighbouring tasks share many ids: the far tree nodes appear in
+// almost every list), aggregates reference counts in a small shared-memory
+// hash table and adds them to the global counters once per block; ids that
+// do not find a table slot fall back to global atomics.
+constexpr int MARK_HASH = 2048;
+
 __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, uint64_t ns,
                        uint64_t id_cap, const uint8_t *known, uint32_t *ref_epoch,
-                       uint32_t *ref_count, uint32_t epoch, unsigned long long *ctr)
+                       uint32_t *ref_count, uint32_t epoch, unsigned long long *ctr,
+                       uint64_t chunk)
 {
-    uint64_t n = nt + ns;
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < n;
-         e += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t id = e < nt ? tgt[e] : src[e - nt];
+    __shared__ uint32_t hkey[MARK_HASH];
+    __shared__ uint32_t hcnt[MARK_HASH];
+    for (int i = threadIdx.x; i < MARK_HASH; i += blockDim.x) {
+        hkey[i] = GC_NONE;
+        hcnt[i] = 0;
+    }
+    __syncthreads();
+    const uint64_t n = nt + ns;
+    const uint64_t b0 = (uint64_t)blockIdx.x * chunk;
+    const uint64_t b1 = min(n, b0 + chunk);
+    bool bad = false;
+    for (uint64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
+        const uint32_t id = e < nt ? tgt[e] : src[e - nt];
         if ((uint64_t)id >= id_cap || !known[id]) {
-            atomicOr(&ctr[CTR_FLAGS], (unsigned long long)GC_FLAG_UNKNOWN_ID);
+            bad = true;
             continue;
         }
         if (ref_epoch[id] != epoch) ref_epoch[id] = epoch;
-        atomicAdd(&ref_count[id], 1u);
+        uint32_t h = (id * 2654435761u) & (MARK_HASH - 1);
+        bool done = false;
+        for (int probe = 0; probe < 8; ++probe) {
+            uint32_t k = hkey[h];
+            if (k == GC_NONE) k = atomicCAS(&hkey[h], GC_NONE, id);
+            if (k == GC_NONE || k == id) {
+                atomicAdd(&hcnt[h], 1u);
+                done = true;
+                break;
+            }
+            h = (h + 1) & (MARK_HASH - 1);
+        }
+        if (!done) atomicAdd(&ref_count[id], 1u);
     }
+    if (bad) atomicOr(&ctr[CTR_FLAGS], (unsigned long long)GC_FLAG_UNKNOWN_ID);
+    __syncthreads();
+    for (int i = threadIdx.x; i < MARK_HASH; i += blockDim.x)
+        if (hkey[i] != GC_NONE) atomicAdd(&ref_count[hkey[i]], hcnt[i]);
 }
 
 __device__ __forceinline__ int hist_bin(uint32_t c)
@@ -287,6 +320,17 @@ inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
 
 }  // namespace
 
+// Slots of the given ids (introspection of the chare table).
+int gc_entry_slots(gc_pool *p, const uint32_t *ids, uint64_t n, uint32_t *out)
+{
+    if (n == 0) return GC_OK;
+    ++p->stats.kernel_launches;
+    k_entry_slots<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(ids, n, p->d_slot_of_id,
+                                                                      out);
+    GC_CUDA_TRY(cudaGetLastError());
+    return GC_OK;
+}
+
 int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev,
                const uint32_t *arr, uint32_t *out, unsigned long long *count_out)
 {
@@ -341,7 +385,7 @@ int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint6
 }
 
 int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
-                 uint64_t ns, uint32_t *tgt_slot, uint32_t *src_slot)
+                 uint64_t ns)
 {
     const uint64_t id_cap = p->cfg.id_capacity, cap = p->cfg.pool_capacity;
     const uint64_t n = nt + ns;
@@ -353,10 +397,11 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
     GC_CUDA_TRY(cudaMemsetAsync(ctr + CTR_UNIQUE, 0,
                                 sizeof(unsigned long long) * (CTR_COUNT - CTR_UNIQUE), p->s));
     if (n > 0) {
+        const uint64_t chunk = 8192;
         ++p->stats.kernel_launches;
-        k_mark<<<grid_for(n, 256, maxb), 256, 0, p->s>>>(tgt, nt, src, ns, id_cap, p->d_known,
-                                                         p->d_ref_epoch, p->d_ref_count,
-                                                         p->epoch, ctr);
+        k_mark<<<(unsigned)((n + chunk - 1) / chunk), 512, 0, p->s>>>(
+            tgt, nt, src, ns, id_cap, p->d_known, p->d_ref_epoch, p->d_ref_count, p->epoch, ctr,
+            chunk);
     }
     uint64_t ubound = n < id_cap ? n : id_cap;
     GC_TRY(p->uniq.reserve((ubound + 1) * sizeof(uint32_t)));
@@ -418,16 +463,6 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         k_touch<<<grid_for(U, 256, maxb), 256, 0, p->s>>>(p->uniq.as<uint32_t>(), U,
                                                           p->d_slot_of_id, p->d_last_use,
                                                           p->epoch);
-    }
-    if (nt) {
-        ++p->stats.kernel_launches;
-        k_entry_slots<<<grid_for(nt, 256, maxb), 256, 0, p->s>>>(tgt, nt, p->d_slot_of_id,
-                                                                 tgt_slot);
-    }
-    if (ns) {
-        ++p->stats.kernel_launches;
-        k_entry_slots<<<grid_for(ns, 256, maxb), 256, 0, p->s>>>(src, ns, p->d_slot_of_id,
-                                                                 src_slot);
     }
     GC_CUDA_TRY(cudaGetLastError());
 
