@@ -608,15 +608,26 @@ int gc_wait(gc_pool_t *p, uint64_t batch, uint64_t timeout_ns)
 {
     if (!p) return GC_ERR_ARG;
     if (!p->have_last || batch > p->last_batch) return GC_ERR_NOT_READY;
+    auto device_status = [p]() -> int {
+        unsigned long long f = 0;
+        if (cudaMemcpy(&f, p->d_ctr + CTR_FLAGS, sizeof f, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return GC_ERR_CUDA;
+        if (f & GC_FLAG_TIMEOUT) {
+            unsigned long long keep = f & ~(unsigned long long)GC_FLAG_TIMEOUT;
+            cudaMemcpy(p->d_ctr + CTR_FLAGS, &keep, sizeof keep, cudaMemcpyHostToDevice);
+            return GC_ERR_TIMEOUT;
+        }
+        return GC_OK;
+    };
     if (timeout_ns == 0) {
         GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
-        return GC_OK;
+        return device_status();
     }
     struct timespec t0, t1;
     clock_gettime(CLOCK_MONOTONIC, &t0);
     for (;;) {
         cudaError_t e = cudaEventQuery(p->ev_done);
-        if (e == cudaSuccess) return GC_OK;
+        if (e == cudaSuccess) return device_status();
         if (e != cudaErrorNotReady) return GC_ERR_CUDA;
         clock_gettime(CLOCK_MONOTONIC, &t1);
         uint64_t el = (uint64_t)(t1.tv_sec - t0.tv_sec) * 1000000000ull +

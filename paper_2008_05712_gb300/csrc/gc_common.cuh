@@ -22,6 +22,7 @@ struct __align__(32) gcd4 {
 #define GC_FLAG_UNKNOWN_ID 1u     // a batch entry names an id never uploaded
 #define GC_FLAG_ID_RANGE 2u       // an id >= id_capacity (device upload/build)
 #define GC_FLAG_BAD_TASK 4u       // unknown kind, or LJ_SELF with sources
+#define GC_FLAG_TIMEOUT 8u        // a device-side wait ran out of its limit
 
 // Indices into the device counter block (pool->d_ctr, uint64 each).  The
 // residency counters (CTR_UNIQUE .. end) are cleared at every wave.

@@ -10,6 +10,7 @@
 //             Lennard-Jones on cell pairs, both cells updated (Section 4.2),
 //   scatter : per-id FP64 totals, each id's rows summed in admission order.
 #include "gc_common.cuh"
+#include "gc_ptx.cuh"
 
 namespace {
 
@@ -121,6 +122,7 @@ __global__ void k_prep_fill(TaskRec *tasks, uint64_t n, const uint64_t *row_off,
 // The extra float4 per task keeps every padded segment inside its own range.
 
 constexpr int PK_CAP = 4096;          // entries sorted in shared memory at once
+constexpr int PK_CAP_SMALL = 2048;    // lists up to this size use half the shared memory
 constexpr int PK_THREADS = 256;
 constexpr int PK_WARPS = PK_THREADS / 32;
 
@@ -218,10 +220,11 @@ __global__ void k_pack_small(PackArgs a)
     }
 }
 
+template <int CAP>
 struct PackSmem {
-    uint32_t ka[PK_CAP], kb[PK_CAP];     // slots
-    uint16_t pa[PK_CAP], pb[PK_CAP];     // list positions (within a chunk)
-    uint32_t hist[256][PK_WARPS];        // per (digit, warp) counts, then offsets
+    uint32_t ka[CAP], kb[CAP];           // slots
+    uint16_t pa[CAP], pb[CAP];           // list positions (within a chunk)
+    uint32_t hist[PK_WARPS][256];        // per (warp, digit) counts, then offsets
     uint32_t wsum[PK_WARPS];
     int skip;
 };
@@ -249,7 +252,8 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *wsu
 // with __match_any_sync, so equal digits keep their order (warp by warp,
 // chunk by chunk, lane by lane).  Returns 0 if the result is in ka/pa, 1 if
 // in kb/pb.
-__device__ int block_radix_sort(PackSmem &sm, int n, int passes)
+template <int CAP>
+__device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -268,16 +272,16 @@ __device__ int block_radix_sort(PackSmem &sm, int n, int passes)
             const bool v = k < b1;
             const uint32_t d = v ? ((ka[k] >> sh) & 255u) : 256u + (uint32_t)lane;
             const uint32_t m = __match_any_sync(0xffffffffu, d);
-            if (v && (m & lt) == 0) sm.hist[d][w] += (uint32_t)__popc(m);
+            if (v && (m & lt) == 0) sm.hist[w][d] += (uint32_t)__popc(m);
         }
         __syncthreads();
         uint32_t s = 0;
-        for (int q = 0; q < PK_WARPS; ++q) s += sm.hist[threadIdx.x][q];
+        for (int q = 0; q < PK_WARPS; ++q) s += sm.hist[q][threadIdx.x];
         if (s == (uint32_t)n) sm.skip = 1;       // one digit value: pass is the identity
         uint32_t run = block_excl_scan256(s, sm.wsum);
         for (int q = 0; q < PK_WARPS; ++q) {
-            uint32_t c = sm.hist[threadIdx.x][q];
-            sm.hist[threadIdx.x][q] = run;
+            uint32_t c = sm.hist[q][threadIdx.x];
+            sm.hist[q][threadIdx.x] = run;
             run += c;
         }
         __syncthreads();
@@ -289,12 +293,12 @@ __device__ int block_radix_sort(PackSmem &sm, int n, int passes)
             const uint32_t d = v ? ((key >> sh) & 255u) : 256u + (uint32_t)lane;
             const uint32_t m = __match_any_sync(0xffffffffu, d);
             if (v) {
-                const uint32_t dst = sm.hist[d][w] + (uint32_t)__popc(m & lt);
+                const uint32_t dst = sm.hist[w][d] + (uint32_t)__popc(m & lt);
                 kb[dst] = key;
                 pb[dst] = pa[k];
             }
             __syncwarp();
-            if (v && (m & lt) == 0) sm.hist[d][w] += (uint32_t)__popc(m);
+            if (v && (m & lt) == 0) sm.hist[w][d] += (uint32_t)__popc(m);
             __syncwarp();
         }
         __syncthreads();
@@ -310,15 +314,20 @@ __device__ int block_radix_sort(PackSmem &sm, int n, int passes)
 // and merged pairwise in global scratch (keys (slot << 32 | pos) are
 // unique, so an element's output index is its rank in its own run plus its
 // rank in the other run).
+// CAP = PK_CAP_SMALL handles lists of 33..PK_CAP_SMALL entries; CAP = PK_CAP
+// handles every longer list (chunked beyond PK_CAP).
+template <int CAP>
 __global__ void __launch_bounds__(PK_THREADS) k_pack_large(PackArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PackSmem &sm = *reinterpret_cast<PackSmem *>(smem_raw);
+    PackSmem<CAP> &sm = *reinterpret_cast<PackSmem<CAP> *>(smem_raw);
+    const uint32_t lo_n = (CAP == PK_CAP) ? (uint32_t)PK_CAP_SMALL : 32u;
+    const uint32_t hi_n = (CAP == PK_CAP) ? 0xFFFFFFFFu : (uint32_t)CAP;
     for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
         PackList l = list_of(a, L);
-        if (l.n <= 32) continue;
+        if (l.n <= lo_n || l.n > hi_n) continue;
         const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
-        if (l.n <= (uint32_t)PK_CAP) {
+        if (l.n <= (uint32_t)CAP) {
             for (int k = threadIdx.x; k < (int)l.n; k += blockDim.x) {
                 sm.ka[k] = a.slot_of_id[ids[k]];
                 sm.pa[k] = (uint16_t)k;
@@ -335,8 +344,8 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack_large(PackArgs a)
         uint64_t *A = a.ma + loc;
         uint64_t *B = a.mb + loc;
         const uint32_t n = l.n;
-        for (uint32_t c0 = 0; c0 < n; c0 += PK_CAP) {
-            const int cn = (int)min((uint32_t)PK_CAP, n - c0);
+        for (uint32_t c0 = 0; c0 < n; c0 += CAP) {
+            const int cn = (int)min((uint32_t)CAP, n - c0);
             for (int k = threadIdx.x; k < cn; k += blockDim.x) {
                 sm.ka[k] = a.slot_of_id[ids[c0 + k]];
                 sm.pa[k] = (uint16_t)k;
@@ -349,7 +358,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack_large(PackArgs a)
                 A[c0 + k] = ((uint64_t)kk[k] << 32) | (uint64_t)(c0 + pp[k]);
             __syncthreads();
         }
-        for (uint32_t w = PK_CAP; w < n; w <<= 1) {
+        for (uint32_t w = CAP; w < n; w <<= 1) {
             for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
                 const uint32_t r = e / w;
                 const uint32_t ls = (r & ~1u) * w;
@@ -408,6 +417,7 @@ struct InterArgs {
     uint32_t *row_id;
     unsigned long long *queue;   // work-queue head
     unsigned long long *lj_in;
+    unsigned long long *flags;   // device error bits
 };
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
@@ -460,23 +470,45 @@ __device__ __forceinline__ void split_store(float4 *dst, double v0, double v1, d
         bp = __ffma2_rn(mr, m1, bp);                                      \
     } while (0)
 
+constexpr int TP = 128;                 // source pairs per staged tile (4 KB)
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
+
+struct GravSmem {
+    float4 buf[GRAV_WARPS][2][2 * TP];  // per warp: two tiles of source pairs
+    uint64_t bar[GRAV_WARPS][2];        // one mbarrier per tile buffer
+    double red[GRAV_WARPS][32][4];      // cross-lane FP64 combine
+};
+
 // One warp per work unit (task, block of <= 16 targets).  With T targets in
 // the block, the warp splits into S = 32 / T source lanes per target: lane
-// (t, s) accumulates target t over source pairs s, s + S, ...; every source
-// pair is evaluated with paired FP32 instructions (two interactions per
-// instruction), partial sums of KB pairs are added with compensation, and
-// the S lane results of a target are combined in FP64 in lane order.  Work
-// units are pulled from a device queue (persistent kernel); with a null
-// queue each warp takes a fixed share (one-launch-per-task mode).
+// (t, s) accumulates target t over source pairs s, s + S, ... of each tile.
+// Source pairs stream through two shared-memory tile buffers per warp,
+// filled by 1-D bulk copies (TMA) that complete on mbarriers, one tile
+// ahead of the compute.  Every source pair is evaluated with paired FP32
+// instructions (two interactions per instruction); partial sums of KB pairs
+// are added with compensation; the S lane results of a target are combined
+// in FP64 in lane order.  Work units come from a device queue (persistent
+// kernel); with a null queue each warp takes a fixed share
+// (one-launch-per-task mode).  A bulk copy that does not complete within the
+// polling limit sets GC_FLAG_TIMEOUT and the warp stops.
 __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
 {
-    __shared__ double red[GRAV_WARPS][32][4];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GravSmem &sm = *reinterpret_cast<GravSmem *>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const float2 m1 = make_float2(-1.0f, -1.0f);
     const float2 e2 = make_float2(a.eps2, a.eps2);
+    uint64_t *bar = sm.bar[wib];
+    if (lane == 0) {
+        gc_mbar_init(&bar[0], 1);
+        gc_mbar_init(&bar[1], 1);
+        gc_fence_mbar_init();
+    }
+    __syncwarp();
+    uint32_t parity = 0;     // bit b: parity of the next completion of buffer b
     for (uint64_t it = 0;; ++it) {
         unsigned long long w = gwarp + it * nwarps;
         if (a.queue) {
@@ -490,58 +522,96 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
         const int S = 32 / T;
         const int t = lane % T;
         const int sl = lane / T;
+        const bool active = sl < S;
         const float4 *P = a.stg_s + (r.src_off - a.src_base) + (u.task - a.task_base);
         const uint32_t np = (r.ns + 1u) >> 1;
+        const uint32_t ntiles = (np + TP - 1) / TP;
         const float4 xi = a.stg_t[r.tgt_off - a.tgt_base + u.t0 + t];
         const float2 nx = make_float2(-xi.x, -xi.x);
         const float2 ny = make_float2(-xi.y, -xi.y);
         const float2 nz = make_float2(-xi.z, -xi.z);
         float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
         float2 cx = sx, cy = sx, cz = sx, cp = sx;
-        const uint32_t nq = (sl < S && (uint32_t)sl < np) ? (np - (uint32_t)sl + S - 1) / S : 0u;
-        const float4 *q = P + 2 * sl;
-        const uint32_t stride = 2u * (uint32_t)S;
-        uint32_t i = 0;
-        for (; i + KB <= nq; i += KB) {
-            float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
+        if (lane == 0) {
+            for (uint32_t b = 0; b < 2 && b < ntiles; ++b) {
+                const uint32_t bytes = min((uint32_t)TP, np - b * TP) * 32u;
+                gc_mbar_arrive_expect_tx(&bar[b], bytes);
+                gc_bulk_g2s(sm.buf[wib][b], P + 2 * b * TP, bytes, &bar[b]);
+            }
+        }
+        bool ok = true;
+        uint32_t failed_at = 0;
+        for (uint32_t i = 0; i < ntiles; ++i) {
+            const uint32_t b = i & 1u;
+            if (!gc_mbar_wait_bounded(&bar[b], (parity >> b) & 1u, WAIT_LIMIT)) {
+                ok = false;
+                failed_at = i;
+                break;
+            }
+            parity ^= 1u << b;
+            const uint32_t m = min((uint32_t)TP, np - i * TP);
+            const uint32_t nq = (active && (uint32_t)sl < m) ? (m - (uint32_t)sl + S - 1) / S : 0u;
+            const float4 *q = sm.buf[wib][b] + 2 * sl;
+            const uint32_t stride = 2u * (uint32_t)S;
+            uint32_t j = 0;
+            for (; j + KB <= nq; j += KB) {
+                float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
 #pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                const float4 A = __ldg(q);
-                const float4 B = __ldg(q + 1);
-                q += stride;
-                GRAV_PAIR(A, B);
+                for (int k = 0; k < KB; ++k) {
+                    const float4 A = q[0];
+                    const float4 B = q[1];
+                    q += stride;
+                    GRAV_PAIR(A, B);
+                }
+                kahan_add2(sx, cx, bx, m1);
+                kahan_add2(sy, cy, by, m1);
+                kahan_add2(sz, cz, bz, m1);
+                kahan_add2(sp, cp, bp, m1);
             }
-            kahan_add2(sx, cx, bx, m1);
-            kahan_add2(sy, cy, by, m1);
-            kahan_add2(sz, cz, bz, m1);
-            kahan_add2(sp, cp, bp, m1);
-        }
-        if (i < nq) {
-            float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
-            for (; i < nq; ++i) {
-                const float4 A = __ldg(q);
-                const float4 B = __ldg(q + 1);
-                q += stride;
-                GRAV_PAIR(A, B);
+            if (j < nq) {
+                float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
+                for (; j < nq; ++j) {
+                    const float4 A = q[0];
+                    const float4 B = q[1];
+                    q += stride;
+                    GRAV_PAIR(A, B);
+                }
+                kahan_add2(sx, cx, bx, m1);
+                kahan_add2(sy, cy, by, m1);
+                kahan_add2(sz, cz, bz, m1);
+                kahan_add2(sp, cp, bp, m1);
             }
-            kahan_add2(sx, cx, bx, m1);
-            kahan_add2(sy, cy, by, m1);
-            kahan_add2(sz, cz, bz, m1);
-            kahan_add2(sp, cp, bp, m1);
+            gc_fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0 && i + 2 < ntiles) {
+                const uint32_t bytes = min((uint32_t)TP, np - (i + 2) * TP) * 32u;
+                gc_mbar_arrive_expect_tx(&bar[b], bytes);
+                gc_bulk_g2s(sm.buf[wib][b], P + 2 * (i + 2) * TP, bytes, &bar[b]);
+            }
         }
-        red[wib][lane][0] = ((double)sx.x - (double)cx.x) + ((double)sx.y - (double)cx.y);
-        red[wib][lane][1] = ((double)sy.x - (double)cy.x) + ((double)sy.y - (double)cy.y);
-        red[wib][lane][2] = ((double)sz.x - (double)cz.x) + ((double)sz.y - (double)cz.y);
-        red[wib][lane][3] = ((double)sp.x - (double)cp.x) + ((double)sp.y - (double)cp.y);
+        if (!ok) {
+            // a copy never completed: report, wait (bounded) for the other
+            // copy of this work unit still in flight, stop this warp
+            if (lane == 0) atomicOr(a.flags, (unsigned long long)GC_FLAG_TIMEOUT);
+            if (failed_at + 1 < ntiles) {
+                const uint32_t ob = (failed_at + 1) & 1u;
+                gc_mbar_wait_bounded(&bar[ob], (parity >> ob) & 1u, WAIT_LIMIT);
+            }
+            return;
+        }
+        sm.red[wib][lane][0] = ((double)sx.x - (double)cx.x) + ((double)sx.y - (double)cx.y);
+        sm.red[wib][lane][1] = ((double)sy.x - (double)cy.x) + ((double)sy.y - (double)cy.y);
+        sm.red[wib][lane][2] = ((double)sz.x - (double)cz.x) + ((double)sz.y - (double)cz.y);
+        sm.red[wib][lane][3] = ((double)sp.x - (double)cp.x) + ((double)sp.y - (double)cp.y);
         __syncwarp();
         if (sl == 0) {
             double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
             for (int s = 0; s < S; ++s) {
                 const int l = s * T + t;
-                v0 += red[wib][l][0];
-                v1 += red[wib][l][1];
-                v2 += red[wib][l][2];
-                v3 += red[wib][l][3];
+                v0 += sm.red[wib][l][0];
+                v1 += sm.red[wib][l][1];
+                v2 += sm.red[wib][l][2];
+                v3 += sm.red[wib][l][3];
             }
             const uint64_t e = r.tgt_off + u.t0 + t;
             const uint32_t pos = a.perm_t[e];
@@ -766,8 +836,12 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
     if (t1 <= t0) return GC_OK;
     static bool attr_set = false;
     if (!attr_set) {
-        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PackSmem)));
+        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large<PK_CAP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PackSmem<PK_CAP>)));
+        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large<PK_CAP_SMALL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PackSmem<PK_CAP_SMALL>)));
         attr_set = true;
     }
     PackArgs a;
@@ -794,8 +868,11 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
     ++p->stats.kernel_launches;
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, p->s>>>(a);
     ++p->stats.kernel_launches;
-    k_pack_large<<<grid_for(a.n_lists, 1, p->num_sms * 4), PK_THREADS, sizeof(PackSmem),
-                   p->s>>>(a);
+    k_pack_large<PK_CAP_SMALL><<<grid_for(a.n_lists, 1, p->num_sms * 7), PK_THREADS,
+                                 sizeof(PackSmem<PK_CAP_SMALL>), p->s>>>(a);
+    ++p->stats.kernel_launches;
+    k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
+                           sizeof(PackSmem<PK_CAP>), p->s>>>(a);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
@@ -824,14 +901,31 @@ static int fill_inter_args(gc_pool *p, const TaskRec *tasks, uint64_t tgt_base,
     a.row_id = p->row_id.as<uint32_t>();
     a.queue = p->d_ctr + CTR_QUEUE;
     a.lj_in = p->d_ctr + CTR_LJ_IN;
+    a.flags = p->d_ctr + CTR_FLAGS;
     return GC_OK;
 }
 
+static int grav_setup()
+{
+    static int done = 0;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_gravity, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(GravSmem)) != cudaSuccess)
+            return GC_ERR_CUDA;
+        done = 1;
+    }
+    return GC_OK;
+}
+
+// Persistent grid of the gravity kernel: resident blocks per SM (occupancy
+// API) x SMs -- the number of work units one launch runs at once.
 int gc_grav_blocks(gc_pool *p)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gravity, GRAV_THREADS, 0) !=
-        cudaSuccess || per_sm < 1)
+    if (grav_setup() != GC_OK ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gravity, GRAV_THREADS,
+                                                      sizeof(GravSmem)) != cudaSuccess ||
+        per_sm < 1)
         per_sm = 1;
     return per_sm * p->num_sms;
 }
@@ -854,7 +948,7 @@ int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
         uint64_t need = (a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS;
         unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
         ++p->stats.kernel_launches;
-        k_gravity<<<g, GRAV_THREADS, 0, p->s>>>(a);
+        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), p->s>>>(a);
     }
     if (l1 > l0) {
         a.wu = nullptr;
@@ -886,8 +980,9 @@ int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_i
         a.lj_list = nullptr;
         a.n_lj = 0;
         unsigned g = (unsigned)((a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS);
+        GC_TRY(grav_setup());
         ++p->stats.kernel_launches;
-        k_gravity<<<g, GRAV_THREADS, 0, p->s>>>(a);
+        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), p->s>>>(a);
     }
     if (l1 > l0) {
         a.wu = nullptr;

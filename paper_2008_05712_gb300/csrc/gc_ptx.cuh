@@ -1,0 +1,69 @@
+// gc_ptx.cuh -- inline-PTX helpers for Blackwell bulk copies (TMA, 1-D) and
+// shared-memory mbarriers.
+#pragma once
+#include <stdint.h>
+
+__device__ __forceinline__ uint32_t gc_smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void gc_mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gc_smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// make barrier initialisation visible to the asynchronous (bulk-copy) proxy
+__device__ __forceinline__ void gc_fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// order this thread's generic-proxy shared-memory accesses before later
+// asynchronous-proxy writes to the same memory
+__device__ __forceinline__ void gc_fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void gc_mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gc_smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes and
+// addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void gc_bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            gc_smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(gc_smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool gc_mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(gc_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false if the limit ran out.
+__device__ __forceinline__ bool gc_mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                     uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i)
+        if (gc_mbar_try_wait(bar, parity)) return true;
+    return false;
+}
