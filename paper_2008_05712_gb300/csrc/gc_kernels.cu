@@ -309,6 +309,139 @@ __device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
     return flip;
 }
 
+// Lists of 33..PM_CAP entries: one block of 4 warps per list, LSD radix
+// sort of (slot, pos) with 8-bit digits.  Warp w owns a contiguous range of
+// the current layout; within a warp, 32 items at a time are ranked among
+// equal digits with __match_any_sync (stable: warp by warp, chunk by chunk,
+// lane by lane).  The digit-0 histogram is gathered while loading, and each
+// scatter also counts the next pass's per-warp histogram from the
+// destinations it writes, so a pass is one sweep between two barriers.
+constexpr int PM_CAP = 2048;
+constexpr int PM_THREADS = 128;
+constexpr int PM_W = PM_THREADS / 32;
+
+struct PackSmemMid {
+    uint32_t ka[PM_CAP], kb[PM_CAP];
+    uint16_t pa[PM_CAP], pb[PM_CAP];
+    uint32_t hist[2][PM_W][256];
+    uint32_t wsum[PM_W];
+    int skip;
+};
+
+__device__ __forceinline__ uint32_t block_excl_scan128(uint32_t v, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int q = 0; q < w; ++q) before += wsum[q];
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PackSmemMid &sm = *reinterpret_cast<PackSmemMid *>(smem_raw);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
+        const PackList l = list_of(a, L);
+        if (l.n <= 32 || l.n > (uint32_t)PM_CAP) continue;
+        const int n = (int)l.n;
+        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
+        const int per = (((n + PM_W - 1) / PM_W) + 31) & ~31;
+        const int b0 = min(n, w * per), b1 = min(n, b0 + per);
+        for (int i = threadIdx.x; i < 2 * PM_W * 256; i += PM_THREADS) (&sm.hist[0][0][0])[i] = 0;
+        __syncthreads();
+        // load, and count digit 0 per warp range
+        for (int c = b0; c < b1; c += 32) {
+            const int k = c + lane;
+            const bool v = k < b1;
+            uint32_t key = 0;
+            if (v) {
+                key = a.slot_of_id[ids[k]];
+                sm.ka[k] = key;
+                sm.pa[k] = (uint16_t)k;
+            }
+            const uint32_t d = v ? (key & 255u) : 256u + (uint32_t)lane;
+            const uint32_t m = __match_any_sync(0xffffffffu, d);
+            if (v && (m & lt) == 0) sm.hist[0][w][d] += (uint32_t)__popc(m);
+        }
+        __syncthreads();
+        uint32_t *ka = sm.ka, *kb = sm.kb;
+        uint16_t *pa = sm.pa, *pb = sm.pb;
+        int cur = 0;
+        for (int pass = 0; pass < a.passes; ++pass) {
+            const int sh = 8 * pass;
+            const bool last = pass + 1 == a.passes;
+            // exclusive offsets over (digit, warp); thread t owns digits t, t+128
+            uint32_t c0 = 0, c1 = 0;
+            for (int q = 0; q < PM_W; ++q) {
+                c0 += sm.hist[cur][q][threadIdx.x];
+                c1 += sm.hist[cur][q][threadIdx.x + 128];
+            }
+            if (threadIdx.x == 0) sm.skip = 0;
+            __syncthreads();
+            if (c0 == (uint32_t)n || c1 == (uint32_t)n) sm.skip = 1;
+            uint32_t run = block_excl_scan128(c0 + c1, sm.wsum);
+            for (int q = 0; q < PM_W; ++q) {
+                uint32_t c = sm.hist[cur][q][threadIdx.x];
+                sm.hist[cur][q][threadIdx.x] = run;
+                run += c;
+            }
+            for (int q = 0; q < PM_W; ++q) {
+                uint32_t c = sm.hist[cur][q][threadIdx.x + 128];
+                sm.hist[cur][q][threadIdx.x + 128] = run;
+                run += c;
+            }
+            for (int i = threadIdx.x; i < PM_W * 256; i += PM_THREADS)
+                (&sm.hist[cur ^ 1][0][0])[i] = 0;
+            __syncthreads();
+            const bool skip = sm.skip != 0;
+            for (int c = b0; c < b1; c += 32) {
+                const int k = c + lane;
+                const bool v = k < b1;
+                const uint32_t key = v ? ka[k] : 0u;
+                int dst = k;
+                if (!skip) {
+                    const uint32_t d = v ? ((key >> sh) & 255u) : 256u + (uint32_t)lane;
+                    const uint32_t m = __match_any_sync(0xffffffffu, d);
+                    if (v) {
+                        dst = (int)(sm.hist[cur][w][d] + (uint32_t)__popc(m & lt));
+                        kb[dst] = key;
+                        pb[dst] = pa[k];
+                    }
+                    __syncwarp();
+                    if (v && (m & lt) == 0) sm.hist[cur][w][d] += (uint32_t)__popc(m);
+                }
+                if (!last) {
+                    // next pass: count (warp range of dst, next digit)
+                    const uint32_t wd = (uint32_t)(dst / per);
+                    const uint32_t d2 = v ? wd * 256u + ((key >> (sh + 8)) & 255u)
+                                          : 4096u + (uint32_t)lane;
+                    const uint32_t m2 = __match_any_sync(0xffffffffu, d2);
+                    if (v && (m2 & lt) == 0)
+                        atomicAdd(&sm.hist[cur ^ 1][0][0] + d2, (uint32_t)__popc(m2));
+                }
+            }
+            __syncthreads();
+            if (!skip) {
+                uint32_t *tk = ka; ka = kb; kb = tk;
+                uint16_t *tp = pa; pa = pb; pb = tp;
+            }
+            cur ^= 1;
+        }
+        for (int k = threadIdx.x; k < n; k += PM_THREADS) emit(a, l, (uint32_t)k, ka[k], pa[k]);
+        __syncthreads();
+    }
+}
+
 // Lists of more than 32 entries: one block.  Up to PK_CAP entries are
 // radix-sorted in shared memory; longer lists are sorted in chunks of PK_CAP
 // and merged pairwise in global scratch (keys (slot << 32 | pos) are
@@ -321,7 +454,7 @@ __global__ void __launch_bounds__(PK_THREADS) k_pack_large(PackArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PackSmem<CAP> &sm = *reinterpret_cast<PackSmem<CAP> *>(smem_raw);
-    const uint32_t lo_n = (CAP == PK_CAP) ? (uint32_t)PK_CAP_SMALL : 32u;
+    const uint32_t lo_n = (CAP == PK_CAP) ? (uint32_t)PM_CAP : 32u;
     const uint32_t hi_n = (CAP == PK_CAP) ? 0xFFFFFFFFu : (uint32_t)CAP;
     for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
         PackList l = list_of(a, L);
@@ -839,9 +972,8 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
         GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large<PK_CAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(PackSmem<PK_CAP>)));
-        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large<PK_CAP_SMALL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PackSmem<PK_CAP_SMALL>)));
+        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_mid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(PackSmemMid)));
         attr_set = true;
     }
     PackArgs a;
@@ -868,8 +1000,8 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
     ++p->stats.kernel_launches;
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, p->s>>>(a);
     ++p->stats.kernel_launches;
-    k_pack_large<PK_CAP_SMALL><<<grid_for(a.n_lists, 1, p->num_sms * 7), PK_THREADS,
-                                 sizeof(PackSmem<PK_CAP_SMALL>), p->s>>>(a);
+    k_pack_mid<<<grid_for(a.n_lists, 1, p->num_sms * 7), PM_THREADS, sizeof(PackSmemMid),
+                 p->s>>>(a);
     ++p->stats.kernel_launches;
     k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
                            sizeof(PackSmem<PK_CAP>), p->s>>>(a);
