@@ -380,24 +380,25 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
         for (int pass = 0; pass < a.passes; ++pass) {
             const int sh = 8 * pass;
             const bool last = pass + 1 == a.passes;
-            // exclusive offsets over (digit, warp); thread t owns digits t, t+128
+            // exclusive offsets over (digit, warp); thread t owns digits 2t, 2t+1
+            const int d0 = 2 * threadIdx.x, d1 = d0 + 1;
             uint32_t c0 = 0, c1 = 0;
             for (int q = 0; q < PM_W; ++q) {
-                c0 += sm.hist[cur][q][threadIdx.x];
-                c1 += sm.hist[cur][q][threadIdx.x + 128];
+                c0 += sm.hist[cur][q][d0];
+                c1 += sm.hist[cur][q][d1];
             }
             if (threadIdx.x == 0) sm.skip = 0;
             __syncthreads();
             if (c0 == (uint32_t)n || c1 == (uint32_t)n) sm.skip = 1;
             uint32_t run = block_excl_scan128(c0 + c1, sm.wsum);
             for (int q = 0; q < PM_W; ++q) {
-                uint32_t c = sm.hist[cur][q][threadIdx.x];
-                sm.hist[cur][q][threadIdx.x] = run;
+                uint32_t c = sm.hist[cur][q][d0];
+                sm.hist[cur][q][d0] = run;
                 run += c;
             }
             for (int q = 0; q < PM_W; ++q) {
-                uint32_t c = sm.hist[cur][q][threadIdx.x + 128];
-                sm.hist[cur][q][threadIdx.x + 128] = run;
+                uint32_t c = sm.hist[cur][q][d1];
+                sm.hist[cur][q][d1] = run;
                 run += c;
             }
             for (int i = threadIdx.x; i < PM_W * 256; i += PM_THREADS)
