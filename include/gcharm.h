@@ -64,6 +64,7 @@ typedef struct gc_pool gc_pool_t;
 #define GC_ERR_TIMEOUT (-7)     /* wait or device-side poll ran out        */
 #define GC_ERR_CUDA (-8)        /* a CUDA runtime call failed              */
 #define GC_ERR_STATE (-9)       /* call not valid in the pool's state      */
+#define GC_ERR_TOO_LARGE (-10)  /* request exceeds a fixed size limit      */
 
 /* ---- task kinds -------------------------------------------------------- */
 #define GC_GRAVITY 0u
@@ -308,6 +309,41 @@ int gc_flush_per_task(gc_pool_t *pool);
  * with CUDA events on the pool's stream: {residency, pack, interaction,
  * scatter, total}.  Valid after gc_wait. */
 int gc_last_timings(gc_pool_t *pool, float ms_out[5]);
+
+/* ---- evaluation without allocation -------------------------------------- */
+
+/* Limits of gc_gravity_noalloc (its scratch is a fixed array). */
+#define GC_NOALLOC_MAX_TASKS 65536u
+#define GC_NOALLOC_MAX_TARGETS 262144u
+
+/* Softened gravity (the GC_GRAVITY terms) for n_tasks tasks whose values are
+ * already in device memory, without allocating anything: no cudaMalloc, no
+ * cudaFree, no allocating library call.  The paper has no counterpart; this
+ * is for callers that cannot allocate when they need the result -- code
+ * running during stream capture, code inside a framework whose allocator
+ * owns device memory, latency-critical threads that must not take the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ *   tgt_off, src_off : device, n_tasks + 1 offsets each, starting at 0 and
+ *                      not decreasing; tgt_off[n_tasks] must equal
+ *                      n_tgt_total (checked on the device: otherwise
+ *                      nothing is computed)
+ *   tgt_xyzm         : device, 4 floats per target (x, y, z, m), 16-byte aligned
+ *   src_xyzm         : device, 4 floats per source, 16-byte aligned
+ *   out_rows         : device, 8 floats per target, in target order: the
+ *                      compensated partial (s0..s3, c0..c3), value s - c =
+ *                      (ax, ay, az, phi)
+ *   cuda_stream      : cudaStream_t (NULL = legacy default stream)
+ * Scratch: one fixed file-scope device array of about 4.5 MiB, kept on
+ * every GPU that loads the library until the process exits; shared by all
+ * calls, which therefore race if they overlap on the GPU.  The first call
+ * on a device (with that device current) performs a one-time set-up
+ * (symbol lookup); make it before any stream capture.  Errors:
+ * GC_ERR_TOO_LARGE (n_tasks > GC_NOALLOC_MAX_TASKS or n_tgt_total >
+ * GC_NOALLOC_MAX_TARGETS), GC_ERR_ARG (eps2 <= 0, null or misaligned
+ * pointers), GC_ERR_CUDA.  Asynchronous: returns after queueing. */
+int gc_gravity_noalloc(uint64_t n_tasks, const uint64_t *tgt_off, const float *tgt_xyzm,
+                       const uint64_t *src_off, const float *src_xyzm, uint64_t n_tgt_total,
+                       float eps2, float *out_rows, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -196,6 +196,7 @@ const char *gc_strerror(int status)
     case GC_ERR_TIMEOUT: return "timeout";
     case GC_ERR_CUDA: return "CUDA error";
     case GC_ERR_STATE: return "invalid state";
+    case GC_ERR_TOO_LARGE: return "request exceeds a fixed size limit";
     default: return "unknown status";
     }
 }

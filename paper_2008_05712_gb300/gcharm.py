@@ -26,6 +26,9 @@ GC_ERR_NOT_READY = -6
 GC_ERR_TIMEOUT = -7
 GC_ERR_CUDA = -8
 GC_ERR_STATE = -9
+GC_ERR_TOO_LARGE = -10
+NOALLOC_MAX_TASKS = 65536
+NOALLOC_MAX_TARGETS = 262144
 
 GC_GRAVITY = 0
 GC_LJ_PAIR = 1
@@ -101,6 +104,7 @@ _SIGS = {
     "gc_build_md_tasks": [P, P, U64, C.c_int, U64, P],
     "gc_read_md_cells": [P, P, P],
     "gc_last_timings": [P, P],
+    "gc_gravity_noalloc": [U64, P, P, P, P, U64, C.c_float, P, P],
 }
 
 
@@ -375,3 +379,18 @@ class Pool:
 def value(res):
     """FP64 value s - c of result rows (rows, 8) -> (rows, 4)."""
     return res[:, :4].astype(np.float64) - res[:, 4:].astype(np.float64)
+
+
+def gravity_noalloc(tgt_off, tgt_xyzm, src_off, src_xyzm, n_tgt_total, eps2, out_rows,
+                    stream=None):
+    """Softened gravity of a CSR batch already in device memory, without any
+    allocation (for callers that cannot allocate at that point: stream
+    capture, foreign allocators, latency-critical threads).  All arguments
+    are CUDA tensors (offsets as 64-bit integers, values (n, 4) float32, out
+    (n_tgt_total, 8) float32); the call is queued on ``stream`` (a raw
+    cudaStream_t handle; None = the legacy default stream)."""
+    lib = load()
+    _check(lib.gc_gravity_noalloc(tgt_off.numel() - 1, _dptr(tgt_off), _dptr(tgt_xyzm),
+                                  _dptr(src_off), _dptr(src_xyzm), int(n_tgt_total),
+                                  float(eps2), _dptr(out_rows), stream),
+           "gc_gravity_noalloc")
