@@ -132,7 +132,6 @@ void free_pool(gc_pool *p)
                     &p->ekeys, &p->ekeys2, &p->evicted, &p->wu, &p->wu_cnt, &p->wu_off,
                     &p->rowcnt, &p->res, &p->row_id, &p->rid_sorted, &p->row_sorted,
                     &p->rows_tmp, &p->runs, &p->merge_a, &p->merge_b, &p->cub_tmp, &p->small,
-                    &p->pack_flags,
                     &p->nb.keys, &p->nb.keys2, &p->nb.ids, &p->nb.ids2, &p->nb.lcp, &p->nb.win,
                     &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a, &p->nb.node_b,
                     &p->nb.node_val, &p->nb.bucket, &p->nb.bbox, &p->nb.list_off,

@@ -124,7 +124,7 @@ struct gc_pool {
     DBuf tgt_perm, src_perm, stg_tgt, stg_src;
     DBuf uniq, miss, freel, tiles, ekeys, ekeys2, evicted;
     DBuf wu, wu_cnt, wu_off, rowcnt, res, row_id, rid_sorted, row_sorted, rows_tmp;
-    DBuf runs, merge_a, merge_b, cub_tmp, small, pack_flags;
+    DBuf runs, merge_a, merge_b, cub_tmp, small;
     uint64_t n_evicted_last = 0;
     uint32_t epoch = 0;
 

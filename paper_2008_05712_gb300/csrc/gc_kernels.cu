@@ -138,7 +138,6 @@ struct PackArgs {
     uint64_t *ma, *mb;                   // merge scratch: targets at the wave-local
     uint64_t msrc;                       // target index, sources at msrc + local index
     int passes;                          // radix passes of 8 bits over the slot
-    uint8_t *fallback;                   // per list: 1 = left to the radix kernel
 };
 
 struct PackList {
@@ -310,216 +309,6 @@ __device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
     return flip;
 }
 
-// Lists of 33..PB_CAP entries, fast path: the keys (slot << 32 | pos) are
-// unique, so no stable passes are needed.  One pass distributes the keys
-// over B ~ 2n buckets by a monotone map of the slot onto the list's own
-// [min, max] slot range (shared-memory atomics, arrival order irrelevant),
-// then every bucket -- a handful of keys -- is insertion-sorted by the full
-// key by one thread.  The concatenation of the buckets is the unique sorted
-// order.  A list with a bucket larger than PB_BUCKET_MAX is flagged for the
-// radix kernel instead.
-constexpr int PB_CAP = 2048;
-constexpr int PB_THREADS = 256;
-constexpr int PB_BMAX = 4096;
-constexpr uint32_t PB_THREAD_MAX = 16;    // buckets up to this size: one thread
-constexpr uint32_t PB_BUCKET_MAX = 256;   // larger buckets: one warp; beyond: radix
-constexpr int PB_BIG_MAX = 64;            // warp-sorted buckets per list
-
-struct PackSmemBucket {
-    uint64_t K[PB_CAP], K2[PB_CAP];
-    uint32_t cnt[PB_BMAX + 1];
-    uint32_t red[3][PB_THREADS / 32];
-    uint32_t big[PB_BIG_MAX];
-    uint32_t n_big;
-};
-
-// Bitonic sort of 32*R keys held R per lane (lane-major: key e = lane*R + r),
-// ascending.
-template <int R>
-__device__ __forceinline__ void warp_bitonic(uint64_t (&v)[R])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= 32 * R; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= R) {
-                const int lm = j / R;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int e = lane * R + r;
-                    const uint64_t o = __shfl_xor_sync(0xffffffffu, v[r], lm);
-                    const bool up = (e & k) == 0;
-                    const bool lower = (lane & lm) == 0;
-                    const uint64_t lo = v[r] < o ? v[r] : o, hi = v[r] < o ? o : v[r];
-                    v[r] = (lower == up) ? lo : hi;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int rp = r ^ j;
-                    if (rp > r) {
-                        const bool up = ((lane * R + r) & k) == 0;
-                        const uint64_t x = v[r], y = v[rp];
-                        const bool sw = (x > y) == up;
-                        v[r] = sw ? y : x;
-                        v[rp] = sw ? x : y;
-                    }
-                }
-            }
-        }
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void warp_sort_segment(uint64_t *seg, uint32_t m)
-{
-    const int lane = threadIdx.x & 31;
-    uint64_t v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t e = (uint32_t)(lane * R + r);
-        v[r] = e < m ? seg[e] : ~0ull;
-    }
-    warp_bitonic<R>(v);
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t e = (uint32_t)(lane * R + r);
-        if (e < m) seg[e] = v[r];
-    }
-    __syncwarp();
-}
-
-__global__ void __launch_bounds__(PB_THREADS) k_pack_bucket(PackArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    PackSmemBucket &sm = *reinterpret_cast<PackSmemBucket *>(smem_raw);
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
-        const PackList l = list_of(a, L);
-        if (l.n <= 32 || l.n > (uint32_t)PB_CAP) continue;
-        const int n = (int)l.n;
-        int B = 64;
-        while (B < 2 * n && B < PB_BMAX) B <<= 1;
-        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
-        uint32_t mn = 0xFFFFFFFFu, mx = 0u;
-        for (int k = tid; k < n; k += PB_THREADS) {
-            const uint32_t s = a.slot_of_id[ids[k]];
-            sm.K[k] = ((uint64_t)s << 32) | (uint64_t)k;
-            mn = min(mn, s);
-            mx = max(mx, s);
-        }
-        for (int i = tid; i <= B; i += PB_THREADS) sm.cnt[i] = 0u;
-        if (tid == 0) sm.n_big = 0u;
-        for (int o = 16; o; o >>= 1) {
-            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if (lane == 0) {
-            sm.red[0][w] = mn;
-            sm.red[1][w] = mx;
-        }
-        __syncthreads();
-        mn = sm.red[0][0];
-        mx = sm.red[1][0];
-        for (int q = 1; q < PB_THREADS / 32; ++q) {
-            mn = min(mn, sm.red[0][q]);
-            mx = max(mx, sm.red[1][q]);
-        }
-        const float scale = (float)B / ((float)(mx - mn) + 1.0f);
-        const uint32_t bmax = (uint32_t)B - 1u;
-        for (int k = tid; k < n; k += PB_THREADS) {
-            const uint32_t s = (uint32_t)(sm.K[k] >> 32);
-            const uint32_t b = min(bmax, (uint32_t)((float)(s - mn) * scale));
-            atomicAdd(&sm.cnt[b], 1u);
-        }
-        __syncthreads();
-        // exclusive scan of the B counts (contiguous runs per thread) and the
-        // largest bucket
-        const int per = (B + PB_THREADS - 1) / PB_THREADS;
-        const int c0 = min(B, tid * per), c1 = min(B, c0 + per);
-        uint32_t sum = 0, big = 0;
-        for (int i = c0; i < c1; ++i) {
-            sum += sm.cnt[i];
-            big = max(big, sm.cnt[i]);
-        }
-        uint32_t x = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        for (int o = 16; o; o >>= 1) big = max(big, __shfl_xor_sync(0xffffffffu, big, o));
-        if (lane == 31) sm.red[2][w] = x;
-        if (lane == 0) sm.red[0][w] = big;
-        __syncthreads();
-        uint32_t before = 0;
-        big = 0;
-        for (int q = 0; q < PB_THREADS / 32; ++q) {
-            if (q < w) before += sm.red[2][q];
-            big = max(big, sm.red[0][q]);
-        }
-        if (big > PB_BUCKET_MAX) {               // uniform across the block
-            if (tid == 0) a.fallback[L] = 1;
-            __syncthreads();
-            continue;
-        }
-        uint32_t run = before + x - sum;
-        for (int i = c0; i < c1; ++i) {
-            const uint32_t c = sm.cnt[i];
-            sm.cnt[i] = run;
-            run += c;
-        }
-        __syncthreads();
-        for (int k = tid; k < n; k += PB_THREADS) {
-            const uint64_t key = sm.K[k];
-            const uint32_t s = (uint32_t)(key >> 32);
-            const uint32_t b = min(bmax, (uint32_t)((float)(s - mn) * scale));
-            sm.K2[atomicAdd(&sm.cnt[b], 1u)] = key;
-        }
-        __syncthreads();
-        // after the scatter cnt[b] is the end of bucket b; small buckets are
-        // insertion-sorted by one thread, larger ones queued for a warp
-        for (int b = tid; b < B; b += PB_THREADS) {
-            const uint32_t lo = b ? sm.cnt[b - 1] : 0u, hi = sm.cnt[b];
-            if (hi - lo > PB_THREAD_MAX) {
-                const uint32_t at = atomicAdd(&sm.n_big, 1u);
-                if (at < (uint32_t)PB_BIG_MAX) sm.big[at] = (uint32_t)b;
-                continue;
-            }
-            for (uint32_t i = lo + 1; i < hi; ++i) {
-                const uint64_t v = sm.K2[i];
-                uint32_t j = i;
-                while (j > lo && sm.K2[j - 1] > v) {
-                    sm.K2[j] = sm.K2[j - 1];
-                    --j;
-                }
-                sm.K2[j] = v;
-            }
-        }
-        __syncthreads();
-        if (sm.n_big > (uint32_t)PB_BIG_MAX) {   // uniform across the block
-            if (tid == 0) a.fallback[L] = 1;
-            __syncthreads();
-            continue;
-        }
-        for (uint32_t q = (uint32_t)w; q < sm.n_big; q += PB_THREADS / 32) {
-            const uint32_t b = sm.big[q];
-            const uint32_t lo = b ? sm.cnt[b - 1] : 0u, hi = sm.cnt[b];
-            if (hi - lo <= 64)
-                warp_sort_segment<2>(sm.K2 + lo, hi - lo);
-            else
-                warp_sort_segment<8>(sm.K2 + lo, hi - lo);
-        }
-        __syncthreads();
-        for (int k = tid; k < n; k += PB_THREADS)
-            emit(a, l, (uint32_t)k, (uint32_t)(sm.K2[k] >> 32),
-                 (uint32_t)(sm.K2[k] & 0xFFFFFFFFu));
-        if (tid == 0) a.fallback[L] = 0;
-        __syncthreads();
-    }
-}
-
 // Lists of 33..PM_CAP entries: one block of 4 warps per list, LSD radix
 // sort of (slot, pos) with 8-bit digits.  Warp w owns a contiguous range of
 // the current layout; within a warp, 32 items at a time are ranked among
@@ -530,6 +319,7 @@ __global__ void __launch_bounds__(PB_THREADS) k_pack_bucket(PackArgs a)
 constexpr int PM_CAP = 2048;
 constexpr int PM_THREADS = 128;
 constexpr int PM_W = PM_THREADS / 32;
+static_assert(PM_W == 4, "the destination-warp test below assumes four warps");
 
 struct PackSmemMid {
     uint32_t ka[PM_CAP], kb[PM_CAP];
@@ -563,7 +353,7 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
     const uint32_t lt = (1u << lane) - 1u;
     for (uint64_t L = blockIdx.x; L < a.n_lists; L += gridDim.x) {
         const PackList l = list_of(a, L);
-        if (l.n <= 32 || l.n > (uint32_t)PM_CAP || !a.fallback[L]) continue;
+        if (l.n <= 32 || l.n > (uint32_t)PM_CAP) continue;
         const int n = (int)l.n;
         const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
         const int per = (((n + PM_W - 1) / PM_W) + 31) & ~31;
@@ -634,7 +424,8 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
                 }
                 if (!last) {
                     // next pass: count (warp range of dst, next digit)
-                    const uint32_t wd = (uint32_t)(dst / per);
+                    const uint32_t wd = (uint32_t)(dst >= per) + (uint32_t)(dst >= 2 * per) +
+                                        (uint32_t)(dst >= 3 * per);
                     const uint32_t d2 = v ? wd * 256u + ((key >> (sh + 8)) & 255u)
                                           : 4096u + (uint32_t)lane;
                     const uint32_t m2 = __match_any_sync(0xffffffffu, d2);
@@ -1186,9 +977,7 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
                                          (int)sizeof(PackSmem<PK_CAP>)));
         GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_mid, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(PackSmemMid)));
-        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_bucket,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PackSmemBucket)));
+
         attr_set = true;
     }
     PackArgs a;
@@ -1212,15 +1001,11 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
     a.ma = p->merge_a.as<uint64_t>();
     a.mb = p->merge_b.as<uint64_t>();
     a.msrc = msrc;
-    GC_TRY(p->pack_flags.reserve(a.n_lists + 16));
-    a.fallback = p->pack_flags.as<uint8_t>();
+
     ++p->stats.kernel_launches;
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, p->s>>>(a);
     ++p->stats.kernel_launches;
-    k_pack_bucket<<<grid_for(a.n_lists, 1, p->num_sms * 4), PB_THREADS,
-                    sizeof(PackSmemBucket), p->s>>>(a);
-    ++p->stats.kernel_launches;
-    k_pack_mid<<<grid_for(a.n_lists, 1, p->num_sms * 7), PM_THREADS, sizeof(PackSmemMid),
+    k_pack_mid<<<grid_for(a.n_lists, 1, p->num_sms * 8), PM_THREADS, sizeof(PackSmemMid),
                  p->s>>>(a);
     ++p->stats.kernel_launches;
     k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,

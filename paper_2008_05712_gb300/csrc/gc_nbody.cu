@@ -25,6 +25,7 @@
 // The walk visits nodes in preorder with skips (no stack): an accepted or
 // leaf node continues at k + size(k), an opened internal node at k + 1.
 #include <cub/device/device_scan.cuh>
+#include <climits>
 
 #include "gc_common.cuh"
 
@@ -284,46 +285,88 @@ __global__ void k_emit_buckets(const uint4 *node_a, uint64_t nn, const uint32_t 
     }
 }
 
-// Stackless preorder walk.  FILL = false: count list entries; true: write them.
+// Acceptance thresholds per level: a node of edge s (doubled units) is
+// accepted iff td^2 s^2 < tn^2 d^2, i.e. (integers, tn > 0) iff
+// d^2 > floor(td^2 s^2 / tn^2); with tn = 0 nothing is accepted.
+struct WalkThresholds {
+    int64_t t[22];
+};
+
+// Stackless preorder walk.  FILL = false: count list entries; true: write
+// them.  Each step loads both possible successors of the current node (the
+// next node in preorder and the node after its subtree) ahead of the
+// decision, so the dependent chain per visited node is one decision.
 template <bool FILL>
 __global__ void k_walk(const uint4 *node_a, const uint4 *node_b, uint32_t nn,
                        const uint4 *bucket, const int4 *blo, const int4 *bhi, uint64_t nb,
-                       const uint32_t *sorted_ids, uint32_t n_part, int64_t tn2, int64_t td2,
+                       const uint32_t *sorted_ids, uint32_t n_part, WalkThresholds th,
                        uint32_t *len, const uint64_t *off, uint32_t *out)
 {
     GRID_STRIDE(b, nb) {
-        uint32_t bf = bucket[b].x;
-        int4 lo = blo[b], hi = bhi[b];
+        const uint32_t bf = bucket[b].x;
+        const int4 lo = blo[b], hi = bhi[b];
         uint32_t cnt = 0;
         uint32_t *o = FILL ? out + off[b] : nullptr;
         uint32_t k = 0;
+        uint4 A = node_a[0], C = node_b[0];
         while (k < nn) {
-            uint4 A = node_a[k];
-            bool contains = (A.x <= bf) && (bf < A.x + A.y);
+            // prefetch both successors
+            const uint32_t k_open = k + 1, k_skip = k + A.z;
+            uint4 An = make_uint4(0, 0, 1, 0), Cn = make_uint4(0, 0, 0, 0);
+            uint4 As = An, Cs = Cn;
+            if (k_open < nn) {
+                An = node_a[k_open];
+                Cn = node_b[k_open];
+            }
+            if (k_skip == k_open) {
+                As = An;
+                Cs = Cn;
+            } else if (k_skip < nn) {
+                As = node_a[k_skip];
+                Cs = node_b[k_skip];
+            }
+            const bool contains = (A.x <= bf) && (bf < A.x + A.y);
+            bool skip = false;
             if (!contains) {
-                uint4 C = node_b[k];
-                int lvl = (int)(A.w & 255u);
-                int64_t s = (int64_t)1 << (22 - lvl);
-                int64_t h = s >> 1;
-                int64_t cx = (int64_t)C.x * s + h, cy = (int64_t)C.y * s + h,
-                        cz = (int64_t)C.z * s + h;
-                int64_t dx = max((int64_t)0, max((int64_t)lo.x - cx, cx - (int64_t)hi.x));
-                int64_t dy = max((int64_t)0, max((int64_t)lo.y - cy, cy - (int64_t)hi.y));
-                int64_t dz = max((int64_t)0, max((int64_t)lo.z - cz, cz - (int64_t)hi.z));
-                int64_t d2 = dx * dx + dy * dy + dz * dz;
-                if (td2 * s * s < tn2 * d2) {
+                const int lvl = (int)(A.w & 255u);
+                const int s = 1 << (22 - lvl), h = s >> 1;
+                const int cx = (int)C.x * s + h, cy = (int)C.y * s + h, cz = (int)C.z * s + h;
+                const uint32_t dx = (uint32_t)max(0, max(lo.x - cx, cx - hi.x));
+                const uint32_t dy = (uint32_t)max(0, max(lo.y - cy, cy - hi.y));
+                const uint32_t dz = (uint32_t)max(0, max(lo.z - cz, cz - hi.z));
+                const uint64_t d2 = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
+                if ((int64_t)d2 > th.t[lvl]) {
                     if (FILL) o[cnt] = n_part + k;
                     ++cnt;
-                    k += A.z;
-                    continue;
+                    skip = true;
                 }
             }
-            if (A.w & 256u) {
-                if (FILL)
-                    for (uint32_t q = 0; q < A.y; ++q) o[cnt + q] = sorted_ids[A.x + q];
+            if (!skip && (A.w & 256u)) {
+                if (FILL) {
+                    const uint32_t *src = sorted_ids + A.x;
+                    uint32_t *dst = o + cnt;
+                    uint32_t q = 0;
+                    for (; q + 4 <= A.y; q += 4) {
+                        const uint32_t v0 = src[q], v1 = src[q + 1], v2 = src[q + 2], v3 = src[q + 3];
+                        dst[q] = v0;
+                        dst[q + 1] = v1;
+                        dst[q + 2] = v2;
+                        dst[q + 3] = v3;
+                    }
+                    for (; q < A.y; ++q) dst[q] = src[q];
+                }
                 cnt += A.y;
+                skip = true;   // a leaf's subtree is itself
             }
-            k += 1;
+            if (skip) {
+                k = k_skip;
+                A = As;
+                C = Cs;
+            } else {
+                k = k_open;
+                A = An;
+                C = Cn;
+            }
         }
         if (!FILL) len[b] = cnt;
     }
@@ -463,10 +506,15 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     uint64_t *llen64 = S.list_off.as<uint64_t>();
     uint64_t *loff = llen64 + (NB + 1);
     const int64_t tn2 = (int64_t)theta_num * theta_num, td2 = (int64_t)theta_den * theta_den;
+    WalkThresholds th;
+    for (int l = 0; l < 22; ++l) {
+        const int64_t sz = (int64_t)1 << (22 - l);
+        th.t[l] = tn2 ? (td2 * sz * sz) / tn2 : INT64_MAX;
+    }
     ++p->stats.kernel_launches;
     k_walk<false><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
-        (uint32_t)n, tn2, td2, llen, nullptr, nullptr);
+        (uint32_t)n, th, llen, nullptr, nullptr);
     GC_CUDA_TRY(cudaMemsetAsync(llen + NB, 0, 4, s));
     ++p->stats.kernel_launches;
     k_u32_to_u64<<<grid_for(NB + 1, 256, maxb), 256, 0, s>>>(llen, llen64, (uint64_t)NB + 1);
@@ -485,7 +533,7 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     ++p->stats.kernel_launches;
     k_walk<true><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
-        (uint32_t)n, tn2, td2, nullptr, loff, ds);
+        (uint32_t)n, th, nullptr, loff, ds);
     GC_CUDA_TRY(cudaMemcpyAsync(dt, sid, n * 4, cudaMemcpyDeviceToDevice, s));
     ++p->stats.kernel_launches;
     k_nbody_tasks<<<grid_for(NB, 256, maxb), 256, 0, s>>>(S.bucket.as<uint4>(), NB, loff, llen,
