@@ -310,6 +310,49 @@ int gc_flush_per_task(gc_pool_t *pool);
  * scatter, total}.  Valid after gc_wait. */
 int gc_last_timings(gc_pool_t *pool, float ms_out[5]);
 
+/* ---- combining policy (Section 3.1, Section 4.3) ------------------------- */
+
+#define GC_COMBINE_ADAPTIVE 0        /* paper's rule: maxSize, 2 x running-max interval */
+#define GC_COMBINE_ADAPTIVE_WINDOW 1 /* same, max over the last `window` intervals      */
+#define GC_COMBINE_STATIC 2          /* paper's baseline: all pending every static_n
+                                        arrivals (100 in Section 4.3)                    */
+#define GC_COMBINE_PER_TASK 3        /* no combining: one task per batch                */
+
+typedef struct gc_combiner gc_combiner_t;
+
+/* Decide when pending work requests are combined into a batch (Section
+ * 3.1): maxSize = requests one combined launch runs at full occupancy;
+ * maxInterval = running maximum of the intervals between arrivals; at each
+ * poll, with >= maxSize pending combine maxSize, otherwise combine all
+ * pending once the time since the last arrival exceeds 2 x maxInterval.
+ * GC_COMBINE_STATIC combines all pending after every static_n arrivals
+ * (the paper's static strategy, Section 4.3).  Host-side, no device work.
+ * Errors: GC_ERR_ARG (unknown policy, max_size 0 for the adaptive rules,
+ * static_n 0 for the static rule, window 0 for the windowed rule). */
+int gc_combiner_create(int policy, uint64_t max_size, uint64_t static_n, uint64_t window,
+                       gc_combiner_t **out);
+int gc_combiner_destroy(gc_combiner_t *c);
+
+/* Record `count` requests arriving at time t_ns (monotonic nanoseconds). */
+int gc_combiner_arrive(gc_combiner_t *c, uint64_t t_ns, uint64_t count);
+
+/* At time t_ns with `queued` requests pending: *take_out = how many to
+ * combine now (0 = keep waiting), oldest first. */
+int gc_combiner_poll(gc_combiner_t *c, uint64_t t_ns, uint64_t queued, uint64_t *take_out);
+
+/* Current maxInterval in nanoseconds. */
+int gc_combiner_max_interval(gc_combiner_t *c, uint64_t *ns_out);
+
+/* maxSize from an occupancy figure (Section 4.3): round(occupancy x
+ * max_blocks_per_sm) x n_sm -- one work request per resident block. */
+uint64_t gc_combine_size_from_occupancy(double occupancy, uint32_t max_blocks_per_sm,
+                                        uint32_t n_sm);
+
+/* maxSize of this engine on this GPU: work units (one per warp) the gravity
+ * kernel keeps resident at once, from cudaOccupancyMaxActiveBlocksPerMultiprocessor
+ * x warps per block x SMs. */
+int gc_max_combine_size(gc_pool_t *pool, uint64_t *out);
+
 /* ---- evaluation without allocation -------------------------------------- */
 
 /* Limits of gc_gravity_noalloc (its scratch is a fixed array). */

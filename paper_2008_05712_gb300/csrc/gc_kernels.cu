@@ -1067,6 +1067,13 @@ int gc_grav_blocks(gc_pool *p)
     return per_sm * p->num_sms;
 }
 
+extern "C" int gc_max_combine_size(gc_pool_t *p, uint64_t *out)
+{
+    if (!p || !out) return GC_ERR_ARG;
+    *out = (uint64_t)gc_grav_blocks(p) * (uint64_t)GRAV_WARPS;
+    return GC_OK;
+}
+
 // Launch the interaction kernels over gravity work units [w0, w1) and LJ
 // tasks [l0, l1) of the prepared batch.
 int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,

@@ -34,6 +34,11 @@ GC_GRAVITY = 0
 GC_LJ_PAIR = 1
 GC_LJ_SELF = 2
 
+GC_COMBINE_ADAPTIVE = 0
+GC_COMBINE_ADAPTIVE_WINDOW = 1
+GC_COMBINE_STATIC = 2
+GC_COMBINE_PER_TASK = 3
+
 NONE32 = 0xFFFFFFFF
 
 
@@ -105,7 +110,16 @@ _SIGS = {
     "gc_read_md_cells": [P, P, P],
     "gc_last_timings": [P, P],
     "gc_gravity_noalloc": [U64, P, P, P, P, U64, C.c_float, P, P],
+    "gc_combiner_create": [C.c_int, U64, U64, U64, C.POINTER(P)],
+    "gc_combiner_destroy": [P],
+    "gc_combiner_arrive": [P, U64, U64],
+    "gc_combiner_poll": [P, U64, U64, U64P],
+    "gc_combiner_max_interval": [P, U64P],
+    "gc_combine_size_from_occupancy": [C.c_double, C.c_uint32, C.c_uint32],
+    "gc_max_combine_size": [P, U64P],
 }
+
+_RESTYPES = {"gc_strerror": C.c_char_p, "gc_combine_size_from_occupancy": C.c_uint64}
 
 
 def exported_symbols():
@@ -124,7 +138,7 @@ def load(path: str = LIB_PATH):
     for name, args in _SIGS.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = C.c_char_p if name == "gc_strerror" else C.c_int
+        fn.restype = _RESTYPES.get(name, C.c_int)
     _lib = lib
     return lib
 
@@ -285,6 +299,11 @@ class Pool:
         d["primitive_calls"] = s.primitive_calls
         return d
 
+    def max_combine_size(self):
+        v = C.c_uint64()
+        _check(self.lib.gc_max_combine_size(self.h, C.byref(v)), "gc_max_combine_size")
+        return v.value
+
     def timings(self):
         ms = np.zeros(5, np.float32)
         _check(self.lib.gc_last_timings(self.h, _p(ms)), "gc_last_timings")
@@ -394,3 +413,44 @@ def gravity_noalloc(tgt_off, tgt_xyzm, src_off, src_xyzm, n_tgt_total, eps2, out
                                   _dptr(src_off), _dptr(src_xyzm), int(n_tgt_total),
                                   float(eps2), _dptr(out_rows), stream),
            "gc_gravity_noalloc")
+
+
+class Combiner:
+    """The combining policy of Section 3.1 (host-side; times in ns)."""
+
+    def __init__(self, policy, max_size=0, static_n=0, window=0):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.gc_combiner_create(policy, max_size, static_n, window, C.byref(h)),
+               "gc_combiner_create")
+        self.h, self.lib = h, lib
+
+    def arrive(self, t_ns, count=1):
+        _check(self.lib.gc_combiner_arrive(self.h, int(t_ns), int(count)), "gc_combiner_arrive")
+
+    def poll(self, t_ns, queued):
+        v = C.c_uint64()
+        _check(self.lib.gc_combiner_poll(self.h, int(t_ns), int(queued), C.byref(v)),
+               "gc_combiner_poll")
+        return v.value
+
+    def max_interval(self):
+        v = C.c_uint64()
+        _check(self.lib.gc_combiner_max_interval(self.h, C.byref(v)), "gc_combiner_max_interval")
+        return v.value
+
+    def close(self):
+        if self.h:
+            self.lib.gc_combiner_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def combine_size_from_occupancy(occupancy, max_blocks_per_sm, n_sm):
+    return load().gc_combine_size_from_occupancy(float(occupancy), int(max_blocks_per_sm),
+                                                 int(n_sm))
