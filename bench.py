@@ -353,6 +353,8 @@ def main():
             "cpu_baseline": cpu,
         }
         line["config"]["tasks_per_step"] = int(s1["tasks"] - s0["tasks"]) // max(K, 1)
+        line["config"]["interactions_per_step"] = int(interactions) // max(K, 1)
+        line["config"]["list_entries_per_step"] = int(s1["entries"] - s0["entries"]) // max(K, 1)
         print(json.dumps(line), flush=True)
     pool.close()
     if ws > 1:

@@ -285,6 +285,8 @@ __global__ void k_emit_buckets(const uint4 *node_a, uint64_t nn, const uint32_t 
     }
 }
 
+constexpr int WALK_ITEMS = 8;   // independent sub-walks per bucket
+
 // Acceptance thresholds per level: a node of edge s (doubled units) is
 // accepted iff td^2 s^2 < tn^2 d^2, i.e. (integers, tn > 0) iff
 // d^2 > floor(td^2 s^2 / tn^2); with tn = 0 nothing is accepted.
@@ -292,83 +294,124 @@ struct WalkThresholds {
     int64_t t[22];
 };
 
-// Stackless preorder walk.  FILL = false: count list entries; true: write
-// them.  Each step loads both possible successors of the current node (the
-// next node in preorder and the node after its subtree) ahead of the
-// decision, so the dependent chain per visited node is one decision.
+// Stackless preorder walk of one preorder range [k0, k_end) for one bucket.
+// FILL = false: count list entries; true: write them.  Each step loads both
+// possible successors of the current node (the next node in preorder and the
+// node after its subtree) ahead of the decision, so the dependent chain per
+// visited node is one decision.
 template <bool FILL>
-__global__ void k_walk(const uint4 *node_a, const uint4 *node_b, uint32_t nn,
-                       const uint4 *bucket, const int4 *blo, const int4 *bhi, uint64_t nb,
-                       const uint32_t *sorted_ids, uint32_t n_part, WalkThresholds th,
-                       uint32_t *len, const uint64_t *off, uint32_t *out)
+__device__ __forceinline__ uint32_t walk_range(const uint4 *node_a, const uint4 *node_b,
+                                               uint32_t k0, uint32_t k_end, uint32_t bf,
+                                               int4 lo, int4 hi, const uint32_t *sorted_ids,
+                                               uint32_t n_part, const WalkThresholds &th,
+                                               uint32_t *o)
 {
-    GRID_STRIDE(b, nb) {
-        const uint32_t bf = bucket[b].x;
-        const int4 lo = blo[b], hi = bhi[b];
-        uint32_t cnt = 0;
-        uint32_t *o = FILL ? out + off[b] : nullptr;
-        uint32_t k = 0;
-        uint4 A = node_a[0], C = node_b[0];
-        while (k < nn) {
-            // prefetch both successors
-            const uint32_t k_open = k + 1, k_skip = k + A.z;
-            uint4 An = make_uint4(0, 0, 1, 0), Cn = make_uint4(0, 0, 0, 0);
-            uint4 As = An, Cs = Cn;
-            if (k_open < nn) {
-                An = node_a[k_open];
-                Cn = node_b[k_open];
-            }
-            if (k_skip == k_open) {
-                As = An;
-                Cs = Cn;
-            } else if (k_skip < nn) {
-                As = node_a[k_skip];
-                Cs = node_b[k_skip];
-            }
-            const bool contains = (A.x <= bf) && (bf < A.x + A.y);
-            bool skip = false;
-            if (!contains) {
-                const int lvl = (int)(A.w & 255u);
-                const int s = 1 << (22 - lvl), h = s >> 1;
-                const int cx = (int)C.x * s + h, cy = (int)C.y * s + h, cz = (int)C.z * s + h;
-                const uint32_t dx = (uint32_t)max(0, max(lo.x - cx, cx - hi.x));
-                const uint32_t dy = (uint32_t)max(0, max(lo.y - cy, cy - hi.y));
-                const uint32_t dz = (uint32_t)max(0, max(lo.z - cz, cz - hi.z));
-                const uint64_t d2 = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
-                if ((int64_t)d2 > th.t[lvl]) {
-                    if (FILL) o[cnt] = n_part + k;
-                    ++cnt;
-                    skip = true;
-                }
-            }
-            if (!skip && (A.w & 256u)) {
-                if (FILL) {
-                    const uint32_t *src = sorted_ids + A.x;
-                    uint32_t *dst = o + cnt;
-                    uint32_t q = 0;
-                    for (; q + 4 <= A.y; q += 4) {
-                        const uint32_t v0 = src[q], v1 = src[q + 1], v2 = src[q + 2], v3 = src[q + 3];
-                        dst[q] = v0;
-                        dst[q + 1] = v1;
-                        dst[q + 2] = v2;
-                        dst[q + 3] = v3;
-                    }
-                    for (; q < A.y; ++q) dst[q] = src[q];
-                }
-                cnt += A.y;
-                skip = true;   // a leaf's subtree is itself
-            }
-            if (skip) {
-                k = k_skip;
-                A = As;
-                C = Cs;
-            } else {
-                k = k_open;
-                A = An;
-                C = Cn;
+    uint32_t cnt = 0;
+    uint32_t k = k0;
+    uint4 A = node_a[k0], C = node_b[k0];
+    while (k < k_end) {
+        const uint32_t k_open = k + 1, k_skip = k + A.z;
+        uint4 An = make_uint4(0, 0, 1, 0), Cn = make_uint4(0, 0, 0, 0);
+        uint4 As = An, Cs = Cn;
+        if (k_open < k_end) {
+            An = node_a[k_open];
+            Cn = node_b[k_open];
+        }
+        if (k_skip == k_open) {
+            As = An;
+            Cs = Cn;
+        } else if (k_skip < k_end) {
+            As = node_a[k_skip];
+            Cs = node_b[k_skip];
+        }
+        const bool contains = (A.x <= bf) && (bf < A.x + A.y);
+        bool skip = false;
+        if (!contains) {
+            const int lvl = (int)(A.w & 255u);
+            const int s = 1 << (22 - lvl), h = s >> 1;
+            const int cx = (int)C.x * s + h, cy = (int)C.y * s + h, cz = (int)C.z * s + h;
+            const uint32_t dx = (uint32_t)max(0, max(lo.x - cx, cx - hi.x));
+            const uint32_t dy = (uint32_t)max(0, max(lo.y - cy, cy - hi.y));
+            const uint32_t dz = (uint32_t)max(0, max(lo.z - cz, cz - hi.z));
+            const uint64_t d2 = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
+            if ((int64_t)d2 > th.t[lvl]) {
+                if (FILL) o[cnt] = n_part + k;
+                ++cnt;
+                skip = true;
             }
         }
-        if (!FILL) len[b] = cnt;
+        if (!skip && (A.w & 256u)) {
+            if (FILL) {
+                const uint32_t *src = sorted_ids + A.x;
+                uint32_t *dst = o + cnt;
+                uint32_t q = 0;
+                for (; q + 4 <= A.y; q += 4) {
+                    const uint32_t v0 = src[q], v1 = src[q + 1], v2 = src[q + 2], v3 = src[q + 3];
+                    dst[q] = v0;
+                    dst[q + 1] = v1;
+                    dst[q + 2] = v2;
+                    dst[q + 3] = v3;
+                }
+                for (; q < A.y; ++q) dst[q] = src[q];
+            }
+            cnt += A.y;
+            skip = true;   // a leaf's subtree is itself
+        }
+        if (skip) {
+            k = k_skip;
+            A = As;
+            C = Cs;
+        } else {
+            k = k_open;
+            A = An;
+            C = Cn;
+        }
+    }
+    return cnt;
+}
+
+// Preorder ranges of the walk items: the subtrees of the root's children in
+// octant order (the root always contains the bucket and is opened), or the
+// whole tree when the root is a leaf.  The lists of the items, concatenated
+// in item order, are the depth-first list.
+__global__ void k_walk_items(const uint4 *node_a, uint32_t nn, uint32_t *item_lo,
+                             uint32_t *item_hi)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint4 root = node_a[0];
+    for (int j = 0; j < WALK_ITEMS; ++j) item_lo[j] = item_hi[j] = 0;
+    if (root.w & 256u) {
+        item_lo[0] = 0;
+        item_hi[0] = nn;
+        return;
+    }
+    uint32_t k = 1;
+    int j = 0;
+    while (k < root.z && j < WALK_ITEMS) {
+        item_lo[j] = k;
+        item_hi[j] = k + node_a[k].z;
+        k = item_hi[j];
+        ++j;
+    }
+}
+
+// One thread per (bucket, item); items of a bucket are adjacent.
+template <bool FILL>
+__global__ void k_walk(const uint4 *node_a, const uint4 *node_b, const uint32_t *item_lo,
+                       const uint32_t *item_hi, const uint4 *bucket, const int4 *blo,
+                       const int4 *bhi, uint64_t nb, const uint32_t *sorted_ids,
+                       uint32_t n_part, WalkThresholds th, uint32_t *len, const uint64_t *off,
+                       uint32_t *out)
+{
+    GRID_STRIDE(it, nb * WALK_ITEMS) {
+        const uint64_t b = it / WALK_ITEMS;
+        const int j = (int)(it % WALK_ITEMS);
+        const uint32_t k0 = item_lo[j], k1 = item_hi[j];
+        uint32_t cnt = 0;
+        if (k1 > k0)
+            cnt = walk_range<FILL>(node_a, node_b, k0, k1, bucket[b].x, blo[b], bhi[b],
+                                   sorted_ids, n_part, th, FILL ? out + off[it] : nullptr);
+        if (!FILL) len[it] = cnt;
     }
 }
 
@@ -377,9 +420,20 @@ __global__ void k_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n)
     GRID_STRIDE(i, n) out[i] = in[i];
 }
 
+// per-bucket list offsets from the per-item offsets (items of a bucket are
+// adjacent); also the per-bucket lengths
+__global__ void k_bucket_offsets(const uint64_t *ioff, uint64_t nb, uint64_t *loff,
+                                 uint64_t *blen)
+{
+    GRID_STRIDE(b, nb + 1) {
+        loff[b] = ioff[b * WALK_ITEMS];
+        if (b < nb) blen[b] = ioff[(b + 1) * WALK_ITEMS] - ioff[b * WALK_ITEMS];
+    }
+}
+
 __global__ void k_nbody_tasks(const uint4 *bucket, uint64_t nb, const uint64_t *list_off,
-                              const uint32_t *list_len, uint64_t tgt_base, uint64_t src_base,
-                              uint64_t id_base, TaskRec *out)
+                              uint64_t tgt_base, uint64_t src_base, uint64_t id_base,
+                              TaskRec *out)
 {
     GRID_STRIDE(b, nb) {
         TaskRec r;
@@ -390,7 +444,7 @@ __global__ void k_nbody_tasks(const uint4 *bucket, uint64_t nb, const uint64_t *
         r.row_off = 0;
         r.kind = GC_GRAVITY;
         r.nt = B.y;
-        r.ns = list_len[b];
+        r.ns = (uint32_t)(list_off[b + 1] - list_off[b]);
         r.shift[0] = r.shift[1] = r.shift[2] = r.shift[3] = 0;
         out[b] = r;
     }
@@ -500,11 +554,14 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     ++p->stats.kernel_launches;
     k_emit_buckets<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, boff, K, B,
                                                            S.bucket.as<uint4>(), blo, bhi);
-    GC_TRY(S.list_off.reserve(((uint64_t)NB + 1) * 8 * 2));
-    GC_TRY(S.win.reserve(((uint64_t)NB + 1) * 4));   // reused for list lengths
+    const uint64_t NI = (uint64_t)NB * WALK_ITEMS;           // walk items
+    GC_TRY(S.list_off.reserve((NI + 1) * 8 * 2 + (NB + 1) * 8));
+    GC_TRY(S.win.reserve((NI + 1) * 4 + 2 * WALK_ITEMS * 4));   // reused: item lengths + ranges
     uint32_t *llen = S.win.as<uint32_t>();
+    uint32_t *item_lo = llen + (NI + 1), *item_hi = item_lo + WALK_ITEMS;
     uint64_t *llen64 = S.list_off.as<uint64_t>();
-    uint64_t *loff = llen64 + (NB + 1);
+    uint64_t *ioff = llen64 + (NI + 1);                       // per-item offsets
+    uint64_t *loff = ioff + (NI + 1);                         // per-bucket offsets
     const int64_t tn2 = (int64_t)theta_num * theta_num, td2 = (int64_t)theta_den * theta_den;
     WalkThresholds th;
     for (int l = 0; l < 22; ++l) {
@@ -512,14 +569,18 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
         th.t[l] = tn2 ? (td2 * sz * sz) / tn2 : INT64_MAX;
     }
     ++p->stats.kernel_launches;
-    k_walk<false><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
-        S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
-        (uint32_t)n, th, llen, nullptr, nullptr);
-    GC_CUDA_TRY(cudaMemsetAsync(llen + NB, 0, 4, s));
+    k_walk_items<<<1, 32, 0, s>>>(S.node_a.as<uint4>(), NN, item_lo, item_hi);
     ++p->stats.kernel_launches;
-    k_u32_to_u64<<<grid_for(NB + 1, 256, maxb), 256, 0, s>>>(llen, llen64, (uint64_t)NB + 1);
+    k_walk<false><<<grid_for(NI, 128, 1 << 20), 128, 0, s>>>(
+        S.node_a.as<uint4>(), S.node_b.as<uint4>(), item_lo, item_hi, S.bucket.as<uint4>(), blo,
+        bhi, NB, sid, (uint32_t)n, th, llen, nullptr, nullptr);
+    GC_CUDA_TRY(cudaMemsetAsync(llen + NI, 0, 4, s));
+    ++p->stats.kernel_launches;
+    k_u32_to_u64<<<grid_for(NI + 1, 256, maxb), 256, 0, s>>>(llen, llen64, NI + 1);
     ++p->stats.primitive_calls;
-    GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, llen64, loff, (uint64_t)NB + 1, s));
+    GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, llen64, ioff, NI + 1, s));
+    ++p->stats.kernel_launches;
+    k_bucket_offsets<<<grid_for(NB + 1, 256, maxb), 256, 0, s>>>(ioff, NB, loff, llen64);
     uint64_t NL = 0;
     uint32_t maxlen = 0;
     GC_CUDA_TRY(cudaMemcpyAsync(&NL, loff + NB, 8, cudaMemcpyDeviceToHost, s));
@@ -531,12 +592,12 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     uint32_t *ds = p->src_ids.as<uint32_t>() + p->nb_src;
     TaskRec *recs = p->tasks.as<TaskRec>() + p->nb_tasks;
     ++p->stats.kernel_launches;
-    k_walk<true><<<grid_for(NB, 128, 1 << 20), 128, 0, s>>>(
-        S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, S.bucket.as<uint4>(), blo, bhi, NB, sid,
-        (uint32_t)n, th, nullptr, loff, ds);
+    k_walk<true><<<grid_for(NI, 128, 1 << 20), 128, 0, s>>>(
+        S.node_a.as<uint4>(), S.node_b.as<uint4>(), item_lo, item_hi, S.bucket.as<uint4>(), blo,
+        bhi, NB, sid, (uint32_t)n, th, nullptr, ioff, ds);
     GC_CUDA_TRY(cudaMemcpyAsync(dt, sid, n * 4, cudaMemcpyDeviceToDevice, s));
     ++p->stats.kernel_launches;
-    k_nbody_tasks<<<grid_for(NB, 256, maxb), 256, 0, s>>>(S.bucket.as<uint4>(), NB, loff, llen,
+    k_nbody_tasks<<<grid_for(NB, 256, maxb), 256, 0, s>>>(S.bucket.as<uint4>(), NB, loff,
                                                           p->nb_tgt, p->nb_src, task_id_base,
                                                           recs);
     GC_CUDA_TRY(cudaGetLastError());
@@ -597,7 +658,8 @@ extern "C" int gc_read_nbody_tree(gc_pool_t *p, uint32_t *sorted_ids, uint64_t *
             if (bucket_node) bucket_node[b] = bk[b].z;
         }
     }
-    const uint64_t *loff = S.list_off.as<uint64_t>() + (NB + 1);
+    const uint64_t NI = NB * WALK_ITEMS;
+    const uint64_t *loff = S.list_off.as<uint64_t>() + 2 * (NI + 1);
     if (list_off) GC_CUDA_TRY(cudaMemcpy(list_off, loff, (NB + 1) * 8, cudaMemcpyDeviceToHost));
     if (list_ids) {
         // the lists live in the batch source array (pending, or last flushed)
