@@ -189,6 +189,14 @@ int gc_flush(gc_pool_t *pool);
  * for at most timeout_ns (0 = forever).  GC_ERR_TIMEOUT if it has not. */
 int gc_wait(gc_pool_t *pool, uint64_t batch, uint64_t timeout_ns);
 
+/* Non-blocking completion check of batch `batch`: *done_out = 1 once it has
+ * completed (0 while it runs or has not been flushed). */
+int gc_batch_done(gc_pool_t *pool, uint64_t batch, int *done_out);
+
+/* Batches run alternately on two flush contexts, each with its own stream:
+ * batch k+1's chare-table step and pack overlap batch k's interaction on the
+ * device.  Results of batch k stay readable until batch k+2 is flushed. */
+
 /* ---- results ----------------------------------------------------------- */
 
 /* Number of result rows of the last completed batch: one per target, plus

@@ -11,18 +11,7 @@
 #include "gc_common.cuh"
 
 // ---- helpers declared in other translation units ----------------------------
-int gc_prepare(gc_pool *p, TaskRec *tasks, uint64_t n, uint64_t info[5]);
-int gc_read_wu_offsets(gc_pool *p, uint64_t n, std::vector<uint32_t> &wu_off,
-                       std::vector<uint32_t> &lj_off);
-int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uint32_t *src_ids,
-            uint64_t t0, uint64_t t1, uint64_t tgt_base, uint64_t src_base, uint64_t msrc);
-int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
-                      const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
-                      uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
-int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
-                         const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
-                         uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
-int gc_entry_slots(gc_pool *p, const uint32_t *ids, uint64_t n, uint32_t *out);
+int gc_entry_slots(gc_pool *p, cudaStream_t s, const uint32_t *ids, uint64_t n, uint32_t *out);
 
 // ---- DBuf ---------------------------------------------------------------------
 int DBuf::reserve(size_t bytes)
@@ -112,6 +101,23 @@ __global__ void k_gather_totals(const gcd4 *totals, const uint32_t *ids, uint64_
     }
 }
 
+void free_ctx(FlushCtx &c)
+{
+    DBuf *bufs[] = {&c.tasks, &c.tgt_ids, &c.src_ids, &c.tgt_perm, &c.src_perm, &c.stg_tgt,
+                    &c.stg_src, &c.wu, &c.wu_cnt, &c.wu_off, &c.rowcnt, &c.lj_list, &c.res,
+                    &c.row_id, &c.rid_sorted, &c.row_sorted, &c.rows_tmp, &c.runs, &c.tiles,
+                    &c.merge_a, &c.merge_b, &c.cub_tmp};
+    for (DBuf *b : bufs) b->release();
+    for (int i = 0; i < 6; ++i)
+        if (c.ev_stage[i]) cudaEventDestroy(c.ev_stage[i]);
+    if (c.ev_done) cudaEventDestroy(c.ev_done);
+    if (c.ev_packed) cudaEventDestroy(c.ev_packed);
+    if (c.ev_scattered) cudaEventDestroy(c.ev_scattered);
+    if (c.d_ctr) cudaFree(c.d_ctr);
+    if (c.h_ctr) cudaFreeHost(c.h_ctr);
+    if (c.owns_stream && c.s) cudaStreamDestroy(c.s);
+}
+
 void free_pool(gc_pool *p)
 {
     if (!p) return;
@@ -126,24 +132,62 @@ void free_pool(gc_pool *p)
     cudaFree(p->d_ctr);
     if (p->h_mirror) cudaFreeHost(p->h_mirror);
     if (p->h_ctr) cudaFreeHost(p->h_ctr);
-    DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->last_tasks_buf, &p->last_tgt_ids,
-                    &p->last_src_ids, &p->tgt_perm, &p->src_perm,
-                    &p->stg_tgt, &p->stg_src, &p->uniq, &p->miss, &p->freel, &p->tiles,
-                    &p->ekeys, &p->ekeys2, &p->evicted, &p->wu, &p->wu_cnt, &p->wu_off,
-                    &p->rowcnt, &p->res, &p->row_id, &p->rid_sorted, &p->row_sorted,
-                    &p->rows_tmp, &p->runs, &p->merge_a, &p->merge_b, &p->cub_tmp, &p->small,
-                    &p->nb.keys, &p->nb.keys2, &p->nb.ids, &p->nb.ids2, &p->nb.lcp, &p->nb.win,
-                    &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a, &p->nb.node_b,
-                    &p->nb.node_val, &p->nb.bucket, &p->nb.bbox, &p->nb.list_off,
-                    &p->nb.list_len, &p->nb.list, &p->nb.bounds, &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->md.hostcopy, &p->md.keys,
+    DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->uniq, &p->miss, &p->freel,
+                    &p->tiles, &p->ekeys, &p->ekeys2, &p->evicted, &p->cub_tmp, &p->io_a,
+                    &p->io_b, &p->nb.keys, &p->nb.keys2, &p->nb.ids, &p->nb.ids2, &p->nb.lcp,
+                    &p->nb.win, &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a,
+                    &p->nb.node_b, &p->nb.node_val, &p->nb.bucket, &p->nb.bbox,
+                    &p->nb.list_off, &p->nb.list_len, &p->nb.list, &p->nb.bounds,
+                    &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->md.hostcopy, &p->md.keys,
                     &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
                     &p->md.cnt_s, &p->md.cub_tmp};
     for (DBuf *b : bufs) b->release();
-    for (int i = 0; i < 6; ++i)
-        if (p->ev_stage[i]) cudaEventDestroy(p->ev_stage[i]);
-    if (p->ev_done) cudaEventDestroy(p->ev_done);
-    if (p->owns_stream && p->s) cudaStreamDestroy(p->s);
+    for (int i = 0; i < 2; ++i) free_ctx(p->ctx[i]);
     delete p;
+}
+
+int init_ctx(FlushCtx &c, cudaStream_t given)
+{
+    if (given) {
+        c.s = given;
+        c.owns_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking) != cudaSuccess)
+            return GC_ERR_CUDA;
+        c.owns_stream = true;
+    }
+    if (cudaMalloc((void **)&c.d_ctr, sizeof(unsigned long long) * FC_COUNT) != cudaSuccess ||
+        cudaHostAlloc((void **)&c.h_ctr, sizeof(unsigned long long) * FC_COUNT,
+                      cudaHostAllocDefault) != cudaSuccess)
+        return GC_ERR_OOM;
+    for (int i = 0; i < 6; ++i)
+        if (cudaEventCreate(&c.ev_stage[i]) != cudaSuccess) return GC_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.ev_packed, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c.ev_scattered, cudaEventDisableTiming) != cudaSuccess)
+        return GC_ERR_CUDA;
+    if (cudaMemsetAsync(c.d_ctr, 0, sizeof(unsigned long long) * FC_COUNT, c.s) != cudaSuccess)
+        return GC_ERR_CUDA;
+    return GC_OK;
+}
+
+// The context holding batch `batch`, or null if neither does.
+FlushCtx *ctx_of(gc_pool *p, uint64_t batch)
+{
+    for (int i = 0; i < 2; ++i)
+        if (p->ctx[i].valid && p->ctx[i].batch == batch) return &p->ctx[i];
+    return nullptr;
+}
+
+FlushCtx *last_ctx(gc_pool *p) { return p->last >= 0 ? &p->ctx[p->last] : nullptr; }
+
+// Make the issue stream wait for every scatter in flight (per-id totals).
+int order_after_scatters(gc_pool *p)
+{
+    for (int i = 0; i < 2; ++i)
+        if (p->ctx[i].valid && p->ctx[i].s != p->s)
+            GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ctx[i].ev_scattered, 0));
+    return GC_OK;
 }
 
 template <class T>
@@ -174,10 +218,6 @@ void clear_last_stats(gc_pool *p)
     for (int b = 0; b < 8; ++b) s.reuse_hist[b] = 0;
 }
 
-void drop_pending(gc_pool *p)
-{
-    p->nb_tasks = p->nb_tgt = p->nb_src = 0;
-}
 
 }  // namespace
 
@@ -210,7 +250,6 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
         return GC_ERR_ARG;
     gc_pool *p = new gc_pool();
     std::memset(&p->stats, 0, sizeof p->stats);
-    for (int i = 0; i < 6; ++i) p->ev_stage[i] = nullptr;
     p->cfg = *cfg;
     int64_t rc2g = 0, eg = 0;
     if (cfg->lj_rc2 > 0.0f) {
@@ -231,15 +270,19 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
         delete p;
         return GC_ERR_CUDA;
     }
-    if (cfg->cuda_stream) {
-        p->s = (cudaStream_t)cfg->cuda_stream;
-        p->owns_stream = false;
-    } else {
-        if (cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking) != cudaSuccess) {
-            delete p;
-            return GC_ERR_CUDA;
+    // flush context 0 issues on the caller's stream (or an owned one), context
+    // 1 on an owned stream; consecutive batches alternate between them
+    {
+        int rc0 = init_ctx(p->ctx[0], (cudaStream_t)cfg->cuda_stream);
+        if (rc0 == GC_OK) rc0 = init_ctx(p->ctx[1], nullptr);
+        if (rc0 != GC_OK) {
+            cudaGetLastError();
+            free_pool(p);
+            return rc0;
         }
-        p->owns_stream = true;
+        p->cur = 0;
+        p->last = -1;
+        p->s = p->ctx[0].s;
     }
     const uint64_t idc = cfg->id_capacity, cap = cfg->pool_capacity;
     int rc = GC_OK;
@@ -272,11 +315,6 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
         cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * idc, p->s);
         cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned long long) * CTR_COUNT, p->s);
         std::memset(p->h_mirror, 0, sizeof(float4) * idc);
-        for (int i = 0; i < 6 && rc == GC_OK; ++i)
-            if (cudaEventCreate(&p->ev_stage[i]) != cudaSuccess) rc = GC_ERR_CUDA;
-        if (rc == GC_OK && cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming) !=
-                               cudaSuccess)
-            rc = GC_ERR_CUDA;
         if (rc == GC_OK && cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
     }
     if (rc != GC_OK) {
@@ -290,7 +328,8 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
 int gc_pool_destroy(gc_pool_t *p)
 {
     if (!p) return GC_ERR_ARG;
-    cudaStreamSynchronize(p->s);
+    cudaStreamSynchronize(p->ctx[0].s);
+    cudaStreamSynchronize(p->ctx[1].s);
     free_pool(p);
     return GC_OK;
 }
@@ -301,26 +340,26 @@ int gc_pool_upload(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_
     if (n == 0) return GC_OK;
     for (uint64_t i = 0; i < n; ++i)
         if (ids[i] >= p->cfg.id_capacity) return GC_ERR_ARG;
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));   // no flush may be reading the mirror
-    for (uint64_t i = 0; i < n; ++i)
-        std::memcpy(&p->h_mirror[ids[i]], xyzm + 4 * i, sizeof(float4));
-    DBuf tmp_ids, tmp_vals;
-    GC_TRY(tmp_ids.reserve(n * sizeof(uint32_t)));
-    if (tmp_vals.reserve(n * sizeof(float4)) != GC_OK) {
-        tmp_ids.release();
-        return GC_ERR_OOM;
-    }
+    // no device work may be reading the mirror meanwhile
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[0].s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[1].s));
+    bool run = true;
+    for (uint64_t i = 0; i < n && run; ++i) run = ids[i] == ids[0] + i;
+    if (run)
+        std::memcpy(&p->h_mirror[ids[0]], xyzm, n * sizeof(float4));
+    else
+        for (uint64_t i = 0; i < n; ++i)
+            std::memcpy(&p->h_mirror[ids[i]], xyzm + 4 * i, sizeof(float4));
+    GC_TRY(grow_keep(p->io_a, n * sizeof(uint32_t) + 16, 0, p->s));
+    GC_TRY(grow_keep(p->io_b, n * sizeof(float4) + 16, 0, p->s));
     int rc = GC_OK;
-    if (cudaMemcpyAsync(tmp_ids.p, ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice, p->s) !=
+    if (cudaMemcpyAsync(p->io_a.p, ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice, p->s) !=
             cudaSuccess ||
-        cudaMemcpyAsync(tmp_vals.p, xyzm, n * sizeof(float4), cudaMemcpyHostToDevice, p->s) !=
+        cudaMemcpyAsync(p->io_b.p, xyzm, n * sizeof(float4), cudaMemcpyHostToDevice, p->s) !=
             cudaSuccess)
         rc = GC_ERR_CUDA;
-    if (rc == GC_OK)
-        rc = gc_launch_upload(p, tmp_ids.as<uint32_t>(), tmp_vals.as<float4>(), n, 0);
+    if (rc == GC_OK) rc = gc_launch_upload(p, p->io_a.as<uint32_t>(), p->io_b.as<float4>(), n, 0);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
-    tmp_ids.release();
-    tmp_vals.release();
     p->stats.h2d_bytes += n * (sizeof(uint32_t) + sizeof(float4));
     return rc;
 }
@@ -380,9 +419,8 @@ static int gc_submit_csr_impl(gc_pool *p, uint64_t n_tasks, const uint64_t *task
         size_t o_ids = 0, o_k = (o_ids + b_ids + 15) & ~15ull, o_sh = (o_k + b_k + 15) & ~15ull,
                o_to = (o_sh + b_sh + 15) & ~15ull, o_so = (o_to + b_off + 15) & ~15ull,
                total = o_so + b_off;
-        DBuf tmp;
-        GC_TRY(tmp.reserve(total));
-        char *base = (char *)tmp.p;
+        GC_TRY(grow_keep(p->io_a, total + 16, 0, p->s));
+        char *base = (char *)p->io_a.p;
         int rc = GC_OK;
         if (task_ids && cudaMemcpyAsync(base + o_ids, task_ids, b_ids, cudaMemcpyHostToDevice,
                                         p->s) != cudaSuccess)
@@ -412,7 +450,6 @@ static int gc_submit_csr_impl(gc_pool *p, uint64_t n_tasks, const uint64_t *task
                                    (uint64_t *)(base + o_to), (uint64_t *)(base + o_so),
                                    p->nb_tgt, p->nb_src, id_base, recs);
         if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
-        tmp.release();
         if (rc != GC_OK) return rc;
         p->stats.h2d_bytes += total + 4 * (n_tgt_total + n_src_total);
     }
@@ -455,33 +492,56 @@ int gc_submit(gc_pool_t *p, const gc_task *tasks, uint64_t n, uint64_t *batch_ou
 }
 
 // ---- flush ----------------------------------------------------------------------
+//
+// Batch k runs on flush context ctx[k % 2] and its stream.  Two event edges
+// keep consecutive batches correct while they overlap on the device:
+//   - the next batch's chare-table step (which may move or refill pool
+//     slots) and any upload or task build issued after gc_flush returns wait
+//     for this batch's pack (the last reader of the pool);
+//   - the next batch's scatter waits for this batch's scatter (per-id totals
+//     accumulate in admission order).
+// The interaction of batch k thus runs while batch k+1 is residency-checked
+// and packed.  A context is reused by batch k+2, in stream order after
+// batch k, so results of a batch stay readable until batch k+2 is flushed.
 
 static int flush_impl(gc_pool *p, int per_task)
 {
     if (!p) return GC_ERR_ARG;
     if (p->nb_tasks == 0) return GC_OK;
-    const uint64_t T = p->nb_tasks, NT = p->nb_tgt, NS = p->nb_src;
-    TaskRec *tasks = p->tasks.as<TaskRec>();
-    const uint32_t *tgt_ids = p->tgt_ids.as<uint32_t>();
-    const uint32_t *src_ids = p->src_ids.as<uint32_t>();
+    FlushCtx &c = p->ctx[p->cur];
+    FlushCtx *prev = last_ctx(p);
+    // the batch becomes this context's batch; the context's previous batch
+    // arrays become the next pending arrays (every later write to them is
+    // ordered after this context's stream passes the point below)
+    std::swap(p->tasks, c.tasks);
+    std::swap(p->tgt_ids, c.tgt_ids);
+    std::swap(p->src_ids, c.src_ids);
+    c.n_tasks = p->nb_tasks;
+    c.n_tgt = p->nb_tgt;
+    c.n_src = p->nb_src;
+    c.batch = p->submitted_batches;
+    c.valid = false;
+    c.host_tasks_valid = false;
+    c.timing_valid = false;
+    p->nb_tasks = p->nb_tgt = p->nb_src = 0;
+    const uint64_t T = c.n_tasks, NT = c.n_tgt, NS = c.n_src;
     clear_last_stats(p);
-    p->timing_valid = false;
 
     uint64_t info[5];
-    int rc = gc_prepare(p, tasks, T, info);
+    int rc = gc_prepare(p, c, info);
     if (rc != GC_OK) return rc;
     GC_CUDA_TRY(cudaMemcpy(p->h_ctr, p->d_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     if (p->h_ctr[CTR_FLAGS] & GC_FLAG_BAD_TASK) {
-        cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, sizeof(unsigned long long), p->s);
-        drop_pending(p);
+        cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, sizeof(unsigned long long), c.s);
         return GC_ERR_ARG;
     }
     const uint64_t R = info[0], W = info[1], L = info[2], inter = info[3], max_list = info[4];
+    c.n_rows = R;
 
-    GC_TRY(p->tgt_perm.reserve((NT + 1) * 4));
-    GC_TRY(p->src_perm.reserve((NS + 1) * 4));
-    GC_TRY(p->res.reserve((R + 1) * 2 * sizeof(float4)));
-    GC_TRY(p->row_id.reserve((R + 1) * 4));
+    GC_TRY(c.tgt_perm.reserve((NT + 1) * 4));
+    GC_TRY(c.src_perm.reserve((NS + 1) * 4));
+    GC_TRY(c.res.reserve((R + 1) * 2 * sizeof(float4)));
+    GC_TRY(c.row_id.reserve((R + 1) * 4));
 
     // waves under the staging budget
     struct Wave { uint64_t t0, t1, tg0, tg1, s0, s1; };
@@ -491,7 +551,7 @@ static int flush_impl(gc_pool *p, int per_task)
     bool need_offsets = per_task != 0;
     if (budget && (NT + NS) * sizeof(float4) > budget) {
         std::vector<TaskRec> h(T);
-        GC_CUDA_TRY(cudaMemcpy(h.data(), tasks, T * sizeof(TaskRec), cudaMemcpyDeviceToHost));
+        GC_CUDA_TRY(cudaMemcpy(h.data(), c.tasks.p, T * sizeof(TaskRec), cudaMemcpyDeviceToHost));
         uint64_t t0 = 0;
         while (t0 < T) {
             uint64_t t1 = t0, bytes = 0;
@@ -499,10 +559,7 @@ static int flush_impl(gc_pool *p, int per_task)
                 bytes += (uint64_t)(h[t1].nt + h[t1].ns) * sizeof(float4);
                 ++t1;
             }
-            if (t1 == t0) {
-                drop_pending(p);
-                return GC_ERR_BUDGET;
-            }
+            if (t1 == t0) return GC_ERR_BUDGET;
             Wave w;
             w.t0 = t0; w.t1 = t1;
             w.tg0 = h[t0].tgt_off; w.tg1 = (t1 < T) ? h[t1].tgt_off : NT;
@@ -514,7 +571,7 @@ static int flush_impl(gc_pool *p, int per_task)
     } else {
         waves.push_back(Wave{0, T, 0, NT, 0, NS});
     }
-    if (need_offsets) GC_TRY(gc_read_wu_offsets(p, T, wu_off, lj_off));
+    if (need_offsets) GC_TRY(gc_read_wu_offsets(p, c, wu_off, lj_off));
 
     // source staging holds one extra float4 per task (pad of odd gravity lists)
     uint64_t max_wt = 0, max_ws = 0;
@@ -522,60 +579,60 @@ static int flush_impl(gc_pool *p, int per_task)
         if (w.tg1 - w.tg0 > max_wt) max_wt = w.tg1 - w.tg0;
         if (w.s1 - w.s0 + (w.t1 - w.t0) > max_ws) max_ws = w.s1 - w.s0 + (w.t1 - w.t0);
     }
-    GC_TRY(p->stg_tgt.reserve((max_wt + 1) * sizeof(float4)));
-    GC_TRY(p->stg_src.reserve((max_ws + 1) * sizeof(float4)));
+    GC_TRY(c.stg_tgt.reserve((max_wt + 1) * sizeof(float4)));
+    GC_TRY(c.stg_src.reserve((max_ws + 1) * sizeof(float4)));
     if (max_list > 4096) {
-        GC_TRY(p->merge_a.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
-        GC_TRY(p->merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
+        GC_TRY(c.merge_a.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
+        GC_TRY(c.merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
     }
 
     float ms_res = 0, ms_pack = 0, ms_int = 0;
-    GC_CUDA_TRY(cudaMemsetAsync(p->d_ctr + CTR_LJ_IN, 0, sizeof(unsigned long long), p->s));
-    GC_CUDA_TRY(cudaEventRecord(p->ev_stage[0], p->s));
+    const uint32_t *tgt_ids = c.tgt_ids.as<uint32_t>();
+    const uint32_t *src_ids = c.src_ids.as<uint32_t>();
+    GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
     for (size_t k = 0; k < waves.size(); ++k) {
         const Wave &w = waves[k];
-        cudaEvent_t e0 = p->ev_stage[0];
-        if (k > 0) GC_CUDA_TRY(cudaEventRecord(e0, p->s));
+        if (k > 0) GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
         rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0);
-        if (rc != GC_OK) {
-            drop_pending(p);
-            return rc;
-        }
-        GC_CUDA_TRY(cudaEventRecord(p->ev_stage[1], p->s));
-        GC_TRY(gc_pack(p, tasks, tgt_ids, src_ids, w.t0, w.t1, w.tg0, w.s0, max_wt + 1));
-        GC_CUDA_TRY(cudaEventRecord(p->ev_stage[2], p->s));
+        if (rc != GC_OK) return rc;
+        GC_CUDA_TRY(cudaEventRecord(c.ev_stage[1], c.s));
+        GC_TRY(gc_pack(p, c, w.t0, w.t1, w.tg0, w.s0, max_wt + 1));
+        GC_CUDA_TRY(cudaEventRecord(c.ev_stage[2], c.s));
         uint64_t w0 = 0, w1 = W, l0 = 0, l1 = L;
         if (need_offsets) {
             w0 = wu_off[w.t0]; w1 = wu_off[w.t1];
             l0 = lj_off[w.t0]; l1 = lj_off[w.t1];
         }
         if (!per_task) {
-            GC_TRY(gc_interact_range(p, tasks, tgt_ids, src_ids, w0, w1, l0, l1, w.tg0, w.s0,
-                                     w.t0));
+            GC_TRY(gc_interact_range(p, c, w0, w1, l0, l1, w.tg0, w.s0, w.t0));
         } else {
             for (uint64_t t = w.t0; t < w.t1; ++t)
-                GC_TRY(gc_interact_one_task(p, tasks, tgt_ids, src_ids, wu_off[t],
-                                            wu_off[t + 1], lj_off[t], lj_off[t + 1], w.tg0,
-                                            w.s0, w.t0));
+                GC_TRY(gc_interact_one_task(p, c, wu_off[t], wu_off[t + 1], lj_off[t],
+                                            lj_off[t + 1], w.tg0, w.s0, w.t0));
         }
-        GC_CUDA_TRY(cudaEventRecord(p->ev_stage[3], p->s));
+        GC_CUDA_TRY(cudaEventRecord(c.ev_stage[3], c.s));
         if (waves.size() > 1) {
-            float a = 0, b = 0, c = 0;
-            GC_CUDA_TRY(cudaEventSynchronize(p->ev_stage[3]));
-            cudaEventElapsedTime(&a, p->ev_stage[0], p->ev_stage[1]);
-            cudaEventElapsedTime(&b, p->ev_stage[1], p->ev_stage[2]);
-            cudaEventElapsedTime(&c, p->ev_stage[2], p->ev_stage[3]);
-            ms_res += a; ms_pack += b; ms_int += c;
+            float a = 0, b = 0, d = 0;
+            GC_CUDA_TRY(cudaEventSynchronize(c.ev_stage[3]));
+            cudaEventElapsedTime(&a, c.ev_stage[0], c.ev_stage[1]);
+            cudaEventElapsedTime(&b, c.ev_stage[1], c.ev_stage[2]);
+            cudaEventElapsedTime(&d, c.ev_stage[2], c.ev_stage[3]);
+            ms_res += a; ms_pack += b; ms_int += d;
         }
     }
-    GC_TRY(gc_scatter(p, R));
-    GC_CUDA_TRY(cudaEventRecord(p->ev_stage[4], p->s));
-    GC_CUDA_TRY(cudaEventRecord(p->ev_done, p->s));
-    p->multiwave_ms[0] = ms_res;
-    p->multiwave_ms[1] = ms_pack;
-    p->multiwave_ms[2] = ms_int;
-    p->n_waves_last = waves.size();
-    p->timing_valid = true;
+    // pack done: later pool changes may proceed
+    GC_CUDA_TRY(cudaEventRecord(c.ev_packed, c.s));
+    if (prev && prev != &c && prev->valid) GC_CUDA_TRY(cudaStreamWaitEvent(c.s, prev->ev_scattered, 0));
+    GC_TRY(gc_scatter(p, c));
+    GC_CUDA_TRY(cudaEventRecord(c.ev_scattered, c.s));
+    GC_CUDA_TRY(cudaEventRecord(c.ev_stage[4], c.s));
+    GC_CUDA_TRY(cudaEventRecord(c.ev_done, c.s));
+    c.multiwave_ms[0] = ms_res;
+    c.multiwave_ms[1] = ms_pack;
+    c.multiwave_ms[2] = ms_int;
+    c.n_waves = waves.size();
+    c.timing_valid = true;
+    c.valid = true;
 
     gc_stats_t &st = p->stats;
     st.flushes += 1;
@@ -584,20 +641,11 @@ static int flush_impl(gc_pool *p, int per_task)
     st.last_waves = waves.size();
     st.last_staging_bytes = (NT + NS) * sizeof(float4);
 
-    // the executed batch becomes the "last" batch; its buffers are kept for
-    // result mapping and introspection
-    std::swap(p->tasks, p->last_tasks_buf);
-    std::swap(p->tgt_ids, p->last_tgt_ids);
-    std::swap(p->src_ids, p->last_src_ids);
-    p->last_tasks = T;
-    p->last_tgt = NT;
-    p->last_src = NS;
-    p->last_rows = R;
-    p->last_batch = p->submitted_batches;
-    p->have_last = true;
+    p->last = p->cur;
     p->submitted_batches += 1;
-    drop_pending(p);
-    p->host_tasks_valid = false;
+    p->cur ^= 1;
+    p->s = p->ctx[p->cur].s;
+    GC_CUDA_TRY(cudaStreamWaitEvent(p->s, c.ev_packed, 0));
     return GC_OK;
 }
 
@@ -608,7 +656,7 @@ int gc_flush_per_task(gc_pool_t *p) { return flush_impl(p, 1); }
 int gc_wait(gc_pool_t *p, uint64_t batch, uint64_t timeout_ns)
 {
     if (!p) return GC_ERR_ARG;
-    if (!p->have_last || batch > p->last_batch) return GC_ERR_NOT_READY;
+    if (p->last < 0 || batch >= p->submitted_batches) return GC_ERR_NOT_READY;
     auto device_status = [p]() -> int {
         unsigned long long f = 0;
         if (cudaMemcpy(&f, p->d_ctr + CTR_FLAGS, sizeof f, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -620,70 +668,109 @@ int gc_wait(gc_pool_t *p, uint64_t batch, uint64_t timeout_ns)
         }
         return GC_OK;
     };
-    if (timeout_ns == 0) {
-        GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
-        return device_status();
+    // the batch's context, or (an older batch) both: stream order makes a
+    // later batch on the same context complete after it
+    std::vector<cudaEvent_t> evs;
+    if (FlushCtx *c = ctx_of(p, batch)) {
+        evs.push_back(c->ev_done);
+    } else {
+        for (int i = 0; i < 2; ++i)
+            if (p->ctx[i].valid) evs.push_back(p->ctx[i].ev_done);
     }
     struct timespec t0, t1;
     clock_gettime(CLOCK_MONOTONIC, &t0);
-    for (;;) {
-        cudaError_t e = cudaEventQuery(p->ev_done);
-        if (e == cudaSuccess) return device_status();
-        if (e != cudaErrorNotReady) return GC_ERR_CUDA;
-        clock_gettime(CLOCK_MONOTONIC, &t1);
-        uint64_t el = (uint64_t)(t1.tv_sec - t0.tv_sec) * 1000000000ull +
-                      (uint64_t)(t1.tv_nsec - t0.tv_nsec);
-        if (el >= timeout_ns) return GC_ERR_TIMEOUT;
+    for (cudaEvent_t e : evs) {
+        if (timeout_ns == 0) {
+            GC_CUDA_TRY(cudaEventSynchronize(e));
+            continue;
+        }
+        for (;;) {
+            cudaError_t q = cudaEventQuery(e);
+            if (q == cudaSuccess) break;
+            if (q != cudaErrorNotReady) return GC_ERR_CUDA;
+            clock_gettime(CLOCK_MONOTONIC, &t1);
+            uint64_t el = (uint64_t)(t1.tv_sec - t0.tv_sec) * 1000000000ull +
+                          (uint64_t)(t1.tv_nsec - t0.tv_nsec);
+            if (el >= timeout_ns) return GC_ERR_TIMEOUT;
+        }
     }
+    return device_status();
+}
+
+int gc_batch_done(gc_pool_t *p, uint64_t batch, int *done_out)
+{
+    if (!p || !done_out) return GC_ERR_ARG;
+    *done_out = 0;
+    if (p->last < 0 || batch >= p->submitted_batches) return GC_OK;
+    FlushCtx *c = ctx_of(p, batch);
+    cudaError_t q = cudaSuccess;
+    if (c) {
+        q = cudaEventQuery(c->ev_done);
+    } else {
+        for (int i = 0; i < 2 && q == cudaSuccess; ++i)
+            if (p->ctx[i].valid) q = cudaEventQuery(p->ctx[i].ev_done);
+    }
+    if (q == cudaSuccess) *done_out = 1;
+    else if (q != cudaErrorNotReady) return GC_ERR_CUDA;
+    return GC_OK;
 }
 
 // ---- results -----------------------------------------------------------------------
 
+static FlushCtx *result_ctx(gc_pool *p)
+{
+    FlushCtx *c = last_ctx(p);
+    return (c && c->valid) ? c : nullptr;
+}
+
 int gc_result_rows(gc_pool_t *p, uint64_t *rows_out)
 {
     if (!p || !rows_out) return GC_ERR_ARG;
-    *rows_out = p->have_last ? p->last_rows : 0;
+    FlushCtx *c = result_ctx(p);
+    *rows_out = c ? c->n_rows : 0;
     return GC_OK;
 }
 
 int gc_read_batch_results(gc_pool_t *p, uint64_t first_row, uint64_t n_rows, float *out)
 {
     if (!p || (n_rows && !out)) return GC_ERR_ARG;
-    if (!p->have_last || first_row + n_rows > p->last_rows) return GC_ERR_ARG;
-    GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
-    GC_CUDA_TRY(cudaMemcpy(out, p->res.as<float4>() + 2 * first_row, n_rows * 2 * sizeof(float4),
+    FlushCtx *c = result_ctx(p);
+    if (!c || first_row + n_rows > c->n_rows) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaEventSynchronize(c->ev_done));
+    GC_CUDA_TRY(cudaMemcpy(out, c->res.as<float4>() + 2 * first_row, n_rows * 2 * sizeof(float4),
                            cudaMemcpyDeviceToHost));
     return GC_OK;
 }
 
-static int ensure_host_tasks(gc_pool *p)
+static int ensure_host_tasks(FlushCtx &c)
 {
-    if (p->host_tasks_valid) return GC_OK;
-    p->host_tasks.resize(p->last_tasks);
-    GC_CUDA_TRY(cudaEventSynchronize(p->ev_done));
-    GC_CUDA_TRY(cudaMemcpy(p->host_tasks.data(), p->last_tasks_buf.p,
-                           p->last_tasks * sizeof(TaskRec), cudaMemcpyDeviceToHost));
-    p->task_index.clear();
-    p->task_index.reserve(p->last_tasks * 2);
-    for (uint64_t t = 0; t < p->last_tasks; ++t) p->task_index[p->host_tasks[t].task_id] = t;
-    p->host_tasks_valid = true;
+    if (c.host_tasks_valid) return GC_OK;
+    c.host_tasks.resize(c.n_tasks);
+    GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
+    GC_CUDA_TRY(cudaMemcpy(c.host_tasks.data(), c.tasks.p, c.n_tasks * sizeof(TaskRec),
+                           cudaMemcpyDeviceToHost));
+    c.task_index.clear();
+    c.task_index.reserve(c.n_tasks * 2);
+    for (uint64_t t = 0; t < c.n_tasks; ++t) c.task_index[c.host_tasks[t].task_id] = t;
+    c.host_tasks_valid = true;
     return GC_OK;
 }
 
 int gc_read_results(gc_pool_t *p, const uint64_t *task_ids, uint64_t n, float *out)
 {
     if (!p || (n && (!task_ids || !out))) return GC_ERR_ARG;
-    if (!p->have_last) return GC_ERR_NOT_READY;
-    GC_TRY(ensure_host_tasks(p));
-    std::vector<float4> all(2 * p->last_rows + 2);
-    if (p->last_rows)
-        GC_CUDA_TRY(cudaMemcpy(all.data(), p->res.p, p->last_rows * 2 * sizeof(float4),
+    FlushCtx *c = result_ctx(p);
+    if (!c) return GC_ERR_NOT_READY;
+    GC_TRY(ensure_host_tasks(*c));
+    std::vector<float4> all(2 * c->n_rows + 2);
+    if (c->n_rows)
+        GC_CUDA_TRY(cudaMemcpy(all.data(), c->res.p, c->n_rows * 2 * sizeof(float4),
                                cudaMemcpyDeviceToHost));
     uint64_t w = 0;
     for (uint64_t i = 0; i < n; ++i) {
-        auto it = p->task_index.find(task_ids[i]);
-        if (it == p->task_index.end()) return GC_ERR_ARG;
-        const TaskRec &r = p->host_tasks[it->second];
+        auto it = c->task_index.find(task_ids[i]);
+        if (it == c->task_index.end()) return GC_ERR_ARG;
+        const TaskRec &r = c->host_tasks[it->second];
         uint64_t rows = r.nt + (r.kind == GC_LJ_PAIR ? r.ns : 0u);
         std::memcpy(out + 8 * w, &all[2 * r.row_off], rows * 2 * sizeof(float4));
         w += rows;
@@ -695,28 +782,23 @@ int gc_read_totals(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
 {
     if (!p || (n && (!ids || !acc4))) return GC_ERR_ARG;
     if (n == 0) return GC_OK;
-    DBuf di, dout;
-    GC_TRY(di.reserve(n * 4));
-    if (dout.reserve(n * sizeof(gcd4)) != GC_OK) {
-        di.release();
-        return GC_ERR_OOM;
-    }
+    GC_TRY(order_after_scatters(p));
+    GC_TRY(grow_keep(p->io_a, n * 4 + 16, 0, p->s));
+    GC_TRY(grow_keep(p->io_b, n * sizeof(gcd4) + 32, 0, p->s));
     int rc = GC_OK;
-    if (cudaMemcpyAsync(di.p, ids, n * 4, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
+    if (cudaMemcpyAsync(p->io_a.p, ids, n * 4, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
         rc = GC_ERR_CUDA;
     if (rc == GC_OK) {
         unsigned g = (unsigned)((n + 255) / 256);
         if (g > 65535u * 8) g = 65535u * 8;
         ++p->stats.kernel_launches;
-        k_gather_totals<<<g, 256, 0, p->s>>>(p->d_totals, di.as<uint32_t>(), n,
-                                             p->cfg.id_capacity, dout.as<gcd4>());
-        if (cudaMemcpyAsync(acc4, dout.p, n * sizeof(gcd4), cudaMemcpyDeviceToHost, p->s) !=
+        k_gather_totals<<<g, 256, 0, p->s>>>(p->d_totals, p->io_a.as<uint32_t>(), n,
+                                             p->cfg.id_capacity, p->io_b.as<gcd4>());
+        if (cudaMemcpyAsync(acc4, p->io_b.p, n * sizeof(gcd4), cudaMemcpyDeviceToHost, p->s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(p->s) != cudaSuccess)
             rc = GC_ERR_CUDA;
     }
-    di.release();
-    dout.release();
     return rc;
 }
 
@@ -730,6 +812,7 @@ int gc_totals_device(gc_pool_t *p, const double **totals_dev)
 int gc_reset_totals(gc_pool_t *p)
 {
     if (!p) return GC_ERR_ARG;
+    GC_TRY(order_after_scatters(p));
     GC_CUDA_TRY(cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * p->cfg.id_capacity, p->s));
     return GC_OK;
 }
@@ -737,33 +820,41 @@ int gc_reset_totals(gc_pool_t *p)
 int gc_stats(gc_pool_t *p, gc_stats_t *out)
 {
     if (!p || !out) return GC_ERR_ARG;
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[0].s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[1].s));
     unsigned long long c[CTR_COUNT];
     GC_CUDA_TRY(cudaMemcpy(c, p->d_ctr, sizeof c, cudaMemcpyDeviceToHost));
     *out = p->stats;
     out->updates = c[CTR_UPDATES];
-    out->lj_pairs_in_cutoff = c[CTR_LJ_IN];
+    FlushCtx *l = result_ctx(p);
+    out->lj_pairs_in_cutoff = 0;
+    if (l) {
+        unsigned long long v = 0;
+        GC_CUDA_TRY(cudaMemcpy(&v, l->d_ctr + FC_LJ_IN, sizeof v, cudaMemcpyDeviceToHost));
+        out->lj_pairs_in_cutoff = v;
+    }
     return GC_OK;
 }
 
 int gc_last_timings(gc_pool_t *p, float ms[5])
 {
     if (!p || !ms) return GC_ERR_ARG;
-    if (!p->timing_valid) return GC_ERR_NOT_READY;
-    GC_CUDA_TRY(cudaEventSynchronize(p->ev_stage[4]));
-    if (p->n_waves_last > 1) {
-        ms[0] = p->multiwave_ms[0];
-        ms[1] = p->multiwave_ms[1];
-        ms[2] = p->multiwave_ms[2];
-        cudaEventElapsedTime(&ms[3], p->ev_stage[3], p->ev_stage[4]);
+    FlushCtx *c = result_ctx(p);
+    if (!c || !c->timing_valid) return GC_ERR_NOT_READY;
+    GC_CUDA_TRY(cudaEventSynchronize(c->ev_stage[4]));
+    if (c->n_waves > 1) {
+        ms[0] = c->multiwave_ms[0];
+        ms[1] = c->multiwave_ms[1];
+        ms[2] = c->multiwave_ms[2];
+        cudaEventElapsedTime(&ms[3], c->ev_stage[3], c->ev_stage[4]);
         ms[4] = ms[0] + ms[1] + ms[2] + ms[3];
         return GC_OK;
     }
-    cudaEventElapsedTime(&ms[0], p->ev_stage[0], p->ev_stage[1]);
-    cudaEventElapsedTime(&ms[1], p->ev_stage[1], p->ev_stage[2]);
-    cudaEventElapsedTime(&ms[2], p->ev_stage[2], p->ev_stage[3]);
-    cudaEventElapsedTime(&ms[3], p->ev_stage[3], p->ev_stage[4]);
-    cudaEventElapsedTime(&ms[4], p->ev_stage[0], p->ev_stage[4]);
+    cudaEventElapsedTime(&ms[0], c->ev_stage[0], c->ev_stage[1]);
+    cudaEventElapsedTime(&ms[1], c->ev_stage[1], c->ev_stage[2]);
+    cudaEventElapsedTime(&ms[2], c->ev_stage[2], c->ev_stage[3]);
+    cudaEventElapsedTime(&ms[3], c->ev_stage[3], c->ev_stage[4]);
+    cudaEventElapsedTime(&ms[4], c->ev_stage[0], c->ev_stage[4]);
     return GC_OK;
 }
 
@@ -772,42 +863,42 @@ int gc_last_timings(gc_pool_t *p, float ms[5])
 int gc_batch_sizes(gc_pool_t *p, uint64_t *n_tasks, uint64_t *n_tgt, uint64_t *n_src)
 {
     if (!p) return GC_ERR_ARG;
-    if (n_tasks) *n_tasks = p->have_last ? p->last_tasks : 0;
-    if (n_tgt) *n_tgt = p->have_last ? p->last_tgt : 0;
-    if (n_src) *n_src = p->have_last ? p->last_src : 0;
+    FlushCtx *c = result_ctx(p);
+    if (n_tasks) *n_tasks = c ? c->n_tasks : 0;
+    if (n_tgt) *n_tgt = c ? c->n_tgt : 0;
+    if (n_src) *n_src = c ? c->n_src : 0;
     return GC_OK;
 }
 
 int gc_read_entry_slots(gc_pool_t *p, uint32_t *tgt_slots, uint32_t *src_slots)
 {
-    if (!p || !p->have_last) return GC_ERR_STATE;
+    FlushCtx *c = p ? result_ctx(p) : nullptr;
+    if (!c) return GC_ERR_STATE;
+    GC_CUDA_TRY(cudaEventSynchronize(c->ev_done));
     // looked up in the chare table now (the pack reads the table directly)
-    DBuf tmp;
-    GC_TRY(tmp.reserve((p->last_tgt + p->last_src + 1) * 4));
-    uint32_t *d = tmp.as<uint32_t>();
-    int rc = gc_entry_slots(p, p->last_tgt_ids.as<uint32_t>(), p->last_tgt, d);
-    if (rc == GC_OK)
-        rc = gc_entry_slots(p, p->last_src_ids.as<uint32_t>(), p->last_src, d + p->last_tgt);
-    if (rc == GC_OK && cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
-    if (rc == GC_OK && tgt_slots && p->last_tgt &&
-        cudaMemcpy(tgt_slots, d, p->last_tgt * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    GC_TRY(grow_keep(p->io_a, (c->n_tgt + c->n_src + 1) * 4, 0, c->s));
+    uint32_t *d = p->io_a.as<uint32_t>();
+    int rc = gc_entry_slots(p, c->s, c->tgt_ids.as<uint32_t>(), c->n_tgt, d);
+    if (rc == GC_OK) rc = gc_entry_slots(p, c->s, c->src_ids.as<uint32_t>(), c->n_src, d + c->n_tgt);
+    if (rc == GC_OK && cudaStreamSynchronize(c->s) != cudaSuccess) rc = GC_ERR_CUDA;
+    if (rc == GC_OK && tgt_slots && c->n_tgt &&
+        cudaMemcpy(tgt_slots, d, c->n_tgt * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         rc = GC_ERR_CUDA;
-    if (rc == GC_OK && src_slots && p->last_src &&
-        cudaMemcpy(src_slots, d + p->last_tgt, p->last_src * 4, cudaMemcpyDeviceToHost) !=
-            cudaSuccess)
+    if (rc == GC_OK && src_slots && c->n_src &&
+        cudaMemcpy(src_slots, d + c->n_tgt, c->n_src * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         rc = GC_ERR_CUDA;
-    tmp.release();
     return rc;
 }
 
 int gc_read_pack_perm(gc_pool_t *p, uint32_t *tgt_perm, uint32_t *src_perm)
 {
-    if (!p || !p->have_last) return GC_ERR_STATE;
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
-    if (tgt_perm && p->last_tgt)
-        GC_CUDA_TRY(cudaMemcpy(tgt_perm, p->tgt_perm.p, p->last_tgt * 4, cudaMemcpyDeviceToHost));
-    if (src_perm && p->last_src)
-        GC_CUDA_TRY(cudaMemcpy(src_perm, p->src_perm.p, p->last_src * 4, cudaMemcpyDeviceToHost));
+    FlushCtx *c = p ? result_ctx(p) : nullptr;
+    if (!c) return GC_ERR_STATE;
+    GC_CUDA_TRY(cudaEventSynchronize(c->ev_done));
+    if (tgt_perm && c->n_tgt)
+        GC_CUDA_TRY(cudaMemcpy(tgt_perm, c->tgt_perm.p, c->n_tgt * 4, cudaMemcpyDeviceToHost));
+    if (src_perm && c->n_src)
+        GC_CUDA_TRY(cudaMemcpy(src_perm, c->src_perm.p, c->n_src * 4, cudaMemcpyDeviceToHost));
     return GC_OK;
 }
 
@@ -815,7 +906,8 @@ int gc_read_residency(gc_pool_t *p, uint32_t *slot_of_id, uint32_t *id_of_slot,
                       uint32_t *last_use)
 {
     if (!p) return GC_ERR_ARG;
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[0].s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[1].s));
     if (slot_of_id)
         GC_CUDA_TRY(cudaMemcpy(slot_of_id, p->d_slot_of_id, p->cfg.id_capacity * 4,
                                cudaMemcpyDeviceToHost));
@@ -831,7 +923,8 @@ int gc_read_residency(gc_pool_t *p, uint32_t *slot_of_id, uint32_t *id_of_slot,
 int gc_read_evicted(gc_pool_t *p, uint32_t *ids, uint64_t cap, uint64_t *n_out)
 {
     if (!p || !n_out) return GC_ERR_ARG;
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[0].s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[1].s));
     *n_out = p->n_evicted_last;
     uint64_t k = p->n_evicted_last < cap ? p->n_evicted_last : cap;
     if (k && ids) GC_CUDA_TRY(cudaMemcpy(ids, p->evicted.p, k * 4, cudaMemcpyDeviceToHost));

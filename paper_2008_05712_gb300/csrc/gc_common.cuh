@@ -24,24 +24,29 @@ struct __align__(32) gcd4 {
 #define GC_FLAG_BAD_TASK 4u       // unknown kind, or LJ_SELF with sources
 #define GC_FLAG_TIMEOUT 8u        // a device-side wait ran out of its limit
 
-// Indices into the device counter block (pool->d_ctr, uint64 each).  The
-// residency counters (CTR_UNIQUE .. end) are cleared at every wave.
+// Indices into the pool's device counter block (pool->d_ctr, uint64 each).
+// The residency counters (CTR_UNIQUE .. end) are cleared at every wave.
 enum {
     CTR_FLAGS = 0,      // error bits
     CTR_UPDATES,        // uploads that hit a resident slot
-    CTR_LJ_IN,          // LJ pairs inside the cutoff
-    CTR_QUEUE,          // work-queue head of the persistent interaction kernel
-    CTR_INTER,          // pair interactions of the batch
-    CTR_NGRAV_WU,       // gravity work units of the batch
-    CTR_NLJ,            // LJ tasks of the batch
-    CTR_MAXLIST,        // longest list of the batch
-    CTR_RUNS,           // distinct ids among result rows
     CTR_UNIQUE,         // distinct ids in the current wave
     CTR_HITS,
     CTR_MISSES,
     CTR_FREE,
     CTR_HIST0,          // 8 reuse-histogram bins
     CTR_COUNT = CTR_HIST0 + 8
+};
+
+// Indices into a flush context's counter block (ctx.d_ctr).
+enum {
+    FC_QUEUE = 0,       // work-queue head of the persistent interaction kernel
+    FC_INTER,           // pair interactions of the batch
+    FC_NGRAV_WU,        // gravity work units of the batch
+    FC_NLJ,             // LJ tasks of the batch
+    FC_MAXLIST,         // longest list of the batch
+    FC_RUNS,            // distinct ids among result rows
+    FC_LJ_IN,           // LJ pairs inside the cutoff
+    FC_COUNT = 8
 };
 
 // One task as the kernels see it (48 bytes).
@@ -86,10 +91,32 @@ struct MDState {
     DBuf keys, keys2, ids, ids2, cell_start, cnt_t, cnt_s, cub_tmp, hostcopy;
 };
 
-struct gc_pool {
-    gc_config cfg;
+// Everything one in-flight batch owns: its stream, its batch arrays, work
+// buffers, counters and events.
+struct FlushCtx {
     cudaStream_t s = nullptr;
     bool owns_stream = false;
+    unsigned long long *d_ctr = nullptr;   // [FC_COUNT]
+    unsigned long long *h_ctr = nullptr;   // pinned copy
+    DBuf tasks, tgt_ids, src_ids;          // the executed batch
+    uint64_t n_tasks = 0, n_tgt = 0, n_src = 0, n_rows = 0, batch = 0;
+    bool valid = false;
+    DBuf tgt_perm, src_perm, stg_tgt, stg_src;
+    DBuf wu, wu_cnt, wu_off, rowcnt, lj_list, res, row_id;
+    DBuf rid_sorted, row_sorted, rows_tmp, runs, tiles, merge_a, merge_b, cub_tmp;
+    cudaEvent_t ev_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_done = nullptr, ev_packed = nullptr, ev_scattered = nullptr;
+    bool timing_valid = false;
+    float multiwave_ms[3] = {0, 0, 0};
+    uint64_t n_waves = 0;
+    std::vector<TaskRec> host_tasks;       // for gc_read_results
+    std::unordered_map<uint64_t, uint64_t> task_index;
+    bool host_tasks_valid = false;
+};
+
+struct gc_pool {
+    gc_config cfg;
+    cudaStream_t s = nullptr;         // issue stream = ctx[cur].s
     int device = 0;
     int num_sms = 0;
     int64_t rc2_grid = 0;       // cutoff^2 in (2^-21)^2 units
@@ -109,36 +136,21 @@ struct gc_pool {
     unsigned long long *d_ctr = nullptr;   // [CTR_COUNT]
     unsigned long long *h_ctr = nullptr;   // pinned copy
 
-    // pending batch (device-resident)
+    // pending batch (device-resident), swapped into a flush context by gc_flush
     uint64_t nb_tasks = 0, nb_tgt = 0, nb_src = 0;
     DBuf tasks, tgt_ids, src_ids;
     uint64_t submitted_batches = 0;   // index of the pending batch
 
-    // last executed batch
-    uint64_t last_tasks = 0, last_tgt = 0, last_src = 0, last_rows = 0;
-    uint64_t last_batch = 0;          // index of the last flushed batch
-    bool have_last = false;
-    DBuf last_tasks_buf, last_tgt_ids, last_src_ids;   // swapped with pending
+    // two flush contexts: batch k runs on ctx[k % 2]; `cur` takes the next
+    // flush, `last` holds the last flushed batch (-1: none yet)
+    FlushCtx ctx[2];
+    int cur = 0, last = -1;
 
-    // per-flush work buffers
-    DBuf tgt_perm, src_perm, stg_tgt, stg_src;
-    DBuf uniq, miss, freel, tiles, ekeys, ekeys2, evicted;
-    DBuf wu, wu_cnt, wu_off, rowcnt, res, row_id, rid_sorted, row_sorted, rows_tmp;
-    DBuf runs, merge_a, merge_b, cub_tmp, small;
+    // residency work buffers (the chare-table step is serialised)
+    DBuf uniq, miss, freel, tiles, ekeys, ekeys2, evicted, cub_tmp;
+    DBuf io_a, io_b;                  // host <-> device staging of uploads and reads
     uint64_t n_evicted_last = 0;
     uint32_t epoch = 0;
-
-    // completion
-    cudaEvent_t ev_stage[6];
-    cudaEvent_t ev_done = nullptr;
-    bool timing_valid = false;
-    float multiwave_ms[3] = {0, 0, 0};
-    uint64_t n_waves_last = 0;
-
-    // host copy of the last batch's task records (for gc_read_results)
-    std::vector<TaskRec> host_tasks;
-    std::unordered_map<uint64_t, uint64_t> task_index;
-    bool host_tasks_valid = false;
 
     gc_stats_t stats;
     NBodyState nb;
@@ -180,7 +192,16 @@ int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64
                      int write_mirror);
 
 // ---- pack / interaction / scatter (gc_kernels.cu) -----------------------------
-int gc_scatter(gc_pool *p, uint64_t n_rows);
+int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5]);
+int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
+                       std::vector<uint32_t> &lj_off);
+int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,
+            uint64_t src_base, uint64_t msrc);
+int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,
+                      uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
+int gc_interact_one_task(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,
+                         uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
+int gc_scatter(gc_pool *p, FlushCtx &c);
 int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
                       const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
                       const uint64_t *src_off, uint64_t tgt_base, uint64_t src_base,
@@ -194,8 +215,9 @@ enum CompactKind {
     CK_FREE,            // s: id_of_slot[s] == NONE           (slot space)
     CK_RUN_START        // i < count: i == 0 || key[i] != key[i-1]
 };
-int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev,
-               const uint32_t *arr, uint32_t *out, unsigned long long *count_out);
+int gc_compact(gc_pool *p, DBuf &tiles, cudaStream_t s, int kind, uint64_t n_bound,
+               const uint64_t *count_dev, const uint32_t *arr, uint32_t *out,
+               unsigned long long *count_out);
 
 // ---- builders --------------------------------------------------------------------
 // If ptr is host memory, copy bytes of it into buf (stream-ordered, then

@@ -74,8 +74,8 @@ __global__ void k_prep_counts(const TaskRec *tasks, uint64_t n, uint64_t *rows,
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     if ((threadIdx.x & 31) == 0) {
-        if (inter) atomicAdd(&ctr[CTR_INTER], inter);
-        atomicMax(&ctr[CTR_MAXLIST], (unsigned long long)mx);
+        if (inter) atomicAdd(&ctr[FC_INTER], inter);
+        atomicMax(&ctr[FC_MAXLIST], (unsigned long long)mx);
     }
 }
 
@@ -901,73 +901,76 @@ int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
     return GC_OK;
 }
 
-// Result rows, work units and LJ task list of the whole batch.  Reads back
-// {rows, gravity work units, LJ tasks, interactions, longest list}.
-int gc_prepare(gc_pool *p, TaskRec *tasks, uint64_t n, uint64_t info[5])
+// Result rows, work units and LJ task list of the batch in context c.  Reads
+// back {rows, gravity work units, LJ tasks, interactions, longest list}.
+int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
 {
-    GC_TRY(p->rowcnt.reserve((n + 1) * sizeof(uint64_t) * 2));
-    GC_TRY(p->wu_cnt.reserve((n + 1) * sizeof(uint32_t) * 2));
-    GC_TRY(p->wu_off.reserve((n + 1) * sizeof(uint32_t) * 2));
-    uint64_t *rows = p->rowcnt.as<uint64_t>();
+    const uint64_t n = c.n_tasks;
+    TaskRec *tasks = c.tasks.as<TaskRec>();
+    GC_TRY(c.rowcnt.reserve((n + 1) * sizeof(uint64_t) * 2));
+    GC_TRY(c.wu_cnt.reserve((n + 1) * sizeof(uint32_t) * 2));
+    GC_TRY(c.wu_off.reserve((n + 1) * sizeof(uint32_t) * 2));
+    uint64_t *rows = c.rowcnt.as<uint64_t>();
     uint64_t *row_off = rows + (n + 1);
-    uint32_t *wu_g = p->wu_cnt.as<uint32_t>();
+    uint32_t *wu_g = c.wu_cnt.as<uint32_t>();
     uint32_t *lj = wu_g + (n + 1);
-    uint32_t *wu_off = p->wu_off.as<uint32_t>();
+    uint32_t *wu_off = c.wu_off.as<uint32_t>();
     uint32_t *lj_off = wu_off + (n + 1);
-    GC_CUDA_TRY(cudaMemsetAsync(p->d_ctr + CTR_INTER, 0, sizeof(unsigned long long) * 5, p->s));
-    GC_CUDA_TRY(cudaMemsetAsync(rows + n, 0, sizeof(uint64_t), p->s));
-    GC_CUDA_TRY(cudaMemsetAsync(wu_g + n, 0, sizeof(uint32_t), p->s));
-    GC_CUDA_TRY(cudaMemsetAsync(lj + n, 0, sizeof(uint32_t), p->s));
+    GC_CUDA_TRY(cudaMemsetAsync(c.d_ctr, 0, sizeof(unsigned long long) * FC_COUNT, c.s));
+    GC_CUDA_TRY(cudaMemsetAsync(rows + n, 0, sizeof(uint64_t), c.s));
+    GC_CUDA_TRY(cudaMemsetAsync(wu_g + n, 0, sizeof(uint32_t), c.s));
+    GC_CUDA_TRY(cudaMemsetAsync(lj + n, 0, sizeof(uint32_t), c.s));
     ++p->stats.kernel_launches;
-    k_prep_counts<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(tasks, n, rows, wu_g, lj,
-                                                                       p->d_ctr);
+    k_prep_counts<<<grid_for(n, 256, p->num_sms * 16), 256, 0, c.s>>>(tasks, n, rows, wu_g, lj,
+                                                                       c.d_ctr);
     ++p->stats.primitive_calls;
-    GC_TRY(gc_exclusive_scan_u64(p->cub_tmp, rows, row_off, n + 1, p->s));
+    GC_TRY(gc_exclusive_scan_u64(c.cub_tmp, rows, row_off, n + 1, c.s));
     ++p->stats.primitive_calls;
-    GC_TRY(gc_exclusive_scan_u32(p->cub_tmp, wu_g, wu_off, n + 1, p->s));
+    GC_TRY(gc_exclusive_scan_u32(c.cub_tmp, wu_g, wu_off, n + 1, c.s));
     ++p->stats.primitive_calls;
-    GC_TRY(gc_exclusive_scan_u32(p->cub_tmp, lj, lj_off, n + 1, p->s));
-    // totals at index n
+    GC_TRY(gc_exclusive_scan_u32(c.cub_tmp, lj, lj_off, n + 1, c.s));
     uint64_t h_rows = 0;
     uint32_t h_wu = 0, h_lj = 0;
-    GC_CUDA_TRY(cudaMemcpyAsync(&h_rows, row_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, p->s));
-    GC_CUDA_TRY(cudaMemcpyAsync(&h_wu, wu_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, p->s));
-    GC_CUDA_TRY(cudaMemcpyAsync(&h_lj, lj_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, p->s));
-    GC_CUDA_TRY(cudaMemcpyAsync(p->h_ctr + CTR_INTER, p->d_ctr + CTR_INTER,
-                                sizeof(unsigned long long) * 5, cudaMemcpyDeviceToHost, p->s));
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
-    GC_TRY(p->wu.reserve(((uint64_t)h_wu + 1) * sizeof(GravWU)));
-    GC_TRY(p->small.reserve(((uint64_t)h_lj + 1) * sizeof(uint32_t)));
+    GC_CUDA_TRY(cudaMemcpyAsync(&h_rows, row_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaMemcpyAsync(&h_wu, wu_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaMemcpyAsync(&h_lj, lj_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaMemcpyAsync(c.h_ctr, c.d_ctr, sizeof(unsigned long long) * FC_COUNT,
+                                cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
+    GC_TRY(c.wu.reserve(((uint64_t)h_wu + 1) * sizeof(GravWU)));
+    GC_TRY(c.lj_list.reserve(((uint64_t)h_lj + 1) * sizeof(uint32_t)));
     ++p->stats.kernel_launches;
-    k_prep_fill<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
-        tasks, n, row_off, wu_off, lj_off, p->wu.as<GravWU>(), p->small.as<uint32_t>());
+    k_prep_fill<<<grid_for(n, 256, p->num_sms * 16), 256, 0, c.s>>>(
+        tasks, n, row_off, wu_off, lj_off, c.wu.as<GravWU>(), c.lj_list.as<uint32_t>());
     GC_CUDA_TRY(cudaGetLastError());
     info[0] = h_rows;
     info[1] = h_wu;
     info[2] = h_lj;
-    info[3] = p->h_ctr[CTR_INTER];
-    info[4] = p->h_ctr[CTR_MAXLIST];
+    info[3] = c.h_ctr[FC_INTER];
+    info[4] = c.h_ctr[FC_MAXLIST];
     return GC_OK;
 }
 
 // Host copies of the per-task work-unit offsets (for waves and per-task
 // launches): wu_off[0..n], lj_off[0..n].
-int gc_read_wu_offsets(gc_pool *p, uint64_t n, std::vector<uint32_t> &wu_off,
+int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
                        std::vector<uint32_t> &lj_off)
 {
+    (void)p;
+    const uint64_t n = c.n_tasks;
     wu_off.resize(n + 1);
     lj_off.resize(n + 1);
-    uint32_t *d_wu_off = p->wu_off.as<uint32_t>();
+    uint32_t *d_wu_off = c.wu_off.as<uint32_t>();
     GC_CUDA_TRY(cudaMemcpyAsync(wu_off.data(), d_wu_off, (n + 1) * sizeof(uint32_t),
-                                cudaMemcpyDeviceToHost, p->s));
+                                cudaMemcpyDeviceToHost, c.s));
     GC_CUDA_TRY(cudaMemcpyAsync(lj_off.data(), d_wu_off + (n + 1), (n + 1) * sizeof(uint32_t),
-                                cudaMemcpyDeviceToHost, p->s));
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+                                cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
     return GC_OK;
 }
 
-int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uint32_t *src_ids,
-            uint64_t t0, uint64_t t1, uint64_t tgt_base, uint64_t src_base, uint64_t msrc)
+int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,
+            uint64_t src_base, uint64_t msrc)
 {
     if (t1 <= t0) return GC_OK;
     static bool attr_set = false;
@@ -977,69 +980,65 @@ int gc_pack(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids, const uin
                                          (int)sizeof(PackSmem<PK_CAP>)));
         GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_mid, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(PackSmemMid)));
-
         attr_set = true;
     }
     PackArgs a;
-    a.tasks = tasks;
+    a.tasks = c.tasks.as<TaskRec>();
     a.t0 = t0;
     a.n_lists = 2 * (t1 - t0);
-    a.tgt_ids = tgt_ids;
-    a.src_ids = src_ids;
+    a.tgt_ids = c.tgt_ids.as<uint32_t>();
+    a.src_ids = c.src_ids.as<uint32_t>();
     a.slot_of_id = p->d_slot_of_id;
     a.task_base = t0;
     int bits = 1;
     while (bits < 32 && ((uint64_t)1 << bits) < p->cfg.pool_capacity) ++bits;
     a.passes = (bits + 7) / 8;
-    a.perm_t = p->tgt_perm.as<uint32_t>();
-    a.perm_s = p->src_perm.as<uint32_t>();
-    a.stg_t = p->stg_tgt.as<float4>();
-    a.stg_s = p->stg_src.as<float4>();
+    a.perm_t = c.tgt_perm.as<uint32_t>();
+    a.perm_s = c.src_perm.as<uint32_t>();
+    a.stg_t = c.stg_tgt.as<float4>();
+    a.stg_s = c.stg_src.as<float4>();
     a.tgt_base = tgt_base;
     a.src_base = src_base;
     a.pool = p->d_pool;
-    a.ma = p->merge_a.as<uint64_t>();
-    a.mb = p->merge_b.as<uint64_t>();
+    a.ma = c.merge_a.as<uint64_t>();
+    a.mb = c.merge_b.as<uint64_t>();
     a.msrc = msrc;
-
     ++p->stats.kernel_launches;
-    k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, p->s>>>(a);
+    k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, c.s>>>(a);
     ++p->stats.kernel_launches;
     k_pack_mid<<<grid_for(a.n_lists, 1, p->num_sms * 8), PM_THREADS, sizeof(PackSmemMid),
-                 p->s>>>(a);
+                 c.s>>>(a);
     ++p->stats.kernel_launches;
     k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
-                           sizeof(PackSmem<PK_CAP>), p->s>>>(a);
+                           sizeof(PackSmem<PK_CAP>), c.s>>>(a);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
 
-static int fill_inter_args(gc_pool *p, const TaskRec *tasks, uint64_t tgt_base,
-                           uint64_t src_base, uint64_t task_base, const uint32_t *tgt_ids,
-                           const uint32_t *src_ids, InterArgs &a)
+static void fill_inter_args(gc_pool *p, FlushCtx &c, uint64_t tgt_base, uint64_t src_base,
+                            uint64_t task_base, InterArgs &a)
 {
-    a.tasks = tasks;
+    a.tasks = c.tasks.as<TaskRec>();
     a.task_base = task_base;
-    a.stg_t = p->stg_tgt.as<float4>();
-    a.stg_s = p->stg_src.as<float4>();
+    a.stg_t = c.stg_tgt.as<float4>();
+    a.stg_s = c.stg_src.as<float4>();
     a.tgt_base = tgt_base;
     a.src_base = src_base;
-    a.perm_t = p->tgt_perm.as<uint32_t>();
-    a.perm_s = p->src_perm.as<uint32_t>();
-    a.tgt_ids = tgt_ids;
-    a.src_ids = src_ids;
+    a.perm_t = c.tgt_perm.as<uint32_t>();
+    a.perm_s = c.src_perm.as<uint32_t>();
+    a.tgt_ids = c.tgt_ids.as<uint32_t>();
+    a.src_ids = c.src_ids.as<uint32_t>();
     a.eps2 = p->cfg.eps2;
     a.lj_eps24 = 24.0f * p->cfg.lj_eps;
     a.lj_eps4 = 4.0f * p->cfg.lj_eps;
     a.lj_sig2 = p->cfg.lj_sigma * p->cfg.lj_sigma;
     a.rc2_grid = p->rc2_grid;
     a.edge_grid = p->md_edge_grid;
-    a.res = p->res.as<float4>();
-    a.row_id = p->row_id.as<uint32_t>();
-    a.queue = p->d_ctr + CTR_QUEUE;
-    a.lj_in = p->d_ctr + CTR_LJ_IN;
+    a.res = c.res.as<float4>();
+    a.row_id = c.row_id.as<uint32_t>();
+    a.queue = c.d_ctr + FC_QUEUE;
+    a.lj_in = c.d_ctr + FC_LJ_IN;
     a.flags = p->d_ctr + CTR_FLAGS;
-    return GC_OK;
 }
 
 static int grav_setup()
@@ -1076,34 +1075,33 @@ extern "C" int gc_max_combine_size(gc_pool_t *p, uint64_t *out)
 
 // Launch the interaction kernels over gravity work units [w0, w1) and LJ
 // tasks [l0, l1) of the prepared batch.
-int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
-                      const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
+int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,
                       uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base)
 {
     InterArgs a;
-    fill_inter_args(p, tasks, tgt_base, src_base, task_base, tgt_ids, src_ids, a);
-    int full = gc_grav_blocks(p);
+    fill_inter_args(p, c, tgt_base, src_base, task_base, a);
+    const int full = gc_grav_blocks(p);
     if (w1 > w0) {
-        a.wu = p->wu.as<GravWU>() + w0;
+        a.wu = c.wu.as<GravWU>() + w0;
         a.n_wu = w1 - w0;
         a.lj_list = nullptr;
         a.n_lj = 0;
-        GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), p->s));
-        uint64_t need = (a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS;
-        unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
+        GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
+        const uint64_t need = (a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS;
+        const unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
         ++p->stats.kernel_launches;
-        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), p->s>>>(a);
+        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), c.s>>>(a);
     }
     if (l1 > l0) {
         a.wu = nullptr;
         a.n_wu = 0;
-        a.lj_list = p->small.as<uint32_t>() + l0;
+        a.lj_list = c.lj_list.as<uint32_t>() + l0;
         a.n_lj = l1 - l0;
-        GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), p->s));
-        uint64_t need = (a.n_lj + GRAV_WARPS - 1) / GRAV_WARPS;
-        unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
+        GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
+        const uint64_t need = (a.n_lj + GRAV_WARPS - 1) / GRAV_WARPS;
+        const unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
         ++p->stats.kernel_launches;
-        k_lj<<<g, GRAV_THREADS, 0, p->s>>>(a);
+        k_lj<<<g, GRAV_THREADS, 0, c.s>>>(a);
     }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
@@ -1111,57 +1109,57 @@ int gc_interact_range(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
 
 // One launch per task (the uncombined baseline): the same kernels, static
 // work assignment, grid sized to the task.
-int gc_interact_one_task(gc_pool *p, const TaskRec *tasks, const uint32_t *tgt_ids,
-                         const uint32_t *src_ids, uint64_t w0, uint64_t w1, uint64_t l0,
+int gc_interact_one_task(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,
                          uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base)
 {
     InterArgs a;
-    fill_inter_args(p, tasks, tgt_base, src_base, task_base, tgt_ids, src_ids, a);
+    fill_inter_args(p, c, tgt_base, src_base, task_base, a);
     a.queue = nullptr;
     if (w1 > w0) {
-        a.wu = p->wu.as<GravWU>() + w0;
+        a.wu = c.wu.as<GravWU>() + w0;
         a.n_wu = w1 - w0;
         a.lj_list = nullptr;
         a.n_lj = 0;
-        unsigned g = (unsigned)((a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS);
+        const unsigned g = (unsigned)((a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS);
         GC_TRY(grav_setup());
         ++p->stats.kernel_launches;
-        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), p->s>>>(a);
+        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), c.s>>>(a);
     }
     if (l1 > l0) {
         a.wu = nullptr;
         a.n_wu = 0;
-        a.lj_list = p->small.as<uint32_t>() + l0;
+        a.lj_list = c.lj_list.as<uint32_t>() + l0;
         a.n_lj = l1 - l0;
         ++p->stats.kernel_launches;
-        k_lj<<<1, 32, 0, p->s>>>(a);
+        k_lj<<<1, 32, 0, c.s>>>(a);
     }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
 
-int gc_scatter(gc_pool *p, uint64_t n_rows)
+int gc_scatter(gc_pool *p, FlushCtx &c)
 {
+    const uint64_t n_rows = c.n_rows;
     if (n_rows == 0) return GC_OK;
-    GC_TRY(p->rows_tmp.reserve(n_rows * sizeof(uint32_t)));
-    GC_TRY(p->rid_sorted.reserve(n_rows * sizeof(uint32_t)));
-    GC_TRY(p->row_sorted.reserve(n_rows * sizeof(uint32_t)));
-    GC_TRY(p->runs.reserve((n_rows + 1) * sizeof(uint32_t)));
+    GC_TRY(c.rows_tmp.reserve(n_rows * sizeof(uint32_t)));
+    GC_TRY(c.rid_sorted.reserve(n_rows * sizeof(uint32_t)));
+    GC_TRY(c.row_sorted.reserve(n_rows * sizeof(uint32_t)));
+    GC_TRY(c.runs.reserve((n_rows + 1) * sizeof(uint32_t)));
     const int maxb = p->num_sms * 16;
     ++p->stats.kernel_launches;
-    k_iota<<<grid_for(n_rows, 256, maxb), 256, 0, p->s>>>(p->rows_tmp.as<uint32_t>(), n_rows);
+    k_iota<<<grid_for(n_rows, 256, maxb), 256, 0, c.s>>>(c.rows_tmp.as<uint32_t>(), n_rows);
     int bits = 1;
     while (bits < 32 && ((uint64_t)1 << bits) < p->cfg.id_capacity) ++bits;
     ++p->stats.primitive_calls;
-    GC_TRY(gc_sort_pairs_u32(p->cub_tmp, p->row_id.as<uint32_t>(), p->rid_sorted.as<uint32_t>(),
-                             p->rows_tmp.as<uint32_t>(), p->row_sorted.as<uint32_t>(), n_rows,
-                             bits, p->s));
-    GC_TRY(gc_compact(p, CK_RUN_START, n_rows, nullptr, p->rid_sorted.as<uint32_t>(),
-                      p->runs.as<uint32_t>(), p->d_ctr + CTR_RUNS));
+    GC_TRY(gc_sort_pairs_u32(c.cub_tmp, c.row_id.as<uint32_t>(), c.rid_sorted.as<uint32_t>(),
+                             c.rows_tmp.as<uint32_t>(), c.row_sorted.as<uint32_t>(), n_rows,
+                             bits, c.s));
+    GC_TRY(gc_compact(p, c.tiles, c.s, CK_RUN_START, n_rows, nullptr,
+                      c.rid_sorted.as<uint32_t>(), c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS));
     ++p->stats.kernel_launches;
-    k_reduce_runs<<<grid_for(n_rows, 256, maxb), 256, 0, p->s>>>(
-        p->runs.as<uint32_t>(), p->d_ctr + CTR_RUNS, n_rows, p->rid_sorted.as<uint32_t>(),
-        p->row_sorted.as<uint32_t>(), p->res.as<float4>(), p->d_totals);
+    k_reduce_runs<<<grid_for(n_rows, 256, maxb), 256, 0, c.s>>>(
+        c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, n_rows, c.rid_sorted.as<uint32_t>(),
+        c.row_sorted.as<uint32_t>(), c.res.as<float4>(), p->d_totals);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }

@@ -395,7 +395,9 @@ __global__ void k_walk_items(const uint4 *node_a, uint32_t nn, uint32_t *item_lo
     }
 }
 
-// One thread per (bucket, item); items of a bucket are adjacent.
+// One thread per (bucket, item).  Threads run item-major (a warp walks the
+// same subtree for 32 consecutive buckets, which take similar paths); the
+// lengths and offsets are stored bucket-major (the order of the lists).
 template <bool FILL>
 __global__ void k_walk(const uint4 *node_a, const uint4 *node_b, const uint32_t *item_lo,
                        const uint32_t *item_hi, const uint4 *bucket, const int4 *blo,
@@ -403,9 +405,10 @@ __global__ void k_walk(const uint4 *node_a, const uint4 *node_b, const uint32_t 
                        uint32_t n_part, WalkThresholds th, uint32_t *len, const uint64_t *off,
                        uint32_t *out)
 {
-    GRID_STRIDE(it, nb * WALK_ITEMS) {
-        const uint64_t b = it / WALK_ITEMS;
-        const int j = (int)(it % WALK_ITEMS);
+    GRID_STRIDE(t, nb * WALK_ITEMS) {
+        const uint64_t b = t % nb;
+        const int j = (int)(t / nb);
+        const uint64_t it = b * WALK_ITEMS + (uint64_t)j;
         const uint32_t k0 = item_lo[j], k1 = item_hi[j];
         uint32_t cnt = 0;
         if (k1 > k0)
@@ -668,9 +671,11 @@ extern "C" int gc_read_nbody_tree(gc_pool_t *p, uint32_t *sorted_ids, uint64_t *
         if (p->nb_src >= S.n_list && p->nb_tasks >= NB) {
             src = p->src_ids.as<uint32_t>();
             base = p->nb_src - S.n_list;
-        } else if (p->have_last && p->last_src >= S.n_list) {
-            src = p->last_src_ids.as<uint32_t>();
-            base = p->last_src - S.n_list;
+        } else if (p->last >= 0 && p->ctx[p->last].valid && p->ctx[p->last].n_src >= S.n_list) {
+            const FlushCtx &c = p->ctx[p->last];
+            GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
+            src = c.src_ids.as<uint32_t>();
+            base = c.n_src - S.n_list;
         }
         if (!src) return GC_ERR_STATE;
         GC_CUDA_TRY(cudaMemcpy(list_ids, src + base, S.n_list * 4, cudaMemcpyDeviceToHost));

@@ -321,25 +321,26 @@ inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
 }  // namespace
 
 // Slots of the given ids (introspection of the chare table).
-int gc_entry_slots(gc_pool *p, const uint32_t *ids, uint64_t n, uint32_t *out)
+int gc_entry_slots(gc_pool *p, cudaStream_t s, const uint32_t *ids, uint64_t n, uint32_t *out)
 {
     if (n == 0) return GC_OK;
     ++p->stats.kernel_launches;
-    k_entry_slots<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(ids, n, p->d_slot_of_id,
-                                                                      out);
+    k_entry_slots<<<grid_for(n, 256, p->num_sms * 16), 256, 0, s>>>(ids, n, p->d_slot_of_id,
+                                                                    out);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
 
-int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev,
-               const uint32_t *arr, uint32_t *out, unsigned long long *count_out)
+int gc_compact(gc_pool *p, DBuf &tiles, cudaStream_t s, int kind, uint64_t n_bound,
+               const uint64_t *count_dev, const uint32_t *arr, uint32_t *out,
+               unsigned long long *count_out)
 {
     uint64_t n_tiles = (n_bound + CT_TILE - 1) / CT_TILE;
     if (n_tiles == 0) {
-        GC_CUDA_TRY(cudaMemsetAsync(count_out, 0, sizeof(unsigned long long), p->s));
+        GC_CUDA_TRY(cudaMemsetAsync(count_out, 0, sizeof(unsigned long long), s));
         return GC_OK;
     }
-    GC_TRY(p->tiles.reserve(n_tiles * sizeof(uint32_t)));
+    GC_TRY(tiles.reserve(n_tiles * sizeof(uint32_t)));
     CompactArgs a;
     a.kind = kind;
     a.n = n_bound;
@@ -350,11 +351,11 @@ int gc_compact(gc_pool *p, int kind, uint64_t n_bound, const uint64_t *count_dev
     a.id_of_slot = p->d_id_of_slot;
     a.epoch = p->epoch;
     ++p->stats.kernel_launches;
-    k_compact_count<<<(unsigned)n_tiles, CT_THREADS, 0, p->s>>>(a, p->tiles.as<uint32_t>());
+    k_compact_count<<<(unsigned)n_tiles, CT_THREADS, 0, s>>>(a, tiles.as<uint32_t>());
     ++p->stats.kernel_launches;
-    k_compact_scan<<<1, CT_THREADS, 0, p->s>>>(p->tiles.as<uint32_t>(), n_tiles, count_out);
+    k_compact_scan<<<1, CT_THREADS, 0, s>>>(tiles.as<uint32_t>(), n_tiles, count_out);
     ++p->stats.kernel_launches;
-    k_compact_write<<<(unsigned)n_tiles, CT_THREADS, 0, p->s>>>(a, p->tiles.as<uint32_t>(), out);
+    k_compact_write<<<(unsigned)n_tiles, CT_THREADS, 0, s>>>(a, tiles.as<uint32_t>(), out);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
@@ -407,14 +408,14 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
     GC_TRY(p->uniq.reserve((ubound + 1) * sizeof(uint32_t)));
     GC_TRY(p->miss.reserve((ubound + 1) * sizeof(uint32_t)));
     GC_TRY(p->freel.reserve((cap + 1) * sizeof(uint32_t)));
-    GC_TRY(gc_compact(p, CK_REF_EPOCH, id_cap, nullptr, nullptr, p->uniq.as<uint32_t>(),
+    GC_TRY(gc_compact(p, p->tiles, p->s, CK_REF_EPOCH, id_cap, nullptr, nullptr, p->uniq.as<uint32_t>(),
                       ctr + CTR_UNIQUE));
     ++p->stats.kernel_launches;
     k_classify<<<grid_for(ubound, 256, maxb), 256, 0, p->s>>>(
         p->uniq.as<uint32_t>(), ctr + CTR_UNIQUE, p->d_slot_of_id, p->d_ref_count, ctr);
-    GC_TRY(gc_compact(p, CK_MISS, ubound, (const uint64_t *)(ctr + CTR_UNIQUE),
+    GC_TRY(gc_compact(p, p->tiles, p->s, CK_MISS, ubound, (const uint64_t *)(ctr + CTR_UNIQUE),
                       p->uniq.as<uint32_t>(), p->miss.as<uint32_t>(), ctr + CTR_MISSES));
-    GC_TRY(gc_compact(p, CK_FREE, cap, nullptr, nullptr, p->freel.as<uint32_t>(),
+    GC_TRY(gc_compact(p, p->tiles, p->s, CK_FREE, cap, nullptr, nullptr, p->freel.as<uint32_t>(),
                       ctr + CTR_FREE));
     GC_CUDA_TRY(cudaMemcpyAsync(p->h_ctr, ctr, sizeof(unsigned long long) * CTR_COUNT,
                                 cudaMemcpyDeviceToHost, p->s));
@@ -448,7 +449,7 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         k_evict_apply<<<grid_for(need, 256, maxb), 256, 0, p->s>>>(
             p->ekeys2.as<uint64_t>(), need, p->d_id_of_slot, p->d_slot_of_id, p->d_pool,
             p->d_mirror, p->evicted.as<uint32_t>());
-        GC_TRY(gc_compact(p, CK_FREE, cap, nullptr, nullptr, p->freel.as<uint32_t>(),
+        GC_TRY(gc_compact(p, p->tiles, p->s, CK_FREE, cap, nullptr, nullptr, p->freel.as<uint32_t>(),
                           ctr + CTR_FREE));
         p->n_evicted_last = need;
     }

@@ -91,6 +91,7 @@ _SIGS = {
     "gc_flush": [P],
     "gc_flush_per_task": [P],
     "gc_wait": [P, U64, U64],
+    "gc_batch_done": [P, U64, C.POINTER(C.c_int)],
     "gc_result_rows": [P, U64P],
     "gc_read_batch_results": [P, U64, U64, P],
     "gc_read_results": [P, P, U64, P],
@@ -251,6 +252,11 @@ class Pool:
 
     def flush_per_task(self):
         _check(self.lib.gc_flush_per_task(self.h), "gc_flush_per_task")
+
+    def done(self, batch):
+        d = C.c_int()
+        _check(self.lib.gc_batch_done(self.h, int(batch), C.byref(d)), "gc_batch_done")
+        return bool(d.value)
 
     def wait(self, batch, timeout_ns=0):
         _check(self.lib.gc_wait(self.h, int(batch), int(timeout_ns)), "gc_wait")
