@@ -44,6 +44,11 @@ WORKLOAD = ("nbody_plummer_1M: 1,048,576 Plummer particles, theta=0.7, buckets<=
 FLOPS_PER_INTERACTION = 19
 SM_COUNT = 152
 FP32_LANES = 128
+# DRAM bytes (read + write) per interaction of k_gravity, from one ncu capture
+# of the 262,144-particle step (profiles/k_gravity_nbody262k.md: 505.7 MB for
+# ~2.98e8 interactions); traffic scales with the list entries, i.e. with the
+# interactions at a fixed bucket occupancy.
+GRAVITY_DRAM_BYTES_PER_INTERACTION = 505.7e6 / 2.98e8
 
 
 def peaks():
@@ -337,7 +342,8 @@ def main():
                        "l2": "inputs larger than L2 (staging ~4 GB per step)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": GRAVITY_DRAM_BYTES_PER_INTERACTION * avg_int_n,
                          "kernel": "k_gravity",
                          "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x "
                                        f"{sm_max:.0f} MHz (fallback derivation, no FP32 "
