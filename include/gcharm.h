@@ -210,6 +210,12 @@ int gc_result_rows(gc_pool_t *pool, uint64_t *rows_out);
 int gc_read_batch_results(gc_pool_t *pool, uint64_t first_row, uint64_t n_rows,
                           float *out);
 
+/* As gc_read_batch_results, for batch `batch` (one of the two most recently
+ * flushed batches).  Waits for that batch.  Errors: GC_ERR_ARG (batch no
+ * longer held, range outside the batch). */
+int gc_read_batch_rows(gc_pool_t *pool, uint64_t batch, uint64_t first_row, uint64_t n_rows,
+                       float *out);
+
 /* Copy the result rows of the tasks with the given tags (each from the last
  * batch), task after task, 8 floats per row.  Errors: GC_ERR_ARG (tag not in
  * the last batch). */
@@ -325,6 +331,10 @@ int gc_last_timings(gc_pool_t *pool, float ms_out[5]);
 #define GC_COMBINE_STATIC 2          /* paper's baseline: all pending every static_n
                                         arrivals (100 in Section 4.3)                    */
 #define GC_COMBINE_PER_TASK 3        /* no combining: one task per batch                */
+#define GC_COMBINE_GREEDY 4          /* every poll: all pending, up to maxSize (no
+                                        counterpart in the paper; work-conserving form
+                                        for a caller that polls when the device has
+                                        room for another batch)                          */
 
 typedef struct gc_combiner gc_combiner_t;
 
@@ -334,8 +344,9 @@ typedef struct gc_combiner gc_combiner_t;
  * poll, with >= maxSize pending combine maxSize, otherwise combine all
  * pending once the time since the last arrival exceeds 2 x maxInterval.
  * GC_COMBINE_STATIC combines all pending after every static_n arrivals
- * (the paper's static strategy, Section 4.3).  Host-side, no device work.
- * Errors: GC_ERR_ARG (unknown policy, max_size 0 for the adaptive rules,
+ * (the paper's static strategy, Section 4.3).  GC_COMBINE_GREEDY combines
+ * min(pending, maxSize) at every poll.  Host-side, no device work.
+ * Errors: GC_ERR_ARG (unknown policy, max_size 0 for the adaptive and greedy rules,
  * static_n 0 for the static rule, window 0 for the windowed rule). */
 int gc_combiner_create(int policy, uint64_t max_size, uint64_t static_n, uint64_t window,
                        gc_combiner_t **out);
@@ -360,6 +371,53 @@ uint64_t gc_combine_size_from_occupancy(double occupancy, uint32_t max_blocks_pe
  * kernel keeps resident at once, from cudaOccupancyMaxActiveBlocksPerMultiprocessor
  * x warps per block x SMs. */
 int gc_max_combine_size(gc_pool_t *pool, uint64_t *out);
+
+/* ---- serving loop (Section 3.1: requests combined as they arrive) -------- */
+
+typedef struct {
+    int policy;               /* GC_COMBINE_*                                  */
+    uint64_t max_size;        /* maxSize in requests; 0 = gc_max_combine_size  */
+    uint64_t static_n;        /* GC_COMBINE_STATIC: arrivals per combine       */
+    uint64_t window;          /* GC_COMBINE_ADAPTIVE_WINDOW: intervals kept    */
+    uint32_t max_in_flight;   /* batches on the device at once: 1 or 2         */
+    uint64_t poll_ns;         /* longest idle sleep while nothing is queued    */
+    uint64_t timeout_ns;      /* a batch not complete after this long fails the
+                                 call with GC_ERR_TIMEOUT; 0 = 60 s           */
+} gc_serve_config;
+
+typedef struct {
+    uint64_t tasks, batches;
+    uint64_t interactions;    /* pair interactions evaluated by the call       */
+    uint64_t max_size;        /* maxSize used                                  */
+    double wall_s;            /* first scheduled arrival .. last completion    */
+    double interactions_per_s;
+    double lat_mean_us, lat_p50_us, lat_p99_us, lat_max_us;
+    double mean_batch;        /* tasks per batch                               */
+    double busy_s;            /* time with requests queued and no free batch
+                                 slot (both flush contexts busy)              */
+} gc_serve_report;
+
+/* Replay an open-loop arrival schedule in real time on this thread: task t
+ * (CSR arrays as in gc_submit_csr, host memory, offsets starting at 0)
+ * becomes pending at arrival_ns[t] nanoseconds after the call starts
+ * (non-decreasing).  The loop tells the combiner of each arrival, retires
+ * completed batches without blocking, and, while fewer than max_in_flight
+ * batches run, asks the combiner how many pending tasks to combine, admits
+ * the oldest of them that fit the pool's staging budget (at least one) and
+ * flushes them: a batch's chare-table step and pack then overlap the
+ * interaction of the batch before it.  The static rule drains what is left
+ * once the schedule has ended.  Latency of a task = completion observed by
+ * the loop - its scheduled arrival (CLOCK_MONOTONIC), so queueing behind a
+ * busy device is counted.  latency_ns_out (n values) and results_out (8
+ * floats per result row, rows of task after task as gc_read_batch_results
+ * gives them) may be NULL.  The pool must have no pending tasks; per-id
+ * totals accumulate as for any flush.  Errors: GC_ERR_ARG (bad pointers,
+ * decreasing arrivals, max_in_flight not 1 or 2), GC_ERR_STATE (pending
+ * tasks), GC_ERR_TIMEOUT, and any error of gc_submit_csr / gc_flush. */
+int gc_serve(gc_pool_t *pool, uint64_t n, const uint64_t *arrival_ns, const uint32_t *kinds,
+             const int8_t *shifts, const uint64_t *tgt_off, const uint32_t *tgt_ids,
+             const uint64_t *src_off, const uint32_t *src_ids, const gc_serve_config *cfg,
+             uint64_t *latency_ns_out, float *results_out, gc_serve_report *report);
 
 /* ---- evaluation without allocation -------------------------------------- */
 

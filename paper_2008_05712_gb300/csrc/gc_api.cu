@@ -742,6 +742,20 @@ int gc_read_batch_results(gc_pool_t *p, uint64_t first_row, uint64_t n_rows, flo
     return GC_OK;
 }
 
+int gc_read_batch_rows(gc_pool_t *p, uint64_t batch, uint64_t first_row, uint64_t n_rows,
+                       float *out)
+{
+    if (!p || (n_rows && !out)) return GC_ERR_ARG;
+    FlushCtx *c = ctx_of(p, batch);
+    if (!c || !c->valid) return GC_ERR_ARG;
+    if (first_row + n_rows > c->n_rows) return GC_ERR_ARG;
+    GC_CUDA_TRY(cudaEventSynchronize(c->ev_done));
+    if (n_rows)
+        GC_CUDA_TRY(cudaMemcpy(out, c->res.as<float4>() + 2 * first_row,
+                               n_rows * 2 * sizeof(float4), cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
 static int ensure_host_tasks(FlushCtx &c)
 {
     if (c.host_tasks_valid) return GC_OK;

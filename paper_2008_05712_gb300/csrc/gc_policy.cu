@@ -8,7 +8,10 @@
 // pending it combines maxSize of them; with fewer, it combines everything
 // pending once the time since the last arrival exceeds 2 x maxInterval.
 // The paper's static baseline (Section 4.3) combines whatever is pending
-// after every 100 requests.  Host-side logic only (no device work).
+// after every 100 requests.  The greedy rule (no counterpart in the paper)
+// is the work-conserving form for a caller that polls only when it has room
+// for another batch on the device: combine everything pending, up to
+// maxSize, at every poll.  Host-side logic only (no device work).
 #include <cmath>
 #include <deque>
 
@@ -33,8 +36,9 @@ int gc_combiner_create(int policy, uint64_t max_size, uint64_t static_n, uint64_
 {
     if (!out) return GC_ERR_ARG;
     *out = nullptr;
-    if (policy < GC_COMBINE_ADAPTIVE || policy > GC_COMBINE_PER_TASK) return GC_ERR_ARG;
-    if ((policy == GC_COMBINE_ADAPTIVE || policy == GC_COMBINE_ADAPTIVE_WINDOW) && max_size == 0)
+    if (policy < GC_COMBINE_ADAPTIVE || policy > GC_COMBINE_GREEDY) return GC_ERR_ARG;
+    if ((policy == GC_COMBINE_ADAPTIVE || policy == GC_COMBINE_ADAPTIVE_WINDOW ||
+         policy == GC_COMBINE_GREEDY) && max_size == 0)
         return GC_ERR_ARG;
     if (policy == GC_COMBINE_STATIC && static_n == 0) return GC_ERR_ARG;
     if (policy == GC_COMBINE_ADAPTIVE_WINDOW && window == 0) return GC_ERR_ARG;
@@ -95,6 +99,9 @@ int gc_combiner_poll(gc_combiner_t *c, uint64_t t_ns, uint64_t queued, uint64_t 
         }
         case GC_COMBINE_STATIC:
             if (c->since_combine >= c->static_n) take = queued;
+            break;
+        case GC_COMBINE_GREEDY:
+            take = queued < c->max_size ? queued : c->max_size;
             break;
         default:   // GC_COMBINE_PER_TASK
             take = 1;

@@ -38,6 +38,7 @@ GC_COMBINE_ADAPTIVE = 0
 GC_COMBINE_ADAPTIVE_WINDOW = 1
 GC_COMBINE_STATIC = 2
 GC_COMBINE_PER_TASK = 3
+GC_COMBINE_GREEDY = 4
 
 NONE32 = 0xFFFFFFFF
 
@@ -67,6 +68,22 @@ class GcStats(C.Structure):
                 + [("kernel_launches", C.c_uint64), ("primitive_calls", C.c_uint64)])
 
 
+class GcServeConfig(C.Structure):
+    _fields_ = [("policy", C.c_int), ("max_size", C.c_uint64), ("static_n", C.c_uint64),
+                ("window", C.c_uint64), ("max_in_flight", C.c_uint32),
+                ("poll_ns", C.c_uint64), ("timeout_ns", C.c_uint64)]
+
+
+_SERVE_FIELDS = ["tasks", "batches", "interactions", "max_size"]
+_SERVE_DFIELDS = ["wall_s", "interactions_per_s", "lat_mean_us", "lat_p50_us", "lat_p99_us",
+                  "lat_max_us", "mean_batch", "busy_s"]
+
+
+class GcServeReport(C.Structure):
+    _fields_ = ([(f, C.c_uint64) for f in _SERVE_FIELDS]
+                + [(f, C.c_double) for f in _SERVE_DFIELDS])
+
+
 class GcError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -94,6 +111,7 @@ _SIGS = {
     "gc_batch_done": [P, U64, C.POINTER(C.c_int)],
     "gc_result_rows": [P, U64P],
     "gc_read_batch_results": [P, U64, U64, P],
+    "gc_read_batch_rows": [P, U64, U64, U64, P],
     "gc_read_results": [P, P, U64, P],
     "gc_read_totals": [P, P, U64, P],
     "gc_totals_device": [P, C.POINTER(P)],
@@ -118,6 +136,8 @@ _SIGS = {
     "gc_combiner_max_interval": [P, U64P],
     "gc_combine_size_from_occupancy": [C.c_double, C.c_uint32, C.c_uint32],
     "gc_max_combine_size": [P, U64P],
+    "gc_serve": [P, U64, P, P, P, P, P, P, P, C.POINTER(GcServeConfig), P, P,
+                 C.POINTER(GcServeReport)],
 }
 
 _RESTYPES = {"gc_strerror": C.c_char_p, "gc_combine_size_from_occupancy": C.c_uint64}
@@ -275,6 +295,44 @@ class Pool:
         _check(self.lib.gc_read_batch_results(self.h, first, n, _p(out)),
                "gc_read_batch_results")
         return out
+
+    def batch_rows(self, batch, first=0, n=None):
+        """Result rows of one of the two most recent batches, like results()."""
+        if n is None:
+            raise ValueError("n is required")
+        out = np.empty((n, 8), np.float32)
+        _check(self.lib.gc_read_batch_rows(self.h, int(batch), first, n, _p(out)),
+               "gc_read_batch_rows")
+        return out
+
+    def serve(self, arrival_ns, kinds, tgt_off, tgt_ids, src_off, src_ids, shifts=None,
+              policy=GC_COMBINE_GREEDY, max_size=0, static_n=100, window=1024,
+              max_in_flight=2, poll_ns=50_000, timeout_ns=0, want_results=False):
+        """Replay an arrival schedule through the serving loop (gc_serve).
+
+        Returns (report dict, latency_ns array, rows or None); rows are the
+        result rows of every task in task order, (n_rows, 8) float32."""
+        arr = np.ascontiguousarray(arrival_ns, np.uint64)
+        kinds = np.ascontiguousarray(kinds, np.uint32)
+        to = np.ascontiguousarray(tgt_off, np.uint64)
+        so = np.ascontiguousarray(src_off, np.uint64)
+        tg = np.ascontiguousarray(tgt_ids, np.uint32)
+        sr = np.ascontiguousarray(src_ids, np.uint32)
+        sh = None if shifts is None else np.ascontiguousarray(shifts, np.int8)
+        n = arr.shape[0]
+        cfg = GcServeConfig(policy=policy, max_size=max_size, static_n=static_n, window=window,
+                            max_in_flight=max_in_flight, poll_ns=poll_ns, timeout_ns=timeout_ns)
+        lat = np.zeros(n, np.uint64)
+        rows = None
+        if want_results:
+            n_rows = int(to[-1]) + int(np.sum((so[1:] - so[:-1])[kinds == GC_LJ_PAIR]))
+            rows = np.zeros((n_rows, 8), np.float32)
+        rep = GcServeReport()
+        _check(self.lib.gc_serve(self.h, n, _p(arr), _p(kinds), _p(sh), _p(to), _p(tg), _p(so),
+                                 _p(sr), C.byref(cfg), _p(lat), _p(rows), C.byref(rep)),
+               "gc_serve")
+        d = {f: getattr(rep, f) for f in _SERVE_FIELDS + _SERVE_DFIELDS}
+        return d, lat, rows
 
     def read_results(self, task_ids, n_rows):
         ti = np.ascontiguousarray(task_ids, np.uint64)

@@ -221,3 +221,26 @@ def random_id_batches(id_space: int, n_batches: int, per_batch: int, seed: int,
         g.shuffle(v)
         out.append(v)
     return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int, producers: int = 16) -> np.ndarray:
+    """Open-loop arrival schedule of ``n`` requests, uint64 nanoseconds.
+
+    ``producers`` independent Poisson producers, each at ``rate/producers``
+    requests per second (exponential inter-arrival times), merged in time
+    order; the merged stream is Poisson at the aggregate ``rate``.  Returns
+    the first ``n`` arrival times of the merged stream, non-decreasing.
+    """
+    g = rng(seed)
+    per = rate / producers
+    # enough arrivals per producer to cover the first n of the merge with
+    # overwhelming probability
+    k = int(n / producers + 8 * math.sqrt(n / producers) + 16)
+    while True:
+        gaps = g.exponential(1.0 / per, size=(producers, k))
+        t = np.cumsum(gaps, axis=1).ravel()
+        t.sort()
+        horizon = np.cumsum(gaps, axis=1)[:, -1].min()
+        if t.shape[0] >= n and t[n - 1] <= horizon:
+            return np.round(t[:n] * 1e9).astype(np.uint64)
+        k *= 2

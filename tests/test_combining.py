@@ -89,3 +89,35 @@ def test_per_task_and_bad_arguments():
                  (g.GC_COMBINE_ADAPTIVE_WINDOW, 4, 0, 0), (7, 1, 1, 1)]:
         with pytest.raises(g.GcError):
             g.Combiner(*args)
+
+
+def test_greedy_takes_everything_up_to_max_size():
+    c = g.Combiner(g.GC_COMBINE_GREEDY, max_size=5)
+    assert c.poll(0, 0) == 0
+    assert c.poll(0, 3) == 3              # no waiting: all pending
+    assert c.poll(0, 12) == 5             # capped at maxSize
+    with pytest.raises(g.GcError):
+        g.Combiner(g.GC_COMBINE_GREEDY, max_size=0)
+
+
+def test_adaptive_rule_under_poisson_arrivals_waits_for_max_size():
+    """With Poisson arrivals the idle timeout 2 x maxInterval (running max of
+    the gaps) almost never expires between arrivals, so the adaptive rule
+    combines at maxSize; the greedy rule combines at every poll."""
+    import numpy as np
+    from paper_2008_05712_gb300 import inputs
+    arr = inputs.poisson_arrivals(4000, 1e4, 3)
+    for policy, window in [(g.GC_COMBINE_ADAPTIVE, 0), (g.GC_COMBINE_ADAPTIVE_WINDOW, 256)]:
+        c = g.Combiner(policy, max_size=64, window=window)
+        queued, sizes = 0, []
+        for k, t in enumerate(arr):
+            c.arrive(int(t))
+            queued += 1
+            # poll just before the next arrival (the longest the queue can idle)
+            t_poll = int(arr[k + 1]) - 1 if k + 1 < len(arr) else int(t) + 10 ** 9
+            take = c.poll(t_poll, queued)
+            if take:
+                sizes.append(take)
+                queued -= take
+        sizes = np.array(sizes)
+        assert (sizes[:-1] == 64).mean() > 0.95, np.bincount(sizes)
