@@ -51,6 +51,22 @@ FP32_LANES = 128
 GRAVITY_DRAM_BYTES_PER_INTERACTION = 505.7e6 / 2.98e8
 
 
+# Uneven batch and serving workload: a two-Plummer merger of 4,194,304
+# particles (3:1 mass, separation 10); 200,000 gravity tasks, target counts
+# log-uniform on 8..1024 (contiguous Morton-order runs), source lists
+# log-uniform on 16..16384 (runs of <= 32 Morton-consecutive ids); staging
+# budget 2 GiB, so one batch of all tasks runs in waves.
+C4_N = (3 << 20, 1 << 20)
+C4_TASKS = 200_000
+C4_T_RANGE = (8, 1024)
+C4_S_RANGE = (16, 16384)
+C4_BUDGET = 2 << 30
+C4_WORKLOAD = ("uneven_200k: 200,000 gravity tasks over a 4,194,304-particle two-Plummer "
+               "merger, nT ~ logU[8,1024], nS ~ logU[16,16384], staging budget 2 GiB")
+# serving: (aggregate Poisson rate of 16 producers in tasks/s, schedule seconds)
+SERVE_RATES = ((1e4, 1.0), (1e5, 1.0), (1e6, 0.2))
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -81,10 +97,15 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # the timed region starts once the first sample is in
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -174,15 +195,97 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3):
+    """The 200k-task uneven batch (device-resident task arrays, timed with
+    events) and the serving loop at three arrival rates (host task arrays,
+    host clock, latency from each task's scheduled arrival)."""
+    x = inputs.merger(*C4_N, seed)
+    n = x.shape[0]
+    ids = np.arange(n, dtype=np.uint32)
+    pool = gcharm.Pool(id_capacity=2 * n + 1024, pool_capacity=2 * n + 1024, eps2=EPS2,
+                       staging_budget_bytes=C4_BUDGET, stream=stream.cuda_stream)
+    pool.upload(ids, x)
+    # Morton order of the merger from the library's own tree build (the
+    # built N-body step is flushed: it doubles as a warm-up)
+    pool.build_nbody(x, BUCKET, *THETA)
+    pool.flush()
+    order = pool.nbody_sorted_ids(n)
+    to, tg, so, sr = inputs.uneven_tasks(n, C4_TASKS, seed + 1, C4_T_RANGE, C4_S_RANGE,
+                                         order=order)
+    kinds = np.zeros(C4_TASKS, np.uint32)
+    nt = (to[1:] - to[:-1]).astype(np.float64)
+    ns = (so[1:] - so[:-1]).astype(np.float64)
+    inter = float((nt * ns).sum())
+
+    # one batch of all tasks, task arrays resident in HBM
+    dk = torch.from_numpy(kinds.view(np.int32)).cuda()
+    dto = torch.from_numpy(to.view(np.int64)).cuda()
+    dso = torch.from_numpy(so.view(np.int64)).cuda()
+    dtg = torch.from_numpy(tg.view(np.int32)).cuda()
+    dsr = torch.from_numpy(sr.view(np.int32)).cuda()
+    torch.cuda.synchronize()
+
+    def batch():
+        pool.submit_csr_device(dk, dto, dtg, dso, dsr, tg.shape[0], sr.shape[0])
+        pool.flush()
+
+    batch()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    i0 = pool.stats()["interactions"]
+    e0.record(stream)
+    for _ in range(batch_reps):
+        batch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / batch_reps
+    st = pool.stats()
+    uneven = {"workload": C4_WORKLOAD, "tasks": C4_TASKS,
+              "interactions": int((st["interactions"] - i0) / batch_reps),
+              "list_entries": int(tg.shape[0] + sr.shape[0]),
+              "ms_per_batch": ms, "value": inter / (ms / 1e3), "unit": "interactions/s",
+              "waves": st["last_waves"], "stage_ms_last_batch": pool.timings(),
+              "reps": batch_reps}
+    del dk, dto, dso, dtg, dsr
+
+    # serving: open-loop Poisson arrivals (16 producers merged)
+    serving = {"workload": C4_WORKLOAD + "; tasks arrive as open-loop Poisson streams of "
+                                         "16 producers, in task order",
+               "latency": "host CLOCK_MONOTONIC, scheduled arrival -> completion observed",
+               "runs": []}
+    runs = [(r, d, gcharm.GC_COMBINE_GREEDY) for r, d in SERVE_RATES]
+    runs.append((1e5, 1.0, gcharm.GC_COMBINE_ADAPTIVE_WINDOW))
+    names = {gcharm.GC_COMBINE_GREEDY: "greedy (continuous batching)",
+             gcharm.GC_COMBINE_ADAPTIVE_WINDOW: "adaptive, windowed running max (Section 3.1)"}
+    for k, (rate, dur, policy) in enumerate(runs):
+        m = min(C4_TASKS, int(rate * dur))
+        arr = inputs.poisson_arrivals(m, rate, seed + 10 + k)
+        a, b = int(to[m]), int(so[m])
+        rep, lat, _ = pool.serve(arr, kinds[:m], to[:m + 1], tg[:a], so[:m + 1], sr[:b],
+                                 policy=policy)
+        serving["runs"].append({
+            "rate_tasks_per_s": rate, "policy": names[policy], "tasks": m,
+            "p50_us": rep["lat_p50_us"], "p99_us": rep["lat_p99_us"],
+            "max_us": rep["lat_max_us"], "mean_us": rep["lat_mean_us"],
+            "interactions_per_s": rep["interactions_per_s"], "wall_s": rep["wall_s"],
+            "batches": rep["batches"], "mean_batch": rep["mean_batch"],
+            "max_size": rep["max_size"], "busy_s": rep["busy_s"]})
+    pool.close()
+    return uneven, serving
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-task", action="store_true")
     ap.add_argument("--n", type=int, default=N_PART)
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the uneven-batch and serving measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -324,6 +427,13 @@ def main():
             "speedup_flush": tp["total"] / tb["total"],
         }
 
+    uneven = serving = None
+    if rank == 0 and not args.no_serve:
+        pool.close()
+        del X
+        torch.cuda.empty_cache()
+        uneven, serving = uneven_and_serving(gcharm, torch, inputs.SEED_BASE + 4, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ci, ct, cn = oracle_sample(xs[W], 60000, 77)
@@ -356,13 +466,16 @@ def main():
             "gpu_launches": launches,
             "primitive_calls": prims,
             "per_task_launch": per_task,
+            "uneven_batch": uneven,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         line["config"]["tasks_per_step"] = int(s1["tasks"] - s0["tasks"]) // max(K, 1)
         line["config"]["interactions_per_step"] = int(interactions) // max(K, 1)
         line["config"]["list_entries_per_step"] = int(s1["entries"] - s0["entries"]) // max(K, 1)
         print(json.dumps(line), flush=True)
-    pool.close()
+    if pool.h:
+        pool.close()
     if ws > 1:
         dist.destroy_process_group()
 

@@ -440,6 +440,13 @@ class Pool:
                "gc_read_nbody_tree")
         return out
 
+    def nbody_sorted_ids(self, n):
+        """Particle ids of the last N-body build in Morton (key, id) order."""
+        out = np.empty(n, np.uint32)
+        _check(self.lib.gc_read_nbody_tree(self.h, _p(out), *([None] * 13)),
+               "gc_read_nbody_tree")
+        return out
+
     def build_md(self, cell, m, task_id_base=0):
         """cell: CUDA tensor or host numpy array of uint32/int32 cell indices."""
         info = np.zeros(4, np.uint64)
