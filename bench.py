@@ -44,11 +44,14 @@ WORKLOAD = ("nbody_plummer_1M: 1,048,576 Plummer particles, theta=0.7, buckets<=
 FLOPS_PER_INTERACTION = 19
 SM_COUNT = 152
 FP32_LANES = 128
-# DRAM bytes (read + write) per interaction of k_gravity, from one ncu capture
-# of the 262,144-particle step (profiles/k_gravity_nbody262k.md: 505.7 MB for
-# ~2.98e8 interactions); traffic scales with the list entries, i.e. with the
-# interactions at a fixed bucket occupancy.
-GRAVITY_DRAM_BYTES_PER_INTERACTION = 505.7e6 / 2.98e8
+# Algorithmic bytes of the pack per list entry: 4 B slot, 16 B value gathered
+# from the pool, 16 B staging write, 4 B permutation write.
+PACK_BYTES_PER_ENTRY = 40
+# DRAM bytes (read + write) per unit of work from ncu captures of the current
+# kernels (None until captured again after a kernel change):
+# k_gravity per interaction, the pack kernels per list entry.
+GRAVITY_DRAM_BYTES_PER_INTERACTION = None
+PACK_DRAM_BYTES_PER_ENTRY = None
 
 
 # Uneven batch and serving workload: a two-Plummer merger of 4,194,304
@@ -162,6 +165,42 @@ def oracle_sample(x, n_tasks, seed, budget_s=None):
     dt = time.perf_counter() - t0
     inter = int(np.sum(np.diff(to.astype(np.int64)) * np.diff(off.astype(np.int64))))
     return inter, dt, len(pick)
+
+
+def _oracle_worker(x, buckets, barrier):
+    from oracle import oracle as O
+    tr = O.Tree(x, bucket_max=BUCKET)
+    tab = np.concatenate([x, tr.node_table()])
+    barrier.wait()
+    t0 = time.time()
+    off, ids = tr.lists(THETA[0], THETA[1], buckets=buckets)
+    to, tg = tr.bucket_targets(buckets)
+    O.gravity_batch(tab, to, tg, off, ids, EPS2)
+    t1 = time.time()
+    inter = int(np.sum(np.diff(to.astype(np.int64)) * np.diff(off.astype(np.int64))))
+    return inter, t0, t1
+
+
+def oracle_all_cores(x, workers):
+    """The oracle as it stands, one process per host core (spawned), each
+    on an interleaved share of every bucket of the step: tree build untimed,
+    walk + FP64 gravity timed from a common start.  Returns (interactions,
+    seconds, buckets)."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    tr = O.Tree(x, bucket_max=BUCKET)
+    nb = tr.n_buckets
+    del tr
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(workers)
+        with ctx.Pool(workers) as pool:
+            res = pool.starmap(_oracle_worker,
+                               [(x, np.arange(w, nb, workers), barrier) for w in range(workers)])
+    inter = sum(r[0] for r in res)
+    dt = max(r[2] for r in res) - min(r[1] for r in res)
+    return inter, dt, nb
 
 
 def run_reference(args):
@@ -335,15 +374,10 @@ def main():
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    inter_ms, inter_n = [], []
     torch.cuda.synchronize()
     e0.record(stream)
     for k in range(W, W + K):
-        before = pool.stats()["interactions"]
         step(k)
-        t = pool.timings()                 # stage times of this flush (events)
-        inter_ms.append(t["interact"])
-        inter_n.append(pool.stats()["interactions"] - before)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -364,16 +398,41 @@ def main():
     else:
         interactions_all = interactions
     value = interactions_all / (ms / 1e3)
-    last_timing = pool.timings()
     hits, uniq = s1["last_hits"], s1["last_unique"]
 
-    # roofline of the dominant kernel (the interaction kernel)
-    avg_int_ms = float(np.mean(inter_ms))
-    avg_int_n = float(np.mean(inter_n))
-    achieved = FLOPS_PER_INTERACTION * avg_int_n / (avg_int_ms / 1e3) / 1e12
+    # rooflines: per-stage device times of the timed flushes (CUDA events on
+    # the flush streams, summed by the library), algorithmic work per step
+    nb = s1["timed_batches"] - s0["timed_batches"]
+    stage = {k: (s1["stage_ms_sum"][k] - s0["stage_ms_sum"][k]) / max(nb, 1)
+             for k in s1["stage_ms_sum"]}
+    per_step_int = interactions / K
+    per_step_entries = (s1["entries"] - s0["entries"]) / K
     pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(sm_max)
+    fp32_measured = gcharm.fp32_peak()
+    grav = {"kernel": "k_gravity (interaction)", "bound": "alu",
+            "achieved": FLOPS_PER_INTERACTION * per_step_int / (stage["interact"] / 1e3) / 1e12,
+            "peak": fp32_measured, "unit": "TFLOP/s",
+            "peak_basis": "measured: paired-FP32 FMA probe (gc_fp32_peak); clock-derived "
+                          f"{fp32_peak_tflops(sm_max):.1f} TFLOP/s = {SM_COUNT} SMs x "
+                          f"{FP32_LANES} lanes x 2 x {sm_max:.0f} MHz",
+            "work_per_unit": f"{FLOPS_PER_INTERACTION} flop per interaction",
+            "units_per_launch": per_step_int, "ms_per_launch": stage["interact"],
+            "traffic": (GRAVITY_DRAM_BYTES_PER_INTERACTION * per_step_int
+                        if GRAVITY_DRAM_BYTES_PER_INTERACTION else None)}
+    grav["frac"] = grav["achieved"] / grav["peak"]
+    pack = {"kernel": "pack (k_pack_small, k_pack_mid<1024>, k_pack_mid<2048>, k_pack_large)",
+            "bound": "hbm",
+            "achieved": PACK_BYTES_PER_ENTRY * per_step_entries / (stage["pack"] / 1e3) / 1e9,
+            "peak": float(pk.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+            "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                          if "hbm_gbs" in pk else "fallback 6800 GB/s",
+            "work_per_unit": f"{PACK_BYTES_PER_ENTRY} B per list entry",
+            "units_per_launch": per_step_entries, "ms_per_launch": stage["pack"],
+            "traffic": (PACK_DRAM_BYTES_PER_ENTRY * per_step_entries
+                        if PACK_DRAM_BYTES_PER_ENTRY else None)}
+    pack["frac"] = pack["achieved"] / pack["peak"]
+    dominant = pack if stage["pack"] >= stage["interact"] else grav
 
     # end-to-end through the C ABI with host buffers (pinned), copies timed
     pinned = torch.empty((K, n, 4), dtype=torch.float32, pin_memory=True)
@@ -441,6 +500,14 @@ def main():
                "sample": f"{cn} seeded-random buckets of the first timed step "
                          f"({ci} interactions): oracle walk + FP64 gravity, one thread; "
                          "tree build untimed"}
+        cores = os.cpu_count() or 1
+        if cores > 1:
+            ai, at, an = oracle_all_cores(xs[W], cores)
+            cpu["all_cores"] = {"value": ai / at, "unit": "interactions/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"all {an} buckets of the first timed step "
+                                          f"({ai} interactions), one spawned process per "
+                                          "core on interleaved buckets; tree build untimed"}
 
     if rank == 0:
         line = {
@@ -451,15 +518,9 @@ def main():
             "config": {"workload": WORKLOAD, "particles": n, "tasks_per_step": None,
                        "l2": "inputs larger than L2 (staging ~4 GB per step)",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": GRAVITY_DRAM_BYTES_PER_INTERACTION * avg_int_n,
-                         "kernel": "k_gravity",
-                         "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x "
-                                       f"{sm_max:.0f} MHz (fallback derivation, no FP32 "
-                                       "figure measured)",
-                         "flops_per_interaction": FLOPS_PER_INTERACTION},
-            "stage_ms_last_step": last_timing,
+            "roofline": dominant,
+            "rooflines": {"interaction": grav, "pack": pack},
+            "stage_ms_avg": stage,
             "reuse": {"last_hits": hits, "last_unique": uniq},
             "clocks": clk,
             "e2e": e2e,

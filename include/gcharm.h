@@ -121,6 +121,11 @@ typedef struct {
     uint64_t kernel_launches;     /* kernels of this library launched      */
     uint64_t primitive_calls;     /* device-wide sort/scan calls (CUB), each
                                      a few launches of its own              */
+    double stage_ms_sum[5];       /* device time of every completed flush,
+                                     summed per stage {residency, pack,
+                                     interaction, scatter, total} (CUDA
+                                     events on the flush's stream)          */
+    uint64_t timed_batches;       /* flushes counted in stage_ms_sum        */
 } gc_stats_t;
 
 /* ---- pool lifetime and data -------------------------------------------- */
@@ -164,8 +169,9 @@ int gc_submit(gc_pool_t *pool, const gc_task *tasks, uint64_t n,
  * zero), tag task_ids[t] (NULL: running task counter).  on_device = 0:
  * all arrays are host arrays.  on_device = 1: all arrays are device arrays
  * and n_tgt_total / n_src_total must equal tgt_off[n_tasks] /
- * src_off[n_tasks] (the offsets are not read on the host).  Offsets must
- * start at 0 and not decrease. */
+ * src_off[n_tasks] (the offsets are not read on the host); they are read in
+ * stream order on the pool's stream, so keep them unchanged until the next
+ * gc_flush has returned.  Offsets must start at 0 and not decrease. */
 int gc_submit_csr(gc_pool_t *pool, uint64_t n_tasks, const uint64_t *task_ids,
                   const uint32_t *kinds, const int8_t *shifts,
                   const uint64_t *tgt_off, const uint32_t *tgt_ids,
@@ -410,7 +416,9 @@ typedef struct {
  * the loop - its scheduled arrival (CLOCK_MONOTONIC), so queueing behind a
  * busy device is counted.  latency_ns_out (n values) and results_out (8
  * floats per result row, rows of task after task as gc_read_batch_results
- * gives them) may be NULL.  The pool must have no pending tasks; per-id
+ * gives them) may be NULL.  tgt_ids and src_ids are page-locked for the
+ * duration of the call (cudaHostRegister) unless they already are, so that
+ * the per-batch copies run as direct DMA.  The pool must have no pending tasks; per-id
  * totals accumulate as for any flush.  Errors: GC_ERR_ARG (bad pointers,
  * decreasing arrivals, max_in_flight not 1 or 2), GC_ERR_STATE (pending
  * tasks), GC_ERR_TIMEOUT, and any error of gc_submit_csr / gc_flush. */
@@ -418,6 +426,47 @@ int gc_serve(gc_pool_t *pool, uint64_t n, const uint64_t *arrival_ns, const uint
              const int8_t *shifts, const uint64_t *tgt_off, const uint32_t *tgt_ids,
              const uint64_t *src_off, const uint32_t *src_ids, const gc_serve_config *cfg,
              uint64_t *latency_ns_out, float *results_out, gc_serve_report *report);
+
+/* ---- interaction schedule and its autotuner ------------------------------ */
+
+#define GC_SCHED_FIFO 0u   /* work units handed out in admission order          */
+#define GC_SCHED_LPT 1u    /* longest first (targets x sources, descending;
+                              admission order among equals)                    */
+
+typedef struct {
+    uint32_t wu_max_targets;  /* targets per gravity work unit (one warp): 8, 16
+                                 or 32; a task of nT targets becomes
+                                 ceil(nT / wu_max_targets) units of near-equal
+                                 size, each run by T targets x 32/T source lanes */
+    uint32_t schedule;        /* GC_SCHED_FIFO | GC_SCHED_LPT                  */
+} gc_tuning;
+
+/* Set / read the interaction schedule used by later flushes (default 16,
+ * FIFO).  The results change only by FP32 summation order (within the
+ * per-result tolerance).  Errors: GC_ERR_ARG (other values). */
+int gc_set_tuning(gc_pool_t *pool, const gc_tuning *t);
+int gc_get_tuning(gc_pool_t *pool, gc_tuning *t);
+
+/* Autotuner: re-run the interaction stage of the last flushed batch (one
+ * wave, gravity tasks) under every schedule {8, 16, 32} x {FIFO, LPT}, timing
+ * each with CUDA events (best of `reps`), and keep the fastest for later
+ * flushes.  ms_out (may be NULL) receives the 6 times, in the order
+ * (8,FIFO), (8,LPT), (16,FIFO), (16,LPT), (32,FIFO), (32,LPT); *best_out (may
+ * be NULL) the choice.  The batch's result rows are rewritten by the re-runs
+ * (same values up to summation order); per-id totals are not touched.
+ * Errors: GC_ERR_NOT_READY (no batch), GC_ERR_STATE (the batch ran in more
+ * than one wave, or has no gravity task), GC_ERR_CUDA. */
+int gc_autotune(gc_pool_t *pool, int reps, gc_tuning *best_out, float ms_out[6]);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* FP32 throughput of the current device, measured: independent paired-FP32
+ * FMA chains (2 FMAs = 4 flops per instruction) on every lane of every SM,
+ * best of three timed launches (CUDA events).  *tflops_out = TFLOP/s,
+ * *ms_out (may be NULL) = the best launch time.  The denominator of the
+ * interaction kernel's roofline; no counterpart in the paper.  Allocates a
+ * small buffer.  Errors: GC_ERR_ARG, GC_ERR_CUDA. */
+int gc_fp32_peak(double *tflops_out, double *ms_out);
 
 /* ---- evaluation without allocation -------------------------------------- */
 

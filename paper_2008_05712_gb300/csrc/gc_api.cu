@@ -504,12 +504,15 @@ int gc_submit(gc_pool_t *p, const gc_task *tasks, uint64_t n, uint64_t *batch_ou
 // and packed.  A context is reused by batch k+2, in stream order after
 // batch k, so results of a batch stay readable until batch k+2 is flushed.
 
+static void count_timing(gc_pool *p, FlushCtx &c, bool block);
+
 static int flush_impl(gc_pool *p, int per_task)
 {
     if (!p) return GC_ERR_ARG;
     if (p->nb_tasks == 0) return GC_OK;
     FlushCtx &c = p->ctx[p->cur];
     FlushCtx *prev = last_ctx(p);
+    count_timing(p, c, true);   // the context's previous batch (two batches ago)
     // the batch becomes this context's batch; the context's previous batch
     // arrays become the next pending arrays (every later write to them is
     // ordered after this context's stream passes the point below)
@@ -523,6 +526,7 @@ static int flush_impl(gc_pool *p, int per_task)
     c.valid = false;
     c.host_tasks_valid = false;
     c.timing_valid = false;
+    c.timing_counted = false;
     p->nb_tasks = p->nb_tgt = p->nb_src = 0;
     const uint64_t T = c.n_tasks, NT = c.n_tgt, NS = c.n_src;
     clear_last_stats(p);
@@ -838,6 +842,7 @@ int gc_stats(gc_pool_t *p, gc_stats_t *out)
     GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[1].s));
     unsigned long long c[CTR_COUNT];
     GC_CUDA_TRY(cudaMemcpy(c, p->d_ctr, sizeof c, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 2; ++i) count_timing(p, p->ctx[i], false);
     *out = p->stats;
     out->updates = c[CTR_UPDATES];
     FlushCtx *l = result_ctx(p);
@@ -850,25 +855,50 @@ int gc_stats(gc_pool_t *p, gc_stats_t *out)
     return GC_OK;
 }
 
+// Stage times of a context's completed batch (its events have fired).
+static void timings_of(const FlushCtx &c, float ms[5])
+{
+    if (c.n_waves > 1) {
+        ms[0] = c.multiwave_ms[0];
+        ms[1] = c.multiwave_ms[1];
+        ms[2] = c.multiwave_ms[2];
+        cudaEventElapsedTime(&ms[3], c.ev_stage[3], c.ev_stage[4]);
+        ms[4] = ms[0] + ms[1] + ms[2] + ms[3];
+        return;
+    }
+    cudaEventElapsedTime(&ms[0], c.ev_stage[0], c.ev_stage[1]);
+    cudaEventElapsedTime(&ms[1], c.ev_stage[1], c.ev_stage[2]);
+    cudaEventElapsedTime(&ms[2], c.ev_stage[2], c.ev_stage[3]);
+    cudaEventElapsedTime(&ms[3], c.ev_stage[3], c.ev_stage[4]);
+    cudaEventElapsedTime(&ms[4], c.ev_stage[0], c.ev_stage[4]);
+}
+
+// Add a completed batch's stage times to the pool's sums, once.  block:
+// wait for the batch; otherwise count it only if it has completed.
+static void count_timing(gc_pool *p, FlushCtx &c, bool block)
+{
+    if (!c.timing_valid || c.timing_counted) return;
+    if (block) {
+        if (cudaEventSynchronize(c.ev_stage[4]) != cudaSuccess) return;
+    } else if (cudaEventQuery(c.ev_stage[4]) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    float ms[5];
+    timings_of(c, ms);
+    for (int i = 0; i < 5; ++i) p->stats.stage_ms_sum[i] += ms[i];
+    ++p->stats.timed_batches;
+    c.timing_counted = true;
+}
+
 int gc_last_timings(gc_pool_t *p, float ms[5])
 {
     if (!p || !ms) return GC_ERR_ARG;
     FlushCtx *c = result_ctx(p);
     if (!c || !c->timing_valid) return GC_ERR_NOT_READY;
     GC_CUDA_TRY(cudaEventSynchronize(c->ev_stage[4]));
-    if (c->n_waves > 1) {
-        ms[0] = c->multiwave_ms[0];
-        ms[1] = c->multiwave_ms[1];
-        ms[2] = c->multiwave_ms[2];
-        cudaEventElapsedTime(&ms[3], c->ev_stage[3], c->ev_stage[4]);
-        ms[4] = ms[0] + ms[1] + ms[2] + ms[3];
-        return GC_OK;
-    }
-    cudaEventElapsedTime(&ms[0], c->ev_stage[0], c->ev_stage[1]);
-    cudaEventElapsedTime(&ms[1], c->ev_stage[1], c->ev_stage[2]);
-    cudaEventElapsedTime(&ms[2], c->ev_stage[2], c->ev_stage[3]);
-    cudaEventElapsedTime(&ms[3], c->ev_stage[3], c->ev_stage[4]);
-    cudaEventElapsedTime(&ms[4], c->ev_stage[0], c->ev_stage[4]);
+    timings_of(*c, ms);
+    count_timing(p, *c, true);
     return GC_OK;
 }
 

@@ -104,10 +104,12 @@ struct FlushCtx {
     bool valid = false;
     DBuf tgt_perm, src_perm, stg_tgt, stg_src;
     DBuf wu, wu_cnt, wu_off, rowcnt, lj_list, res, row_id;
+    DBuf lpt;                          // longest-first ordering scratch
     DBuf rid_sorted, row_sorted, rows_tmp, runs, tiles, merge_a, merge_b, cub_tmp;
     cudaEvent_t ev_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_done = nullptr, ev_packed = nullptr, ev_scattered = nullptr;
     bool timing_valid = false;
+    bool timing_counted = false;   // stage times added to the pool's sums
     float multiwave_ms[3] = {0, 0, 0};
     uint64_t n_waves = 0;
     std::vector<TaskRec> host_tasks;       // for gc_read_results
@@ -154,6 +156,9 @@ struct gc_pool {
     uint32_t epoch = 0;
 
     gc_stats_t stats;
+    // interaction schedule (gc_set_tuning / gc_autotune)
+    uint32_t wu_max_targets = 16;      // targets per gravity work unit: 8, 16 or 32
+    uint32_t wu_schedule = GC_SCHED_FIFO;
     NBodyState nb;
     MDState md;
 };

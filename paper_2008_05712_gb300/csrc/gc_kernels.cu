@@ -53,7 +53,8 @@ __global__ void k_task_recs(uint64_t n, const uint64_t *task_ids, const uint32_t
 }
 
 __global__ void k_prep_counts(const TaskRec *tasks, uint64_t n, uint64_t *rows,
-                              uint32_t *wu_g, uint32_t *lj, unsigned long long *ctr)
+                              uint32_t *wu_g, uint32_t *lj, unsigned long long *ctr,
+                              uint32_t wu_max)
 {
     unsigned long long inter = 0;
     unsigned int mx = 0;
@@ -61,7 +62,7 @@ __global__ void k_prep_counts(const TaskRec *tasks, uint64_t n, uint64_t *rows,
         TaskRec r = tasks[t];
         uint64_t rw = r.nt + (r.kind == GC_LJ_PAIR ? r.ns : 0u);
         rows[t] = rw;
-        wu_g[t] = (r.kind == GC_GRAVITY) ? (r.nt + 15u) / 16u : 0u;
+        wu_g[t] = (r.kind == GC_GRAVITY) ? (r.nt + wu_max - 1u) / wu_max : 0u;
         lj[t] = (r.kind != GC_GRAVITY) ? 1u : 0u;
         if (r.kind == GC_GRAVITY) inter += (unsigned long long)r.nt * r.ns;
         else if (r.kind == GC_LJ_PAIR) inter += (unsigned long long)r.nt * r.ns;
@@ -81,15 +82,14 @@ __global__ void k_prep_counts(const TaskRec *tasks, uint64_t n, uint64_t *rows,
 
 __global__ void k_prep_fill(TaskRec *tasks, uint64_t n, const uint64_t *row_off,
                             const uint32_t *wu_off, const uint32_t *lj_off, GravWU *wu,
-                            uint32_t *lj_list)
+                            uint32_t *lj_list, uint32_t wu_max)
 {
     GRID_STRIDE(t, n) {
         TaskRec &r = tasks[t];
-        r.row_off = row_off[t];
+        if (row_off) r.row_off = row_off[t];
         if (r.kind == GC_GRAVITY) {
-            // blocks of at most 16 targets, sizes as equal as possible, so
-            // that a warp keeps >= 2 source lanes per target
-            uint32_t nb = (r.nt + 15u) / 16u;
+            // blocks of at most wu_max targets, sizes as equal as possible
+            uint32_t nb = (r.nt + wu_max - 1u) / wu_max;
             uint32_t bs = nb ? (r.nt + nb - 1u) / nb : 0u;
             for (uint32_t b = 0; b < nb; ++b) {
                 GravWU w;
@@ -99,10 +99,28 @@ __global__ void k_prep_fill(TaskRec *tasks, uint64_t n, const uint64_t *row_off,
                 w.pad = 0;
                 wu[wu_off[t] + b] = w;
             }
-        } else {
+        } else if (lj_list) {
             lj_list[lj_off[t]] = (uint32_t)t;
         }
     }
+}
+
+// Longest-first order of work units: sort key = (2^40 - 1) - targets x
+// sources (a stable radix sort keeps admission order among equal costs).
+__global__ void k_wu_cost(const GravWU *wu, uint64_t n, const TaskRec *tasks, uint64_t *key,
+                          uint32_t *idx)
+{
+    GRID_STRIDE(i, n) {
+        const GravWU w = wu[i];
+        const uint64_t cost = (uint64_t)w.tn * tasks[w.task].ns;
+        key[i] = ((1ull << 40) - 1ull) - cost;
+        idx[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_wu_gather(const GravWU *wu, const uint32_t *idx, uint64_t n, GravWU *out)
+{
+    GRID_STRIDE(i, n) out[i] = wu[idx[i]];
 }
 
 // ---------------------------------------------------------------------------
@@ -708,17 +726,17 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 b, float
     s = t;
 }
 
-// Store the FP64 value v as the float pair (s, c) with s - c ~= v.
-__device__ __forceinline__ void split_store(float4 *dst, double v0, double v1, double v2,
-                                            double v3)
+// Compensated pair (s, c), value s - c, plus another such pair (s2, c2): the
+// sums s + s2 are split exactly (Knuth's two-sum) and the rounding error is
+// carried into the compensation.  FP32 only: the FP64 pipe of this GPU runs
+// at 1/64 of the FP32 rate, so per-lane FP64 work would dominate the kernel.
+__device__ __forceinline__ void comp_add(float &s, float &c, float s2, float c2)
 {
-    float4 s, c;
-    s.x = (float)v0; c.x = (float)((double)s.x - v0);
-    s.y = (float)v1; c.y = (float)((double)s.y - v1);
-    s.z = (float)v2; c.z = (float)((double)s.z - v2);
-    s.w = (float)v3; c.w = (float)((double)s.w - v3);
-    dst[0] = s;
-    dst[1] = c;
+    const float t = __fadd_rn(s, s2);
+    const float bb = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));  // s + s2 = t + e
+    c = __fsub_rn(__fadd_rn(c, c2), e);
+    s = t;
 }
 
 // One source pair against one target, paired FP32 arithmetic.
@@ -745,7 +763,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
 struct GravSmem {
     float4 buf[GRAV_WARPS][2][2 * TP];  // per warp: two tiles of source pairs
     uint64_t bar[GRAV_WARPS][2];        // one mbarrier per tile buffer
-    double red[GRAV_WARPS][32][4];      // cross-lane FP64 combine
+    float4 red[GRAV_WARPS][32][2];      // cross-lane combine: (sum, compensation)
 };
 
 // One warp per work unit (task, block of <= 16 targets).  With T targets in
@@ -756,7 +774,7 @@ struct GravSmem {
 // ahead of the compute.  Every source pair is evaluated with paired FP32
 // instructions (two interactions per instruction); partial sums of KB pairs
 // are added with compensation; the S lane results of a target are combined
-// in FP64 in lane order.  Work units come from a device queue (persistent
+// as compensated FP32 pairs in lane order.  Work units come from a device queue (persistent
 // kernel); with a null queue each warp takes a fixed share
 // (one-launch-per-task mode).  A bulk copy that does not complete within the
 // polling limit sets GC_FLAG_TIMEOUT and the warp stops.
@@ -868,24 +886,30 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
             }
             return;
         }
-        sm.red[wib][lane][0] = ((double)sx.x - (double)cx.x) + ((double)sx.y - (double)cx.y);
-        sm.red[wib][lane][1] = ((double)sy.x - (double)cy.x) + ((double)sy.y - (double)cy.y);
-        sm.red[wib][lane][2] = ((double)sz.x - (double)cz.x) + ((double)sz.y - (double)cz.y);
-        sm.red[wib][lane][3] = ((double)sp.x - (double)cp.x) + ((double)sp.y - (double)cp.y);
+        // the two halves of each lane, then the S lanes of a target in lane
+        // order, all as compensated FP32 pairs
+        comp_add(sx.x, cx.x, sx.y, cx.y);
+        comp_add(sy.x, cy.x, sy.y, cy.y);
+        comp_add(sz.x, cz.x, sz.y, cz.y);
+        comp_add(sp.x, cp.x, sp.y, cp.y);
+        sm.red[wib][lane][0] = make_float4(sx.x, sy.x, sz.x, sp.x);
+        sm.red[wib][lane][1] = make_float4(cx.x, cy.x, cz.x, cp.x);
         __syncwarp();
         if (sl == 0) {
-            double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
-            for (int s = 0; s < S; ++s) {
+            float4 vs = sm.red[wib][t][0], vc = sm.red[wib][t][1];
+            for (int s = 1; s < S; ++s) {
                 const int l = s * T + t;
-                v0 += sm.red[wib][l][0];
-                v1 += sm.red[wib][l][1];
-                v2 += sm.red[wib][l][2];
-                v3 += sm.red[wib][l][3];
+                const float4 ws = sm.red[wib][l][0], wc = sm.red[wib][l][1];
+                comp_add(vs.x, vc.x, ws.x, wc.x);
+                comp_add(vs.y, vc.y, ws.y, wc.y);
+                comp_add(vs.z, vc.z, ws.z, wc.z);
+                comp_add(vs.w, vc.w, ws.w, wc.w);
             }
             const uint64_t e = r.tgt_off + u.t0 + t;
             const uint32_t pos = a.perm_t[e];
             const uint64_t row = r.row_off + pos;
-            split_store(a.res + 2 * row, v0, v1, v2, v3);
+            a.res[2 * row] = vs;
+            a.res[2 * row + 1] = vc;
             a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
         }
         __syncwarp();
@@ -974,8 +998,8 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
                 row = r.row_off + nA + pos;
                 id = a.src_ids[r.src_off + pos];
             }
-            split_store(a.res + 2 * row, (double)sx - (double)cx, (double)sy - (double)cy,
-                        (double)sz - (double)cz, (double)su - (double)cu);
+            a.res[2 * row] = make_float4(sx, sy, sz, su);        // value s - c, as stored
+            a.res[2 * row + 1] = make_float4(cx, cy, cz, cu);
             a.row_id[row] = id;
         }
         for (int s = 16; s; s >>= 1) inside += __shfl_xor_sync(0xffffffffu, inside, s);
@@ -1055,7 +1079,8 @@ int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
     GC_CUDA_TRY(cudaMemsetAsync(lj + n, 0, sizeof(uint32_t), c.s));
     ++p->stats.kernel_launches;
     k_prep_counts<<<grid_for(n, 256, p->num_sms * 16), 256, 0, c.s>>>(tasks, n, rows, wu_g, lj,
-                                                                       c.d_ctr);
+                                                                       c.d_ctr,
+                                                                       p->wu_max_targets);
     ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(c.cub_tmp, rows, row_off, n + 1, c.s));
     ++p->stats.primitive_calls;
@@ -1074,7 +1099,8 @@ int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
     GC_TRY(c.lj_list.reserve(((uint64_t)h_lj + 1) * sizeof(uint32_t)));
     ++p->stats.kernel_launches;
     k_prep_fill<<<grid_for(n, 256, p->num_sms * 16), 256, 0, c.s>>>(
-        tasks, n, row_off, wu_off, lj_off, c.wu.as<GravWU>(), c.lj_list.as<uint32_t>());
+        tasks, n, row_off, wu_off, lj_off, c.wu.as<GravWU>(), c.lj_list.as<uint32_t>(),
+        p->wu_max_targets);
     GC_CUDA_TRY(cudaGetLastError());
     info[0] = h_rows;
     info[1] = h_wu;
@@ -1227,6 +1253,26 @@ int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_
         a.n_wu = w1 - w0;
         a.lj_list = nullptr;
         a.n_lj = 0;
+        if (p->wu_schedule == GC_SCHED_LPT && a.n_wu > 1) {
+            // reorder this wave's work units longest first, in place
+            const uint64_t m = a.n_wu;
+            GC_TRY(c.lpt.reserve(m * (2 * sizeof(uint64_t) + 2 * sizeof(uint32_t) +
+                                      sizeof(GravWU)) + 64));
+            char *b = (char *)c.lpt.p;
+            GravWU *tmp = (GravWU *)b;
+            uint64_t *k0 = (uint64_t *)(b + m * sizeof(GravWU));
+            uint64_t *k1 = k0 + m;
+            uint32_t *i0 = (uint32_t *)(k1 + m);
+            uint32_t *i1 = i0 + m;
+            GravWU *w = c.wu.as<GravWU>() + w0;
+            p->stats.kernel_launches += 2;
+            k_wu_cost<<<grid_for(m, 256, p->num_sms * 16), 256, 0, c.s>>>(w, m, a.tasks, k0, i0);
+            ++p->stats.primitive_calls;
+            GC_TRY(gc_sort_pairs_u64(c.cub_tmp, k0, k1, i0, i1, m, 40, c.s));
+            k_wu_gather<<<grid_for(m, 256, p->num_sms * 16), 256, 0, c.s>>>(w, i1, m, tmp);
+            GC_CUDA_TRY(cudaMemcpyAsync(w, tmp, m * sizeof(GravWU), cudaMemcpyDeviceToDevice,
+                                        c.s));
+        }
         GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
         const uint64_t need = (a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS;
         const unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
@@ -1302,5 +1348,128 @@ int gc_scatter(gc_pool *p, FlushCtx &c)
         c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, n_rows, c.rid_sorted.as<uint32_t>(),
         c.row_sorted.as<uint32_t>(), c.res.as<float4>(), p->d_totals);
     GC_CUDA_TRY(cudaGetLastError());
+    return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// interaction schedule: set / get / autotune
+// ---------------------------------------------------------------------------
+
+extern "C" int gc_set_tuning(gc_pool_t *p, const gc_tuning *t)
+{
+    if (!p || !t) return GC_ERR_ARG;
+    if (t->wu_max_targets != 8 && t->wu_max_targets != 16 && t->wu_max_targets != 32)
+        return GC_ERR_ARG;
+    if (t->schedule != GC_SCHED_FIFO && t->schedule != GC_SCHED_LPT) return GC_ERR_ARG;
+    p->wu_max_targets = t->wu_max_targets;
+    p->wu_schedule = t->schedule;
+    return GC_OK;
+}
+
+extern "C" int gc_get_tuning(gc_pool_t *p, gc_tuning *t)
+{
+    if (!p || !t) return GC_ERR_ARG;
+    t->wu_max_targets = p->wu_max_targets;
+    t->schedule = p->wu_schedule;
+    return GC_OK;
+}
+
+// Rebuild the gravity work units of a context's batch for work units of at
+// most wu_max targets; *n_wu_out = their number.
+static int rebuild_wus(gc_pool *p, FlushCtx &c, uint32_t wu_max, uint64_t *n_wu_out)
+{
+    const uint64_t n = c.n_tasks;
+    TaskRec *tasks = c.tasks.as<TaskRec>();
+    uint64_t *rows = c.rowcnt.as<uint64_t>();
+    uint32_t *wu_g = c.wu_cnt.as<uint32_t>();
+    uint32_t *lj = wu_g + (n + 1);
+    uint32_t *wu_off = c.wu_off.as<uint32_t>();
+    GC_CUDA_TRY(cudaMemsetAsync(wu_g + n, 0, sizeof(uint32_t), c.s));
+    p->stats.kernel_launches += 1;
+    // counters of the batch are recounted into a scratch copy
+    GC_TRY(c.lpt.reserve(sizeof(unsigned long long) * FC_COUNT + 64));
+    unsigned long long *scratch_ctr = c.lpt.as<unsigned long long>();
+    GC_CUDA_TRY(cudaMemsetAsync(scratch_ctr, 0, sizeof(unsigned long long) * FC_COUNT, c.s));
+    k_prep_counts<<<grid_for(n, 256, p->num_sms * 16), 256, 0, c.s>>>(tasks, n, rows, wu_g, lj,
+                                                                       scratch_ctr, wu_max);
+    ++p->stats.primitive_calls;
+    GC_TRY(gc_exclusive_scan_u32(c.cub_tmp, wu_g, wu_off, n + 1, c.s));
+    uint32_t h_wu = 0;
+    GC_CUDA_TRY(cudaMemcpyAsync(&h_wu, wu_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
+    GC_TRY(c.wu.reserve(((uint64_t)h_wu + 1) * sizeof(GravWU)));
+    ++p->stats.kernel_launches;
+    k_prep_fill<<<grid_for(n, 256, p->num_sms * 16), 256, 0, c.s>>>(
+        tasks, n, nullptr, wu_off, nullptr, c.wu.as<GravWU>(), nullptr, wu_max);
+    GC_CUDA_TRY(cudaGetLastError());
+    *n_wu_out = h_wu;
+    return GC_OK;
+}
+
+extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out, float ms_out[6])
+{
+    if (!p || reps < 1) return GC_ERR_ARG;
+    if (p->last < 0 || !p->ctx[p->last].valid) return GC_ERR_NOT_READY;
+    FlushCtx &c = p->ctx[p->last];
+    GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
+    if (c.n_waves != 1) return GC_ERR_STATE;
+    const uint32_t saved_max = p->wu_max_targets, saved_sched = p->wu_schedule;
+    const uint32_t tiles[3] = {8, 16, 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return GC_ERR_CUDA;
+    }
+    float best = 1e30f;
+    gc_tuning choice{saved_max, saved_sched};
+    int rc = GC_OK;
+    for (int ti = 0; ti < 3 && rc == GC_OK; ++ti) {
+        for (uint32_t sched = 0; sched < 2 && rc == GC_OK; ++sched) {
+            p->wu_max_targets = tiles[ti];
+            p->wu_schedule = sched;
+            float tbest = 1e30f;
+            for (int r = 0; r < reps && rc == GC_OK; ++r) {
+                uint64_t W = 0;
+                rc = rebuild_wus(p, c, tiles[ti], &W);
+                if (rc != GC_OK) break;
+                if (W == 0) {
+                    rc = GC_ERR_STATE;
+                    break;
+                }
+                // the ordering pass (LPT) is part of the schedule's cost
+                cudaEventRecord(e0, c.s);
+                rc = gc_interact_range(p, c, 0, W, 0, 0, 0, 0, 0);
+                cudaEventRecord(e1, c.s);
+                if (rc != GC_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = GC_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < tbest) tbest = ms;
+            }
+            if (rc != GC_OK) break;
+            if (ms_out) ms_out[2 * ti + sched] = tbest;
+            if (tbest < best) {
+                best = tbest;
+                choice.wu_max_targets = tiles[ti];
+                choice.schedule = sched;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != GC_OK) {
+        p->wu_max_targets = saved_max;
+        p->wu_schedule = saved_sched;
+        return rc;
+    }
+    p->wu_max_targets = choice.wu_max_targets;
+    p->wu_schedule = choice.schedule;
+    uint64_t W = 0;
+    GC_TRY(rebuild_wus(p, c, choice.wu_max_targets, &W));   // context matches the choice
+    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
+    if (best_out) *best_out = choice;
     return GC_OK;
 }

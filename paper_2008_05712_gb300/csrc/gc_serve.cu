@@ -75,6 +75,25 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
         const uint64_t nt = tgt_off[t + 1] - tgt_off[t], ns = src_off[t + 1] - src_off[t];
         row_off[t + 1] = row_off[t] + nt + (kinds[t] == GC_LJ_PAIR ? ns : 0);
     }
+    // page-lock the caller's id arrays for the call (unless they already
+    // are): the per-batch host-to-device copies then run as direct DMA
+    // instead of through the driver's pageable staging
+    std::vector<void *> pinned;
+    auto pin = [&](const void *ptr, uint64_t bytes) {
+        if (!ptr || !bytes) return;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) == cudaSuccess &&
+            at.type != cudaMemoryTypeUnregistered)
+            return;
+        cudaGetLastError();
+        if (cudaHostRegister(const_cast<void *>(ptr), bytes, cudaHostRegisterDefault) ==
+            cudaSuccess)
+            pinned.push_back(const_cast<void *>(ptr));
+        else
+            cudaGetLastError();   // stays pageable: slower copies, same results
+    };
+    pin(tgt_ids, tgt_off[n] * sizeof(uint32_t));
+    pin(src_ids, src_off[n] * sizeof(uint32_t));
     const uint64_t budget = p->cfg.staging_budget_bytes;
     std::vector<uint64_t> lat(n, 0);
     std::vector<uint64_t> to, so;
@@ -172,6 +191,7 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     }
     const uint64_t wall = now_ns() - start;
     gc_combiner_destroy(comb);
+    for (void *ptr : pinned) cudaHostUnregister(ptr);
     if (rc != GC_OK) return rc;
     gc_stats_t s1;
     GC_TRY(gc_stats(p, &s1));

@@ -39,6 +39,8 @@ GC_COMBINE_ADAPTIVE_WINDOW = 1
 GC_COMBINE_STATIC = 2
 GC_COMBINE_PER_TASK = 3
 GC_COMBINE_GREEDY = 4
+GC_SCHED_FIFO = 0
+GC_SCHED_LPT = 1
 
 NONE32 = 0xFFFFFFFF
 
@@ -65,7 +67,8 @@ _STAT_FIELDS = ["flushes", "tasks", "entries", "unique", "hits", "misses", "upda
 
 class GcStats(C.Structure):
     _fields_ = ([(f, C.c_uint64) for f in _STAT_FIELDS] + [("reuse_hist", C.c_uint64 * 8)]
-                + [("kernel_launches", C.c_uint64), ("primitive_calls", C.c_uint64)])
+                + [("kernel_launches", C.c_uint64), ("primitive_calls", C.c_uint64),
+                   ("stage_ms_sum", C.c_double * 5), ("timed_batches", C.c_uint64)])
 
 
 class GcServeConfig(C.Structure):
@@ -82,6 +85,10 @@ _SERVE_DFIELDS = ["wall_s", "interactions_per_s", "lat_mean_us", "lat_p50_us", "
 class GcServeReport(C.Structure):
     _fields_ = ([(f, C.c_uint64) for f in _SERVE_FIELDS]
                 + [(f, C.c_double) for f in _SERVE_DFIELDS])
+
+
+class GcTuning(C.Structure):
+    _fields_ = [("wu_max_targets", C.c_uint32), ("schedule", C.c_uint32)]
 
 
 class GcError(RuntimeError):
@@ -138,6 +145,10 @@ _SIGS = {
     "gc_max_combine_size": [P, U64P],
     "gc_serve": [P, U64, P, P, P, P, P, P, P, C.POINTER(GcServeConfig), P, P,
                  C.POINTER(GcServeReport)],
+    "gc_fp32_peak": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "gc_set_tuning": [P, C.POINTER(GcTuning)],
+    "gc_get_tuning": [P, C.POINTER(GcTuning)],
+    "gc_autotune": [P, C.c_int, C.POINTER(GcTuning), P],
 }
 
 _RESTYPES = {"gc_strerror": C.c_char_p, "gc_combine_size_from_occupancy": C.c_uint64}
@@ -361,7 +372,52 @@ class Pool:
         d["reuse_hist"] = list(s.reuse_hist)
         d["kernel_launches"] = s.kernel_launches
         d["primitive_calls"] = s.primitive_calls
+        d["stage_ms_sum"] = dict(zip(["residency", "pack", "interact", "scatter", "total"],
+                                     list(s.stage_ms_sum)))
+        d["timed_batches"] = s.timed_batches
         return d
+
+    def set_tuning(self, wu_max_targets=16, schedule=GC_SCHED_FIFO):
+        t = GcTuning(wu_max_targets=wu_max_targets, schedule=schedule)
+        _check(self.lib.gc_set_tuning(self.h, C.byref(t)), "gc_set_tuning")
+
+    def tuning(self):
+        t = GcTuning()
+        _check(self.lib.gc_get_tuning(self.h, C.byref(t)), "gc_get_tuning")
+        return {"wu_max_targets": t.wu_max_targets, "schedule": t.schedule}
+
+    def autotune(self, reps=3, cache=None, key=None):
+        """Pick the interaction schedule on the last flushed batch (gc_autotune).
+
+        With ``cache`` (a JSON file path) and ``key`` (a workload name), a
+        choice stored under ``key`` is applied without tuning; otherwise the
+        tuned choice is stored there.  Returns (choice, times_ms or None)."""
+        import json
+        if cache and key:
+            try:
+                with open(cache) as f:
+                    stored = json.load(f).get(key)
+            except (OSError, ValueError):
+                stored = None
+            if stored:
+                self.set_tuning(stored["wu_max_targets"], stored["schedule"])
+                return stored, None
+        best = GcTuning()
+        ms = np.zeros(6, np.float32)
+        _check(self.lib.gc_autotune(self.h, int(reps), C.byref(best), _p(ms)), "gc_autotune")
+        choice = {"wu_max_targets": best.wu_max_targets, "schedule": best.schedule}
+        times = {f"{t},{'lpt' if k else 'fifo'}": float(ms[2 * i + k])
+                 for i, t in enumerate((8, 16, 32)) for k in (0, 1)}
+        if cache and key:
+            try:
+                with open(cache) as f:
+                    data = json.load(f)
+            except (OSError, ValueError):
+                data = {}
+            data[key] = dict(choice, times_ms=times)
+            with open(cache, "w") as f:
+                json.dump(data, f, indent=1, sort_keys=True)
+        return choice, times
 
     def max_combine_size(self):
         v = C.c_uint64()
@@ -520,6 +576,14 @@ class Combiner:
             self.close()
         except Exception:
             pass
+
+
+def fp32_peak():
+    """Measured FP32 TFLOP/s of the current device (paired-FMA probe)."""
+    lib = load()
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib.gc_fp32_peak(C.byref(tf), C.byref(ms)), "gc_fp32_peak")
+    return tf.value
 
 
 def combine_size_from_occupancy(occupancy, max_blocks_per_sm, n_sm):

@@ -57,9 +57,10 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "gcharm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gc_config), offsetof(gc_config, cuda_stream),
-         sizeof(gc_task), offsetof(gc_task, target_ids), offsetof(gc_task, shift),
-         sizeof(gc_stats_t));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gc_config),
+         offsetof(gc_config, cuda_stream), sizeof(gc_task), offsetof(gc_task, target_ids),
+         offsetof(gc_task, shift), sizeof(gc_stats_t), offsetof(gc_stats_t, stage_ms_sum),
+         sizeof(gc_serve_config), sizeof(gc_serve_report), offsetof(gc_serve_report, wall_s));
   return 0;
 }
 """)
@@ -70,7 +71,9 @@ int main(void) {
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(gcharm.GcConfig), gcharm.GcConfig.cuda_stream.offset,
             ctypes.sizeof(gcharm.GcTask), gcharm.GcTask.target_ids.offset,
-            gcharm.GcTask.shift.offset, ctypes.sizeof(gcharm.GcStats)]
+            gcharm.GcTask.shift.offset, ctypes.sizeof(gcharm.GcStats),
+            gcharm.GcStats.stage_ms_sum.offset, ctypes.sizeof(gcharm.GcServeConfig),
+            ctypes.sizeof(gcharm.GcServeReport), gcharm.GcServeReport.wall_s.offset]
     assert got == want
 
 

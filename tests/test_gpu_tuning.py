@@ -1,0 +1,99 @@
+"""GPU tests of the interaction schedule (work-unit size 8 / 16 / 32 targets,
+admission-order or longest-first hand-out) and its autotuner: every schedule
+matches the FP64 oracle within the per-result tolerance, the work-unit order
+alone leaves every result bit-identical, and the autotuner keeps its fastest
+measured choice."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2008_05712_gb300 import inputs
+from gpu_util import EPS2, TOL, make_pool, per_task_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_2008_05712_gb300 import gcharm
+    gcharm.load()
+    return gcharm
+
+
+@pytest.fixture(scope="module")
+def batch():
+    n = 20000
+    x = inputs.merger(3 * n // 4, n // 4, 21)
+    to, tg, so, sr = inputs.uneven_tasks(n, 300, 22, (1, 100), (1, 5000))
+    return x, to, tg, so, sr
+
+
+def run(gc, x, to, tg, so, sr, wu_max, sched):
+    n = x.shape[0]
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    pool.set_tuning(wu_max, sched)
+    b = pool.submit_csr(np.zeros(len(to) - 1, np.uint32), to, tg, so, sr)
+    pool.flush()
+    pool.wait(b)
+    rows = pool.results()
+    return pool, rows
+
+
+def test_every_schedule_matches_oracle(gc, orc, batch):
+    x, to, tg, so, sr = batch
+    ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
+    for wu_max in (8, 16, 32):
+        per_order = []
+        for sched in (gc.GC_SCHED_FIFO, gc.GC_SCHED_LPT):
+            pool, rows = run(gc, x, to, tg, so, sr, wu_max, sched)
+            assert pool.tuning() == {"wu_max_targets": wu_max, "schedule": sched}
+            errs = per_task_errors(gc.value(rows), ref, to)
+            assert errs.max() <= TOL, (wu_max, sched, errs.max())
+            per_order.append(rows)
+            pool.close()
+        # the hand-out order changes which warp runs a unit, not its sums
+        assert np.array_equal(per_order[0], per_order[1])
+
+
+def test_bad_tuning_rejected(gc, batch):
+    x = batch[0]
+    pool = make_pool(gc, torch, x.shape[0], x.shape[0])
+    for wu_max, sched in [(12, 0), (64, 0), (16, 2)]:
+        with pytest.raises(gc.GcError) as e:
+            pool.set_tuning(wu_max, sched)
+        assert e.value.code == gc.GC_ERR_ARG
+    with pytest.raises(gc.GcError) as e:
+        pool.autotune()                      # nothing flushed yet
+    assert e.value.code == gc.GC_ERR_NOT_READY
+    pool.close()
+
+
+def test_autotune_keeps_fastest_and_caches(gc, orc, batch, tmp_path):
+    x, to, tg, so, sr = batch
+    pool, _ = run(gc, x, to, tg, so, sr, 16, gc.GC_SCHED_FIFO)
+    choice, times = pool.autotune(reps=2)
+    assert len(times) == 6 and all(v > 0 for v in times.values())
+    key = f"{choice['wu_max_targets']},{'lpt' if choice['schedule'] else 'fifo'}"
+    assert times[key] == min(times.values())
+    assert pool.tuning() == choice
+    # the re-run rows of the tuned batch still match the oracle
+    ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
+    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    # the next flush runs under the choice
+    b = pool.submit_csr(np.zeros(len(to) - 1, np.uint32), to, tg, so, sr)
+    pool.flush()
+    pool.wait(b)
+    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    # JSON cache: stored on the first call, applied without tuning on the next
+    cache = str(tmp_path / "tuning.json")
+    c1, t1 = pool.autotune(reps=1, cache=cache, key="uneven300")
+    assert t1 is not None and json.load(open(cache))["uneven300"]["wu_max_targets"] == \
+        c1["wu_max_targets"]
+    pool.set_tuning(8, gc.GC_SCHED_FIFO)
+    c2, t2 = pool.autotune(cache=cache, key="uneven300")
+    assert t2 is None and c2["wu_max_targets"] == c1["wu_max_targets"]
+    assert pool.tuning()["wu_max_targets"] == c1["wu_max_targets"]
+    pool.close()
