@@ -66,6 +66,9 @@ C4_S_RANGE = (16, 16384)
 C4_BUDGET = 2 << 30
 C4_WORKLOAD = ("uneven_200k: 200,000 gravity tasks over a 4,194,304-particle two-Plummer "
                "merger, nT ~ logU[8,1024], nS ~ logU[16,16384], staging budget 2 GiB")
+# Interaction schedules chosen by the autotuner on this GPU, per workload
+# (written on the first run, then reused).
+TUNE_CACHE = os.path.join(ROOT, "paper_2008_05712_gb300", "tuning.json")
 # serving: (aggregate Poisson rate of 16 producers in tasks/s, schedule seconds)
 SERVE_RATES = ((1e4, 1.0), (1e5, 1.0), (1e6, 0.2))
 
@@ -140,6 +143,23 @@ class ClockSampler:
                    sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
                    samples=len(rows))
         return out
+
+
+def replica_seed(rank):
+    """Seed of rank `rank`'s replica problem (independent problems per rank)."""
+    return inputs.SEED_BASE + 2 + 1000 * rank
+
+
+def reduce_over_ranks(seconds, count, device):
+    """Whole-job figures over the ranks of the default process group: the
+    slowest rank's time (max) and the units all ranks processed (sum)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), int(c.item())
 
 
 def dist_env():
@@ -268,6 +288,11 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3):
         pool.submit_csr_device(dk, dto, dtg, dso, dsr, tg.shape[0], sr.shape[0])
         pool.flush()
 
+    # autotune the interaction schedule on the first 40,000 tasks (one wave)
+    m = 40_000
+    pool.submit_csr(kinds[:m], to[:m + 1], tg[:int(to[m])], so[:m + 1], sr[:int(so[m])])
+    pool.flush()
+    tuning, tune_ms = pool.autotune(reps=2, cache=TUNE_CACHE, key="uneven_200k")
     batch()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -276,6 +301,7 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3):
     e0.record(stream)
     for _ in range(batch_reps):
         batch()
+    pool.join(stream.cuda_stream)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / batch_reps
@@ -285,7 +311,29 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3):
               "list_entries": int(tg.shape[0] + sr.shape[0]),
               "ms_per_batch": ms, "value": inter / (ms / 1e3), "unit": "interactions/s",
               "waves": st["last_waves"], "stage_ms_last_batch": pool.timings(),
-              "reps": batch_reps}
+              "reps": batch_reps,
+              "tuning": {"wu_max_targets": tuning["wu_max_targets"],
+                         "schedule": "lpt" if tuning["schedule"] else "fifo",
+                         "autotune_ms": tune_ms or tuning.get("times_ms")}}
+    # the persistent + graph form: the batch captured once, then replayed
+    pool.submit_csr_device(dk, dto, dtg, dso, dsr, tg.shape[0], sr.shape[0])
+    graph = gcharm.Graph(pool)
+    graph.launch()
+    graph.wait()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(batch_reps):
+        graph.launch()
+    pool.join(stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gms = e0.elapsed_time(e1) / batch_reps
+    graph.wait()
+    uneven["graph_replay"] = {"ms_per_batch": gms, "value": inter / (gms / 1e3),
+                              "unit": "interactions/s", "reps": batch_reps,
+                              "note": "same tasks and chare table each replay; values read "
+                                      "from the pool at replay time"}
+    graph.close()
     del dk, dto, dso, dtg, dsr
 
     # serving: open-loop Poisson arrivals (16 producers merged)
@@ -342,7 +390,7 @@ def main():
     gcharm.load()
     n = args.n
     K, W = args.steps, max(args.warmup, 3)
-    seed = inputs.SEED_BASE + 2 + 1000 * rank
+    seed = replica_seed(rank)
 
     # pre-generate all steps' positions (a drift walk), resident in HBM
     xs = [inputs.plummer(n, seed)]
@@ -364,7 +412,10 @@ def main():
         pool.build_nbody(X[k], BUCKET, *THETA)
         pool.flush()
 
-    for k in range(W):
+    step(0)
+    tuning, tune_ms = pool.autotune(reps=2, cache=TUNE_CACHE, key="nbody_plummer_1M"
+                                    if n == N_PART else f"nbody_plummer_{n}")
+    for k in range(1, W):
         step(k)
     torch.cuda.synchronize()
     if ws > 1:
@@ -378,6 +429,7 @@ def main():
     e0.record(stream)
     for k in range(W, W + K):
         step(k)
+    pool.join(stream.cuda_stream)          # the last batch may run on the other context
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -389,12 +441,7 @@ def main():
     launches = s1["kernel_launches"] - s0["kernel_launches"]
     prims = s1["primitive_calls"] - s0["primitive_calls"]
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        c = torch.tensor([float(interactions)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        interactions_all = int(c.item())
+        ms, interactions_all = reduce_over_ranks(ms, interactions, "cuda")
     else:
         interactions_all = interactions
     value = interactions_all / (ms / 1e3)
@@ -452,9 +499,8 @@ def main():
            "h2d_bytes_per_step": int(n * (4 + 16 + 16 + 4)),
            "d2h_bytes_per_step": int(tot.nbytes)}
     if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = interactions_all / float(t.item())
+        e2e_max, _ = reduce_over_ranks(e2e_s, 0, "cuda")
+        e2e["value"] = interactions_all / e2e_max
 
     # the same step with one interaction launch per task (no combining)
     per_task = None
@@ -521,6 +567,10 @@ def main():
             "roofline": dominant,
             "rooflines": {"interaction": grav, "pack": pack},
             "stage_ms_avg": stage,
+            "tuning": {"wu_max_targets": tuning["wu_max_targets"],
+                       "schedule": "lpt" if tuning["schedule"] else "fifo",
+                       "autotune_ms": tune_ms or tuning.get("times_ms"),
+                       "cache": os.path.relpath(TUNE_CACHE, ROOT)},
             "reuse": {"last_hits": hits, "last_unique": uniq},
             "clocks": clk,
             "e2e": e2e,

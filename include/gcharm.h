@@ -199,6 +199,11 @@ int gc_wait(gc_pool_t *pool, uint64_t batch, uint64_t timeout_ns);
  * completed (0 while it runs or has not been flushed). */
 int gc_batch_done(gc_pool_t *pool, uint64_t batch, int *done_out);
 
+/* Make `stream` (a cudaStream_t; NULL = the legacy default stream) wait for
+ * all work the pool has issued so far: every batch in flight and anything
+ * queued on the pool's streams.  No host wait. */
+int gc_join(gc_pool_t *pool, void *stream);
+
 /* Batches run alternately on two flush contexts, each with its own stream:
  * batch k+1's chare-table step and pack overlap batch k's interaction on the
  * device.  Results of batch k stay readable until batch k+2 is flushed. */
@@ -426,6 +431,41 @@ int gc_serve(gc_pool_t *pool, uint64_t n, const uint64_t *arrival_ns, const uint
              const int8_t *shifts, const uint64_t *tgt_off, const uint32_t *tgt_ids,
              const uint64_t *src_off, const uint32_t *src_ids, const gc_serve_config *cfg,
              uint64_t *latency_ns_out, float *results_out, gc_serve_report *report);
+
+/* ---- a combined batch as a replayable CUDA graph -------------------------- */
+
+typedef struct gc_graph gc_graph_t;
+
+/* Capture the pending batch as a replayable step (the combined launch of
+ * Section 3.1 kept as a CUDA graph).  Runs it once as gc_flush does, which
+ * settles the chare table and every size, then records in a CUDA graph the
+ * device work of one more execution on buffers the graph owns: last-use
+ * update of the batch's distinct ids, per wave the pack and interaction
+ * kernels, and the per-id FP64 accumulation in the order the first run
+ * established.  The rows of the first run are readable through
+ * gc_graph_results (not through the pool's result calls).  *out receives the
+ * handle.  Errors: GC_ERR_STATE (no pending task), GC_ERR_POOL_FULL (the
+ * batch's ids do not all fit the pool at once), any gc_flush error,
+ * GC_ERR_CUDA. */
+int gc_graph_capture(gc_pool_t *pool, gc_graph_t **out);
+
+/* Replay the captured step, after the pool's batches in flight and before
+ * any later one: same tasks, current pool values (ids re-uploaded in place
+ * are used), new rows in the graph's buffers, per-id totals accumulated.
+ * Asynchronous.  Errors: GC_ERR_STATE (a slot was assigned or freed since
+ * the capture: capture again), GC_ERR_CUDA. */
+int gc_graph_launch(gc_graph_t *g);
+
+/* Wait for the last replay; GC_ERR_TIMEOUT if a device wait ran out. */
+int gc_graph_wait(gc_graph_t *g);
+
+/* Result rows of the graph's batch (8 floats per row, as
+ * gc_read_batch_results) after the last run or replay. */
+int gc_graph_rows(gc_graph_t *g, uint64_t *rows_out);
+int gc_graph_results(gc_graph_t *g, uint64_t first_row, uint64_t n_rows, float *out);
+
+/* Release the graph and its buffers (waits for its last replay). */
+int gc_graph_destroy(gc_graph_t *g);
 
 /* ---- interaction schedule and its autotuner ------------------------------ */
 

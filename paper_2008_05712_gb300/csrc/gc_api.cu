@@ -101,12 +101,14 @@ __global__ void k_gather_totals(const gcd4 *totals, const uint32_t *ids, uint64_
     }
 }
 
+}  // namespace
+
 void free_ctx(FlushCtx &c)
 {
     DBuf *bufs[] = {&c.tasks, &c.tgt_ids, &c.src_ids, &c.tgt_perm, &c.src_perm, &c.stg_tgt,
                     &c.stg_src, &c.wu, &c.wu_cnt, &c.wu_off, &c.rowcnt, &c.lj_list, &c.res,
                     &c.row_id, &c.rid_sorted, &c.row_sorted, &c.rows_tmp, &c.runs, &c.tiles,
-                    &c.merge_a, &c.merge_b, &c.cub_tmp};
+                    &c.merge_a, &c.merge_b, &c.cub_tmp, &c.lpt};
     for (DBuf *b : bufs) b->release();
     for (int i = 0; i < 6; ++i)
         if (c.ev_stage[i]) cudaEventDestroy(c.ev_stage[i]);
@@ -118,7 +120,7 @@ void free_ctx(FlushCtx &c)
     if (c.owns_stream && c.s) cudaStreamDestroy(c.s);
 }
 
-void free_pool(gc_pool *p)
+static void free_pool(gc_pool *p)
 {
     if (!p) return;
     cudaFree(p->d_pool);
@@ -172,14 +174,14 @@ int init_ctx(FlushCtx &c, cudaStream_t given)
 }
 
 // The context holding batch `batch`, or null if neither does.
-FlushCtx *ctx_of(gc_pool *p, uint64_t batch)
+static FlushCtx *ctx_of(gc_pool *p, uint64_t batch)
 {
     for (int i = 0; i < 2; ++i)
         if (p->ctx[i].valid && p->ctx[i].batch == batch) return &p->ctx[i];
     return nullptr;
 }
 
-FlushCtx *last_ctx(gc_pool *p) { return p->last >= 0 ? &p->ctx[p->last] : nullptr; }
+static FlushCtx *last_ctx(gc_pool *p) { return p->last >= 0 ? &p->ctx[p->last] : nullptr; }
 
 // Make the issue stream wait for every scatter in flight (per-id totals).
 int order_after_scatters(gc_pool *p)
@@ -191,7 +193,7 @@ int order_after_scatters(gc_pool *p)
 }
 
 template <class T>
-int dmalloc(T **ptr, uint64_t count)
+static int dmalloc(T **ptr, uint64_t count)
 {
     if (cudaMalloc((void **)ptr, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
         cudaGetLastError();
@@ -201,7 +203,7 @@ int dmalloc(T **ptr, uint64_t count)
     return GC_OK;
 }
 
-bool on_grid(double v, double scale, int64_t *out)
+static bool on_grid(double v, double scale, int64_t *out)
 {
     double g = v * scale;
     if (!(g >= 0) || g > 9.0e18 || std::floor(g) != g) return false;
@@ -209,7 +211,7 @@ bool on_grid(double v, double scale, int64_t *out)
     return true;
 }
 
-void clear_last_stats(gc_pool *p)
+static void clear_last_stats(gc_pool *p)
 {
     gc_stats_t &s = p->stats;
     s.last_unique = s.last_hits = s.last_misses = s.last_evictions = 0;
@@ -217,9 +219,6 @@ void clear_last_stats(gc_pool *p)
     s.lj_pairs_in_cutoff = 0;
     for (int b = 0; b < 8; ++b) s.reuse_hist[b] = 0;
 }
-
-
-}  // namespace
 
 extern "C" {
 
@@ -590,6 +589,17 @@ static int flush_impl(gc_pool *p, int per_task)
         GC_TRY(c.merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
     }
 
+    c.waves.clear();
+    for (const Wave &w : waves) {
+        WaveRange r{w.t0, w.t1, w.tg0, w.tg1, w.s0, w.s1, 0, W, 0, L};
+        if (need_offsets) {
+            r.w0 = wu_off[w.t0]; r.w1 = wu_off[w.t1];
+            r.l0 = lj_off[w.t0]; r.l1 = lj_off[w.t1];
+        }
+        c.waves.push_back(r);
+    }
+    c.msrc = max_wt + 1;
+
     float ms_res = 0, ms_pack = 0, ms_int = 0;
     const uint32_t *tgt_ids = c.tgt_ids.as<uint32_t>();
     const uint32_t *src_ids = c.src_ids.as<uint32_t>();
@@ -699,6 +709,27 @@ int gc_wait(gc_pool_t *p, uint64_t batch, uint64_t timeout_ns)
         }
     }
     return device_status();
+}
+
+int gc_join(gc_pool_t *p, void *stream)
+{
+    if (!p) return GC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < 2; ++i)
+        if (p->ctx[i].ev_done && p->ctx[i].s != s)
+            GC_CUDA_TRY(cudaStreamWaitEvent(s, p->ctx[i].ev_done, 0));
+    if (p->s != s) {
+        // work issued on the pool's stream after the last flush (uploads,
+        // task builds, graph replays)
+        cudaEvent_t e = nullptr;
+        GC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        int rc = GC_OK;
+        if (cudaEventRecord(e, p->s) != cudaSuccess || cudaStreamWaitEvent(s, e, 0) != cudaSuccess)
+            rc = GC_ERR_CUDA;
+        cudaEventDestroy(e);
+        return rc;
+    }
+    return GC_OK;
 }
 
 int gc_batch_done(gc_pool_t *p, uint64_t batch, int *done_out)

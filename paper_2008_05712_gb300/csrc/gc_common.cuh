@@ -92,6 +92,26 @@ struct MDState {
     DBuf keys, keys2, ids, ids2, cell_start, cnt_t, cnt_s, cub_tmp, hostcopy;
 };
 
+// Blocks for n items at `threads` per block, at most max_blocks (grid-stride
+// loops cover the rest).
+static inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
+{
+    uint64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (uint64_t)max_blocks) b = max_blocks;
+    return (unsigned)b;
+}
+
+#define GRID_STRIDE(i, n)                                                       \
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); \
+         i += (uint64_t)gridDim.x * blockDim.x)
+
+// One wave of a flush: tasks [t0, t1), their target / source entries, and
+// their gravity work units and LJ task slots.
+struct WaveRange {
+    uint64_t t0, t1, tg0, tg1, s0, s1, w0, w1, l0, l1;
+};
+
 // Everything one in-flight batch owns: its stream, its batch arrays, work
 // buffers, counters and events.
 struct FlushCtx {
@@ -112,6 +132,8 @@ struct FlushCtx {
     bool timing_counted = false;   // stage times added to the pool's sums
     float multiwave_ms[3] = {0, 0, 0};
     uint64_t n_waves = 0;
+    std::vector<WaveRange> waves;          // the waves of the batch
+    uint64_t msrc = 0;                     // source offset in the merge scratch
     std::vector<TaskRec> host_tasks;       // for gc_read_results
     std::unordered_map<uint64_t, uint64_t> task_index;
     bool host_tasks_valid = false;
@@ -159,6 +181,7 @@ struct gc_pool {
     // interaction schedule (gc_set_tuning / gc_autotune)
     uint32_t wu_max_targets = 16;      // targets per gravity work unit: 8, 16 or 32
     uint32_t wu_schedule = GC_SCHED_FIFO;
+    uint64_t table_version = 0;        // bumped whenever a slot is assigned or freed
     NBodyState nb;
     MDState md;
 };
@@ -199,6 +222,10 @@ int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64
 
 // ---- pack / interaction / scatter (gc_kernels.cu) -----------------------------
 int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5]);
+int gc_scatter_replay(gc_pool *p, FlushCtx &c);
+int init_ctx(FlushCtx &c, cudaStream_t given);
+void free_ctx(FlushCtx &c);
+int order_after_scatters(gc_pool *p);
 int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
                        std::vector<uint32_t> &lj_off);
 int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,

@@ -14,18 +14,6 @@
 
 namespace {
 
-inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
-{
-    uint64_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > (uint64_t)max_blocks) b = max_blocks;
-    return (unsigned)b;
-}
-
-#define GRID_STRIDE(i, n)                                                       \
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); \
-         i += (uint64_t)gridDim.x * blockDim.x)
-
 // ---------------------------------------------------------------------------
 // task records and preparation
 // ---------------------------------------------------------------------------
@@ -352,9 +340,7 @@ __device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
         for (int c = b0; c < b1; c += 32) {
             const int k = c + lane;
             const bool v = k < b1;
-            const uint32_t d = v ? ((ka[k] >> sh) & 255u) : 0u;
-            const uint32_t m = warp_match<8>(d, __ballot_sync(0xffffffffu, v));
-            if (v && (m & lt) == 0) sm.hist[w][d] += (uint32_t)__popc(m);
+            if (v) atomicAdd(&sm.hist[w][(ka[k] >> sh) & 255u], 1u);
         }
         __syncthreads();
         uint32_t s = 0;
@@ -402,8 +388,9 @@ __device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
 // Sorting: warp w owns a contiguous range of the current layout; within a
 // warp, 32 items at a time are ranked among equal digits with
 // label ballots (stable: warp by warp, chunk by chunk, lane by lane).
-// Each scatter also counts the next pass's per-warp histogram from the
-// destinations it writes, so a pass is one sweep between two barriers.
+// Each scatter also counts the next pass's per-warp histogram (shared-memory
+// atomics) from the destinations it writes, so a pass is one sweep between
+// two barriers.
 constexpr int PM_THREADS = 128;
 constexpr int PM_W = PM_THREADS / 32;
 constexpr int PM_U = 8;             // lookups in flight per thread
@@ -520,9 +507,7 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
         for (int c = b0; c < b1; c += 32) {
             const int k = c + lane;
             const bool v = k < b1;
-            const uint32_t d = v ? (sm.ka[k] & 255u) : 0u;
-            const uint32_t m = warp_match<8>(d, __ballot_sync(0xffffffffu, v));
-            if (v && (m & lt) == 0) sm.hist[0][w][d] += (uint32_t)__popc(m);
+            if (v) atomicAdd(&sm.hist[0][w][sm.ka[k] & 255u], 1u);
         }
         __syncthreads();
         uint32_t *ka = sm.ka, *kb = sm.kb;
@@ -573,14 +558,12 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
                     __syncwarp();
                     if (v && (m & lt) == 0) sm.hist[cur][w][d] += (uint32_t)__popc(m);
                 }
-                if (!last) {
+                if (!last && v) {
                     // next pass: count (warp range of dst, next digit)
                     const uint32_t wd = (uint32_t)(dst >= per) + (uint32_t)(dst >= 2 * per) +
                                         (uint32_t)(dst >= 3 * per);
-                    const uint32_t d2 = wd * 256u + ((key >> (sh + 8)) & 255u);
-                    const uint32_t m2 = warp_match<10>(d2, vm);
-                    if (v && (m2 & lt) == 0)
-                        atomicAdd(&sm.hist[cur ^ 1][0][0] + d2, (uint32_t)__popc(m2));
+                    atomicAdd(&sm.hist[cur ^ 1][0][0] + wd * 256u + ((key >> (sh + 8)) & 255u),
+                              1u);
                 }
             }
             __syncthreads();
@@ -748,7 +731,7 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float s2, float c2)
         float2 r2 = __ffma2_rn(dx, dx, e2);                               \
         r2 = __ffma2_rn(dy, dy, r2);                                      \
         r2 = __ffma2_rn(dz, dz, r2);                                      \
-        float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));              \
+        float2 ri = make_float2(gc_rsqrt(r2.x), gc_rsqrt(r2.y));          \
         float2 mr = __fmul2_rn(make_float2((B).z, (B).w), ri);            \
         float2 mr3 = __fmul2_rn(mr, __fmul2_rn(ri, ri));                  \
         bx = __ffma2_rn(mr3, dx, bx);                                     \
@@ -1346,6 +1329,20 @@ int gc_scatter(gc_pool *p, FlushCtx &c)
     ++p->stats.kernel_launches;
     k_reduce_runs<<<grid_for(n_rows, 256, maxb), 256, 0, c.s>>>(
         c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, n_rows, c.rid_sorted.as<uint32_t>(),
+        c.row_sorted.as<uint32_t>(), c.res.as<float4>(), p->d_totals);
+    GC_CUDA_TRY(cudaGetLastError());
+    return GC_OK;
+}
+
+// The accumulation step of a batch whose rows were sorted by id before (the
+// run boundaries and row order are kept in the context): rows summed into
+// the per-id totals in the same order.
+int gc_scatter_replay(gc_pool *p, FlushCtx &c)
+{
+    if (c.n_rows == 0) return GC_OK;
+    ++p->stats.kernel_launches;
+    k_reduce_runs<<<grid_for(c.n_rows, 256, p->num_sms * 16), 256, 0, c.s>>>(
+        c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, c.n_rows, c.rid_sorted.as<uint32_t>(),
         c.row_sorted.as<uint32_t>(), c.res.as<float4>(), p->d_totals);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;

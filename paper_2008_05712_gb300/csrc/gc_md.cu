@@ -13,18 +13,6 @@
 
 namespace {
 
-#define GRID_STRIDE(i, n)                                                       \
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); \
-         i += (uint64_t)gridDim.x * blockDim.x)
-
-inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
-{
-    uint64_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > (uint64_t)max_blocks) b = max_blocks;
-    return (unsigned)b;
-}
-
 // task slot o = 1..13 -> neighbour offset; slot 0 is the self task
 __constant__ int8_t c_half_shell[13][3] = {
     {0, 0, 1},  {0, 1, -1},  {0, 1, 0},  {0, 1, 1},  {1, -1, -1}, {1, -1, 0}, {1, -1, 1},

@@ -33,18 +33,6 @@ int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint6
 
 namespace {
 
-#define GRID_STRIDE(i, n)                                                       \
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < (n); \
-         i += (uint64_t)gridDim.x * blockDim.x)
-
-inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
-{
-    uint64_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > (uint64_t)max_blocks) b = max_blocks;
-    return (unsigned)b;
-}
-
 struct GridParams {
     double lo[3];
     double scale;   // 2^21 / L, L = smallest power of two >= largest extent

@@ -67,3 +67,13 @@ __device__ __forceinline__ bool gc_mbar_wait_bounded(uint64_t *bar, uint32_t par
         if (gc_mbar_try_wait(bar, parity)) return true;
     return false;
 }
+
+// 1/sqrt(x) by the hardware approximation (rsqrt.approx, relative error
+// below 2^-22) in its flush-to-zero form: the interaction kernel's arguments
+// are r^2 + eps^2 >= eps^2 > 0, never subnormal.
+__device__ __forceinline__ float gc_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}

@@ -310,14 +310,6 @@ __global__ void k_upload(const uint32_t *ids, uint32_t id_base, const float4 *va
     if (threadIdx.x == 0 && upd) atomicAdd(&ctr[CTR_UPDATES], (unsigned long long)upd);
 }
 
-inline unsigned grid_for(uint64_t n, int threads, int max_blocks)
-{
-    uint64_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > (uint64_t)max_blocks) b = max_blocks;
-    return (unsigned)b;
-}
-
 }  // namespace
 
 // Slots of the given ids (introspection of the chare table).
@@ -453,6 +445,7 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
                           ctr + CTR_FREE));
         p->n_evicted_last = need;
     }
+    if (M || need) ++p->table_version;   // slots assigned or freed: captured graphs stale
     if (M) {
         ++p->stats.kernel_launches;
         k_assign<<<grid_for(M, 256, maxb), 256, 0, p->s>>>(

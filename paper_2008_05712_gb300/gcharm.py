@@ -116,6 +116,7 @@ _SIGS = {
     "gc_flush_per_task": [P],
     "gc_wait": [P, U64, U64],
     "gc_batch_done": [P, U64, C.POINTER(C.c_int)],
+    "gc_join": [P, P],
     "gc_result_rows": [P, U64P],
     "gc_read_batch_results": [P, U64, U64, P],
     "gc_read_batch_rows": [P, U64, U64, U64, P],
@@ -149,6 +150,12 @@ _SIGS = {
     "gc_set_tuning": [P, C.POINTER(GcTuning)],
     "gc_get_tuning": [P, C.POINTER(GcTuning)],
     "gc_autotune": [P, C.c_int, C.POINTER(GcTuning), P],
+    "gc_graph_capture": [P, C.POINTER(P)],
+    "gc_graph_launch": [P],
+    "gc_graph_wait": [P],
+    "gc_graph_rows": [P, U64P],
+    "gc_graph_results": [P, U64, U64, P],
+    "gc_graph_destroy": [P],
 }
 
 _RESTYPES = {"gc_strerror": C.c_char_p, "gc_combine_size_from_occupancy": C.c_uint64}
@@ -288,6 +295,11 @@ class Pool:
         d = C.c_int()
         _check(self.lib.gc_batch_done(self.h, int(batch), C.byref(d)), "gc_batch_done")
         return bool(d.value)
+
+    def join(self, stream_handle):
+        """Make the CUDA stream (raw handle, e.g. torch's ``cuda_stream``) wait
+        for all work the pool has issued (gc_join)."""
+        _check(self.lib.gc_join(self.h, C.c_void_p(stream_handle)), "gc_join")
 
     def wait(self, batch, timeout_ns=0):
         _check(self.lib.gc_wait(self.h, int(batch), int(timeout_ns)), "gc_wait")
@@ -520,6 +532,39 @@ class Pool:
         atoms = np.empty(n, np.uint32)
         _check(self.lib.gc_read_md_cells(self.h, _p(start), _p(atoms)), "gc_read_md_cells")
         return start, atoms
+
+
+class Graph:
+    """A pending batch captured as a replayable CUDA graph (gc_graph_*)."""
+
+    def __init__(self, pool):
+        h = C.c_void_p()
+        _check(pool.lib.gc_graph_capture(pool.h, C.byref(h)), "gc_graph_capture")
+        self.h, self.lib, self.pool = h, pool.lib, pool
+
+    def launch(self):
+        _check(self.lib.gc_graph_launch(self.h), "gc_graph_launch")
+
+    def wait(self):
+        _check(self.lib.gc_graph_wait(self.h), "gc_graph_wait")
+
+    def results(self):
+        r = C.c_uint64()
+        _check(self.lib.gc_graph_rows(self.h, C.byref(r)), "gc_graph_rows")
+        out = np.empty((r.value, 8), np.float32)
+        _check(self.lib.gc_graph_results(self.h, 0, r.value, _p(out)), "gc_graph_results")
+        return out
+
+    def close(self):
+        if self.h:
+            _check(self.lib.gc_graph_destroy(self.h), "gc_graph_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def value(res):
