@@ -51,7 +51,8 @@ PACK_BYTES_PER_ENTRY = 40
 # kernels (None until captured again after a kernel change):
 # k_gravity per interaction, the pack kernels per list entry.
 GRAVITY_DRAM_BYTES_PER_INTERACTION = None
-PACK_DRAM_BYTES_PER_ENTRY = None
+# profiles/k_pack_mid_nbody262k.md: 643.1 MB for 3.07e7 entries (262,144-particle step)
+PACK_DRAM_BYTES_PER_ENTRY = 643.1e6 / 3.07e7
 
 
 # Uneven batch and serving workload: a two-Plummer merger of 4,194,304
@@ -413,6 +414,7 @@ def main():
         pool.flush()
 
     step(0)
+    cold_misses = pool.stats()["last_misses"]     # first flush: every id fetched
     tuning, tune_ms = pool.autotune(reps=2, cache=TUNE_CACHE, key="nbody_plummer_1M"
                                     if n == N_PART else f"nbody_plummer_{n}")
     for k in range(1, W):
@@ -480,6 +482,14 @@ def main():
                         if PACK_DRAM_BYTES_PER_ENTRY else None)}
     pack["frac"] = pack["achieved"] / pack["peak"]
     dominant = pack if stage["pack"] >= stage["interact"] else grav
+
+    # reuse ablation (Section 3.2, Fig. 3) on the last timed batch
+    ablation = pool.reuse_ablation(reps=3)
+    ablation["cold_reuse_fetch_bytes"] = cold_misses * 16
+    ablation["note"] = ("kernel times: packed staging (this engine) vs sources read through "
+                        "their pool slots in list order / sorted by slot; transfer: redundant "
+                        "host-packed staging vs the misses the chare table fetched (first "
+                        "step: every id; later steps: none)")
 
     # end-to-end through the C ABI with host buffers (pinned), copies timed
     pinned = torch.empty((K, n, 4), dtype=torch.float32, pin_memory=True)
@@ -577,6 +587,7 @@ def main():
             "gpu_launches": launches,
             "primitive_calls": prims,
             "per_task_launch": per_task,
+            "reuse_ablation": ablation,
             "uneven_batch": uneven,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -498,6 +498,25 @@ int gc_get_tuning(gc_pool_t *pool, gc_tuning *t);
  * than one wave, or has no gravity task), GC_ERR_CUDA. */
 int gc_autotune(gc_pool_t *pool, int reps, gc_tuning *best_out, float ms_out[6]);
 
+/* ---- reuse ablation (Section 3.2, Fig. 3) --------------------------------- */
+
+/* Ways of feeding a batch's sources to the interaction, measured on the last
+ * flushed batch (one wave, gravity tasks only), best of `reps`:
+ *   out[0] interaction kernel on the packed staging (this engine), ms
+ *   out[1] interaction reading every source from the pool through its slot,
+ *          in list order (reuse without coalescing: the address buffer), ms
+ *   out[2] the same with each list's slots sorted (Fig. 1d without the
+ *          gather), ms
+ *   out[3] redundant transfer, host side: every list's sources gathered on
+ *          the host from the authoritative copy into contiguous staging, ms
+ *   out[4] its host-to-device copy (pinned), ms
+ *   out[5] bytes of that copy
+ *   out[6] bytes the batch fetched with reuse (its misses x 16)
+ * The batch's result rows are rewritten by the re-runs (same values up to
+ * summation order).  Errors: GC_ERR_NOT_READY, GC_ERR_STATE (several waves,
+ * LJ tasks), GC_ERR_OOM, GC_ERR_CUDA. */
+int gc_reuse_ablation(gc_pool_t *pool, int reps, double out[7]);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* FP32 throughput of the current device, measured: independent paired-FP32

@@ -11,7 +11,6 @@
 #include "gc_common.cuh"
 
 // ---- helpers declared in other translation units ----------------------------
-int gc_entry_slots(gc_pool *p, cudaStream_t s, const uint32_t *ids, uint64_t n, uint32_t *out);
 
 // ---- DBuf ---------------------------------------------------------------------
 int DBuf::reserve(size_t bytes)
@@ -129,7 +128,6 @@ static void free_pool(gc_pool *p)
     cudaFree(p->d_last_use);
     cudaFree(p->d_ref_epoch);
     cudaFree(p->d_ref_count);
-    cudaFree(p->d_known);
     cudaFree(p->d_totals);
     cudaFree(p->d_ctr);
     if (p->h_mirror) cudaFreeHost(p->h_mirror);
@@ -291,7 +289,6 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
     if (rc == GC_OK) rc = dmalloc(&p->d_last_use, cap);
     if (rc == GC_OK) rc = dmalloc(&p->d_ref_epoch, idc);
     if (rc == GC_OK) rc = dmalloc(&p->d_ref_count, idc);
-    if (rc == GC_OK) rc = dmalloc(&p->d_known, idc);
     if (rc == GC_OK) rc = dmalloc(&p->d_totals, idc);
     if (rc == GC_OK) rc = dmalloc(&p->d_ctr, (uint64_t)CTR_COUNT);
     if (rc == GC_OK) {
@@ -308,9 +305,8 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
         cudaMemsetAsync(p->d_slot_of_id, 0xFF, sizeof(uint32_t) * idc, p->s);
         cudaMemsetAsync(p->d_id_of_slot, 0xFF, sizeof(uint32_t) * cap, p->s);
         cudaMemsetAsync(p->d_last_use, 0, sizeof(uint32_t) * cap, p->s);
-        cudaMemsetAsync(p->d_ref_epoch, 0, sizeof(uint32_t) * idc, p->s);
+        cudaMemsetAsync(p->d_ref_epoch, 0xFF, sizeof(uint32_t) * idc, p->s);   // unknown
         cudaMemsetAsync(p->d_ref_count, 0, sizeof(uint32_t) * idc, p->s);
-        cudaMemsetAsync(p->d_known, 0, idc, p->s);
         cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * idc, p->s);
         cudaMemsetAsync(p->d_ctr, 0, sizeof(unsigned long long) * CTR_COUNT, p->s);
         std::memset(p->h_mirror, 0, sizeof(float4) * idc);

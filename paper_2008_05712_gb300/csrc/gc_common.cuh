@@ -12,6 +12,9 @@
 #include "gcharm.h"
 
 #define GC_NONE 0xFFFFFFFFu
+// ref_epoch[id]: GC_EPOCH_UNKNOWN until the id's value is first uploaded,
+// 0 until first referenced, then the epoch of the last wave referencing it
+#define GC_EPOCH_UNKNOWN 0xFFFFFFFFu
 
 // Four doubles, 32-byte aligned (one per-id FP64 total).
 struct __align__(32) gcd4 {
@@ -154,7 +157,6 @@ struct gc_pool {
     uint32_t *d_last_use = nullptr;    // [pool_capacity]
     uint32_t *d_ref_epoch = nullptr;   // [id_capacity]
     uint32_t *d_ref_count = nullptr;   // [id_capacity]
-    uint8_t *d_known = nullptr;        // [id_capacity]
     float4 *h_mirror = nullptr;        // pinned, mapped [id_capacity]
     float4 *d_mirror = nullptr;        // device alias of h_mirror
     gcd4 *d_totals = nullptr;       // [id_capacity]
@@ -215,6 +217,7 @@ int gc_exclusive_scan_u32(DBuf &tmp, const uint32_t *in, uint32_t *out, uint64_t
 // Runs the chare-table step for the entries tgt[0..nt) and src[0..ns): after
 // it every referenced id is resident.  Returns GC_OK, GC_ERR_UNKNOWN_ID or
 // GC_ERR_POOL_FULL.
+int gc_entry_slots(gc_pool *p, cudaStream_t s, const uint32_t *ids, uint64_t n, uint32_t *out);
 int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
                  uint64_t ns);
 int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64_t n,

@@ -255,7 +255,7 @@ extern "C" int gc_graph_launch(gc_graph_t *g)
     gc_pool *p = g->p;
     if (p->table_version != g->version) return GC_ERR_STATE;
     p->epoch += 1;
-    if (p->epoch == 0) p->epoch = 1;
+    if (p->epoch == 0 || p->epoch == GC_EPOCH_UNKNOWN) p->epoch = 1;
     // totals accumulate in admission order: after every scatter in flight;
     // the pool's issue stream then waits for this replay
     GC_TRY(order_after_scatters(p));

@@ -900,6 +900,112 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// interaction reading sources through their pool slots (reuse ablation)
+// ---------------------------------------------------------------------------
+
+// The same work units and pair arithmetic as k_gravity, but without staging:
+// every source is read from the device pool through its slot, in the order
+// given by `seq` (entry slots of each list in list order -- the "address
+// buffer" of Section 3.2 before sorting -- or sorted by slot).  Lane (t, s)
+// takes source pairs s, s + S, ... of the list, as k_gravity does.
+struct IndirectSmem {
+    float4 red[GRAV_WARPS][32][2];      // cross-lane combine: (sum, compensation)
+};
+
+__global__ void __launch_bounds__(GRAV_THREADS) k_gravity_indirect(InterArgs a,
+                                                                  const uint32_t *seq,
+                                                                  const float4 *pool)
+{
+    __shared__ IndirectSmem sm;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 e2 = make_float2(a.eps2, a.eps2);
+    for (;;) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(a.queue, 1ull);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= a.n_wu) break;
+        const GravWU u = a.wu[w];
+        const TaskRec r = a.tasks[u.task];
+        const int T = (int)u.tn;
+        const int S = 32 / T;
+        const int t = lane % T;
+        const int sl = lane / T;
+        const bool active = sl < S;
+        const uint32_t *q = seq + r.src_off;
+        const uint32_t np = (r.ns + 1u) >> 1;
+        const float4 xi = a.stg_t[r.tgt_off - a.tgt_base + u.t0 + t];
+        const float2 nx = make_float2(-xi.x, -xi.x);
+        const float2 ny = make_float2(-xi.y, -xi.y);
+        const float2 nz = make_float2(-xi.z, -xi.z);
+        float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
+        float2 cx = sx, cy = sx, cz = sx, cp = sx;
+        float2 bx = sx, by = sx, bz = sx, bp = sx;
+        int inblk = 0;
+        for (uint32_t j = active ? (uint32_t)sl : np; j < np; j += (uint32_t)S) {
+            const float4 v0 = pool[q[2 * j]];
+            const float4 v1 = (2 * j + 1 < r.ns) ? pool[q[2 * j + 1]]
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 A = make_float4(v0.x, v1.x, v0.y, v1.y);
+            const float4 B = make_float4(v0.z, v1.z, v0.w, v1.w);
+            GRAV_PAIR(A, B);
+            if (++inblk == KB) {
+                kahan_add2(sx, cx, bx, m1);
+                kahan_add2(sy, cy, by, m1);
+                kahan_add2(sz, cz, bz, m1);
+                kahan_add2(sp, cp, bp, m1);
+                bx = by = bz = bp = make_float2(0.f, 0.f);
+                inblk = 0;
+            }
+        }
+        kahan_add2(sx, cx, bx, m1);
+        kahan_add2(sy, cy, by, m1);
+        kahan_add2(sz, cz, bz, m1);
+        kahan_add2(sp, cp, bp, m1);
+        comp_add(sx.x, cx.x, sx.y, cx.y);
+        comp_add(sy.x, cy.x, sy.y, cy.y);
+        comp_add(sz.x, cz.x, sz.y, cz.y);
+        comp_add(sp.x, cp.x, sp.y, cp.y);
+        sm.red[wib][lane][0] = make_float4(sx.x, sy.x, sz.x, sp.x);
+        sm.red[wib][lane][1] = make_float4(cx.x, cy.x, cz.x, cp.x);
+        __syncwarp();
+        if (sl == 0) {
+            float4 vs = sm.red[wib][t][0], vc = sm.red[wib][t][1];
+            for (int s2 = 1; s2 < S; ++s2) {
+                const int l = s2 * T + t;
+                const float4 ws = sm.red[wib][l][0], wc = sm.red[wib][l][1];
+                comp_add(vs.x, vc.x, ws.x, wc.x);
+                comp_add(vs.y, vc.y, ws.y, wc.y);
+                comp_add(vs.z, vc.z, ws.z, wc.z);
+                comp_add(vs.w, vc.w, ws.w, wc.w);
+            }
+            const uint64_t e = r.tgt_off + u.t0 + t;
+            const uint32_t pos = a.perm_t[e];
+            const uint64_t row = r.row_off + pos;
+            a.res[2 * row] = vs;
+            a.res[2 * row + 1] = vc;
+        }
+        __syncwarp();
+    }
+}
+
+// out[off + k] = in[off + perm[off + k]] within each task's source list
+// (the slots of a list in ascending-slot order); one warp per task.
+__global__ void k_sorted_slots(const TaskRec *tasks, uint64_t n, const uint32_t *in,
+                               const uint32_t *perm, uint32_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t t = warp; t < n; t += nw) {
+        const TaskRec r = tasks[t];
+        for (uint32_t k = lane; k < r.ns; k += 32)
+            out[r.src_off + k] = in[r.src_off + perm[r.src_off + k]];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // interaction: Lennard-Jones cell pairs
 // ---------------------------------------------------------------------------
 
@@ -1469,4 +1575,135 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out, float ms
     GC_CUDA_TRY(cudaStreamSynchronize(c.s));
     if (best_out) *best_out = choice;
     return GC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reuse ablation (Section 3.2, Fig. 3): ways of feeding the sources
+// ---------------------------------------------------------------------------
+
+extern "C" int gc_reuse_ablation(gc_pool_t *p, int reps, double out[7])
+{
+    if (!p || !out || reps < 1) return GC_ERR_ARG;
+    if (p->last < 0 || !p->ctx[p->last].valid) return GC_ERR_NOT_READY;
+    FlushCtx &c = p->ctx[p->last];
+    GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
+    if (c.n_waves != 1 || c.waves.size() != 1) return GC_ERR_STATE;
+    const WaveRange &wv = c.waves[0];
+    if (wv.w1 <= wv.w0 || wv.l1 > wv.l0) return GC_ERR_STATE;   // gravity only
+    const uint64_t T = c.n_tasks, NS = c.n_src;
+    const int maxb = p->num_sms * 16;
+    DBuf seq_list, seq_sorted;
+    int rc = GC_OK;
+    if ((rc = seq_list.reserve((NS + 1) * 4)) != GC_OK ||
+        (rc = seq_sorted.reserve((NS + 1) * 4)) != GC_OK) {
+        seq_list.release();
+        return rc;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const uint32_t saved_sched = p->wu_schedule;
+    p->wu_schedule = GC_SCHED_FIFO;
+    auto timed = [&](auto &&launch, double *ms_out) {
+        float best = 1e30f;
+        for (int r = 0; r < reps && rc == GC_OK; ++r) {
+            GC_CUDA_TRY(cudaEventRecord(e0, c.s));
+            rc = launch();
+            GC_CUDA_TRY(cudaEventRecord(e1, c.s));
+            if (rc != GC_OK) break;
+            GC_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) best = ms;
+        }
+        *ms_out = best;
+        return rc;
+    };
+    // the three device modes share the work units of the batch
+    InterArgs a;
+    fill_inter_args(p, c, 0, 0, 0, a);
+    a.wu = c.wu.as<GravWU>() + wv.w0;
+    a.n_wu = wv.w1 - wv.w0;
+    a.lj_list = nullptr;
+    a.n_lj = 0;
+    const int full = gc_grav_blocks(p);
+    const unsigned g = (unsigned)std::min<uint64_t>((a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS,
+                                                     (uint64_t)full);
+    // entry slots in list order (the address buffer) and sorted per list
+    GC_TRY(gc_entry_slots(p, c.s, c.src_ids.as<uint32_t>(), NS, seq_list.as<uint32_t>()));
+    k_sorted_slots<<<grid_for(T * 32, 256, maxb), 256, 0, c.s>>>(
+        c.tasks.as<TaskRec>(), T, seq_list.as<uint32_t>(), c.src_perm.as<uint32_t>(),
+        seq_sorted.as<uint32_t>());
+    auto indirect = [&](const uint32_t *seq) {
+        return [&, seq]() -> int {
+            GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
+            k_gravity_indirect<<<g, GRAV_THREADS, 0, c.s>>>(a, seq, p->d_pool);
+            GC_CUDA_TRY(cudaGetLastError());
+            return GC_OK;
+        };
+    };
+    timed([&]() { return gc_interact_range(p, c, wv.w0, wv.w1, 0, 0, 0, 0, 0); }, &out[0]);
+    if (rc == GC_OK) timed(indirect(seq_list.as<uint32_t>()), &out[1]);
+    if (rc == GC_OK) timed(indirect(seq_sorted.as<uint32_t>()), &out[2]);
+    // the batch's rows end as the sorted-indirect run left them (same values
+    // up to summation order)
+    // redundant transfer: every list's sources gathered on the host from the
+    // authoritative mirror into contiguous staging, then copied to the device
+    if (rc == GC_OK) {
+        std::vector<uint32_t> ids(NS);
+        std::vector<TaskRec> h(T);
+        if (cudaMemcpy(ids.data(), c.src_ids.p, NS * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(h.data(), c.tasks.p, T * sizeof(TaskRec), cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+            rc = GC_ERR_CUDA;
+        const uint64_t slots = NS + T;   // paired layout, one pad per task
+        float4 *hst = nullptr;
+        if (rc == GC_OK && cudaHostAlloc((void **)&hst, slots * sizeof(float4),
+                                         cudaHostAllocDefault) != cudaSuccess)
+            rc = GC_ERR_OOM;
+        if (rc == GC_OK) {
+            double best_g = 1e30, best_c = 1e30;
+            for (int r = 0; r < reps && rc == GC_OK; ++r) {
+                struct timespec t0, t1;
+                clock_gettime(CLOCK_MONOTONIC, &t0);
+                for (uint64_t t = 0; t < T; ++t) {
+                    const TaskRec &tr = h[t];
+                    float *f = reinterpret_cast<float *>(hst + tr.src_off + t);
+                    for (uint32_t k = 0; k < tr.ns; ++k) {
+                        const float4 v = p->h_mirror[ids[tr.src_off + k]];
+                        float *d = f + 8 * (k >> 1);
+                        const uint32_t hh = k & 1u;
+                        d[hh] = v.x; d[2 + hh] = v.y; d[4 + hh] = v.z; d[6 + hh] = v.w;
+                    }
+                    if (tr.ns & 1u) {
+                        float *d = f + 8 * (tr.ns >> 1);
+                        d[1] = d[3] = d[5] = d[7] = 0.f;
+                    }
+                }
+                clock_gettime(CLOCK_MONOTONIC, &t1);
+                const double gms = (t1.tv_sec - t0.tv_sec) * 1e3 + (t1.tv_nsec - t0.tv_nsec) * 1e-6;
+                if (gms < best_g) best_g = gms;
+                cudaEventRecord(e0, c.s);
+                if (cudaMemcpyAsync(c.stg_src.p, hst, slots * sizeof(float4),
+                                    cudaMemcpyHostToDevice, c.s) != cudaSuccess)
+                    rc = GC_ERR_CUDA;
+                cudaEventRecord(e1, c.s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = GC_ERR_CUDA;
+                float cms = 0.f;
+                cudaEventElapsedTime(&cms, e0, e1);
+                if (cms < best_c) best_c = cms;
+            }
+            out[3] = best_g;
+            out[4] = best_c;
+            out[5] = (double)slots * sizeof(float4);
+        }
+        if (hst) cudaFreeHost(hst);
+    }
+    out[6] = (double)p->stats.last_misses * sizeof(float4);
+    p->wu_schedule = saved_sched;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    seq_list.release();
+    seq_sorted.release();
+    return rc;
 }

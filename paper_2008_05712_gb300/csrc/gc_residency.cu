@@ -149,7 +149,7 @@ __global__ void k_compact_write(CompactArgs a, const uint32_t *tile_off, uint32_
 constexpr int MARK_HASH = 2048;
 
 __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, uint64_t ns,
-                       uint64_t id_cap, const uint8_t *known, uint32_t *ref_epoch,
+                       uint64_t id_cap, uint32_t *ref_epoch,
                        uint32_t *ref_count, uint32_t epoch, unsigned long long *ctr,
                        uint64_t chunk)
 {
@@ -166,11 +166,16 @@ __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, ui
     bool bad = false;
     for (uint64_t e = b0 + threadIdx.x; e < b1; e += blockDim.x) {
         const uint32_t id = e < nt ? tgt[e] : src[e - nt];
-        if ((uint64_t)id >= id_cap || !known[id]) {
+        if ((uint64_t)id >= id_cap) {
             bad = true;
             continue;
         }
-        if (ref_epoch[id] != epoch) ref_epoch[id] = epoch;
+        const uint32_t e0 = ref_epoch[id];   // one word: uploaded? referenced this wave?
+        if (e0 == GC_EPOCH_UNKNOWN) {
+            bad = true;
+            continue;
+        }
+        if (e0 != epoch) ref_epoch[id] = epoch;
         uint32_t h = (id * 2654435761u) & (MARK_HASH - 1);
         bool done = false;
         for (int probe = 0; probe < 8; ++probe) {
@@ -284,7 +289,7 @@ __global__ void k_entry_slots(const uint32_t *ids, uint64_t n, const uint32_t *s
 __global__ void k_upload(const uint32_t *ids, uint32_t id_base, const float4 *vals, uint64_t n,
                          uint64_t id_cap,
                          const uint32_t *slot_of_id, float4 *pool, float4 *mirror,
-                         uint8_t *known, int write_mirror, unsigned long long *ctr)
+                         uint32_t *ref_epoch, int write_mirror, unsigned long long *ctr)
 {
     __shared__ unsigned int upd;
     if (threadIdx.x == 0) upd = 0;
@@ -297,7 +302,7 @@ __global__ void k_upload(const uint32_t *ids, uint32_t id_base, const float4 *va
             continue;
         }
         float4 v = vals[i];
-        known[id] = 1;
+        if (ref_epoch[id] == GC_EPOCH_UNKNOWN) ref_epoch[id] = 0;   // known, never referenced
         uint32_t s = slot_of_id[id];
         if (s != GC_NONE) {
             pool[s] = v;
@@ -359,7 +364,7 @@ int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64
     ++p->stats.kernel_launches;
     k_upload<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
         ids, 0, vals, n, p->cfg.id_capacity, p->d_slot_of_id, p->d_pool, p->d_mirror,
-        p->d_known, write_mirror, p->d_ctr);
+        p->d_ref_epoch, write_mirror, p->d_ctr);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
@@ -372,7 +377,7 @@ int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint6
     ++p->stats.kernel_launches;
     k_upload<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
         nullptr, id_base, vals, n, p->cfg.id_capacity, p->d_slot_of_id, p->d_pool,
-        p->d_mirror, p->d_known, 1, p->d_ctr);
+        p->d_mirror, p->d_ref_epoch, 1, p->d_ctr);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
@@ -384,7 +389,7 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
     const uint64_t n = nt + ns;
     unsigned long long *ctr = p->d_ctr;
     p->epoch += 1;
-    if (p->epoch == 0) p->epoch = 1;   // 0 marks "never referenced"
+    if (p->epoch == 0 || p->epoch == GC_EPOCH_UNKNOWN) p->epoch = 1;   // reserved values
     const int maxb = p->num_sms * 16;
 
     GC_CUDA_TRY(cudaMemsetAsync(ctr + CTR_UNIQUE, 0,
@@ -393,7 +398,7 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         const uint64_t chunk = 8192;
         ++p->stats.kernel_launches;
         k_mark<<<(unsigned)((n + chunk - 1) / chunk), 512, 0, p->s>>>(
-            tgt, nt, src, ns, id_cap, p->d_known, p->d_ref_epoch, p->d_ref_count, p->epoch, ctr,
+            tgt, nt, src, ns, id_cap, p->d_ref_epoch, p->d_ref_count, p->epoch, ctr,
             chunk);
     }
     uint64_t ubound = n < id_cap ? n : id_cap;

@@ -156,6 +156,7 @@ _SIGS = {
     "gc_graph_rows": [P, U64P],
     "gc_graph_results": [P, U64, U64, P],
     "gc_graph_destroy": [P],
+    "gc_reuse_ablation": [P, C.c_int, P],
 }
 
 _RESTYPES = {"gc_strerror": C.c_char_p, "gc_combine_size_from_occupancy": C.c_uint64}
@@ -430,6 +431,15 @@ class Pool:
             with open(cache, "w") as f:
                 json.dump(data, f, indent=1, sort_keys=True)
         return choice, times
+
+    def reuse_ablation(self, reps=3):
+        """Fig. 3 of Section 3.2 on the last batch (gc_reuse_ablation)."""
+        out = np.zeros(7, np.float64)
+        _check(self.lib.gc_reuse_ablation(self.h, int(reps), _p(out)), "gc_reuse_ablation")
+        keys = ["kernel_pack_ms", "kernel_indirect_ms", "kernel_sorted_indirect_ms",
+                "redundant_host_gather_ms", "redundant_h2d_ms", "redundant_bytes",
+                "reuse_fetch_bytes"]
+        return dict(zip(keys, out.tolist()))
 
     def max_combine_size(self):
         v = C.c_uint64()
