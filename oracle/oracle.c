@@ -654,3 +654,27 @@ void orc_reduce(int64_t n, const uint32_t *ids, const double *contrib, double *t
         for (int c = 0; c < 4; ++c)
             totals[4 * (size_t)ids[k] + c] += contrib[4 * k + c];
 }
+
+/* ------------------------------------------------------------------------ */
+/* Time integration (the step around the force computation, Section 4.1)    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Leapfrog with staggered velocities, one step of length dt:
+ *   v' = v + a dt        (kick, a = acceleration at the current positions)
+ *   x' = x + v' dt       (drift)
+ * State in float32 (x, y, z, m and vx, vy, vz, 0 per particle), arithmetic
+ * in FP64, each new value rounded once to float32: v' = fl(v + a*dt),
+ * x' = fl(x + v'*dt) with v' the rounded velocity.  Masses unchanged.
+ */
+void orc_kick_drift(int64_t n, const double *acc, float *xyzm, float *vel, double dt)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        for (int c = 0; c < 3; ++c) {
+            double v = (double)vel[4 * i + c] + acc[4 * i + c] * dt;
+            float vf = (float)v;
+            vel[4 * i + c] = vf;
+            xyzm[4 * i + c] = (float)((double)xyzm[4 * i + c] + (double)vf * dt);
+        }
+    }
+}

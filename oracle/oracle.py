@@ -72,6 +72,8 @@ def _declare(L):
     L.orc_pack_perm_batch.restype = None
     L.orc_reduce.argtypes = [I64, P, P, P]
     L.orc_reduce.restype = None
+    L.orc_kick_drift.argtypes = [I64, P, P, P, C.c_double]
+    L.orc_kick_drift.restype = None
 
 
 def _p(a: np.ndarray):
@@ -280,3 +282,12 @@ def reduce(ids, contrib, id_cap):
     tot = np.zeros((id_cap, 4), np.float64)
     lib().orc_reduce(i.shape[0], _p(i), _p(c), _p(tot))
     return tot
+
+
+def kick_drift(acc, xyzm, vel, dt):
+    """One leapfrog step (kick then drift); returns new (xyzm, vel)."""
+    a = _c(acc, np.float64)
+    x = np.array(xyzm, dtype=np.float32, copy=True, order="C")
+    v = np.array(vel, dtype=np.float32, copy=True, order="C")
+    lib().orc_kick_drift(x.shape[0], _p(a), _p(x), _p(v), float(dt))
+    return x, v
