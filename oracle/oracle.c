@@ -462,6 +462,34 @@ int orc_md_tasks(int64_t m, uint32_t *cell_a, uint32_t *cell_b, int8_t *d3,
     return (int)t;
 }
 
+/* The planar case (the paper's MD is two-dimensional, Section 4.2): a
+ * periodic m x m cell grid, c = x + m y; for every cell, the self task, then
+ * one task per offset (dx, dy) in {-1,0,1}^2 lexicographically greater than
+ * (0,0) with dx most significant (4 offsets); the z offset is 0. */
+int orc_md_tasks_2d(int64_t m, uint32_t *cell_a, uint32_t *cell_b, int8_t *d3,
+                    uint8_t *is_self)
+{
+    int64_t t = 0;
+    for (int64_t c = 0; c < m * m; ++c) {
+        int64_t x = c % m, y = c / m;
+        cell_a[t] = (uint32_t)c; cell_b[t] = (uint32_t)c;
+        d3[3 * t] = 0; d3[3 * t + 1] = 0; d3[3 * t + 2] = 0; is_self[t] = 1;
+        ++t;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy) {
+                int later = (dx > 0) || (dx == 0 && dy > 0);
+                if (!later) continue;
+                int64_t bx = (x + dx + m) % m, by = (y + dy + m) % m;
+                cell_a[t] = (uint32_t)c;
+                cell_b[t] = (uint32_t)(bx + m * by);
+                d3[3 * t] = (int8_t)dx; d3[3 * t + 1] = (int8_t)dy; d3[3 * t + 2] = 0;
+                is_self[t] = 0;
+                ++t;
+            }
+    }
+    return (int)t;
+}
+
 /*
  * Lennard-Jones forces of one cell-pair task.  Atoms carry local offsets u
  * (table: 4 floats per id, u exact multiples of 2^-21); atom j of cell B

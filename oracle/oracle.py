@@ -63,6 +63,7 @@ def _declare(L):
     L.orc_gravity_batch.restype = None
     L.orc_md_cells.argtypes = [I64, P, I64, P, P]
     L.orc_md_tasks.argtypes = [I64, P, P, P, P]
+    L.orc_md_tasks_2d.argtypes = [I64, P, P, P, P]
     L.orc_lj.argtypes = [P, I64, P, I64, P, C.c_int, P, I64, C.c_double, C.c_double,
                          I64, P, P]
     L.orc_residency.argtypes = [I64, I64, P, P, P, C.c_uint32, I64, P, P, P, P, P, P, P]
@@ -213,6 +214,17 @@ def md_tasks(m):
     d = np.empty((nt, 3), np.int8)
     s = np.empty(nt, np.uint8)
     k = lib().orc_md_tasks(m, _p(a), _p(b), _p(d), _p(s))
+    assert k == nt, k
+    return a, b, d, s
+
+
+def md_tasks_2d(m):
+    nt = 5 * m ** 2
+    a = np.empty(nt, np.uint32)
+    b = np.empty(nt, np.uint32)
+    d = np.empty((nt, 3), np.int8)
+    s = np.empty(nt, np.uint8)
+    k = lib().orc_md_tasks_2d(m, _p(a), _p(b), _p(d), _p(s))
     assert k == nt, k
     return a, b, d, s
 

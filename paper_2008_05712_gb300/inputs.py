@@ -143,6 +143,32 @@ def fcc_lj(cells_per_axis: int, seed: int, density: float = 0.8442,
     return MDSystem(cell, U.astype(np.int64), E, ncell)
 
 
+def lj_2d(cells_per_axis: int, seed: int, density: float = 0.7, jitter: float = 0.05,
+          ncell: int = 16) -> MDSystem:
+    """Planar Lennard-Jones system: a jittered square lattice of
+    cells_per_axis^2 atoms at number density ``density`` (per unit area) in a
+    periodic square of ``ncell`` x ``ncell`` cells, in the fixed-point cell
+    format of MDSystem with z = 0 (cell index cx + ncell * cy)."""
+    lat = (1.0 / density) ** 0.5
+    box0 = cells_per_axis * lat
+    E = int(round(box0 / ncell * MD_SCALE))
+    box_units = ncell * E
+    lat_units = box_units / cells_per_axis
+    idx = np.arange(cells_per_axis)
+    gx, gy = np.meshgrid(idx, idx, indexing="ij")
+    pos = np.stack([gx.ravel(), gy.ravel()], axis=1).astype(np.float64) + 0.5
+    g = rng(seed)
+    pos_units = pos * lat_units + g.normal(0.0, jitter, pos.shape) * MD_SCALE
+    X2 = np.mod(np.rint(pos_units).astype(np.int64), box_units)
+    X = np.zeros((X2.shape[0], 3), np.int64)
+    X[:, :2] = X2
+    C = X // E
+    C[:, 2] = 0
+    U = X - C * E
+    cell = (C[:, 0] + ncell * C[:, 1]).astype(np.uint32)
+    return MDSystem(cell, U.astype(np.int64), E, ncell)
+
+
 def md_displace(sys: MDSystem, seed: int, sigma: float) -> MDSystem:
     """Move every atom by N(0, sigma) per axis, re-wrapped into the box."""
     g = rng(seed)
