@@ -170,10 +170,11 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_sample(x, n_tasks, seed, budget_s=None):
+def oracle_sample(x, n_tasks, seed, budget_s=None, keep=None):
     """Oracle (plain FP64 C, one thread) on a seeded sample of this step's
     tasks: tree build, interaction-list walk and gravity of the sampled
-    buckets.  Returns (interactions, seconds of per-task work, n_tasks)."""
+    buckets.  Returns (interactions, seconds of per-task work, n_tasks); with
+    keep a dict, also stores the sampled buckets and their FP64 rows there."""
     from oracle import oracle as O
     tr = O.Tree(x, bucket_max=BUCKET)
     g = inputs.rng(seed)
@@ -182,10 +183,29 @@ def oracle_sample(x, n_tasks, seed, budget_s=None):
     off, ids = tr.lists(THETA[0], THETA[1], buckets=pick)
     to, tg = tr.bucket_targets(pick)
     tab = np.concatenate([x, tr.node_table()])
-    O.gravity_batch(tab, to, tg, off, ids, EPS2)
+    rows = O.gravity_batch(tab, to, tg, off, ids, EPS2)
     dt = time.perf_counter() - t0
     inter = int(np.sum(np.diff(to.astype(np.int64)) * np.diff(off.astype(np.int64))))
+    if keep is not None:
+        keep.update(buckets=pick, tgt_off=to, tgt=tg, rows=rows, n_buckets=tr.n_buckets)
     return inter, dt, len(pick)
+
+
+def error_stats(got_rows, ref_rows, off):
+    """Per-result relative L2 force errors e_r (first 3 components of each
+    task's rows): max, p99, median and the number of results."""
+    errs = []
+    for t in range(len(off) - 1):
+        a, b = int(off[t]), int(off[t + 1])
+        if b == a:
+            continue
+        ref = ref_rows[a:b, :3]
+        nr = np.linalg.norm(ref)
+        d = np.linalg.norm(got_rows[a:b, :3] - ref)
+        errs.append(d / nr if nr > 1e-30 else (0.0 if d == 0 else np.inf))
+    e = np.array(errs)
+    return {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+            "median": float(np.median(e)), "results": int(e.shape[0]), "tolerance": 1e-5}
 
 
 def _oracle_worker(x, buckets, barrier):
@@ -255,7 +275,83 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3):
+MD_WORKLOAD = ("lj_fcc_1M: 1,048,576 Lennard-Jones atoms, jittered FCC at density 0.8442, "
+               "cutoff 2.5 sigma, 42^3 periodic cells, 1,037,232 cell-pair tasks")
+RC2 = 6.25
+
+
+def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True):
+    """The MD workload (Section 4.2 on the 3-D FCC system): task build from
+    device-resident cell indices and one batched flush per step, timed with
+    events; candidate pairs per second; parity on a seeded task sample."""
+    sysm = inputs.fcc_lj(64, seed, ncell=42)
+    n, m = sysm.n, sysm.ncell
+    pool = gcharm.Pool(id_capacity=n, pool_capacity=n, eps2=EPS2, lj_rc2=RC2,
+                       md_edge=sysm.edge, stream=stream.cuda_stream)
+    pool.upload(np.arange(n, dtype=np.uint32), sysm.u)
+    cell = torch.from_numpy(sysm.cell.astype(np.int32)).cuda()
+
+    def step():
+        pool.reset_totals()
+        pool.build_md(cell, m)
+        pool.flush()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    s0 = pool.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    pool.join(stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    s1 = pool.stats()
+    pairs = (s1["interactions"] - s0["interactions"]) / reps
+    nb = s1["timed_batches"] - s0["timed_batches"]
+    stage = {k: (s1["stage_ms_sum"][k] - s0["stage_ms_sum"][k]) / max(nb, 1)
+             for k in s1["stage_ms_sum"]}
+    out = {"workload": MD_WORKLOAD, "ms_per_step": ms, "candidate_pairs_per_step": int(pairs),
+           "value": pairs / (ms / 1e3), "unit": "candidate pairs/s",
+           "pairs_in_cutoff": s1["lj_pairs_in_cutoff"], "stage_ms_avg": stage,
+           "tasks_per_step": int((s1["tasks"] - s0["tasks"]) / reps)}
+    if with_oracle:
+        from oracle import oracle as O
+        start, atoms = O.md_cells(sysm.cell, m ** 3)
+        ta, tb, td, ts = O.md_tasks(m)
+        cnt = (start[1:] - start[:-1]).astype(np.int64)
+        roff = np.concatenate([[0], np.cumsum(cnt[ta] + np.where(ts != 0, 0, cnt[tb]))])
+        rows = gcharm.value(pool.results())
+        pick = np.sort(inputs.rng(seed + 1).choice(len(ta), 2000, replace=False))
+        got, ref, off = [], [], [0]
+        t0 = time.perf_counter()
+        cand = 0
+        for k in pick:
+            A = atoms[start[ta[k]]:start[ta[k] + 1]]
+            B = atoms[start[tb[k]]:start[tb[k] + 1]]
+            fa, fb = O.lj(sysm.u, A, None if ts[k] else B, bool(ts[k]), td[k], sysm.E,
+                          rc2_grid=int(RC2 * (1 << 42)))
+            r = fa if ts[k] else np.concatenate([fa, fb])
+            cand += len(A) * (len(A) - 1) // 2 if ts[k] else len(A) * len(B)
+            ref.append(r)
+            got.append(rows[roff[k]:roff[k + 1]])
+            off.append(off[-1] + len(r))
+        dt = time.perf_counter() - t0
+        out["parity_on_sample"] = error_stats(np.concatenate(got), np.concatenate(ref),
+                                              np.array(off))
+        out["cpu_baseline"] = {"value": cand / dt, "unit": "candidate pairs/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "2000 seeded-random cell-pair tasks of the step "
+                                         "(FP64 LJ, one thread; includes Python call overhead "
+                                         "per task)"}
+    pool.close()
+    return out
+
+
+def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=True):
     """The 200k-task uneven batch (device-resident task arrays, timed with
     events) and the serving loop at three arrival rates (host task arrays,
     host clock, latency from each task's scheduled arrival)."""
@@ -316,6 +412,21 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3):
               "tuning": {"wu_max_targets": tuning["wu_max_targets"],
                          "schedule": "lpt" if tuning["schedule"] else "fifo",
                          "autotune_ms": tune_ms or tuning.get("times_ms")}}
+    if with_oracle:
+        # parity on 300 seeded tasks of the batch against the FP64 oracle
+        from oracle import oracle as O
+        rows = pool.results()
+        pick = np.sort(inputs.rng(seed + 7).choice(C4_TASKS, 300, replace=False))
+        nt_i = (to[1:] - to[:-1]).astype(np.int64)
+        ns_i = (so[1:] - so[:-1]).astype(np.int64)
+        sto = np.concatenate([[0], np.cumsum(nt_i[pick])]).astype(np.uint64)
+        sso = np.concatenate([[0], np.cumsum(ns_i[pick])]).astype(np.uint64)
+        stg = np.concatenate([tg[to[t]:to[t + 1]] for t in pick])
+        ssr = np.concatenate([sr[so[t]:so[t + 1]] for t in pick])
+        ref = O.gravity_batch(x, sto, stg, sso, ssr, EPS2)
+        got = np.concatenate([gcharm.value(rows[to[t]:to[t + 1]]) for t in pick])
+        uneven["parity_on_sample"] = error_stats(got, ref, sto)
+
     # the persistent + graph form: the batch captured once, then replayed
     pool.submit_csr_device(dk, dto, dtg, dso, dsr, tg.shape[0], sr.shape[0])
     graph = gcharm.Graph(pool)
@@ -372,6 +483,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-task", action="store_true")
     ap.add_argument("--n", type=int, default=N_PART)
+    ap.add_argument("--no-md", action="store_true", help="skip the MD measurement")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the uneven-batch and serving measurements")
     args = ap.parse_args()
@@ -542,20 +654,25 @@ def main():
             "speedup_flush": tp["total"] / tb["total"],
         }
 
-    uneven = serving = None
-    if rank == 0 and not args.no_serve:
-        pool.close()
-        del X
-        torch.cuda.empty_cache()
-        uneven, serving = uneven_and_serving(gcharm, torch, inputs.SEED_BASE + 4, stream)
-
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        ci, ct, cn = oracle_sample(xs[W], 60000, 77)
+        keep = {}
+        ci, ct, cn = oracle_sample(xs[W], 60000, 77, keep=keep)
         cpu = {"value": ci / ct, "unit": "interactions/s", "cores": 1, "kind": "oracle",
                "sample": f"{cn} seeded-random buckets of the first timed step "
                          f"({ci} interactions): oracle walk + FP64 gravity, one thread; "
                          "tree build untimed"}
+        # parity of the same sample: the step on these positions through the
+        # engine, rows of the sampled buckets against the oracle's FP64 rows
+        pool.upload(ids_np, xs[W])
+        pool.reset_totals()
+        pool.build_nbody(xs[W], BUCKET, *THETA)
+        pool.flush()
+        counts = pool.nbody_bucket_counts(keep["n_buckets"])
+        boff = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
+        rows_gpu = gcharm.value(pool.results())
+        got = np.concatenate([rows_gpu[boff[b]:boff[b + 1]] for b in keep["buckets"]])
+        cpu["parity_on_sample"] = error_stats(got, keep["rows"], keep["tgt_off"])
         cores = os.cpu_count() or 1
         if cores > 1:
             ai, at, an = oracle_all_cores(xs[W], cores)
@@ -564,6 +681,18 @@ def main():
                                 "sample": f"all {an} buckets of the first timed step "
                                           f"({ai} interactions), one spawned process per "
                                           "core on interleaved buckets; tree build untimed"}
+
+    md = None
+    if rank == 0 and not args.no_md:
+        md = md_section(gcharm, torch, inputs.SEED_BASE + 3, stream,
+                        with_oracle=not args.no_cpu_baseline)
+    uneven = serving = None
+    if rank == 0 and not args.no_serve:
+        pool.close()
+        del X
+        torch.cuda.empty_cache()
+        uneven, serving = uneven_and_serving(gcharm, torch, inputs.SEED_BASE + 4, stream,
+                                             with_oracle=not args.no_cpu_baseline)
 
     if rank == 0:
         line = {
@@ -588,6 +717,7 @@ def main():
             "primitive_calls": prims,
             "per_task_launch": per_task,
             "reuse_ablation": ablation,
+            "md": md,
             "uneven_batch": uneven,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -296,6 +296,19 @@ int gc_build_nbody_tasks(gc_pool_t *pool, const float *xyzm_dev, uint64_t n,
                          int bucket_max, int theta_num, int theta_den,
                          uint64_t task_id_base, uint64_t info_out[4]);
 
+/* One time step around the force computation (Section 4.1): for particles
+ * i = 0..n-1, leapfrog kick then drift,
+ *   v' = fl32(v + a dt),  x' = fl32(x + v' dt)   (FP64 arithmetic),
+ * with a = acc_dev[4i .. 4i+2] (device FP64, 32-byte aligned; e.g. the
+ * pool's per-id totals, gc_totals_device, after the step's flush), state
+ * xyzm_dev (x, y, z, m) and vel_dev (vx, vy, vz, unused), device float4
+ * arrays updated in place; the new positions are then written into the pool
+ * for ids 0..n-1 (in place where resident).  Stream-ordered after every
+ * batch in flight; no host wait.  Errors: GC_ERR_ARG (null or misaligned
+ * pointers, n > id_capacity), GC_ERR_CUDA. */
+int gc_nbody_kick_drift(gc_pool_t *pool, const double *acc_dev, float *xyzm_dev, float *vel_dev,
+                        uint64_t n, double dt);
+
 /* Copy the last N-body tree: sorted ids (n) and keys (n); per node (nn):
  * level, cell[3], first, count, leaf, subtree size; per bucket (nb): first,
  * count, leaf node; and the list CSR (nb+1 offsets, entries).  Any pointer
@@ -318,7 +331,16 @@ int gc_read_nbody_tree(gc_pool_t *pool, uint32_t *sorted_ids, uint64_t *sorted_k
 int gc_build_md_tasks(gc_pool_t *pool, const uint32_t *cell_dev, uint64_t n, int m,
                       uint64_t task_id_base, uint64_t info_out[4]);
 
-/* Copy the last MD cell grouping: cell_start (m^3 + 1), cell_atoms (n). */
+/* The planar case of gc_build_md_tasks (the paper's MD is two-dimensional,
+ * Section 4.2): cell_dev[i] = cx + m*cy on a periodic m x m grid (atoms'
+ * z offsets 0), m >= 3; per cell in ascending index the self task, then one
+ * task per neighbour offset (dx, dy) in {(0,1), (1,-1), (1,0), (1,1)}; the
+ * same results and errors as gc_build_md_tasks. */
+int gc_build_md_tasks_2d(gc_pool_t *pool, const uint32_t *cell_dev, uint64_t n, int m,
+                         uint64_t task_id_base, uint64_t info_out[4]);
+
+/* Copy the last MD cell grouping: cell_start (m^3 + 1, or m^2 + 1 for the
+ * planar case), cell_atoms (n). */
 int gc_read_md_cells(gc_pool_t *pool, uint32_t *cell_start, uint32_t *cell_atoms);
 
 /* ---- single-task launches (the one-launch-per-task baseline) ----------- */

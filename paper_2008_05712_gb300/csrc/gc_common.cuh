@@ -92,6 +92,7 @@ struct NBodyState {
 struct MDState {
     uint64_t n = 0;
     int m = 0;
+    int dim = 3;
     DBuf keys, keys2, ids, ids2, cell_start, cnt_t, cnt_s, cub_tmp, hostcopy;
 };
 

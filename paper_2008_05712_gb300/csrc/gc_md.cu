@@ -17,6 +17,11 @@ namespace {
 __constant__ int8_t c_half_shell[13][3] = {
     {0, 0, 1},  {0, 1, -1},  {0, 1, 0},  {0, 1, 1},  {1, -1, -1}, {1, -1, 0}, {1, -1, 1},
     {1, 0, -1}, {1, 0, 0},   {1, 0, 1},  {1, 1, -1}, {1, 1, 0},   {1, 1, 1}};
+// the planar grid (the paper's two-dimensional MD): slots 1..4
+__constant__ int8_t c_half_ring[4][3] = {{0, 1, 0}, {1, -1, 0}, {1, 0, 0}, {1, 1, 0}};
+
+// tasks per cell: self + half of the 3^dim - 1 neighbours
+__host__ __device__ constexpr int tasks_per_cell(int dim) { return dim == 2 ? 5 : 14; }
 
 __global__ void k_cell_keys(const uint32_t *cell, uint64_t n, uint32_t n_cells, uint32_t *keys,
                             uint32_t *ids, unsigned long long *ctr)
@@ -45,16 +50,25 @@ __global__ void k_cell_start(const uint32_t *keys, uint64_t n, uint32_t n_cells,
     }
 }
 
-__device__ __forceinline__ void task_cells(uint64_t t, int m, uint32_t &ca, uint32_t &cb,
-                                           int8_t d[3], bool &self)
+__device__ __forceinline__ void task_cells(uint64_t t, int m, int dim, uint32_t &ca,
+                                           uint32_t &cb, int8_t d[3], bool &self)
 {
-    uint64_t c = t / 14;
-    int o = (int)(t % 14);
+    const int per = tasks_per_cell(dim);
+    uint64_t c = t / per;
+    int o = (int)(t % per);
     ca = (uint32_t)c;
     self = (o == 0);
     if (self) {
         cb = ca;
         d[0] = d[1] = d[2] = 0;
+        return;
+    }
+    if (dim == 2) {
+        int x = (int)(c % m), y = (int)(c / m);
+        d[0] = c_half_ring[o - 1][0];
+        d[1] = c_half_ring[o - 1][1];
+        d[2] = 0;
+        cb = (uint32_t)((x + d[0] + m) % m + m * ((y + d[1] + m) % m));
         return;
     }
     int x = (int)(c % m), y = (int)((c / m) % m), z = (int)(c / ((uint64_t)m * m));
@@ -65,7 +79,7 @@ __device__ __forceinline__ void task_cells(uint64_t t, int m, uint32_t &ca, uint
     cb = (uint32_t)(bx + m * (by + m * bz));
 }
 
-__global__ void k_md_counts(uint64_t nt, int m, const uint32_t *start, uint64_t *cnt_t,
+__global__ void k_md_counts(uint64_t nt, int m, int dim, const uint32_t *start, uint64_t *cnt_t,
                             uint64_t *cnt_s)
 {
     GRID_STRIDE(t, nt + 1) {
@@ -77,13 +91,14 @@ __global__ void k_md_counts(uint64_t nt, int m, const uint32_t *start, uint64_t 
         uint32_t ca, cb;
         int8_t d[3];
         bool self;
-        task_cells(t, m, ca, cb, d, self);
+        task_cells(t, m, dim, ca, cb, d, self);
         cnt_t[t] = start[ca + 1] - start[ca];
         cnt_s[t] = self ? 0 : (start[cb + 1] - start[cb]);
     }
 }
 
-__global__ void k_md_fill(uint64_t nt, int m, const uint32_t *start, const uint32_t *atoms,
+__global__ void k_md_fill(uint64_t nt, int m, int dim, const uint32_t *start,
+                          const uint32_t *atoms,
                           const uint64_t *off_t, const uint64_t *off_s, uint64_t tgt_base,
                           uint64_t src_base, uint64_t id_base, uint32_t *tgt, uint32_t *src,
                           TaskRec *recs)
@@ -92,7 +107,7 @@ __global__ void k_md_fill(uint64_t nt, int m, const uint32_t *start, const uint3
         uint32_t ca, cb;
         int8_t d[3];
         bool self;
-        task_cells(t, m, ca, cb, d, self);
+        task_cells(t, m, dim, ca, cb, d, self);
         uint32_t a0 = start[ca], a1 = start[ca + 1];
         uint32_t b0 = start[cb], b1 = self ? start[cb] : start[cb + 1];
         uint64_t ot = off_t[t], os = off_s[t];
@@ -116,10 +131,12 @@ __global__ void k_md_fill(uint64_t nt, int m, const uint32_t *start, const uint3
 
 }  // namespace
 
-extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m,
-                                 uint64_t task_id_base, uint64_t info_out[4])
+static int build_md(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m, int dim,
+                    uint64_t task_id_base, uint64_t info_out[4])
 {
-    if (!p || !cell_dev || n == 0 || n > 0x7FFFFFFFull || m < 3 || m > 1024) return GC_ERR_ARG;
+    if (!p || !cell_dev || n == 0 || n > 0x7FFFFFFFull || m < 3 ||
+        m > (dim == 2 ? 32768 : 1024))
+        return GC_ERR_ARG;
     if (n > p->cfg.id_capacity) return GC_ERR_POOL_FULL;
     MDState &S = p->md;
     int vrc = GC_OK;
@@ -127,8 +144,8 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
                                                 &vrc);
     if (vrc != GC_OK) return vrc;
     cudaStream_t s = p->s;
-    const uint32_t n_cells = (uint32_t)m * m * m;
-    const uint64_t nt = 14ull * n_cells;
+    const uint32_t n_cells = dim == 2 ? (uint32_t)m * m : (uint32_t)m * m * m;
+    const uint64_t nt = (uint64_t)tasks_per_cell(dim) * n_cells;
     const int maxb = p->num_sms * 16;
     GC_TRY(S.keys.reserve(n * 4));
     GC_TRY(S.keys2.reserve(n * 4));
@@ -152,7 +169,7 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
     uint64_t *ct = S.cnt_t.as<uint64_t>(), *ot = ct + (nt + 1);
     uint64_t *cs = S.cnt_s.as<uint64_t>(), *os = cs + (nt + 1);
     ++p->stats.kernel_launches;
-    k_md_counts<<<grid_for(nt + 1, 256, maxb), 256, 0, s>>>(nt, m, start, ct, cs);
+    k_md_counts<<<grid_for(nt + 1, 256, maxb), 256, 0, s>>>(nt, m, dim, start, ct, cs);
     ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, ct, ot, nt + 1, s));
     ++p->stats.primitive_calls;
@@ -170,7 +187,7 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
     GC_TRY(gc_reserve_batch(p, nt, tot_t, tot_s));
     ++p->stats.kernel_launches;
     k_md_fill<<<grid_for(nt, 256, maxb), 256, 0, s>>>(
-        nt, m, start, S.ids2.as<uint32_t>(), ot, os, p->nb_tgt, p->nb_src, task_id_base,
+        nt, m, dim, start, S.ids2.as<uint32_t>(), ot, os, p->nb_tgt, p->nb_src, task_id_base,
         p->tgt_ids.as<uint32_t>() + p->nb_tgt, p->src_ids.as<uint32_t>() + p->nb_src,
         p->tasks.as<TaskRec>() + p->nb_tasks);
     GC_CUDA_TRY(cudaGetLastError());
@@ -179,6 +196,7 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
     p->nb_src += tot_s;
     S.n = n;
     S.m = m;
+    S.dim = dim;
     if (info_out) {
         info_out[0] = nt;
         info_out[1] = tot_t;
@@ -188,12 +206,24 @@ extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_
     return GC_OK;
 }
 
+extern "C" int gc_build_md_tasks(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m,
+                                 uint64_t task_id_base, uint64_t info_out[4])
+{
+    return build_md(p, cell_dev, n, m, 3, task_id_base, info_out);
+}
+
+extern "C" int gc_build_md_tasks_2d(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m,
+                                    uint64_t task_id_base, uint64_t info_out[4])
+{
+    return build_md(p, cell_dev, n, m, 2, task_id_base, info_out);
+}
+
 extern "C" int gc_read_md_cells(gc_pool_t *p, uint32_t *cell_start, uint32_t *cell_atoms)
 {
     if (!p || p->md.n == 0) return GC_ERR_STATE;
     MDState &S = p->md;
     GC_CUDA_TRY(cudaStreamSynchronize(p->s));
-    uint64_t nc = (uint64_t)S.m * S.m * S.m;
+    uint64_t nc = S.dim == 2 ? (uint64_t)S.m * S.m : (uint64_t)S.m * S.m * S.m;
     if (cell_start)
         GC_CUDA_TRY(cudaMemcpy(cell_start, S.cell_start.p, (nc + 1) * 4, cudaMemcpyDeviceToHost));
     if (cell_atoms)

@@ -441,6 +441,24 @@ __global__ void k_nbody_tasks(const uint4 *bucket, uint64_t nb, const uint64_t *
     }
 }
 
+// One leapfrog step (kick then drift) per particle: v' = fl(v + a dt),
+// x' = fl(x + v' dt), FP64 arithmetic without contraction, float32 state.
+__global__ void k_kick_drift(const gcd4 *acc, float4 *x, float4 *v, uint64_t n, double dt)
+{
+    GRID_STRIDE(i, n) {
+        const gcd4 a = acc[i];
+        float4 xi = x[i], vi = v[i];
+        vi.x = (float)__dadd_rn((double)vi.x, __dmul_rn(a.x, dt));
+        vi.y = (float)__dadd_rn((double)vi.y, __dmul_rn(a.y, dt));
+        vi.z = (float)__dadd_rn((double)vi.z, __dmul_rn(a.z, dt));
+        xi.x = (float)__dadd_rn((double)xi.x, __dmul_rn((double)vi.x, dt));
+        xi.y = (float)__dadd_rn((double)xi.y, __dmul_rn((double)vi.y, dt));
+        xi.z = (float)__dadd_rn((double)xi.z, __dmul_rn((double)vi.z, dt));
+        v[i] = vi;
+        x[i] = xi;
+    }
+}
+
 }  // namespace
 
 extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_t n,
@@ -669,4 +687,24 @@ extern "C" int gc_read_nbody_tree(gc_pool_t *p, uint32_t *sorted_ids, uint64_t *
         GC_CUDA_TRY(cudaMemcpy(list_ids, src + base, S.n_list * 4, cudaMemcpyDeviceToHost));
     }
     return GC_OK;
+}
+
+// One time step around the force computation (Section 4.1): leapfrog kick
+// with the accelerations acc (4 doubles per particle, e.g. the pool's
+// per-id totals after the step's flush), drift, and the new positions
+// uploaded into the pool in place (ids 0..n-1).
+extern "C" int gc_nbody_kick_drift(gc_pool_t *p, const double *acc_dev, float *xyzm_dev,
+                                   float *vel_dev, uint64_t n, double dt)
+{
+    if (!p || !acc_dev || !xyzm_dev || !vel_dev) return GC_ERR_ARG;
+    if (n == 0) return GC_OK;
+    if (n > p->cfg.id_capacity || ((uintptr_t)xyzm_dev | (uintptr_t)vel_dev) % 16 ||
+        ((uintptr_t)acc_dev) % 32)
+        return GC_ERR_ARG;
+    GC_TRY(order_after_scatters(p));   // the accelerations of batches in flight
+    ++p->stats.kernel_launches;
+    k_kick_drift<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
+        (const gcd4 *)acc_dev, (float4 *)xyzm_dev, (float4 *)vel_dev, n, dt);
+    GC_CUDA_TRY(cudaGetLastError());
+    return gc_launch_upload_seq(p, 0, (const float4 *)xyzm_dev, n);
 }

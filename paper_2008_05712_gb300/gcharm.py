@@ -134,6 +134,7 @@ _SIGS = {
     "gc_build_nbody_tasks": [P, P, U64, C.c_int, C.c_int, C.c_int, U64, P],
     "gc_read_nbody_tree": [P] + [P] * 14,
     "gc_build_md_tasks": [P, P, U64, C.c_int, U64, P],
+    "gc_build_md_tasks_2d": [P, P, U64, C.c_int, U64, P],
     "gc_read_md_cells": [P, P, P],
     "gc_last_timings": [P, P],
     "gc_gravity_noalloc": [U64, P, P, P, P, U64, C.c_float, P, P],
@@ -157,6 +158,7 @@ _SIGS = {
     "gc_graph_results": [P, U64, U64, P],
     "gc_graph_destroy": [P],
     "gc_reuse_ablation": [P, C.c_int, P],
+    "gc_nbody_kick_drift": [P, P, P, P, U64, C.c_double],
 }
 
 _RESTYPES = {"gc_strerror": C.c_char_p, "gc_combine_size_from_occupancy": C.c_uint64}
@@ -518,6 +520,23 @@ class Pool:
                "gc_read_nbody_tree")
         return out
 
+    def kick_drift(self, acc_ptr, xyzm_t, vel_t, dt):
+        """Leapfrog step on device arrays (gc_nbody_kick_drift); acc_ptr is a
+        device address of 4 doubles per particle (e.g. totals_device_ptr())
+        or a CUDA float64 tensor."""
+        a = acc_ptr if isinstance(acc_ptr, int) else acc_ptr.data_ptr()
+        _check(self.lib.gc_nbody_kick_drift(self.h, C.c_void_p(a), _dptr(xyzm_t), _dptr(vel_t),
+                                            xyzm_t.shape[0], float(dt)),
+               "gc_nbody_kick_drift")
+
+    def nbody_bucket_counts(self, n_buckets):
+        """Targets per bucket of the last N-body build, in bucket order."""
+        out = np.empty(n_buckets, np.uint32)
+        args = [None] * 14
+        args[10] = _p(out)                     # bucket_count
+        _check(self.lib.gc_read_nbody_tree(self.h, *args), "gc_read_nbody_tree")
+        return out
+
     def nbody_sorted_ids(self, n):
         """Particle ids of the last N-body build in Morton (key, id) order."""
         out = np.empty(n, np.uint32)
@@ -525,20 +544,21 @@ class Pool:
                "gc_read_nbody_tree")
         return out
 
-    def build_md(self, cell, m, task_id_base=0):
-        """cell: CUDA tensor or host numpy array of uint32/int32 cell indices."""
+    def build_md(self, cell, m, task_id_base=0, dim=3):
+        """cell: CUDA tensor or host numpy array of uint32/int32 cell indices;
+        dim 3 (m^3 cells) or 2 (the planar m x m grid)."""
         info = np.zeros(4, np.uint64)
         if isinstance(cell, np.ndarray):
             cell = np.ascontiguousarray(cell, np.uint32)
             ptr, n = _p(cell), cell.shape[0]
         else:
             ptr, n = _dptr(cell), cell.numel()
-        _check(self.lib.gc_build_md_tasks(self.h, ptr, n, m, task_id_base, _p(info)),
-               "gc_build_md_tasks")
+        fn = self.lib.gc_build_md_tasks if dim == 3 else self.lib.gc_build_md_tasks_2d
+        _check(fn(self.h, ptr, n, m, task_id_base, _p(info)), "gc_build_md_tasks")
         return dict(tasks=int(info[0]), tgt_entries=int(info[1]), src_entries=int(info[2]))
 
-    def md_cells(self, n, m):
-        start = np.empty(m ** 3 + 1, np.uint32)
+    def md_cells(self, n, m, dim=3):
+        start = np.empty(m ** dim + 1, np.uint32)
         atoms = np.empty(n, np.uint32)
         _check(self.lib.gc_read_md_cells(self.h, _p(start), _p(atoms)), "gc_read_md_cells")
         return start, atoms
