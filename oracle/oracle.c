@@ -706,3 +706,110 @@ void orc_kick_drift(int64_t n, const double *acc, float *xyzm, float *vel, doubl
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Periodic gravity: Ewald correction (the tree code's second combined      */
+/* kernel, Section 4.1)                                                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Ewald summation for a point mass in a periodic cube of side L with a
+ * uniform neutralising background (G = 1, no softening).  For the
+ * displacement r = x_target - x_source, the periodic Green's function is
+ *   psi(r) = sum_n erfc(alpha |r + nL|) / |r + nL|
+ *          + 1/(pi L) sum_{h != 0} exp(-pi^2 h^2 / (alpha L)^2) / h^2 cos(2 pi h.r / L)
+ *          - pi / (alpha^2 L^3),
+ * n over integer vectors with max |n_i| <= nrep, h over integer vectors with
+ * 0 < |h|^2 <= hcut2.  The potential of mass M is -M psi and its
+ * acceleration M grad psi.  The correction returned is the periodic
+ * interaction minus the plain point-mass term of r itself:
+ *   a_corr = M grad psi(r) + M r / |r|^3,   phi_corr = -M (psi(r) - 1/|r|),
+ * finite at r = 0.  The n = 0 real-space term and the subtracted term are
+ * combined (-erf(alpha s)/s, and its gradient) and, for alpha s < 1/2,
+ * evaluated from the Taylor series of erf so that nothing cancels.
+ */
+#define ORC_PI 3.14159265358979323846
+
+static void ewald_pair(const double r[3], double M, double L, double alpha, int nrep,
+                       int hcut2, double out[4])
+{
+    const double sqpi = sqrt(ORC_PI);
+    double ax = 0, ay = 0, az = 0, phi = 0;   /* of grad psi and psi - 1/|r| */
+    for (int nx = -nrep; nx <= nrep; ++nx)
+        for (int ny = -nrep; ny <= nrep; ++ny)
+            for (int nz = -nrep; nz <= nrep; ++nz) {
+                double d[3] = {r[0] + nx * L, r[1] + ny * L, r[2] + nz * L};
+                double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double s = sqrt(s2);
+                double g, p;   /* grad term = -d * g; potential term p */
+                if (nx == 0 && ny == 0 && nz == 0) {
+                    /* erfc(alpha s)/s - 1/s = -erf(alpha s)/s: p = -alpha erf(x)/x,
+                     * and its gradient -d g with g = alpha^3 f(x),
+                     * f(x) = -erf(x)/x^3 + 2/sqrt(pi) exp(-x^2)/x^2 */
+                    double x = alpha * s;
+                    if (x < 0.5) {
+                        /* erf(x)/x = 2/sqrt(pi) sum_{k>=0} (-1)^k x^(2k) / (k! (2k+1))
+                         * f(x)     = 2/sqrt(pi) sum_{k>=1} (-1)^k x^(2k-2) 2k / (k! (2k+1)) */
+                        double x2 = x * x, e = 0.0, fk = 0.0;
+                        double t = 1.0;             /* (-1)^k x^(2k) / k!   at k = 0 */
+                        for (int k = 0; k < 18; ++k) {
+                            e += t / (2 * k + 1);
+                            t *= -x2 / (k + 1);
+                        }
+                        double u = -1.0;            /* (-1)^k x^(2k-2) / k! at k = 1 */
+                        for (int k = 1; k < 18; ++k) {
+                            fk += u * (2.0 * k) / (2 * k + 1);
+                            u *= -x2 / (k + 1);
+                        }
+                        g = alpha * alpha * alpha * (2.0 / sqpi) * fk;
+                        p = -alpha * (2.0 / sqpi) * e;
+                    } else {
+                        g = -erf(x) / (s2 * s) + 2.0 * alpha / sqpi * exp(-x * x) / s2;
+                        p = -erf(x) / s;
+                    }
+                } else {
+                    double x = alpha * s;
+                    g = erfc(x) / (s2 * s) + 2.0 * alpha / sqpi * exp(-x * x) / s2;
+                    p = erfc(x) / s;
+                }
+                /* grad of the term is -d * g */
+                ax -= d[0] * g; ay -= d[1] * g; az -= d[2] * g;
+                phi += p;
+            }
+    const int hm = (int)ceil(sqrt((double)hcut2));
+    for (int hx = -hm; hx <= hm; ++hx)
+        for (int hy = -hm; hy <= hm; ++hy)
+            for (int hz = -hm; hz <= hm; ++hz) {
+                int h2 = hx * hx + hy * hy + hz * hz;
+                if (h2 == 0 || h2 > hcut2) continue;
+                double c = exp(-ORC_PI * ORC_PI * h2 / (alpha * alpha * L * L)) / h2;
+                double arg = 2.0 * ORC_PI * (hx * r[0] + hy * r[1] + hz * r[2]) / L;
+                phi += c * cos(arg) / (ORC_PI * L);
+                double gs = -c * sin(arg) * 2.0 / (L * L);
+                ax += gs * hx; ay += gs * hy; az += gs * hz;
+            }
+    phi -= ORC_PI / (alpha * alpha * L * L * L);
+    out[0] += M * ax;
+    out[1] += M * ay;
+    out[2] += M * az;
+    out[3] += -M * phi;
+}
+
+/* Ewald corrections of nt targets from the same ns sources (table rows
+ * x, y, z, m), summed in source order: out[4t..4t+3] = (ax, ay, az, phi). */
+void orc_ewald(const float *table, int64_t nt, const uint32_t *tgt, int64_t ns,
+               const uint32_t *src, double L, double alpha, int nrep, int hcut2,
+               double *out)
+{
+    for (int64_t t = 0; t < nt; ++t) {
+        const float *xt = table + 4 * (size_t)tgt[t];
+        double acc[4] = {0, 0, 0, 0};
+        for (int64_t j = 0; j < ns; ++j) {
+            const float *xs = table + 4 * (size_t)src[j];
+            double r[3] = {(double)xt[0] - (double)xs[0], (double)xt[1] - (double)xs[1],
+                           (double)xt[2] - (double)xs[2]};
+            ewald_pair(r, (double)xs[3], L, alpha, nrep, hcut2, acc);
+        }
+        for (int c = 0; c < 4; ++c) out[4 * t + c] = acc[c];
+    }
+}

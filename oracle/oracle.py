@@ -75,6 +75,8 @@ def _declare(L):
     L.orc_reduce.restype = None
     L.orc_kick_drift.argtypes = [I64, P, P, P, C.c_double]
     L.orc_kick_drift.restype = None
+    L.orc_ewald.argtypes = [P, I64, P, I64, P, C.c_double, C.c_double, C.c_int, C.c_int, P]
+    L.orc_ewald.restype = None
 
 
 def _p(a: np.ndarray):
@@ -303,3 +305,16 @@ def kick_drift(acc, xyzm, vel, dt):
     v = np.array(vel, dtype=np.float32, copy=True, order="C")
     lib().orc_kick_drift(x.shape[0], _p(a), _p(x), _p(v), float(dt))
     return x, v
+
+
+def ewald(table, tgt, src, L, alpha=None, nrep=2, hcut2=10):
+    """Ewald corrections (periodic minus plain point-mass term) of the
+    targets from the sources, (nt, 4) FP64 (ax, ay, az, phi)."""
+    t = _c(table, np.float32)
+    a = _c(tgt, np.uint32)
+    b = _c(src, np.uint32)
+    out = np.zeros((a.shape[0], 4), np.float64)
+    alpha = 2.0 / L if alpha is None else alpha
+    lib().orc_ewald(_p(t), a.shape[0], _p(a), b.shape[0], _p(b), float(L), float(alpha),
+                    int(nrep), int(hcut2), _p(out))
+    return out
