@@ -351,6 +351,79 @@ def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True):
     return out
 
 
+EWALD_WORKLOAD = ("ewald_1M: Ewald corrections of 1,048,576 particles uniform in a periodic "
+                  "unit cube, one task per tree bucket (targets = the bucket, source = the "
+                  "root monopole), alpha = 2/L, images |n_i| <= 2, |h|^2 <= 10")
+
+
+def ewald_section(gcharm, torch, seed, stream, reps=5, with_oracle=True):
+    """Periodic-gravity corrections (the tree code's Ewald step) as a batch
+    of GC_EWALD tasks over the buckets of a 1M-particle tree."""
+    n = 1 << 20
+    g = inputs.rng(seed)
+    x = np.empty((n, 4), np.float32)
+    x[:, :3] = g.uniform(0.0, 1.0, size=(n, 3))
+    x[:, 3] = 1.0 / n
+    pool = gcharm.Pool(id_capacity=2 * n + 1024, pool_capacity=2 * n + 1024, eps2=EPS2,
+                       stream=stream.cuda_stream, ewald_box=1.0)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    info = pool.build_nbody(x, BUCKET, *THETA)
+    pool.flush()
+    counts = pool.nbody_bucket_counts(info["n_buckets"]).astype(np.int64)
+    sid = pool.nbody_sorted_ids(n)
+    nb = counts.shape[0]
+    to = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    so = np.arange(nb + 1, dtype=np.uint64)
+    sr = np.full(nb, n, np.uint32)                     # node id n + 0: the root
+    dk = torch.full((nb,), 3, dtype=torch.int32, device="cuda")
+    dto = torch.from_numpy(to.view(np.int64)).cuda()
+    dso = torch.from_numpy(so.view(np.int64)).cuda()
+    dtg = torch.from_numpy(sid.view(np.int32)).cuda()
+    dsr = torch.from_numpy(sr.view(np.int32)).cuda()
+    torch.cuda.synchronize()
+
+    def step():
+        pool.submit_csr_device(dk, dto, dtg, dso, dsr, n, nb)
+        pool.flush()
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    s0 = pool.stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    pool.join(stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    s1 = pool.stats()
+    nbt = s1["timed_batches"] - s0["timed_batches"]
+    stage = {k: (s1["stage_ms_sum"][k] - s0["stage_ms_sum"][k]) / max(nbt, 1)
+             for k in s1["stage_ms_sum"]}
+    out = {"workload": EWALD_WORKLOAD, "tasks": nb, "pairs_per_batch": n,
+           "ms_per_batch": ms, "value": n / (ms / 1e3), "unit": "target-source pairs/s",
+           "stage_ms_avg": stage}
+    if with_oracle:
+        from oracle import oracle as O
+        rows = gcharm.value(pool.results())
+        pick = np.sort(inputs.rng(seed + 1).choice(nb, 200, replace=False))
+        tab = np.concatenate([x, np.zeros((1, 4), np.float32)])
+        got, ref, off = [], [], [0]
+        tab[n] = pool.nbody_node_values(info["n_nodes"])[0]   # the root's (COM, mass)
+        for b in pick:
+            tg = sid[to[b]:to[b + 1]]
+            ref.append(O.ewald(tab, tg, [n], 1.0))
+            got.append(rows[to[b]:to[b + 1]])
+            off.append(off[-1] + len(tg))
+        out["parity_on_sample"] = error_stats(np.concatenate(got), np.concatenate(ref),
+                                              np.array(off))
+    pool.close()
+    return out
+
+
 def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=True):
     """The 200k-task uneven batch (device-resident task arrays, timed with
     events) and the serving loop at three arrival rates (host task arrays,
@@ -686,6 +759,10 @@ def main():
     if rank == 0 and not args.no_md:
         md = md_section(gcharm, torch, inputs.SEED_BASE + 3, stream,
                         with_oracle=not args.no_cpu_baseline)
+    ewald = None
+    if rank == 0 and not args.no_md:
+        ewald = ewald_section(gcharm, torch, inputs.SEED_BASE + 8, stream,
+                              with_oracle=not args.no_cpu_baseline)
     uneven = serving = None
     if rank == 0 and not args.no_serve:
         pool.close()
@@ -718,6 +795,7 @@ def main():
             "per_task_launch": per_task,
             "reuse_ablation": ablation,
             "md": md,
+            "ewald": ewald,
             "uneven_batch": uneven,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -70,6 +70,9 @@ typedef struct gc_pool gc_pool_t;
 #define GC_GRAVITY 0u
 #define GC_LJ_PAIR 1u
 #define GC_LJ_SELF 2u
+#define GC_EWALD 3u     /* periodic-gravity correction: targets x sources, the
+                           Ewald interaction minus the plain point-mass term
+                           (needs gc_config.ewald_box > 0)                   */
 
 /* ---- configuration (gc_pool_create) ------------------------------------ */
 typedef struct {
@@ -87,6 +90,10 @@ typedef struct {
                                      order (always on in this version)     */
     void *cuda_stream;            /* cudaStream_t the pool issues on; NULL =
                                      the legacy default stream             */
+    float ewald_box;              /* periodic cube side L for GC_EWALD tasks;
+                                     0 = no Ewald tasks.  Splitting alpha =
+                                     2/L, real-space images |n_i| <= 2,
+                                     reciprocal vectors 0 < |h|^2 <= 10    */
 } gc_config;
 
 /* ---- one task (gc_submit) ---------------------------------------------- */

@@ -130,6 +130,7 @@ static void free_pool(gc_pool *p)
     cudaFree(p->d_ref_count);
     cudaFree(p->d_totals);
     cudaFree(p->d_ctr);
+    if (p->d_ewald_h) cudaFree(p->d_ewald_h);
     if (p->h_mirror) cudaFreeHost(p->h_mirror);
     if (p->h_ctr) cudaFreeHost(p->h_ctr);
     DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->uniq, &p->miss, &p->freel,
@@ -260,6 +261,10 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
     }
     p->rc2_grid = rc2g;
     p->md_edge_grid = (int32_t)eg;
+    if (cfg->ewald_box < 0.0f || !(cfg->ewald_box == cfg->ewald_box)) {
+        delete p;
+        return GC_ERR_ARG;
+    }
     if (cudaGetDevice(&p->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) !=
             cudaSuccess) {
@@ -291,6 +296,28 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
     if (rc == GC_OK) rc = dmalloc(&p->d_ref_count, idc);
     if (rc == GC_OK) rc = dmalloc(&p->d_totals, idc);
     if (rc == GC_OK) rc = dmalloc(&p->d_ctr, (uint64_t)CTR_COUNT);
+    if (rc == GC_OK && cfg->ewald_box > 0.0f) {
+        // reciprocal vectors with 0 < |h|^2 <= 10, one of each pair +-h (the
+        // pair's cos and h sin terms are equal: the coefficient is doubled)
+        const double L = cfg->ewald_box, alpha = 2.0 / L, pi = 3.14159265358979323846;
+        std::vector<float4> hv;
+        for (int hx = -3; hx <= 3; ++hx)
+            for (int hy = -3; hy <= 3; ++hy)
+                for (int hz = -3; hz <= 3; ++hz) {
+                    const int h2 = hx * hx + hy * hy + hz * hz;
+                    if (h2 == 0 || h2 > 10) continue;
+                    const bool upper = hx > 0 || (hx == 0 && (hy > 0 || (hy == 0 && hz > 0)));
+                    if (!upper) continue;
+                    const double c = 2.0 * std::exp(-pi * pi * h2 / (alpha * alpha * L * L)) / h2;
+                    hv.push_back(make_float4((float)hx, (float)hy, (float)hz, (float)c));
+                }
+        rc = dmalloc(&p->d_ewald_h, (uint64_t)hv.size());
+        if (rc == GC_OK &&
+            cudaMemcpy(p->d_ewald_h, hv.data(), hv.size() * sizeof(float4),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = GC_ERR_CUDA;
+        p->n_ewald_h = (int)hv.size();
+    }
     if (rc == GC_OK) {
         if (cudaHostAlloc((void **)&p->h_mirror, sizeof(float4) * idc, cudaHostAllocMapped) !=
                 cudaSuccess ||
@@ -385,7 +412,9 @@ static int gc_submit_csr_impl(gc_pool *p, uint64_t n_tasks, const uint64_t *task
             if (tgt_off[t + 1] < tgt_off[t] || src_off[t + 1] < src_off[t]) return GC_ERR_ARG;
             uint64_t nt = tgt_off[t + 1] - tgt_off[t], ns = src_off[t + 1] - src_off[t];
             if (nt > 0xFFFFFFFFull || ns > 0xFFFFFFFFull) return GC_ERR_ARG;
-            if (kinds[t] > GC_LJ_SELF || (kinds[t] == GC_LJ_SELF && ns)) return GC_ERR_ARG;
+            if (kinds[t] > GC_EWALD || (kinds[t] == GC_LJ_SELF && ns) ||
+                (kinds[t] == GC_EWALD && p->n_ewald_h == 0))
+                return GC_ERR_ARG;
             if (budget && (nt + ns) * sizeof(float4) > budget) return GC_ERR_BUDGET;
         }
         n_tgt_total = tgt_off[n_tasks];

@@ -185,6 +185,10 @@ struct gc_pool {
     uint32_t wu_max_targets = 16;      // targets per gravity work unit: 8, 16 or 32
     uint32_t wu_schedule = GC_SCHED_FIFO;
     uint64_t table_version = 0;        // bumped whenever a slot is assigned or freed
+    // Ewald correction (GC_EWALD tasks): half of the reciprocal vectors
+    // (hx, hy, hz, 2 exp(-pi^2 h^2 / (alpha L)^2) / h^2)
+    float4 *d_ewald_h = nullptr;
+    int n_ewald_h = 0;
     NBodyState nb;
     MDState md;
 };

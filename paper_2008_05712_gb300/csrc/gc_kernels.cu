@@ -21,7 +21,8 @@ namespace {
 __global__ void k_task_recs(uint64_t n, const uint64_t *task_ids, const uint32_t *kinds,
                             const int8_t *shifts, const uint64_t *tgt_off,
                             const uint64_t *src_off, uint64_t tgt_base, uint64_t src_base,
-                            uint64_t id_base, TaskRec *out, unsigned long long *ctr)
+                            uint64_t id_base, TaskRec *out, unsigned long long *ctr,
+                            int ewald_ok)
 {
     GRID_STRIDE(t, n) {
         TaskRec r;
@@ -34,7 +35,8 @@ __global__ void k_task_recs(uint64_t n, const uint64_t *task_ids, const uint32_t
         r.row_off = 0;
         for (int a = 0; a < 3; ++a) r.shift[a] = shifts ? shifts[3 * t + a] : (int8_t)0;
         r.shift[3] = 0;
-        if (r.kind > GC_LJ_SELF || (r.kind == GC_LJ_SELF && r.ns != 0))
+        if (r.kind > GC_EWALD || (r.kind == GC_LJ_SELF && r.ns != 0) ||
+            (r.kind == GC_EWALD && !ewald_ok))
             atomicOr(&ctr[CTR_FLAGS], (unsigned long long)GC_FLAG_BAD_TASK);
         out[t] = r;
     }
@@ -52,8 +54,8 @@ __global__ void k_prep_counts(const TaskRec *tasks, uint64_t n, uint64_t *rows,
         rows[t] = rw;
         wu_g[t] = (r.kind == GC_GRAVITY) ? (r.nt + wu_max - 1u) / wu_max : 0u;
         lj[t] = (r.kind != GC_GRAVITY) ? 1u : 0u;
-        if (r.kind == GC_GRAVITY) inter += (unsigned long long)r.nt * r.ns;
-        else if (r.kind == GC_LJ_PAIR) inter += (unsigned long long)r.nt * r.ns;
+        if (r.kind == GC_GRAVITY || r.kind == GC_LJ_PAIR || r.kind == GC_EWALD)
+            inter += (unsigned long long)r.nt * r.ns;
         else inter += (unsigned long long)r.nt * (r.nt ? r.nt - 1 : 0) / 2;
         mx = max(mx, max(r.nt, r.ns));
     }
@@ -688,6 +690,9 @@ struct InterArgs {
     unsigned long long *queue;   // work-queue head
     unsigned long long *lj_in;
     unsigned long long *flags;   // device error bits
+    const float4 *ewald_h;       // half of the reciprocal vectors (GC_EWALD)
+    int n_ewald_h;
+    float ewald_L;
 };
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
@@ -1029,6 +1034,7 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
         if (w >= a.n_lj) break;
         const uint32_t ti = a.lj_list[w];
         const TaskRec r = a.tasks[ti];
+        if (r.kind == GC_EWALD) continue;   // k_ewald's
         const bool self = r.kind == GC_LJ_SELF;
         const uint32_t nA = r.nt, nB = self ? 0u : r.ns;
         const float4 *As = a.stg_t + (r.tgt_off - a.tgt_base);
@@ -1065,7 +1071,7 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
                 float rx = (float)dx * inv_grid, ry = (float)dy * inv_grid,
                       rz = (float)dz * inv_grid;
                 float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                float ir2 = 1.0f / r2;
+                float ir2 = gc_rcp(r2);
                 float s2 = a.lj_sig2 * ir2;
                 float s6 = s2 * s2 * s2;
                 float coef = a.lj_eps24 * fmaf(2.0f, s6 * s6, -s6) * ir2;
@@ -1093,6 +1099,128 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
         }
         for (int s = 16; s; s >>= 1) inside += __shfl_xor_sync(0xffffffffu, inside, s);
         if (lane == 0 && inside) atomicAdd(a.lj_in, inside);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// interaction: Ewald correction of periodic gravity
+// ---------------------------------------------------------------------------
+
+// Correction of one source of mass M at displacement r = x_target - x_source
+// in a periodic cube of side L (splitting alpha = 2/L): the Ewald sum over
+// the images |n_i| <= 2 and reciprocal vectors 0 < |h|^2 <= 10 minus the
+// plain point-mass term of r.  Adds (grad psi, psi - 1/|r|) scaled to
+// (acceleration, potential) into out.  The zero image and the subtracted
+// term are combined and taken from the series of erf below alpha |r| = 1/2.
+__device__ __forceinline__ void ewald_pair(float rx, float ry, float rz, float M, float L,
+                                           const float4 *hv, int nh, float out[4])
+{
+    const float alpha = 2.0f / L;
+    const float c2 = 1.1283791670955126f;    // 2 / sqrt(pi)
+    float gx = 0.f, gy = 0.f, gz = 0.f, ps = 0.f;
+#pragma unroll 1
+    for (int nx = -2; nx <= 2; ++nx) {
+#pragma unroll 1
+        for (int ny = -2; ny <= 2; ++ny) {
+#pragma unroll
+            for (int nz = -2; nz <= 2; ++nz) {
+                const float dx = rx + (float)nx * L, dy = ry + (float)ny * L,
+                            dz = rz + (float)nz * L;
+                const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float s = sqrtf(s2);
+                const float x = alpha * s;
+                float g, p;
+                if (nx == 0 && ny == 0 && nz == 0) {
+                    if (x < 0.5f) {
+                        // erf(x)/x and -erf(x)/x^3 + c2 exp(-x^2)/x^2 as series in x^2
+                        const float x2 = x * x;
+                        float e = 0.f, fk = 0.f, t = 1.f, u = -1.f;
+                        for (int k = 0; k < 9; ++k) {
+                            e += t / (float)(2 * k + 1);
+                            t *= -x2 / (float)(k + 1);
+                        }
+                        for (int k = 1; k < 10; ++k) {
+                            fk += u * (float)(2 * k) / (float)(2 * k + 1);
+                            u *= -x2 / (float)(k + 1);
+                        }
+                        g = alpha * alpha * alpha * c2 * fk;
+                        p = -alpha * c2 * e;
+                    } else {
+                        const float er = erff(x);
+                        g = -er / (s2 * s) + alpha * c2 * expf(-x * x) / s2;
+                        p = -er / s;
+                    }
+                } else {
+                    const float ec = erfcf(x);
+                    g = ec / (s2 * s) + alpha * c2 * expf(-x * x) / s2;
+                    p = ec / s;
+                }
+                gx = fmaf(-dx, g, gx);
+                gy = fmaf(-dy, g, gy);
+                gz = fmaf(-dz, g, gz);
+                ps += p;
+            }
+        }
+    }
+    const float inv_l = 1.0f / L;
+    const float kphi = inv_l * 0.3183098861837907f;     // 1 / (pi L)
+    const float kacc = -2.0f * inv_l * inv_l;
+    for (int j = 0; j < nh; ++j) {
+        const float4 h = hv[j];
+        float sn, cs;
+        sincospif(2.0f * (h.x * rx + h.y * ry + h.z * rz) * inv_l, &sn, &cs);
+        ps = fmaf(h.w * kphi, cs, ps);
+        const float gs = kacc * h.w * sn;
+        gx = fmaf(gs, h.x, gx);
+        gy = fmaf(gs, h.y, gy);
+        gz = fmaf(gs, h.z, gz);
+    }
+    ps -= 3.14159265358979f / (alpha * alpha * L * L * L);
+    out[0] = M * gx;
+    out[1] = M * gy;
+    out[2] = M * gz;
+    out[3] = -M * ps;
+}
+
+// One warp per GC_EWALD task of the task list: each target owned by a lane,
+// which sums the corrections of all the task's sources with compensation.
+__global__ void __launch_bounds__(GRAV_THREADS) k_ewald(InterArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t it = 0;; ++it) {
+        unsigned long long w = gwarp + it * nwarps;   // fixed share without a queue
+        if (a.queue) {
+            if (lane == 0) w = atomicAdd(a.queue, 1ull);
+            w = __shfl_sync(0xffffffffu, w, 0);
+        }
+        if (w >= a.n_lj) break;
+        const uint32_t ti = a.lj_list[w];
+        const TaskRec r = a.tasks[ti];
+        if (r.kind != GC_EWALD) continue;
+        const float4 *As = a.stg_t + (r.tgt_off - a.tgt_base);
+        const float4 *Bs = a.stg_s + (r.src_off - a.src_base) + (ti - a.task_base);
+        for (uint32_t o = lane; o < r.nt; o += 32) {
+            const float4 me = As[o];
+            float sx = 0.f, sy = 0.f, sz = 0.f, su = 0.f;
+            float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f;
+            for (uint32_t q = 0; q < r.ns; ++q) {
+                const float4 src = Bs[q];
+                float v[4];
+                ewald_pair(me.x - src.x, me.y - src.y, me.z - src.z, src.w, a.ewald_L,
+                           a.ewald_h, a.n_ewald_h, v);
+                kahan_add(sx, cx, v[0]);
+                kahan_add(sy, cy, v[1]);
+                kahan_add(sz, cz, v[2]);
+                kahan_add(su, cu, v[3]);
+            }
+            const uint32_t pos = a.perm_t[r.tgt_off + o];
+            const uint64_t row = r.row_off + pos;
+            a.res[2 * row] = make_float4(sx, sy, sz, su);
+            a.res[2 * row + 1] = make_float4(cx, cy, cz, cu);
+            a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
+        }
     }
 }
 
@@ -1142,7 +1270,7 @@ int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
     ++p->stats.kernel_launches;
     k_task_recs<<<grid_for(n_tasks, 256, p->num_sms * 16), 256, 0, p->s>>>(
         n_tasks, task_ids, kinds, shifts, tgt_off, src_off, tgt_base, src_base, task_id_base,
-        out, p->d_ctr);
+        out, p->d_ctr, p->n_ewald_h > 0 ? 1 : 0);
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
@@ -1294,6 +1422,9 @@ static void fill_inter_args(gc_pool *p, FlushCtx &c, uint64_t tgt_base, uint64_t
     a.row_id = c.row_id.as<uint32_t>();
     a.queue = c.d_ctr + FC_QUEUE;
     a.lj_in = c.d_ctr + FC_LJ_IN;
+    a.ewald_h = p->d_ewald_h;
+    a.n_ewald_h = p->n_ewald_h;
+    a.ewald_L = p->cfg.ewald_box;
     a.flags = p->d_ctr + CTR_FLAGS;
 }
 
@@ -1378,6 +1509,11 @@ int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_
         const unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
         ++p->stats.kernel_launches;
         k_lj<<<g, GRAV_THREADS, 0, c.s>>>(a);
+        if (p->n_ewald_h > 0) {
+            GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
+            ++p->stats.kernel_launches;
+            k_ewald<<<g, GRAV_THREADS, 0, c.s>>>(a);
+        }
     }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
@@ -1408,6 +1544,10 @@ int gc_interact_one_task(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint
         a.n_lj = l1 - l0;
         ++p->stats.kernel_launches;
         k_lj<<<1, 32, 0, c.s>>>(a);
+        if (p->n_ewald_h > 0) {
+            ++p->stats.kernel_launches;
+            k_ewald<<<1, 32, 0, c.s>>>(a);
+        }
     }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;

@@ -77,3 +77,12 @@ __device__ __forceinline__ float gc_rsqrt(float x)
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// 1/x by the hardware approximation (rcp.approx, relative error below
+// 2^-22) in its flush-to-zero form; the LJ kernel's r^2 is never subnormal.
+__device__ __forceinline__ float gc_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}

@@ -33,6 +33,7 @@ NOALLOC_MAX_TARGETS = 262144
 GC_GRAVITY = 0
 GC_LJ_PAIR = 1
 GC_LJ_SELF = 2
+GC_EWALD = 3
 
 GC_COMBINE_ADAPTIVE = 0
 GC_COMBINE_ADAPTIVE_WINDOW = 1
@@ -50,7 +51,7 @@ class GcConfig(C.Structure):
                 ("lj_rc2", C.c_float), ("md_edge", C.c_float),
                 ("id_capacity", C.c_uint64), ("pool_capacity", C.c_uint64),
                 ("staging_budget_bytes", C.c_uint64), ("deterministic", C.c_int),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("ewald_box", C.c_float)]
 
 
 class GcTask(C.Structure):
@@ -207,7 +208,7 @@ class Pool:
     """One device pool (chare table + slots + batch + totals)."""
 
     def __init__(self, id_capacity, pool_capacity, eps2=1e-4, lj_eps=1.0, lj_sigma=1.0,
-                 lj_rc2=0.0, md_edge=0.0, staging_budget_bytes=0, stream=None):
+                 lj_rc2=0.0, md_edge=0.0, staging_budget_bytes=0, stream=None, ewald_box=0.0):
         lib = load()
         cfg = GcConfig()
         cfg.eps2 = eps2
@@ -216,6 +217,7 @@ class Pool:
         cfg.staging_budget_bytes = int(staging_budget_bytes)
         cfg.deterministic = 1
         cfg.cuda_stream = stream
+        cfg.ewald_box = ewald_box
         h = C.c_void_p()
         _check(lib.gc_pool_create(C.byref(cfg), C.byref(h)), "gc_pool_create")
         self.h = h
@@ -534,6 +536,15 @@ class Pool:
         out = np.empty(n_buckets, np.uint32)
         args = [None] * 14
         args[10] = _p(out)                     # bucket_count
+        _check(self.lib.gc_read_nbody_tree(self.h, *args), "gc_read_nbody_tree")
+        return out
+
+    def nbody_node_values(self, n_nodes):
+        """(x, y, z, m) float32 of every node of the last N-body build (node
+        k has data id n + k)."""
+        out = np.empty((n_nodes, 4), np.float32)
+        args = [None] * 14
+        args[8] = _p(out)                      # node_xyzm
         _check(self.lib.gc_read_nbody_tree(self.h, *args), "gc_read_nbody_tree")
         return out
 
