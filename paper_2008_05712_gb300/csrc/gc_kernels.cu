@@ -1106,66 +1106,62 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
 // interaction: Ewald correction of periodic gravity
 // ---------------------------------------------------------------------------
 
-// Correction of one source of mass M at displacement r = x_target - x_source
-// in a periodic cube of side L (splitting alpha = 2/L): the Ewald sum over
-// the images |n_i| <= 2 and reciprocal vectors 0 < |h|^2 <= 10 minus the
-// plain point-mass term of r.  Adds (grad psi, psi - 1/|r|) scaled to
-// (acceleration, potential) into out.  The zero image and the subtracted
-// term are combined and taken from the series of erf below alpha |r| = 1/2.
-__device__ __forceinline__ void ewald_pair(float rx, float ry, float rz, float M, float L,
-                                           const float4 *hv, int nh, float out[4])
+// Part of the correction of one source at displacement r = x_target -
+// x_source in a periodic cube of side L (splitting alpha = 2/L): the terms of
+// the Ewald sum over the real-space images i = part, part + parts, ... of the
+// 125 images |n_j| <= 2 (i = 25 (nx + 2) + 5 (ny + 2) + nz + 2) and over the
+// reciprocal vectors j = part, part + parts, ... of the half set hv, minus
+// the plain point-mass term of r (carried by the zero image, i = 62).  Adds
+// grad psi to (gx, gy, gz) and psi - 1/|r| to ps; the background term is
+// added by part 0.  The zero image and the subtracted term are combined and
+// taken from the series of erf below alpha |r| = 1/2.
+__device__ __forceinline__ void ewald_part(float rx, float ry, float rz, float L,
+                                           const float4 *hv, int nh, int part, int parts,
+                                           float &gx, float &gy, float &gz, float &ps)
 {
     const float alpha = 2.0f / L;
     const float c2 = 1.1283791670955126f;    // 2 / sqrt(pi)
-    float gx = 0.f, gy = 0.f, gz = 0.f, ps = 0.f;
-#pragma unroll 1
-    for (int nx = -2; nx <= 2; ++nx) {
-#pragma unroll 1
-        for (int ny = -2; ny <= 2; ++ny) {
-#pragma unroll
-            for (int nz = -2; nz <= 2; ++nz) {
-                const float dx = rx + (float)nx * L, dy = ry + (float)ny * L,
-                            dz = rz + (float)nz * L;
-                const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float s = sqrtf(s2);
-                const float x = alpha * s;
-                float g, p;
-                if (nx == 0 && ny == 0 && nz == 0) {
-                    if (x < 0.5f) {
-                        // erf(x)/x and -erf(x)/x^3 + c2 exp(-x^2)/x^2 as series in x^2
-                        const float x2 = x * x;
-                        float e = 0.f, fk = 0.f, t = 1.f, u = -1.f;
-                        for (int k = 0; k < 9; ++k) {
-                            e += t / (float)(2 * k + 1);
-                            t *= -x2 / (float)(k + 1);
-                        }
-                        for (int k = 1; k < 10; ++k) {
-                            fk += u * (float)(2 * k) / (float)(2 * k + 1);
-                            u *= -x2 / (float)(k + 1);
-                        }
-                        g = alpha * alpha * alpha * c2 * fk;
-                        p = -alpha * c2 * e;
-                    } else {
-                        const float er = erff(x);
-                        g = -er / (s2 * s) + alpha * c2 * expf(-x * x) / s2;
-                        p = -er / s;
-                    }
-                } else {
-                    const float ec = erfcf(x);
-                    g = ec / (s2 * s) + alpha * c2 * expf(-x * x) / s2;
-                    p = ec / s;
+    for (int i = part; i < 125; i += parts) {
+        const int nx = i / 25 - 2, ny = (i / 5) % 5 - 2, nz = i % 5 - 2;
+        const float dx = rx + (float)nx * L, dy = ry + (float)ny * L, dz = rz + (float)nz * L;
+        const float s2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float s = sqrtf(s2);
+        const float x = alpha * s;
+        float g, p;
+        if (i == 62) {
+            if (x < 0.5f) {
+                // erf(x)/x and -erf(x)/x^3 + c2 exp(-x^2)/x^2 as series in x^2
+                const float x2 = x * x;
+                float e = 0.f, fk = 0.f, t = 1.f, u = -1.f;
+                for (int k = 0; k < 9; ++k) {
+                    e += t / (float)(2 * k + 1);
+                    t *= -x2 / (float)(k + 1);
                 }
-                gx = fmaf(-dx, g, gx);
-                gy = fmaf(-dy, g, gy);
-                gz = fmaf(-dz, g, gz);
-                ps += p;
+                for (int k = 1; k < 10; ++k) {
+                    fk += u * (float)(2 * k) / (float)(2 * k + 1);
+                    u *= -x2 / (float)(k + 1);
+                }
+                g = alpha * alpha * alpha * c2 * fk;
+                p = -alpha * c2 * e;
+            } else {
+                const float er = erff(x);
+                g = -er / (s2 * s) + alpha * c2 * expf(-x * x) / s2;
+                p = -er / s;
             }
+        } else {
+            const float ec = erfcf(x);
+            g = ec / (s2 * s) + alpha * c2 * expf(-x * x) / s2;
+            p = ec / s;
         }
+        gx = fmaf(-dx, g, gx);
+        gy = fmaf(-dy, g, gy);
+        gz = fmaf(-dz, g, gz);
+        ps += p;
     }
     const float inv_l = 1.0f / L;
     const float kphi = inv_l * 0.3183098861837907f;     // 1 / (pi L)
     const float kacc = -2.0f * inv_l * inv_l;
-    for (int j = 0; j < nh; ++j) {
+    for (int j = part; j < nh; j += parts) {
         const float4 h = hv[j];
         float sn, cs;
         sincospif(2.0f * (h.x * rx + h.y * ry + h.z * rz) * inv_l, &sn, &cs);
@@ -1175,18 +1171,23 @@ __device__ __forceinline__ void ewald_pair(float rx, float ry, float rz, float M
         gy = fmaf(gs, h.y, gy);
         gz = fmaf(gs, h.z, gz);
     }
-    ps -= 3.14159265358979f / (alpha * alpha * L * L * L);
-    out[0] = M * gx;
-    out[1] = M * gy;
-    out[2] = M * gz;
-    out[3] = -M * ps;
+    if (part == 0) ps -= 3.14159265358979f / (alpha * alpha * L * L * L);
 }
 
-// One warp per GC_EWALD task of the task list: each target owned by a lane,
-// which sums the corrections of all the task's sources with compensation.
+struct EwaldSmem {
+    float4 red[GRAV_WARPS][32][2];      // cross-lane combine: (sum, compensation)
+};
+
+// One warp per GC_EWALD task of the task list.  Targets are taken 32 at a
+// time; with T targets in a pass the warp splits into S = 32 / T lanes per
+// target, lane (t, s) summing the image and reciprocal-vector parts s, s + S,
+// ... of every source with compensation; the S partial sums of a target are
+// combined as compensated pairs in lane order.
 __global__ void __launch_bounds__(GRAV_THREADS) k_ewald(InterArgs a)
 {
+    __shared__ EwaldSmem sm;
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t it = 0;; ++it) {
@@ -1201,25 +1202,45 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_ewald(InterArgs a)
         if (r.kind != GC_EWALD) continue;
         const float4 *As = a.stg_t + (r.tgt_off - a.tgt_base);
         const float4 *Bs = a.stg_s + (r.src_off - a.src_base) + (ti - a.task_base);
-        for (uint32_t o = lane; o < r.nt; o += 32) {
-            const float4 me = As[o];
+        for (uint32_t o0 = 0; o0 < r.nt; o0 += 32) {
+            const int T = (int)min(32u, r.nt - o0);
+            const int S = 32 / T;
+            const int t = lane % T, sl = lane / T;
             float sx = 0.f, sy = 0.f, sz = 0.f, su = 0.f;
             float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f;
-            for (uint32_t q = 0; q < r.ns; ++q) {
-                const float4 src = Bs[q];
-                float v[4];
-                ewald_pair(me.x - src.x, me.y - src.y, me.z - src.z, src.w, a.ewald_L,
-                           a.ewald_h, a.n_ewald_h, v);
-                kahan_add(sx, cx, v[0]);
-                kahan_add(sy, cy, v[1]);
-                kahan_add(sz, cz, v[2]);
-                kahan_add(su, cu, v[3]);
+            if (sl < S) {
+                const float4 me = As[o0 + t];
+                for (uint32_t q = 0; q < r.ns; ++q) {
+                    const float4 src = Bs[q];
+                    float gx = 0.f, gy = 0.f, gz = 0.f, ps = 0.f;
+                    ewald_part(me.x - src.x, me.y - src.y, me.z - src.z, a.ewald_L, a.ewald_h,
+                               a.n_ewald_h, sl, S, gx, gy, gz, ps);
+                    kahan_add(sx, cx, src.w * gx);
+                    kahan_add(sy, cy, src.w * gy);
+                    kahan_add(sz, cz, src.w * gz);
+                    kahan_add(su, cu, -src.w * ps);
+                }
             }
-            const uint32_t pos = a.perm_t[r.tgt_off + o];
-            const uint64_t row = r.row_off + pos;
-            a.res[2 * row] = make_float4(sx, sy, sz, su);
-            a.res[2 * row + 1] = make_float4(cx, cy, cz, cu);
-            a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
+            sm.red[wib][lane][0] = make_float4(sx, sy, sz, su);
+            sm.red[wib][lane][1] = make_float4(cx, cy, cz, cu);
+            __syncwarp();
+            if (sl == 0) {
+                float4 vs = sm.red[wib][t][0], vc = sm.red[wib][t][1];
+                for (int s2 = 1; s2 < S; ++s2) {
+                    const int l = s2 * T + t;
+                    const float4 ws = sm.red[wib][l][0], wc = sm.red[wib][l][1];
+                    comp_add(vs.x, vc.x, ws.x, wc.x);
+                    comp_add(vs.y, vc.y, ws.y, wc.y);
+                    comp_add(vs.z, vc.z, ws.z, wc.z);
+                    comp_add(vs.w, vc.w, ws.w, wc.w);
+                }
+                const uint32_t pos = a.perm_t[r.tgt_off + o0 + t];
+                const uint64_t row = r.row_off + pos;
+                a.res[2 * row] = vs;
+                a.res[2 * row + 1] = vc;
+                a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
+            }
+            __syncwarp();
         }
     }
 }
