@@ -50,7 +50,8 @@ PACK_BYTES_PER_ENTRY = 40
 # DRAM bytes (read + write) per unit of work from ncu captures of the current
 # kernels (None until captured again after a kernel change):
 # k_gravity per interaction, the pack kernels per list entry.
-GRAVITY_DRAM_BYTES_PER_INTERACTION = None
+# profiles/k_gravity_nbody262k.md: 506.6 MB for 2.949e8 interactions (262,144-particle step)
+GRAVITY_DRAM_BYTES_PER_INTERACTION = 506.6e6 / 2.949e8
 # profiles/k_pack_mid_nbody262k.md: 643.1 MB for 3.07e7 entries (262,144-particle step)
 PACK_DRAM_BYTES_PER_ENTRY = 643.1e6 / 3.07e7
 

@@ -565,6 +565,7 @@ static int flush_impl(gc_pool *p, int per_task)
     }
     const uint64_t R = info[0], W = info[1], L = info[2], inter = info[3], max_list = info[4];
     c.n_rows = R;
+    c.max_list = max_list;
 
     GC_TRY(c.tgt_perm.reserve((NT + 1) * 4));
     GC_TRY(c.src_perm.reserve((NS + 1) * 4));

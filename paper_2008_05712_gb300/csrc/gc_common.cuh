@@ -138,6 +138,7 @@ struct FlushCtx {
     uint64_t n_waves = 0;
     std::vector<WaveRange> waves;          // the waves of the batch
     uint64_t msrc = 0;                     // source offset in the merge scratch
+    uint64_t max_list = 0;                 // longest target or source list
     std::vector<TaskRec> host_tasks;       // for gc_read_results
     std::unordered_map<uint64_t, uint64_t> task_index;
     bool host_tasks_valid = false;

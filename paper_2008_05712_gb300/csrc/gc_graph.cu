@@ -189,6 +189,7 @@ extern "C" int gc_graph_capture(gc_pool_t *p, gc_graph_t **out)
     c.n_rows = src.n_rows;
     c.waves = src.waves;
     c.msrc = src.msrc;
+    c.max_list = src.max_list;
     c.n_waves = src.n_waves;
     c.valid = true;
     src.valid = false;    // its arrays now belong to the graph

@@ -1019,17 +1019,31 @@ __global__ void k_sorted_slots(const TaskRec *tasks, uint64_t n, const uint32_t 
 // over the other A atoms), a B atom over cell A.  Each pair is therefore
 // evaluated from both sides with the same operations, so F_j = -F_i exactly
 // (Newton's third law, Section 4.2: interact() updates both patches).
+constexpr int LJ_STAGE = 128;   // atoms of a task staged in shared memory
+constexpr uint32_t LJ_CHUNK = 8; // list entries claimed per queue access
+
 __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
 {
+    __shared__ float4 lj_buf[GRAV_WARPS][LJ_STAGE];
     const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
     const float inv_grid = 1.0f / 2097152.0f;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    // tasks are small: claim LJ_CHUNK list entries per queue access (one
+    // counter shared by every warp would otherwise serialise the kernel)
+    unsigned long long next = 0;
+    uint32_t left = 0;
     for (uint64_t it = 0;; ++it) {
         unsigned long long w = gwarp + it * nwarps;
         if (a.queue) {
-            if (lane == 0) w = atomicAdd(a.queue, 1ull);
-            w = __shfl_sync(0xffffffffu, w, 0);
+            if (left == 0) {
+                if (lane == 0) next = atomicAdd(a.queue, (unsigned long long)LJ_CHUNK);
+                next = __shfl_sync(0xffffffffu, next, 0);
+                left = LJ_CHUNK;
+            }
+            w = next++;
+            --left;
         }
         if (w >= a.n_lj) break;
         const uint32_t ti = a.lj_list[w];
@@ -1039,48 +1053,73 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
         const uint32_t nA = r.nt, nB = self ? 0u : r.ns;
         const float4 *As = a.stg_t + (r.tgt_off - a.tgt_base);
         const float4 *Bs = a.stg_s + (r.src_off - a.src_base) + (ti - a.task_base);
-        const int32_t shx = (int32_t)r.shift[0] * a.edge_grid;
-        const int32_t shy = (int32_t)r.shift[1] * a.edge_grid;
-        const int32_t shz = (int32_t)r.shift[2] * a.edge_grid;
+        if (nA + nB <= (uint32_t)LJ_STAGE) {
+            // every lane reads every partner: stage the task's atoms once
+            for (uint32_t k = lane; k < nA + nB; k += 32)
+                lj_buf[wib][k] = k < nA ? As[k] : Bs[k - nA];
+            __syncwarp();
+            As = &lj_buf[wib][0];
+            Bs = &lj_buf[wib][nA];
+        }
+        // positions in the frame of cell A: A atoms at u, B atoms at u + shift * edge.
+        // Offsets are multiples of 2^-21 below 2^3, so these sums and the
+        // differences below are exact in FP32.
+        const float edge = (float)a.edge_grid * inv_grid;
+        const float fsx = (float)r.shift[0] * edge, fsy = (float)r.shift[1] * edge,
+                    fsz = (float)r.shift[2] * edge;
+        // |r|^2 in FP32 (relative error below 2^-22) decides the cutoff outside
+        // a band of relative width 2^-18 around rc^2; inside it the decision
+        // is taken exactly on the integer grid
+        const float rc2 = (float)((double)a.rc2_grid * (1.0 / 4398046511104.0));
+        const float rc2_lo = rc2 * (1.0f - 3.814697265625e-6f), rc2_hi = rc2 * (1.0f + 3.814697265625e-6f);
         unsigned long long inside = 0;
         for (uint32_t o = lane; o < nA + nB; o += 32) {
             const bool ownA = o < nA;
             float4 me = ownA ? As[o] : Bs[o - nA];
-            // own integer grid position, with the B shift applied to B atoms
-            int32_t mx = __float2int_rn(me.x * 2097152.0f);
-            int32_t my = __float2int_rn(me.y * 2097152.0f);
-            int32_t mz = __float2int_rn(me.z * 2097152.0f);
-            if (!ownA) { mx += shx; my += shy; mz += shz; }
+            if (!ownA) { me.x += fsx; me.y += fsy; me.z += fsz; }
             const float4 *P = ownA ? (self ? As : Bs) : As;
             const uint32_t np = ownA ? (self ? nA : nB) : nA;
             const bool pshift = ownA && !self;   // partners are B atoms
             float sx = 0.f, sy = 0.f, sz = 0.f, su = 0.f;
             float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f;
-            for (uint32_t q = 0; q < np; ++q) {
-                if (self && q == o) continue;
-                float4 pq = P[q];
-                int32_t px = __float2int_rn(pq.x * 2097152.0f);
-                int32_t py = __float2int_rn(pq.y * 2097152.0f);
-                int32_t pz = __float2int_rn(pq.z * 2097152.0f);
-                if (pshift) { px += shx; py += shy; pz += shz; }
-                // displacement partner - own, exact integers (|d| < 2^24)
-                int32_t dx = px - mx, dy = py - my, dz = pz - mz;
-                int64_t r2g = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
-                if (r2g >= a.rc2_grid) continue;
-                if (ownA && (!self || q > o)) ++inside;
-                float rx = (float)dx * inv_grid, ry = (float)dy * inv_grid,
-                      rz = (float)dz * inv_grid;
-                float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                float ir2 = gc_rcp(r2);
-                float s2 = a.lj_sig2 * ir2;
-                float s6 = s2 * s2 * s2;
-                float coef = a.lj_eps24 * fmaf(2.0f, s6 * s6, -s6) * ir2;
-                float u = a.lj_eps4 * fmaf(s6, s6, -s6);
-                // force on own atom: coef * (x_own - x_partner) = -coef * r
-                kahan_add(sx, cx, -coef * rx);
-                kahan_add(sy, cy, -coef * ry);
-                kahan_add(sz, cz, -coef * rz);
-                kahan_add(su, cu, 0.5f * u);
+            // partners four at a time: their loads and cutoff tests overlap
+            for (uint32_t q0 = 0; q0 < np; q0 += 4) {
+                float rxv[4], ryv[4], rzv[4], r2v[4];
+                bool inv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t q = q0 + u;
+                    float4 pq = q < np ? P[q] : me;
+                    if (pshift) { pq.x += fsx; pq.y += fsy; pq.z += fsz; }
+                    // displacement partner - own (exact)
+                    rxv[u] = pq.x - me.x;
+                    ryv[u] = pq.y - me.y;
+                    rzv[u] = pq.z - me.z;
+                    r2v[u] = fmaf(rxv[u], rxv[u], fmaf(ryv[u], ryv[u], rzv[u] * rzv[u]));
+                    inv[u] = q < np && !(self && q == o) && r2v[u] < rc2_hi;
+                    if (inv[u] && r2v[u] >= rc2_lo) {
+                        const int64_t ix = __float2int_rn(rxv[u] * 2097152.0f);
+                        const int64_t iy = __float2int_rn(ryv[u] * 2097152.0f);
+                        const int64_t iz = __float2int_rn(rzv[u] * 2097152.0f);
+                        inv[u] = ix * ix + iy * iy + iz * iz < a.rc2_grid;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!inv[u]) continue;
+                    if (ownA && (!self || q0 + u > o)) ++inside;
+                    const float r2 = r2v[u];
+                    float ir2 = gc_rcp(r2);
+                    float s2 = a.lj_sig2 * ir2;
+                    float s6 = s2 * s2 * s2;
+                    float coef = a.lj_eps24 * fmaf(2.0f, s6 * s6, -s6) * ir2;
+                    float uu = a.lj_eps4 * fmaf(s6, s6, -s6);
+                    // force on own atom: coef * (x_own - x_partner) = -coef * r
+                    kahan_add(sx, cx, -coef * rxv[u]);
+                    kahan_add(sy, cy, -coef * ryv[u]);
+                    kahan_add(sz, cz, -coef * rzv[u]);
+                    kahan_add(su, cu, 0.5f * uu);
+                }
             }
             uint64_t row;
             uint32_t id;
@@ -1099,6 +1138,7 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
         }
         for (int s = 16; s; s >>= 1) inside += __shfl_xor_sync(0xffffffffu, inside, s);
         if (lane == 0 && inside) atomicAdd(a.lj_in, inside);
+        __syncwarp();   // the staged atoms are read before the next task overwrites them
     }
 }
 
@@ -1264,7 +1304,27 @@ __global__ void k_reduce_runs(const uint32_t *runs, const unsigned long long *n_
         uint32_t e = (k + 1 < nr) ? runs[k + 1] : (uint32_t)n_rows;
         uint32_t id = rid[b];
         gcd4 acc = totals[id];
-        for (uint32_t q = b; q < e; ++q) {
+        uint32_t q = b;
+        // four rows' loads in flight at a time; the sums keep the row order
+        for (; q + 4 <= e; q += 4) {
+            uint32_t rw[4];
+            float4 sv[4], cv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rw[u] = row[q + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                sv[u] = res[2 * (uint64_t)rw[u]];
+                cv[u] = res[2 * (uint64_t)rw[u] + 1];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc.x += (double)sv[u].x - (double)cv[u].x;
+                acc.y += (double)sv[u].y - (double)cv[u].y;
+                acc.z += (double)sv[u].z - (double)cv[u].z;
+                acc.w += (double)sv[u].w - (double)cv[u].w;
+            }
+        }
+        for (; q < e; ++q) {
             uint32_t rw = row[q];
             float4 s = res[2 * (uint64_t)rw], c = res[2 * (uint64_t)rw + 1];
             acc.x += (double)s.x - (double)c.x;
@@ -1408,14 +1468,22 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     a.work = c.d_ctr + FC_PACK_WORK;
     GC_CUDA_TRY(cudaMemsetAsync(a.work, 0, 3 * sizeof(unsigned long long), c.s));
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, c.s>>>(a);
-    p->stats.kernel_launches += 2;
-    k_pack_mid<PM_CAP / 2><<<grid_for(a.n_lists, 1, p->num_sms * 9), PM_THREADS,
-                             sizeof(PackSmemMid<PM_CAP / 2>), c.s>>>(a);
-    k_pack_mid<PM_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 6), PM_THREADS,
-                         sizeof(PackSmemMid<PM_CAP>), c.s>>>(a);
-    ++p->stats.kernel_launches;
-    k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
-                           sizeof(PackSmem<PK_CAP>), c.s>>>(a);
+    // the block-per-list classes only when the batch has lists of their sizes
+    if (c.max_list > 32) {
+        ++p->stats.kernel_launches;
+        k_pack_mid<PM_CAP / 2><<<grid_for(a.n_lists, 1, p->num_sms * 9), PM_THREADS,
+                                 sizeof(PackSmemMid<PM_CAP / 2>), c.s>>>(a);
+    }
+    if (c.max_list > PM_CAP / 2) {
+        ++p->stats.kernel_launches;
+        k_pack_mid<PM_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 6), PM_THREADS,
+                             sizeof(PackSmemMid<PM_CAP>), c.s>>>(a);
+    }
+    if (c.max_list > PM_CAP) {
+        ++p->stats.kernel_launches;
+        k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
+                               sizeof(PackSmem<PK_CAP>), c.s>>>(a);
+    }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;
 }
@@ -1463,6 +1531,35 @@ static int grav_setup()
 
 // Persistent grid of the gravity kernel: resident blocks per SM (occupancy
 // API) x SMs -- the number of work units one launch runs at once.
+// Resident blocks of a kernel on the whole GPU (occupancy API), cached.
+template <class K>
+static int resident_blocks(gc_pool *p, K kernel, int &cache)
+{
+    if (cache == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, GRAV_THREADS, 0) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        cache = per_sm;
+    }
+    return cache * p->num_sms;
+}
+
+static int lj_blocks(gc_pool *p)
+{
+    static int per_sm = 0;
+    return resident_blocks(p, k_lj, per_sm);
+}
+
+static int ewald_blocks(gc_pool *p)
+{
+    static int per_sm = 0;
+    return resident_blocks(p, k_ewald, per_sm);
+}
+
 int gc_grav_blocks(gc_pool *p)
 {
     int per_sm = 0;
@@ -1527,13 +1624,14 @@ int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_
         a.n_lj = l1 - l0;
         GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
         const uint64_t need = (a.n_lj + GRAV_WARPS - 1) / GRAV_WARPS;
-        const unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
+        const unsigned g = (unsigned)std::min<uint64_t>(need, (uint64_t)lj_blocks(p));
         ++p->stats.kernel_launches;
         k_lj<<<g, GRAV_THREADS, 0, c.s>>>(a);
         if (p->n_ewald_h > 0) {
             GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
+            const unsigned ge = (unsigned)std::min<uint64_t>(need, (uint64_t)ewald_blocks(p));
             ++p->stats.kernel_launches;
-            k_ewald<<<g, GRAV_THREADS, 0, c.s>>>(a);
+            k_ewald<<<ge, GRAV_THREADS, 0, c.s>>>(a);
         }
     }
     GC_CUDA_TRY(cudaGetLastError());
