@@ -547,6 +547,10 @@ static int flush_impl(gc_pool *p, int per_task)
     c.n_tgt = p->nb_tgt;
     c.n_src = p->nb_src;
     c.batch = p->submitted_batches;
+    c.md_struct = p->md_pending && c.n_tasks == gc_md_tasks(p->md_pend_m, p->md_pend_dim);
+    c.md_m = p->md_pend_m;
+    c.md_dim = p->md_pend_dim;
+    p->md_pending = false;
     c.valid = false;
     c.host_tasks_valid = false;
     c.timing_valid = false;

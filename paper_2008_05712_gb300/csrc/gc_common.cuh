@@ -139,6 +139,8 @@ struct FlushCtx {
     std::vector<WaveRange> waves;          // the waves of the batch
     uint64_t msrc = 0;                     // source offset in the merge scratch
     uint64_t max_list = 0;                 // longest target or source list
+    bool md_struct = false;                // the batch is one MD build: rows reduced per cell
+    int md_m = 0, md_dim = 3;
     std::vector<TaskRec> host_tasks;       // for gc_read_results
     std::unordered_map<uint64_t, uint64_t> task_index;
     bool host_tasks_valid = false;
@@ -169,6 +171,8 @@ struct gc_pool {
     uint64_t nb_tasks = 0, nb_tgt = 0, nb_src = 0;
     DBuf tasks, tgt_ids, src_ids;
     uint64_t submitted_batches = 0;   // index of the pending batch
+    bool md_pending = false;          // the pending batch began with an MD build
+    int md_pend_m = 0, md_pend_dim = 3;
 
     // two flush contexts: batch k runs on ctx[k % 2]; `cur` takes the next
     // flush, `last` holds the last flushed batch (-1: none yet)
@@ -244,6 +248,9 @@ int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_
 int gc_interact_one_task(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,
                          uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
 int gc_scatter(gc_pool *p, FlushCtx &c);
+// ---- MD batches (gc_md.cu) ----------------------------------------------------
+uint64_t gc_md_tasks(int m, int dim);
+int gc_md_reduce(gc_pool *p, FlushCtx &c);
 int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
                       const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
                       const uint64_t *src_off, uint64_t tgt_base, uint64_t src_base,

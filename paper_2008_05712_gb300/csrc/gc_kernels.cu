@@ -1676,6 +1676,7 @@ int gc_scatter(gc_pool *p, FlushCtx &c)
 {
     const uint64_t n_rows = c.n_rows;
     if (n_rows == 0) return GC_OK;
+    if (c.md_struct) return gc_md_reduce(p, c);
     GC_TRY(c.rows_tmp.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(c.rid_sorted.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(c.row_sorted.reserve(n_rows * sizeof(uint32_t)));
@@ -1705,6 +1706,7 @@ int gc_scatter(gc_pool *p, FlushCtx &c)
 int gc_scatter_replay(gc_pool *p, FlushCtx &c)
 {
     if (c.n_rows == 0) return GC_OK;
+    if (c.md_struct) return gc_md_reduce(p, c);
     ++p->stats.kernel_launches;
     k_reduce_runs<<<grid_for(c.n_rows, 256, p->num_sms * 16), 256, 0, c.s>>>(
         c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, c.n_rows, c.rid_sorted.as<uint32_t>(),

@@ -129,7 +129,112 @@ __global__ void k_md_fill(uint64_t nt, int m, int dim, const uint32_t *start,
     }
 }
 
+// Per-id accumulation of one MD build's rows without a sort.  An atom of
+// cell c has one row in each task touching c: c's self task and its
+// half-shell tasks (c's atoms are their targets) and the half-shell tasks of
+// the cells whose offset lands on c (c's atoms are their sources, after the
+// targets).  One warp per cell ranks those tasks by index, so every atom's
+// rows are summed in ascending row order -- the order of the general path,
+// which sorts the rows by id -- with the same FP64 arithmetic: the totals
+// are bit-identical to it.  A lane holds one component of one atom; a
+// cell's rows in one task are consecutive, so the warp reads whole row
+// ranges.  The FP64 adds bound the kernel (the FP64 pipe runs at a small
+// fraction of the FP32 rate), so all 32 lanes carry them.
+template <int DIM>
+__global__ void k_reduce_md(const TaskRec *tasks, uint32_t n_cells, int m,
+                            const uint32_t *row_id, const float4 *res, gcd4 *totals)
+{
+    constexpr int PER = tasks_per_cell(DIM);
+    constexpr int NREF = 2 * PER - 1;
+    static_assert(NREF <= 32, "one lane per task touching the cell");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gw = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = gw; c < n_cells; c += nw) {
+        // lane j < NREF: a task touching c and the first row of c's atoms in it
+        uint64_t tj = ~0ull, rb = 0;
+        if (lane < PER) {
+            tj = (uint64_t)PER * c + (uint64_t)lane;
+            rb = tasks[tj].row_off;
+        } else if (lane < NREF) {
+            const int o = lane - PER + 1;
+            uint32_t cp;
+            if (DIM == 2) {
+                const int x = (int)(c % m), y = (int)(c / m);
+                cp = (uint32_t)((x - c_half_ring[o - 1][0] + m) % m +
+                                m * ((y - c_half_ring[o - 1][1] + m) % m));
+            } else {
+                const int x = (int)(c % m), y = (int)((c / m) % m),
+                          z = (int)(c / ((uint64_t)m * m));
+                cp = (uint32_t)((x - c_half_shell[o - 1][0] + m) % m +
+                                m * ((y - c_half_shell[o - 1][1] + m) % m +
+                                     m * ((z - c_half_shell[o - 1][2] + m) % m)));
+            }
+            tj = (uint64_t)PER * cp + (uint64_t)o;
+            const TaskRec r = tasks[tj];
+            rb = r.row_off + r.nt;
+        }
+        // ranks by task index (distinct); lane r then takes the rank-r task
+        uint32_t rank = 0;
+#pragma unroll
+        for (int k = 0; k < NREF; ++k) rank += __shfl_sync(FULL, tj, k) < tj ? 1u : 0u;
+        int src = 0;
+#pragma unroll
+        for (int r = 0; r < NREF; ++r) {
+            const uint32_t b = __ballot_sync(FULL, lane < NREF && rank == (uint32_t)r);
+            if (lane == r) src = __ffs(b) - 1;
+        }
+        const uint64_t base_r = __shfl_sync(FULL, rb, src);
+        const TaskRec self = tasks[(uint64_t)PER * c];
+        // lane = (atom, component): eight atoms per step keep every lane's
+        // FP64 adds busy (cells hold about fourteen atoms)
+        const int comp = lane & 3;
+        for (uint32_t a0 = 0; a0 < self.nt; a0 += 8) {
+            const uint32_t i = a0 + (uint32_t)(lane >> 2);
+            const bool v = i < self.nt;
+            const uint32_t id = v ? row_id[self.row_off + i] : 0u;
+            double *tot = reinterpret_cast<double *>(totals + id) + comp;
+            double acc = v ? *tot : 0.0;
+#pragma unroll 9
+            for (int r = 0; r < NREF; ++r) {
+                const uint64_t row = __shfl_sync(FULL, base_r, r) + i;
+                if (v) {
+                    const float sv = reinterpret_cast<const float *>(res + 2 * row)[comp];
+                    const float cv = reinterpret_cast<const float *>(res + 2 * row + 1)[comp];
+                    acc += (double)sv - (double)cv;
+                }
+            }
+            if (v) *tot = acc;
+        }
+    }
+}
+
 }  // namespace
+
+uint64_t gc_md_tasks(int m, int dim)
+{
+    const uint64_t cells = dim == 2 ? (uint64_t)m * m : (uint64_t)m * m * m;
+    return (uint64_t)tasks_per_cell(dim) * cells;
+}
+
+int gc_md_reduce(gc_pool *p, FlushCtx &c)
+{
+    const int m = c.md_m;
+    const uint32_t n_cells = c.md_dim == 2 ? (uint32_t)m * m : (uint32_t)m * m * m;
+    const unsigned grid = grid_for((uint64_t)n_cells * 32, 256, p->num_sms * 16);
+    ++p->stats.kernel_launches;
+    if (c.md_dim == 2)
+        k_reduce_md<2><<<grid, 256, 0, c.s>>>(c.tasks.as<TaskRec>(), n_cells, m,
+                                              c.row_id.as<uint32_t>(), c.res.as<float4>(),
+                                              p->d_totals);
+    else
+        k_reduce_md<3><<<grid, 256, 0, c.s>>>(c.tasks.as<TaskRec>(), n_cells, m,
+                                              c.row_id.as<uint32_t>(), c.res.as<float4>(),
+                                              p->d_totals);
+    GC_CUDA_TRY(cudaGetLastError());
+    return GC_OK;
+}
 
 static int build_md(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m, int dim,
                     uint64_t task_id_base, uint64_t info_out[4])
@@ -184,6 +289,7 @@ static int build_md(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m, i
         GC_CUDA_TRY(cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, 8, s));
         return GC_ERR_ARG;
     }
+    const bool batch_start = p->nb_tasks == 0;
     GC_TRY(gc_reserve_batch(p, nt, tot_t, tot_s));
     ++p->stats.kernel_launches;
     k_md_fill<<<grid_for(nt, 256, maxb), 256, 0, s>>>(
@@ -194,6 +300,10 @@ static int build_md(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m, i
     p->nb_tasks += nt;
     p->nb_tgt += tot_t;
     p->nb_src += tot_s;
+    // a batch that holds exactly this build is reduced per cell at its flush
+    p->md_pending = batch_start;
+    p->md_pend_m = m;
+    p->md_pend_dim = dim;
     S.n = n;
     S.m = m;
     S.dim = dim;

@@ -130,3 +130,59 @@ def test_per_task_launches_match(gc, small_md):
     b = p2.results()
     p2.close()
     assert np.array_equal(a, b)
+
+
+def host_md_batch(gc, orc, sysm, dim=3):
+    """The build's tasks as host CSR arrays (oracle cells and task list)."""
+    m = sysm.ncell
+    start, atoms = orc.md_cells(sysm.cell, m ** dim)
+    ta, tb, td, ts = orc.md_tasks(m) if dim == 3 else orc.md_tasks_2d(m)
+    tg = [atoms[start[a]:start[a + 1]] for a in ta]
+    sr = [atoms[start[b]:start[b + 1]] if not s else atoms[:0] for b, s in zip(tb, ts)]
+    to = np.zeros(len(ta) + 1, np.uint64)
+    so = np.zeros(len(ta) + 1, np.uint64)
+    to[1:] = np.cumsum([len(a) for a in tg])
+    so[1:] = np.cumsum([len(a) for a in sr])
+    kinds = np.where(ts != 0, gc.GC_LJ_SELF, gc.GC_LJ_PAIR).astype(np.uint32)
+    return (kinds, to, np.concatenate(tg).astype(np.uint32), so,
+            np.concatenate(sr).astype(np.uint32), td.astype(np.int8).reshape(-1))
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_cell_reduction_matches_sorted_path(gc, orc, small_md, dim):
+    """A batch holding exactly one MD build sums each atom's rows per cell;
+    the same tasks submitted from the host go through the general path (rows
+    sorted by id).  Rows and per-atom totals agree bit for bit, over two
+    consecutive batches (totals accumulate), and a build followed by another
+    task in the same batch takes the general path."""
+    sysm = small_md if dim == 3 else inputs.lj_2d(40, inputs.SEED_BASE + 6, ncell=13)
+    n, m = sysm.n, sysm.ncell
+    ids = np.arange(n, dtype=np.uint32)
+    cell = torch.from_numpy(sysm.cell.astype(np.int32)).cuda()
+    a = make_pool(gc, torch, n, n, lj_rc2=RC2, md_edge=sysm.edge)
+    a.upload(ids, sysm.u)
+    b = make_pool(gc, torch, n, n, lj_rc2=RC2, md_edge=sysm.edge)
+    b.upload(ids, sysm.u)
+    batch = host_md_batch(gc, orc, sysm, dim)
+    for step in range(2):
+        launches0 = a.stats()["kernel_launches"]
+        a.build_md(cell, m, dim=dim)
+        a.flush()
+        b.submit_csr(*batch[:5], shifts=batch[5])
+        b.flush()
+        ra, rb = a.results(), b.results()
+        assert np.array_equal(ra, rb), step
+        assert np.array_equal(a.totals(ids), b.totals(ids)), step
+        assert a.stats()["kernel_launches"] > launches0
+    # build + one more task in the same batch: general path, same totals
+    a.build_md(cell, m, dim=dim)
+    a.submit_csr(np.array([gc.GC_LJ_SELF], np.uint32), np.array([0, 2], np.uint64),
+                 np.array([0, 1], np.uint32), np.zeros(2, np.uint64), np.zeros(0, np.uint32))
+    a.flush()
+    b.submit_csr(*batch[:5], shifts=batch[5])
+    b.submit_csr(np.array([gc.GC_LJ_SELF], np.uint32), np.array([0, 2], np.uint64),
+                 np.array([0, 1], np.uint32), np.zeros(2, np.uint64), np.zeros(0, np.uint32))
+    b.flush()
+    assert np.array_equal(a.totals(ids), b.totals(ids))
+    a.close()
+    b.close()

@@ -1,0 +1,77 @@
+"""GPU parity of the sorted pack (Section 3.2, Fig. 1d) on lists built to
+stress the sort: every size-class boundary (32/33, 1024/1025, 2048/2049),
+lists of one repeated id (no radix pass needed), lists with heavy
+duplication (stability decides the order), lists spanning the whole slot
+range and lists confined to a narrow one.  The pack permutation must equal a
+stable argsort of the entry slots, bit for bit, and the staged forces must
+match the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2008_05712_gb300 import inputs
+from gpu_util import EPS2, TOL, make_pool, per_task_errors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gc():
+    from paper_2008_05712_gb300 import gcharm
+    gcharm.load()
+    return gcharm
+
+
+def adversarial_lists(n_ids, seed):
+    rng = np.random.default_rng(seed)
+    lists = []
+    for size in (31, 32, 33, 34, 500, 1023, 1024, 1025, 1500, 2047, 2048, 2049, 3000):
+        lists.append(rng.integers(0, n_ids, size))                     # full range
+        lists.append(np.full(size, rng.integers(0, n_ids)))            # one id
+        lists.append(rng.integers(0, 7, size) * 997 % n_ids)           # 7 distinct ids
+        base = int(rng.integers(0, n_ids - 70))
+        lists.append(base + rng.integers(0, 64, size))                 # narrow range
+        lists.append(np.sort(rng.integers(0, n_ids, size))[::-1])      # descending
+    return [a.astype(np.uint32) for a in lists]
+
+
+def csr(lists):
+    off = np.zeros(len(lists) + 1, np.uint64)
+    off[1:] = np.cumsum([len(a) for a in lists])
+    return off, np.concatenate(lists)
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_pack_permutation_adversarial(gc, orc, warm):
+    """warm: a first batch references every id, so ids take slots 0..N-1 and
+    the lists below span a 20-bit slot range (four 6-bit radix passes);
+    otherwise only the referenced ids take slots (a 16-bit range)."""
+    n = 1 << 20
+    x = inputs.plummer(n, 91)
+    srcs = adversarial_lists(n, 92)
+    rng = np.random.default_rng(93)
+    # target lists cycle through the same shapes, kept distinct within a list
+    tgts = [rng.choice(n, min(len(s), 2500), replace=False).astype(np.uint32) for s in srcs]
+    to, tg = csr(tgts)
+    so, sr = csr(srcs)
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    if warm:
+        b = pool.submit_csr(np.zeros(1, np.uint32), np.array([0, n], np.uint64),
+                            np.arange(n, dtype=np.uint32), np.array([0, 1], np.uint64),
+                            np.zeros(1, np.uint32))
+        pool.flush()
+        pool.wait(b)
+    b = pool.submit_csr(np.zeros(len(srcs), np.uint32), to, tg, so, sr)
+    pool.flush()
+    pool.wait(b)
+    st, ss = pool.entry_slots()
+    if warm:
+        assert np.array_equal(ss, sr)          # slot = id after the warm batch
+    pt, ps = pool.pack_perm()
+    assert np.array_equal(ps, orc.pack_perm_batch(so, ss))
+    assert np.array_equal(pt, orc.pack_perm_batch(to, st))
+    ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
+    errs = per_task_errors(gc.value(pool.results()), ref, to)
+    assert errs.max() <= TOL, errs.max()
+    pool.close()
