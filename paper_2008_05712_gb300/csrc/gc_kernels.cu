@@ -1318,19 +1318,19 @@ __global__ void k_reduce_runs(const uint32_t *runs, const unsigned long long *n_
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                acc.x += (double)sv[u].x - (double)cv[u].x;
-                acc.y += (double)sv[u].y - (double)cv[u].y;
-                acc.z += (double)sv[u].z - (double)cv[u].z;
-                acc.w += (double)sv[u].w - (double)cv[u].w;
+                acc.x += gc_f2d(sv[u].x) - gc_f2d(cv[u].x);
+                acc.y += gc_f2d(sv[u].y) - gc_f2d(cv[u].y);
+                acc.z += gc_f2d(sv[u].z) - gc_f2d(cv[u].z);
+                acc.w += gc_f2d(sv[u].w) - gc_f2d(cv[u].w);
             }
         }
         for (; q < e; ++q) {
             uint32_t rw = row[q];
             float4 s = res[2 * (uint64_t)rw], c = res[2 * (uint64_t)rw + 1];
-            acc.x += (double)s.x - (double)c.x;
-            acc.y += (double)s.y - (double)c.y;
-            acc.z += (double)s.z - (double)c.z;
-            acc.w += (double)s.w - (double)c.w;
+            acc.x += gc_f2d(s.x) - gc_f2d(c.x);
+            acc.y += gc_f2d(s.y) - gc_f2d(c.y);
+            acc.z += gc_f2d(s.z) - gc_f2d(c.z);
+            acc.w += gc_f2d(s.w) - gc_f2d(c.w);
         }
         totals[id] = acc;
     }

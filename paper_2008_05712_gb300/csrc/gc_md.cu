@@ -10,6 +10,7 @@
 // above (0,0,0), dx most significant), so every pair of neighbouring cells
 // is visited exactly once.
 #include "gc_common.cuh"
+#include "gc_ptx.cuh"
 
 namespace {
 
@@ -202,7 +203,7 @@ __global__ void k_reduce_md(const TaskRec *tasks, uint32_t n_cells, int m,
                 if (v) {
                     const float sv = reinterpret_cast<const float *>(res + 2 * row)[comp];
                     const float cv = reinterpret_cast<const float *>(res + 2 * row + 1)[comp];
-                    acc += (double)sv - (double)cv;
+                    acc += gc_f2d(sv) - gc_f2d(cv);
                 }
             }
             if (v) *tot = acc;

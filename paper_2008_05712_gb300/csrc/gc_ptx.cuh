@@ -86,3 +86,30 @@ __device__ __forceinline__ float gc_rcp(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+
+// Exact float -> double widening on the integer pipe (IEEE 754 binary32 ->
+// binary64: rebias the exponent by 1023 - 127, move the 23 fraction bits to
+// the top of the 52; a subnormal float is normalised first).  Same value as
+// the hardware conversion for every finite input and infinities; NaNs stay
+// NaN.  The per-id accumulation widens two floats per row component, and on
+// this GPU the FP64 pipe, not memory, bounds that step.
+__device__ __forceinline__ double gc_f2d(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t sign = u & 0x80000000u;
+    const uint32_t e = (u >> 23) & 0xFFu;
+    uint32_t m = u & 0x7FFFFFu;
+    uint32_t hi;
+    if (e != 0u && e != 255u) {
+        hi = sign | ((e + 896u) << 20) | (m >> 3);
+    } else if (e == 255u) {
+        hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);   // inf, quiet NaN
+    } else if (m == 0u) {
+        hi = sign;                                                  // signed zero
+    } else {
+        const uint32_t lz = (uint32_t)__clz((int)m) - 8u;           // to bring the top bit to bit 23
+        m = (m << lz) & 0x7FFFFFu;
+        hi = sign | ((897u - lz) << 20) | (m >> 3);
+    }
+    return __hiloint2double((int)hi, (int)(m << 29));
+}

@@ -202,12 +202,13 @@ def test_uneven_200k(gc, orc):
     assert np.array_equal(st_, s2o[tg]) and np.array_equal(ss_, s2o[sr])
     check_pack_sample(pool, so, ss_, sample, src=True)
     check_pack_sample(pool, to, st_, sample, src=False)
-    # per-id totals = FP64 sums of the rows (value s - c) in admission order
+    # per-id totals = FP64 sums of the rows (value s - c) in admission order,
+    # bit for bit (same widening, same order, same FP64 adds)
     ids = rng.choice(np.unique(tg[:: 997]), 50, replace=False)
     sel = np.isin(tg, ids)
     val = rows[sel, :4].astype(np.float64) - rows[sel, 4:].astype(np.float64)
     exp = np.zeros((n, 4))
     np.add.at(exp, tg[sel], val)
     tot = pool.totals(ids.astype(np.uint32))
-    np.testing.assert_allclose(tot, exp[ids], rtol=1e-12, atol=1e-12)
+    assert np.array_equal(tot, exp[ids])
     pool.close()
