@@ -1082,42 +1082,49 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_lj(InterArgs a)
             const bool pshift = ownA && !self;   // partners are B atoms
             float sx = 0.f, sy = 0.f, sz = 0.f, su = 0.f;
             float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f;
-            // partners four at a time: their loads and cutoff tests overlap
-            for (uint32_t q0 = 0; q0 < np; q0 += 4) {
-                float rxv[4], ryv[4], rzv[4], r2v[4];
-                bool inv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
+            // 32 partners at a time: first every cutoff decision (a bit per
+            // partner), then the force of the partners inside, in ascending
+            // order.  About one candidate in seven is inside, so the warp runs
+            // the force code for the most accepted partners of any lane
+            // instead of for every partner slot that some lane accepts.
+            for (uint32_t q0 = 0; q0 < np; q0 += 32) {
+                const uint32_t qn = min(32u, np - q0);
+                uint32_t mask = 0;
+#pragma unroll 4
+                for (uint32_t u = 0; u < qn; ++u) {
                     const uint32_t q = q0 + u;
-                    float4 pq = q < np ? P[q] : me;
+                    float4 pq = P[q];
                     if (pshift) { pq.x += fsx; pq.y += fsy; pq.z += fsz; }
                     // displacement partner - own (exact)
-                    rxv[u] = pq.x - me.x;
-                    ryv[u] = pq.y - me.y;
-                    rzv[u] = pq.z - me.z;
-                    r2v[u] = fmaf(rxv[u], rxv[u], fmaf(ryv[u], ryv[u], rzv[u] * rzv[u]));
-                    inv[u] = q < np && !(self && q == o) && r2v[u] < rc2_hi;
-                    if (inv[u] && r2v[u] >= rc2_lo) {
-                        const int64_t ix = __float2int_rn(rxv[u] * 2097152.0f);
-                        const int64_t iy = __float2int_rn(ryv[u] * 2097152.0f);
-                        const int64_t iz = __float2int_rn(rzv[u] * 2097152.0f);
-                        inv[u] = ix * ix + iy * iy + iz * iz < a.rc2_grid;
+                    const float rx = pq.x - me.x, ry = pq.y - me.y, rz = pq.z - me.z;
+                    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    bool in = !(self && q == o) && r2 < rc2_hi;
+                    if (in && r2 >= rc2_lo) {
+                        const int64_t ix = __float2int_rn(rx * 2097152.0f);
+                        const int64_t iy = __float2int_rn(ry * 2097152.0f);
+                        const int64_t iz = __float2int_rn(rz * 2097152.0f);
+                        in = ix * ix + iy * iy + iz * iz < a.rc2_grid;
                     }
+                    mask |= (uint32_t)in << u;
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (!inv[u]) continue;
-                    if (ownA && (!self || q0 + u > o)) ++inside;
-                    const float r2 = r2v[u];
+                while (mask) {
+                    const uint32_t u = (uint32_t)__ffs(mask) - 1u;
+                    mask &= mask - 1u;
+                    const uint32_t q = q0 + u;
+                    if (ownA && (!self || q > o)) ++inside;
+                    float4 pq = P[q];
+                    if (pshift) { pq.x += fsx; pq.y += fsy; pq.z += fsz; }
+                    const float rx = pq.x - me.x, ry = pq.y - me.y, rz = pq.z - me.z;
+                    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                     float ir2 = gc_rcp(r2);
                     float s2 = a.lj_sig2 * ir2;
                     float s6 = s2 * s2 * s2;
                     float coef = a.lj_eps24 * fmaf(2.0f, s6 * s6, -s6) * ir2;
                     float uu = a.lj_eps4 * fmaf(s6, s6, -s6);
                     // force on own atom: coef * (x_own - x_partner) = -coef * r
-                    kahan_add(sx, cx, -coef * rxv[u]);
-                    kahan_add(sy, cy, -coef * ryv[u]);
-                    kahan_add(sz, cz, -coef * rzv[u]);
+                    kahan_add(sx, cx, -coef * rx);
+                    kahan_add(sy, cy, -coef * ry);
+                    kahan_add(sz, cz, -coef * rz);
                     kahan_add(su, cu, 0.5f * uu);
                 }
             }
