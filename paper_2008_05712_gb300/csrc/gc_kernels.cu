@@ -246,33 +246,62 @@ __device__ __forceinline__ void emit(const PackArgs &a, const PackList &l, uint3
     }
 }
 
-// Lists of at most 32 entries: one warp, bitonic sort of (slot, pos) keys
-// in registers.
+// Bitonic sort of one (slot << 32 | pos) key per lane over groups of G
+// lanes (G = 16 or 32; xor partners stay inside the group), ascending.
+template <int G>
+__device__ __forceinline__ uint64_t bitonic_lanes(uint64_t key, int gl)
+{
+#pragma unroll
+    for (int k = 2; k <= G; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint64_t other = __shfl_xor_sync(0xffffffffu, key, j);
+            const bool up = (gl & k) == 0;
+            const bool lower = (gl & j) == 0;
+            const uint64_t lo = key < other ? key : other;
+            const uint64_t hi = key < other ? other : key;
+            key = (lower == up) ? lo : hi;
+        }
+    }
+    return key;
+}
+
+// Lists of at most 32 entries: bitonic sort of (slot, pos) keys in
+// registers.  A warp takes the two lists of one task; when both hold at most
+// 16 entries (MD cells hold about 14 atoms) each half-warp sorts one of them
+// at once, otherwise the warp sorts them one after the other.
 __global__ void k_pack_small(PackArgs a)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t L = warp; L < a.n_lists; L += nwarps) {
-        PackList l = list_of(a, L);
-        if (l.n == 0 || l.n > 32) continue;
-        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
-        uint64_t key = ~0ull;
-        if ((uint32_t)lane < l.n) key = ((uint64_t)a.slot_of_id[ids[lane]] << 32) | (uint64_t)lane;
-#pragma unroll
-        for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                uint64_t other = __shfl_xor_sync(0xffffffffu, key, j);
-                bool up = (lane & k) == 0;
-                bool lower = (lane & j) == 0;
-                uint64_t lo = key < other ? key : other;
-                uint64_t hi = key < other ? other : key;
-                key = (lower == up) ? lo : hi;
-            }
+    const uint64_t n_pairs = a.n_lists >> 1;     // targets and sources of one task
+    for (uint64_t t = warp; t < n_pairs; t += nwarps) {
+        const uint32_t n0 = list_n(a, 2 * t), n1 = list_n(a, 2 * t + 1);
+        if (n0 <= 16 && n1 <= 16) {
+            const int h = lane >> 4, hl = lane & 15;
+            const PackList l = list_of(a, 2 * t + (uint64_t)h);
+            const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
+            uint64_t key = ~0ull;
+            if ((uint32_t)hl < l.n)
+                key = ((uint64_t)a.slot_of_id[ids[hl]] << 32) | (uint64_t)hl;
+            key = bitonic_lanes<16>(key, hl);
+            if ((uint32_t)hl < l.n)
+                emit(a, l, hl, (uint32_t)(key >> 32), (uint32_t)(key & 0xFFFFFFFFu));
+            continue;
         }
-        if ((uint32_t)lane < l.n)
-            emit(a, l, lane, (uint32_t)(key >> 32), (uint32_t)(key & 0xFFFFFFFFu));
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t n = h ? n1 : n0;
+            if (n == 0 || n > 32) continue;
+            const PackList l = list_of(a, 2 * t + (uint64_t)h);
+            const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
+            uint64_t key = ~0ull;
+            if ((uint32_t)lane < l.n)
+                key = ((uint64_t)a.slot_of_id[ids[lane]] << 32) | (uint64_t)lane;
+            key = bitonic_lanes<32>(key, lane);
+            if ((uint32_t)lane < l.n)
+                emit(a, l, lane, (uint32_t)(key >> 32), (uint32_t)(key & 0xFFFFFFFFu));
+        }
     }
 }
 

@@ -75,3 +75,35 @@ def test_pack_permutation_adversarial(gc, orc, warm):
     errs = per_task_errors(gc.value(pool.results()), ref, to)
     assert errs.max() <= TOL, errs.max()
     pool.close()
+
+
+def test_pack_permutation_small_lists(gc, orc):
+    """Tasks whose two lists both hold at most 16 entries are sorted one list
+    per half-warp; the others one list per warp.  Every combination of the
+    sizes around those limits, with repeated ids, against the oracle."""
+    n = 5000
+    x = inputs.plummer(n, 94)
+    rng = np.random.default_rng(95)
+    sizes = [0, 1, 2, 7, 15, 16, 17, 31, 32]
+    tgts, srcs = [], []
+    for a_ in sizes:
+        for b_ in sizes:
+            if a_ == 0:
+                continue                      # a task has at least one target
+            tgts.append(rng.choice(n, a_, replace=False).astype(np.uint32))
+            srcs.append(rng.integers(0, 40, b_).astype(np.uint32) * 97 % n)
+    to, tg = csr(tgts)
+    so, sr = csr([s.astype(np.uint32) for s in srcs])
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    b = pool.submit_csr(np.zeros(len(tgts), np.uint32), to, tg, so, sr)
+    pool.flush()
+    pool.wait(b)
+    st, ss = pool.entry_slots()
+    pt, ps = pool.pack_perm()
+    assert np.array_equal(pt, orc.pack_perm_batch(to, st))
+    assert np.array_equal(ps, orc.pack_perm_batch(so, ss))
+    ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
+    errs = per_task_errors(gc.value(pool.results()), ref, to)
+    assert errs.max() <= TOL, errs.max()
+    pool.close()
