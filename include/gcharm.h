@@ -556,6 +556,18 @@ int gc_reuse_ablation(gc_pool_t *pool, int reps, double out[7]);
  * small buffer.  Errors: GC_ERR_ARG, GC_ERR_CUDA. */
 int gc_fp32_peak(double *tflops_out, double *ms_out);
 
+/* ---- failure detection ------------------------------------------------------ */
+
+/* Exercise the expiry path of the bounded barrier waits that the interaction
+ * kernels use for their bulk copies: one device thread waits, `polls` polls
+ * long (1 .. 2^24), on a shared-memory barrier that nothing arrives at, and
+ * on expiry sets the pool's timeout status -- the status a stalled copy
+ * would set -- instead of spinning on or trapping.  Enqueued on the pool's
+ * issue stream; the next gc_wait returns GC_ERR_TIMEOUT and clears the
+ * status, and the pool stays usable.  Diagnostics; no counterpart in the
+ * paper.  Errors: GC_ERR_ARG, GC_ERR_CUDA. */
+int gc_check_wait_expiry(gc_pool_t *pool, uint32_t polls);
+
 /* ---- evaluation without allocation -------------------------------------- */
 
 /* Limits of gc_gravity_noalloc (its scratch is a fixed array). */

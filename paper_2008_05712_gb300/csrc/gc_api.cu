@@ -182,6 +182,20 @@ static FlushCtx *ctx_of(gc_pool *p, uint64_t batch)
 
 static FlushCtx *last_ctx(gc_pool *p) { return p->last >= 0 ? &p->ctx[p->last] : nullptr; }
 
+namespace {
+__global__ void k_clear_flags(unsigned long long *flags, unsigned long long mask)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAnd(flags, ~mask);
+}
+}  // namespace
+
+int gc_clear_flags(gc_pool *p, cudaStream_t s, unsigned long long mask)
+{
+    k_clear_flags<<<1, 32, 0, s>>>(p->d_ctr + CTR_FLAGS, mask);
+    GC_CUDA_TRY(cudaGetLastError());
+    return GC_OK;
+}
+
 // Make the issue stream wait for every scatter in flight (per-id totals).
 int order_after_scatters(gc_pool *p)
 {
@@ -564,7 +578,7 @@ static int flush_impl(gc_pool *p, int per_task)
     if (rc != GC_OK) return rc;
     GC_CUDA_TRY(cudaMemcpy(p->h_ctr, p->d_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     if (p->h_ctr[CTR_FLAGS] & GC_FLAG_BAD_TASK) {
-        cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, sizeof(unsigned long long), c.s);
+        gc_clear_flags(p, c.s, GC_FLAG_BAD_TASK);
         return GC_ERR_ARG;
     }
     const uint64_t R = info[0], W = info[1], L = info[2], inter = info[3], max_list = info[4];
@@ -706,8 +720,9 @@ int gc_wait(gc_pool_t *p, uint64_t batch, uint64_t timeout_ns)
         if (cudaMemcpy(&f, p->d_ctr + CTR_FLAGS, sizeof f, cudaMemcpyDeviceToHost) != cudaSuccess)
             return GC_ERR_CUDA;
         if (f & GC_FLAG_TIMEOUT) {
-            unsigned long long keep = f & ~(unsigned long long)GC_FLAG_TIMEOUT;
-            cudaMemcpy(p->d_ctr + CTR_FLAGS, &keep, sizeof keep, cudaMemcpyHostToDevice);
+            if (gc_clear_flags(p, p->s, GC_FLAG_TIMEOUT) != GC_OK ||
+                cudaStreamSynchronize(p->s) != cudaSuccess)
+                return GC_ERR_CUDA;
             return GC_ERR_TIMEOUT;
         }
         return GC_OK;

@@ -239,6 +239,9 @@ int gc_scatter_replay(gc_pool *p, FlushCtx &c);
 int init_ctx(FlushCtx &c, cudaStream_t given);
 void free_ctx(FlushCtx &c);
 int order_after_scatters(gc_pool *p);
+// Clear the status bits `mask` of the pool's flag word, stream-ordered and
+// atomically (kernels of another batch may be setting other bits meanwhile).
+int gc_clear_flags(gc_pool *p, cudaStream_t s, unsigned long long mask);
 int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
                        std::vector<uint32_t> &lj_off);
 int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,

@@ -150,7 +150,11 @@ extern "C" int gc_graph_capture(gc_pool_t *p, gc_graph_t **out)
     {
         unsigned long long f = 0;
         GC_CUDA_TRY(cudaMemcpy(&f, p->d_ctr + CTR_FLAGS, sizeof f, cudaMemcpyDeviceToHost));
-        if (f & GC_FLAG_TIMEOUT) return GC_ERR_TIMEOUT;
+        if (f & GC_FLAG_TIMEOUT) {   // reported once, like gc_wait
+            GC_TRY(gc_clear_flags(p, p->s, GC_FLAG_TIMEOUT));
+            GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+            return GC_ERR_TIMEOUT;
+        }
     }
     gc_graph *g = new gc_graph();
     g->p = p;
@@ -293,7 +297,11 @@ extern "C" int gc_graph_wait(gc_graph_t *g)
     GC_CUDA_TRY(cudaEventSynchronize(g->ev_done));
     unsigned long long f = 0;
     GC_CUDA_TRY(cudaMemcpy(&f, g->p->d_ctr + CTR_FLAGS, sizeof f, cudaMemcpyDeviceToHost));
-    if (f & GC_FLAG_TIMEOUT) return GC_ERR_TIMEOUT;
+    if (f & GC_FLAG_TIMEOUT) {   // reported once, like gc_wait
+        GC_TRY(gc_clear_flags(g->p, g->c.s, GC_FLAG_TIMEOUT));
+        GC_CUDA_TRY(cudaStreamSynchronize(g->c.s));
+        return GC_ERR_TIMEOUT;
+    }
     return GC_OK;
 }
 

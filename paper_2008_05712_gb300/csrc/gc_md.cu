@@ -287,7 +287,7 @@ static int build_md(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m, i
     GC_CUDA_TRY(cudaMemcpyAsync(&flags, p->d_ctr + CTR_FLAGS, 8, cudaMemcpyDeviceToHost, s));
     GC_CUDA_TRY(cudaStreamSynchronize(s));
     if (flags & GC_FLAG_ID_RANGE) {
-        GC_CUDA_TRY(cudaMemsetAsync(p->d_ctr + CTR_FLAGS, 0, 8, s));
+        GC_TRY(gc_clear_flags(p, s, GC_FLAG_ID_RANGE));
         return GC_ERR_ARG;
     }
     const bool batch_start = p->nb_tasks == 0;

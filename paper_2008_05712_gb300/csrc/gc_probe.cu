@@ -1,8 +1,10 @@
-// gc_probe.cu -- FP32 throughput probe: the denominator of the interaction
-// kernel's roofline.  Independent paired-FP32 FMA chains on every lane of
-// every SM, timed with CUDA events.  No counterpart in the paper (it is
-// measurement, not part of the method).
+// gc_probe.cu -- FP32 throughput probe (the denominator of the interaction
+// kernel's roofline: independent paired-FP32 FMA chains on every lane of
+// every SM, timed with CUDA events) and the check of the bounded-wait expiry
+// path.  No counterpart in the paper (measurement and diagnostics, not part
+// of the method).
 #include "gc_common.cuh"
+#include "gc_ptx.cuh"
 
 namespace {
 
@@ -30,7 +32,25 @@ __global__ void __launch_bounds__(PR_THREADS) k_ffma2_probe(float *sink, int ite
     if (acc == 12345.678f) sink[blockIdx.x] = acc;   // keeps the chains live
 }
 
+// One thread waits on a barrier that nothing arrives at; the bounded wait
+// gives up after `polls` polls and records the timeout status.
+__global__ void k_wait_expiry(unsigned long long *flags, uint32_t polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    gc_mbar_init(&bar, 1);
+    if (!gc_mbar_wait_bounded(&bar, 0, polls)) atomicOr(flags, (unsigned long long)GC_FLAG_TIMEOUT);
+}
+
 }  // namespace
+
+extern "C" int gc_check_wait_expiry(gc_pool_t *p, uint32_t polls)
+{
+    if (!p || polls == 0 || polls > (1u << 24)) return GC_ERR_ARG;
+    k_wait_expiry<<<1, 32, 0, p->s>>>(p->d_ctr + CTR_FLAGS, polls);
+    GC_CUDA_TRY(cudaGetLastError());
+    return GC_OK;
+}
 
 extern "C" int gc_fp32_peak(double *tflops_out, double *ms_out)
 {

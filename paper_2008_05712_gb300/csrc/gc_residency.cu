@@ -419,10 +419,12 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
     GC_CUDA_TRY(cudaStreamSynchronize(p->s));
     GC_CUDA_TRY(cudaGetLastError());
 
-    unsigned long long flags = p->h_ctr[CTR_FLAGS];
+    // this step's own status bits; a timeout of an earlier batch stays for
+    // gc_wait to report
+    const unsigned long long flags = p->h_ctr[CTR_FLAGS] & (GC_FLAG_UNKNOWN_ID | GC_FLAG_ID_RANGE);
     if (flags) {
-        GC_CUDA_TRY(cudaMemsetAsync(ctr + CTR_FLAGS, 0, sizeof(unsigned long long), p->s));
-        if (flags & (GC_FLAG_UNKNOWN_ID | GC_FLAG_ID_RANGE)) return GC_ERR_UNKNOWN_ID;
+        GC_TRY(gc_clear_flags(p, p->s, GC_FLAG_UNKNOWN_ID | GC_FLAG_ID_RANGE));
+        return GC_ERR_UNKNOWN_ID;
     }
     const uint64_t U = p->h_ctr[CTR_UNIQUE], H = p->h_ctr[CTR_HITS];
     const uint64_t M = p->h_ctr[CTR_MISSES], F = p->h_ctr[CTR_FREE];

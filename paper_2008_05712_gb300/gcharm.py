@@ -149,6 +149,7 @@ _SIGS = {
     "gc_serve": [P, U64, P, P, P, P, P, P, P, C.POINTER(GcServeConfig), P, P,
                  C.POINTER(GcServeReport)],
     "gc_fp32_peak": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "gc_check_wait_expiry": [C.c_void_p, C.c_uint32],
     "gc_set_tuning": [P, C.POINTER(GcTuning)],
     "gc_get_tuning": [P, C.POINTER(GcTuning)],
     "gc_autotune": [P, C.c_int, C.POINTER(GcTuning), P],
@@ -435,6 +436,11 @@ class Pool:
             with open(cache, "w") as f:
                 json.dump(data, f, indent=1, sort_keys=True)
         return choice, times
+
+    def check_wait_expiry(self, polls=1024):
+        """Run the bounded barrier wait's expiry path on the issue stream: the
+        next wait() raises GcError(GC_ERR_TIMEOUT) and the pool stays usable."""
+        _check(self.lib.gc_check_wait_expiry(self.h, int(polls)), "gc_check_wait_expiry")
 
     def reuse_ablation(self, reps=3):
         """Fig. 3 of Section 3.2 on the last batch (gc_reuse_ablation)."""

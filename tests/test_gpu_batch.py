@@ -218,3 +218,35 @@ def test_edge_cases(gc, orc):
     assert np.all(got[4, :3] == 0)               # self term: dx = 0
     assert got[4, 3] == pytest.approx(ref[4, 3], rel=1e-6)
     pool.close()
+
+
+def test_wait_expiry_reported_and_pool_stays_usable(gc, orc):
+    """The bounded barrier wait of the interaction kernels gives up instead of
+    hanging: its expiry path (a wait on a barrier nothing arrives at) sets
+    the timeout status, the next wait reports GC_ERR_TIMEOUT once, and the
+    same pool then runs batches that match the oracle."""
+    x, to, tg, so, sr = uneven(n_ids=4000, n_tasks=30, seed=41, s_range=(1, 500))
+    n = x.shape[0]
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
+    b0 = submit_gravity(pool, to, tg, so, sr)
+    pool.flush()
+    pool.wait(b0)
+    pool.check_wait_expiry(2048)
+    b1 = submit_gravity(pool, to, tg, so, sr)
+    pool.flush()
+    with pytest.raises(gc.GcError) as e:
+        pool.wait(b1)
+    assert e.value.code == gc.GC_ERR_TIMEOUT
+    pool.wait(b1)                       # the status was cleared by the report
+    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    b2 = submit_gravity(pool, to, tg, so, sr)
+    pool.flush()
+    pool.wait(b2)
+    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    for bad in (0, (1 << 24) + 1):
+        with pytest.raises(gc.GcError) as e:
+            pool.check_wait_expiry(bad)
+        assert e.value.code == gc.GC_ERR_ARG
+    pool.close()

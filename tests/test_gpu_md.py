@@ -186,3 +186,24 @@ def test_cell_reduction_matches_sorted_path(gc, orc, small_md, dim):
     assert np.array_equal(a.totals(ids), b.totals(ids))
     a.close()
     b.close()
+
+
+def test_bad_cell_index_reported_and_pool_stays_usable(gc, orc, small_md):
+    """A cell index outside the m^3 grid is an argument error of the build;
+    the pool then builds and runs the valid system."""
+    sysm = small_md
+    n, m = sysm.n, sysm.ncell
+    pool = make_pool(gc, torch, n, n, lj_rc2=RC2, md_edge=sysm.edge)
+    pool.upload(np.arange(n, dtype=np.uint32), sysm.u)
+    bad = sysm.cell.astype(np.int32).copy()
+    bad[n // 2] = m ** 3
+    with pytest.raises(gc.GcError) as e:
+        pool.build_md(torch.from_numpy(bad).cuda(), m)
+    assert e.value.code == gc.GC_ERR_ARG
+    pool.build_md(torch.from_numpy(sysm.cell.astype(np.int32)).cuda(), m)
+    pool.flush()
+    start, atoms = pool.md_cells(n, m)
+    s0, a0 = orc.md_cells(sysm.cell, m ** 3)
+    assert np.array_equal(start, s0) and np.array_equal(atoms, a0)
+    assert pool.stats()["lj_pairs_in_cutoff"] > 0
+    pool.close()
