@@ -681,14 +681,17 @@ def main():
     pinned = torch.empty((K, n, 4), dtype=torch.float32, pin_memory=True)
     pinned.copy_(X[W:W + K].cpu())
     hx = pinned.numpy()
+    ids_pin_t = torch.from_numpy(ids_np).pin_memory()
+    tot_pin_t = torch.empty((n, 4), dtype=torch.float64, pin_memory=True)
+    ids_pin, tot_pin = ids_pin_t.numpy(), tot_pin_t.numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(K):
-        pool.upload(ids_np, hx[k])               # ids + values H2D
+        pool.upload(ids_pin, hx[k])              # ids + values H2D
         pool.reset_totals()
         pool.build_nbody(hx[k], BUCKET, *THETA)  # values H2D again
         pool.flush()
-        tot = pool.totals(ids_np)                # ids H2D, totals D2H
+        tot = pool.totals(ids_pin, out=tot_pin)  # ids H2D, totals D2H
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": interactions / K * K / e2e_s if K else 0.0, "unit": "interactions/s",

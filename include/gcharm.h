@@ -138,20 +138,22 @@ typedef struct {
 /* ---- pool lifetime and data -------------------------------------------- */
 
 /* Create a pool: device slots, the chare table (id -> slot), a pinned host
- * mirror of every id's value, and per-id FP64 totals.  *out receives the
- * handle.  Errors: GC_ERR_ARG (zero capacities, eps2 <= 0, bad LJ values),
+ * mirror holding the value of every id that is not resident (a slot's value
+ * is written back to it when the id is evicted), and per-id FP64 totals.
+ * *out receives the handle.  Errors: GC_ERR_ARG (zero capacities, eps2 <= 0, bad LJ values),
  * GC_ERR_OOM, GC_ERR_CUDA. */
 int gc_pool_create(const gc_config *cfg, gc_pool_t **out);
 
 /* Release everything the pool owns.  Waits for its stream first. */
 int gc_pool_destroy(gc_pool_t *pool);
 
-/* Store values for ids (host arrays, n ids and 4n floats).  A resident id is
- * overwritten in its slot (an update, not a miss); a non-resident id is
- * stored in the host mirror and fetched at the next flush that references
- * it.  Duplicate ids in one call: one of the values wins.  Waits for the
- * pool's stream before writing the mirror.  Errors: GC_ERR_ARG (id >=
- * id_capacity), GC_ERR_CUDA. */
+/* Store values for ids (host arrays, n ids and 4n floats; copied before the
+ * call returns).  A resident id is overwritten in its slot (an update, not a
+ * miss); a non-resident id is stored in the host mirror and fetched at the
+ * next flush that references it.  Duplicate ids in one call: one of the
+ * values wins.  Runs on the pool's stream, after the pack of every batch
+ * already flushed.  Errors: GC_ERR_ARG (id >= id_capacity; nothing is
+ * stored), GC_ERR_CUDA. */
 int gc_pool_upload(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
                    uint64_t n);
 

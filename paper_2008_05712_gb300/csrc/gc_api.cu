@@ -374,18 +374,12 @@ int gc_pool_upload(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_
 {
     if (!p || (n && (!ids || !xyzm))) return GC_ERR_ARG;
     if (n == 0) return GC_OK;
-    for (uint64_t i = 0; i < n; ++i)
-        if (ids[i] >= p->cfg.id_capacity) return GC_ERR_ARG;
-    // no device work may be reading the mirror meanwhile
-    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[0].s));
-    GC_CUDA_TRY(cudaStreamSynchronize(p->ctx[1].s));
-    bool run = true;
-    for (uint64_t i = 0; i < n && run; ++i) run = ids[i] == ids[0] + i;
-    if (run)
-        std::memcpy(&p->h_mirror[ids[0]], xyzm, n * sizeof(float4));
-    else
-        for (uint64_t i = 0; i < n; ++i)
-            std::memcpy(&p->h_mirror[ids[i]], xyzm + 4 * i, sizeof(float4));
+    uint32_t bad = 0;
+    for (uint64_t i = 0; i < n; ++i) bad |= (uint64_t)ids[i] >= p->cfg.id_capacity;
+    if (bad) return GC_ERR_ARG;
+    // the device writes resident ids' slots and non-resident ids' mirror
+    // entries (a resident id's mirror entry is refreshed when it is evicted),
+    // in stream order after the batches already flushed have packed
     GC_TRY(grow_keep(p->io_a, n * sizeof(uint32_t) + 16, 0, p->s));
     GC_TRY(grow_keep(p->io_b, n * sizeof(float4) + 16, 0, p->s));
     int rc = GC_OK;
@@ -394,7 +388,7 @@ int gc_pool_upload(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_
         cudaMemcpyAsync(p->io_b.p, xyzm, n * sizeof(float4), cudaMemcpyHostToDevice, p->s) !=
             cudaSuccess)
         rc = GC_ERR_CUDA;
-    if (rc == GC_OK) rc = gc_launch_upload(p, p->io_a.as<uint32_t>(), p->io_b.as<float4>(), n, 0);
+    if (rc == GC_OK) rc = gc_launch_upload(p, p->io_a.as<uint32_t>(), p->io_b.as<float4>(), n, 1);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
     p->stats.h2d_bytes += n * (sizeof(uint32_t) + sizeof(float4));
     return rc;

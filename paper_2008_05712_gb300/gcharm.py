@@ -369,9 +369,15 @@ class Pool:
         _check(self.lib.gc_read_results(self.h, _p(ti), ti.shape[0], _p(out)), "gc_read_results")
         return out
 
-    def totals(self, ids):
+    def totals(self, ids, out=None):
+        """(n, 4) float64 per-id totals; `out` (optional) is a C-contiguous
+        float64 array of that shape to fill, e.g. in pinned memory."""
         ids = np.ascontiguousarray(ids, np.uint32)
-        out = np.empty((ids.shape[0], 4), np.float64)
+        if out is None:
+            out = np.empty((ids.shape[0], 4), np.float64)
+        elif (out.dtype != np.float64 or out.shape != (ids.shape[0], 4) or
+              not out.flags["C_CONTIGUOUS"]):
+            raise ValueError("out must be a C-contiguous float64 array of shape (n, 4)")
         _check(self.lib.gc_read_totals(self.h, _p(ids), ids.shape[0], _p(out)), "gc_read_totals")
         return out
 
