@@ -622,7 +622,7 @@ static int flush_impl(gc_pool *p, int per_task)
     }
     GC_TRY(c.stg_tgt.reserve((max_wt + 1) * sizeof(float4)));
     GC_TRY(c.stg_src.reserve((max_ws + 1) * sizeof(float4)));
-    if (max_list > 4096) {
+    if (max_list > 16384) {   // lists beyond one shared-memory sort: chunk + merge
         GC_TRY(c.merge_a.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
         GC_TRY(c.merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
     }

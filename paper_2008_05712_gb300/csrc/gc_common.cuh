@@ -49,8 +49,8 @@ enum {
     FC_MAXLIST,         // longest list of the batch
     FC_RUNS,            // distinct ids among result rows
     FC_LJ_IN,           // LJ pairs inside the cutoff
-    FC_PACK_WORK,       // list claims of the block-per-list pack kernels (3 counters)
-    FC_COUNT = FC_PACK_WORK + 3
+    FC_PACK_WORK,       // list claims of the block-per-list pack kernels (4 counters)
+    FC_COUNT = FC_PACK_WORK + 4
 };
 
 // One task as the kernels see it (48 bytes).

@@ -130,6 +130,7 @@ __global__ void k_wu_gather(const GravWU *wu, const uint32_t *idx, uint64_t n, G
 // The extra float4 per task keeps every padded segment inside its own range.
 
 constexpr int PK_CAP = 4096;          // entries sorted in shared memory at once
+constexpr int PK_CAP_HUGE = 16384;    // the same, one block per SM (about 200 KB)
 constexpr int PK_CAP_SMALL = 2048;    // lists up to this size use half the shared memory
 constexpr int PK_THREADS = 256;
 constexpr int PK_WARPS = PK_THREADS / 32;
@@ -321,12 +322,12 @@ __device__ __forceinline__ uint32_t warp_match(uint32_t d, uint32_t valid)
     return m;
 }
 
-template <int CAP>
+template <int CAP, int NW = PK_WARPS>
 struct PackSmem {
     uint32_t ka[CAP], kb[CAP];           // slots
     uint16_t pa[CAP], pb[CAP];           // list positions (within a chunk)
-    uint32_t hist[PK_WARPS][256];        // per (warp, digit) counts, then offsets
-    uint32_t wsum[PK_WARPS];
+    uint32_t hist[NW][256];              // per (warp, digit) counts, then offsets
+    uint32_t wsum[NW];
     int skip;
 };
 
@@ -353,19 +354,23 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *wsu
 // by label ballots, so equal digits keep their order (warp by warp,
 // chunk by chunk, lane by lane).  Returns 0 if the result is in ka/pa, 1 if
 // in kb/pb.
-template <int CAP>
-__device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
+// NW warps (256 threads or more); threads 0..255 own one digit each in the
+// scans.
+template <int CAP, int NW>
+__device__ int block_radix_sort(PackSmem<CAP, NW> &sm, int n, int passes)
 {
+    static_assert(NW >= 8, "one thread per digit");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const int per = (((n + PK_WARPS - 1) / PK_WARPS) + 31) & ~31;
+    const bool digit_owner = threadIdx.x < 256;
+    const int per = (((n + NW - 1) / NW) + 31) & ~31;
     const int b0 = min(n, w * per), b1 = min(n, b0 + per);
     uint32_t *ka = sm.ka, *kb = sm.kb;
     uint16_t *pa = sm.pa, *pb = sm.pb;
     int flip = 0;
     for (int pass = 0; pass < passes; ++pass) {
         const int sh = 8 * pass;
-        for (int i = threadIdx.x; i < 256 * PK_WARPS; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
+        for (int i = threadIdx.x; i < 256 * NW; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
         if (threadIdx.x == 0) sm.skip = 0;
         __syncthreads();
         for (int c = b0; c < b1; c += 32) {
@@ -375,14 +380,16 @@ __device__ int block_radix_sort(PackSmem<CAP> &sm, int n, int passes)
         }
         __syncthreads();
         uint32_t s = 0;
-        for (int q = 0; q < PK_WARPS; ++q) s += sm.hist[q][threadIdx.x];
-        if (s == (uint32_t)n) sm.skip = 1;       // one digit value: pass is the identity
+        if (digit_owner)
+            for (int q = 0; q < NW; ++q) s += sm.hist[q][threadIdx.x];
+        if (digit_owner && s == (uint32_t)n) sm.skip = 1;   // one digit value: identity pass
         uint32_t run = block_excl_scan256(s, sm.wsum);
-        for (int q = 0; q < PK_WARPS; ++q) {
-            uint32_t c = sm.hist[q][threadIdx.x];
-            sm.hist[q][threadIdx.x] = run;
-            run += c;
-        }
+        if (digit_owner)
+            for (int q = 0; q < NW; ++q) {
+                uint32_t c = sm.hist[q][threadIdx.x];
+                sm.hist[q][threadIdx.x] = run;
+                run += c;
+            }
         __syncthreads();
         if (sm.skip) continue;
         for (int c = b0; c < b1; c += 32) {
@@ -609,22 +616,28 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
     }
 }
 
-// Lists of more than 32 entries: one block.  Up to PK_CAP entries are
-// radix-sorted in shared memory; longer lists are sorted in chunks of PK_CAP
-// and merged pairwise in global scratch (keys (slot << 32 | pos) are
-// unique, so an element's output index is its rank in its own run plus its
-// rank in the other run).
-// CAP = PK_CAP_SMALL handles lists of 33..PK_CAP_SMALL entries; CAP = PK_CAP
-// handles every longer list (chunked beyond PK_CAP).
+// Lists of more than 2048 entries: one block per list, radix-sorted in
+// shared memory.  CAP = PK_CAP takes lists of 2049..4096 entries (about 56 KB
+// of shared memory, three blocks per SM); CAP = PK_CAP_HUGE every longer
+// list (about 200 KB, one block per SM), and a list beyond PK_CAP_HUGE is
+// sorted in chunks of PK_CAP_HUGE that are merged pairwise in global scratch
+// (keys (slot << 32 | pos) are unique, so an element's output index is its
+// rank in its own run plus its rank in the other run).
+// Warps of each block-sort class: the largest lists take a whole SM.
+template <int CAP> struct PackLargeWarps { static constexpr int value = PK_WARPS; };
+template <> struct PackLargeWarps<PK_CAP_HUGE> { static constexpr int value = 16; };
+
 template <int CAP>
-__global__ void __launch_bounds__(PK_THREADS) k_pack_large(PackArgs a)
+__global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(PackArgs a)
 {
+    constexpr int NW = PackLargeWarps<CAP>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PackSmem<CAP> &sm = *reinterpret_cast<PackSmem<CAP> *>(smem_raw);
-    const uint32_t lo_n = (CAP == PK_CAP) ? (uint32_t)PM_CAP : 32u;
-    const uint32_t hi_n = (CAP == PK_CAP) ? 0xFFFFFFFFu : (uint32_t)CAP;
+    PackSmem<CAP, NW> &sm = *reinterpret_cast<PackSmem<CAP, NW> *>(smem_raw);
+    static_assert(CAP == PK_CAP || CAP == PK_CAP_HUGE, "two block-sort classes");
+    const uint32_t lo_n = (CAP == PK_CAP) ? (uint32_t)PM_CAP : (uint32_t)PK_CAP;
+    const uint32_t hi_n = (CAP == PK_CAP) ? (uint32_t)PK_CAP : 0xFFFFFFFFu;
     __shared__ ListClaim cl;
-    while (claim_lists(a, a.work + 2, lo_n, hi_n, cl))
+    while (claim_lists(a, a.work + (CAP == PK_CAP ? 2 : 3), lo_n, hi_n, cl))
     for (uint32_t ci = 0; ci < cl.cnt; ++ci) {
         PackList l = list_of(a, cl.base + cl.off[ci]);
         const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
@@ -1471,6 +1484,9 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
         GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large<PK_CAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(PackSmem<PK_CAP>)));
+        GC_CUDA_TRY(cudaFuncSetAttribute(
+            k_pack_large<PK_CAP_HUGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)sizeof(PackSmem<PK_CAP_HUGE, PackLargeWarps<PK_CAP_HUGE>::value>)));
         GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_mid<PM_CAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(PackSmemMid<PM_CAP>)));
@@ -1502,7 +1518,7 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     a.msrc = msrc;
     ++p->stats.kernel_launches;
     a.work = c.d_ctr + FC_PACK_WORK;
-    GC_CUDA_TRY(cudaMemsetAsync(a.work, 0, 3 * sizeof(unsigned long long), c.s));
+    GC_CUDA_TRY(cudaMemsetAsync(a.work, 0, 4 * sizeof(unsigned long long), c.s));
     k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, c.s>>>(a);
     // the block-per-list classes only when the batch has lists of their sizes
     if (c.max_list > 32) {
@@ -1519,6 +1535,12 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
         ++p->stats.kernel_launches;
         k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
                                sizeof(PackSmem<PK_CAP>), c.s>>>(a);
+    }
+    if (c.max_list > PK_CAP) {
+        ++p->stats.kernel_launches;
+        constexpr int nw = PackLargeWarps<PK_CAP_HUGE>::value;
+        k_pack_large<PK_CAP_HUGE><<<grid_for(a.n_lists, 1, p->num_sms), nw * 32,
+                                    sizeof(PackSmem<PK_CAP_HUGE, nw>), c.s>>>(a);
     }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;

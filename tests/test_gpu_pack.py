@@ -1,5 +1,6 @@
 """GPU parity of the sorted pack (Section 3.2, Fig. 1d) on lists built to
-stress the sort: every size-class boundary (32/33, 1024/1025, 2048/2049),
+stress the sort: every size-class boundary (32/33, 1024/1025, 2048/2049,
+4096/4097, 16384/16385 and a list merged from three sorted chunks),
 lists of one repeated id (no radix pass needed), lists with heavy
 duplication (stability decides the order), lists spanning the whole slot
 range and lists confined to a narrow one.  The pack permutation must equal a
@@ -25,7 +26,8 @@ def gc():
 def adversarial_lists(n_ids, seed):
     rng = np.random.default_rng(seed)
     lists = []
-    for size in (31, 32, 33, 34, 500, 1023, 1024, 1025, 1500, 2047, 2048, 2049, 3000):
+    for size in (31, 32, 33, 34, 500, 1023, 1024, 1025, 1500, 2047, 2048, 2049, 3000,
+                 4095, 4096, 4097, 10000, 16384, 16385, 40000):
         lists.append(rng.integers(0, n_ids, size))                     # full range
         lists.append(np.full(size, rng.integers(0, n_ids)))            # one id
         lists.append(rng.integers(0, 7, size) * 997 % n_ids)           # 7 distinct ids
@@ -51,7 +53,8 @@ def test_pack_permutation_adversarial(gc, orc, warm):
     srcs = adversarial_lists(n, 92)
     rng = np.random.default_rng(93)
     # target lists cycle through the same shapes, kept distinct within a list
-    tgts = [rng.choice(n, min(len(s), 2500), replace=False).astype(np.uint32) for s in srcs]
+    tgts = [rng.choice(n, min(len(s), 2500) if len(s) <= 3000 else 48, replace=False)
+            .astype(np.uint32) for s in srcs]
     to, tg = csr(tgts)
     so, sr = csr(srcs)
     pool = make_pool(gc, torch, n, n)
