@@ -464,6 +464,7 @@ __device__ __forceinline__ uint32_t block_excl_scan128(uint32_t v, uint32_t *wsu
 // and staging.  Entries k = threadIdx.x + PM_THREADS * j, so the lanes of a
 // warp hold consecutive k: in the paired source layout lanes 2i and 2i+1
 // swap halves with one shuffle pair and each writes a whole float4.
+template <int NT = PM_THREADS>
 __device__ __forceinline__ void emit_block(const PackArgs &a, const PackList &l, int n,
                                            const uint32_t *ka, const uint16_t *pa)
 {
@@ -471,18 +472,18 @@ __device__ __forceinline__ void emit_block(const PackArgs &a, const PackList &l,
     const int h = lane & 1;
     // paired lists also run the (zero) pad lane of an odd list
     const int n_run = l.paired ? ((n + 1) & ~1) : n;
-    for (int base = 0; base < n_run; base += PM_THREADS * PM_U) {
+    for (int base = 0; base < n_run; base += NT * PM_U) {
         float4 v[PM_U];
 #pragma unroll
         for (int j = 0; j < PM_U; ++j) {
-            const int k = base + threadIdx.x + PM_THREADS * j;
+            const int k = base + threadIdx.x + NT * j;
             v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (k < n) v[j] = a.pool[ka[k]];
         }
 #pragma unroll
         for (int j = 0; j < PM_U; ++j) {
-            const int k = base + threadIdx.x + PM_THREADS * j;
-            if (base + PM_THREADS * j >= n_run) break;      // uniform over the block
+            const int k = base + threadIdx.x + NT * j;
+            if (base + NT * j >= n_run) break;      // uniform over the block
             if (k < n) (l.src ? a.perm_s : a.perm_t)[l.off + k] = pa[k];
             if (!l.paired) {
                 if (k < n) (l.src ? a.stg_s : a.stg_t)[l.stg + k] = v[j];
@@ -623,9 +624,39 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
 // sorted in chunks of PK_CAP_HUGE that are merged pairwise in global scratch
 // (keys (slot << 32 | pos) are unique, so an element's output index is its
 // rank in its own run plus its rank in the other run).
+// Slots of entries c0 .. c0+cn-1 of a list into ka (positions 0..cn-1 in
+// pa): PM_U id reads, then PM_U slot lookups, in flight per thread.
+template <int NT>
+__device__ __forceinline__ void load_slots(const PackArgs &a, const uint32_t *ids, int cn,
+                                           uint32_t *ka, uint16_t *pa)
+{
+    for (int base = 0; base < cn; base += NT * PM_U) {
+        uint32_t s[PM_U];
+#pragma unroll
+        for (int j = 0; j < PM_U; ++j) {
+            const int k = base + threadIdx.x + NT * j;
+            s[j] = k < cn ? __ldg(ids + k) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < PM_U; ++j) {
+            const int k = base + threadIdx.x + NT * j;
+            if (k < cn) s[j] = __ldg(a.slot_of_id + s[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < PM_U; ++j) {
+            const int k = base + threadIdx.x + NT * j;
+            if (k < cn) {
+                ka[k] = s[j];
+                pa[k] = (uint16_t)k;
+            }
+        }
+    }
+}
+
 // Warps of each block-sort class: the largest lists take a whole SM.
-template <int CAP> struct PackLargeWarps { static constexpr int value = PK_WARPS; };
-template <> struct PackLargeWarps<PK_CAP_HUGE> { static constexpr int value = 16; };
+constexpr int PK_NW_MID = 16, PK_NW_HUGE = 16;
+template <int CAP> struct PackLargeWarps { static constexpr int value = PK_NW_MID; };
+template <> struct PackLargeWarps<PK_CAP_HUGE> { static constexpr int value = PK_NW_HUGE; };
 
 template <int CAP>
 __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(PackArgs a)
@@ -642,15 +673,10 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
         PackList l = list_of(a, cl.base + cl.off[ci]);
         const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
         if (l.n <= (uint32_t)CAP) {
-            for (int k = threadIdx.x; k < (int)l.n; k += blockDim.x) {
-                sm.ka[k] = a.slot_of_id[ids[k]];
-                sm.pa[k] = (uint16_t)k;
-            }
+            load_slots<NW * 32>(a, ids, (int)l.n, sm.ka, sm.pa);
             __syncthreads();
             int f = block_radix_sort(sm, (int)l.n, a.passes);
-            const uint32_t *kk = f ? sm.kb : sm.ka;
-            const uint16_t *pp = f ? sm.pb : sm.pa;
-            for (int k = threadIdx.x; k < (int)l.n; k += blockDim.x) emit(a, l, k, kk[k], pp[k]);
+            emit_block<NW * 32>(a, l, (int)l.n, f ? sm.kb : sm.ka, f ? sm.pb : sm.pa);
             __syncthreads();
             continue;
         }
@@ -660,10 +686,7 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
         const uint32_t n = l.n;
         for (uint32_t c0 = 0; c0 < n; c0 += CAP) {
             const int cn = (int)min((uint32_t)CAP, n - c0);
-            for (int k = threadIdx.x; k < cn; k += blockDim.x) {
-                sm.ka[k] = a.slot_of_id[ids[c0 + k]];
-                sm.pa[k] = (uint16_t)k;
-            }
+            load_slots<NW * 32>(a, ids + c0, cn, sm.ka, sm.pa);
             __syncthreads();
             int f = block_radix_sort(sm, cn, a.passes);
             const uint32_t *kk = f ? sm.kb : sm.ka;
@@ -1481,9 +1504,9 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     if (t1 <= t0) return GC_OK;
     static bool attr_set = false;
     if (!attr_set) {
-        GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_large<PK_CAP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(PackSmem<PK_CAP>)));
+        GC_CUDA_TRY(cudaFuncSetAttribute(
+            k_pack_large<PK_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            (int)sizeof(PackSmem<PK_CAP, PackLargeWarps<PK_CAP>::value>)));
         GC_CUDA_TRY(cudaFuncSetAttribute(
             k_pack_large<PK_CAP_HUGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
             (int)sizeof(PackSmem<PK_CAP_HUGE, PackLargeWarps<PK_CAP_HUGE>::value>)));
@@ -1533,8 +1556,9 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     }
     if (c.max_list > PM_CAP) {
         ++p->stats.kernel_launches;
-        k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), PK_THREADS,
-                               sizeof(PackSmem<PK_CAP>), c.s>>>(a);
+        constexpr int nw = PackLargeWarps<PK_CAP>::value;
+        k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), nw * 32,
+                               sizeof(PackSmem<PK_CAP, nw>), c.s>>>(a);
     }
     if (c.max_list > PK_CAP) {
         ++p->stats.kernel_launches;
