@@ -250,7 +250,10 @@ int gc_read_totals(gc_pool_t *pool, const uint32_t *ids, uint64_t n,
 /* Device address of the totals array (double4 per id, id_capacity rows). */
 int gc_totals_device(gc_pool_t *pool, const double **totals_dev);
 
-/* Zero all per-id totals (stream-ordered). */
+/* Zero all per-id totals.  Takes effect before the next batch's scatter
+ * (and before any read of the totals, graph replay or kick-drift), so work
+ * issued in between -- uploads, task builds -- does not wait for the batches
+ * still running. */
 int gc_reset_totals(gc_pool_t *pool);
 
 /* Counters since creation plus details of the last flush. */

@@ -196,6 +196,14 @@ int gc_clear_flags(gc_pool *p, cudaStream_t s, unsigned long long mask)
     return GC_OK;
 }
 
+int gc_apply_totals_reset(gc_pool *p, cudaStream_t s)
+{
+    if (!p->totals_reset_pending) return GC_OK;
+    GC_CUDA_TRY(cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * p->cfg.id_capacity, s));
+    p->totals_reset_pending = false;
+    return GC_OK;
+}
+
 // Make the issue stream wait for every scatter in flight (per-id totals).
 int order_after_scatters(gc_pool *p)
 {
@@ -675,6 +683,7 @@ static int flush_impl(gc_pool *p, int per_task)
     // pack done: later pool changes may proceed
     GC_CUDA_TRY(cudaEventRecord(c.ev_packed, c.s));
     if (prev && prev != &c && prev->valid) GC_CUDA_TRY(cudaStreamWaitEvent(c.s, prev->ev_scattered, 0));
+    GC_TRY(gc_apply_totals_reset(p, c.s));
     GC_TRY(gc_scatter(p, c));
     GC_CUDA_TRY(cudaEventRecord(c.ev_scattered, c.s));
     GC_CUDA_TRY(cudaEventRecord(c.ev_stage[4], c.s));
@@ -871,6 +880,7 @@ int gc_read_totals(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
     if (!p || (n && (!ids || !acc4))) return GC_ERR_ARG;
     if (n == 0) return GC_OK;
     GC_TRY(order_after_scatters(p));
+    GC_TRY(gc_apply_totals_reset(p, p->s));
     GC_TRY(grow_keep(p->io_a, n * 4 + 16, 0, p->s));
     GC_TRY(grow_keep(p->io_b, n * sizeof(gcd4) + 32, 0, p->s));
     int rc = GC_OK;
@@ -893,15 +903,22 @@ int gc_read_totals(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
 int gc_totals_device(gc_pool_t *p, const double **totals_dev)
 {
     if (!p || !totals_dev) return GC_ERR_ARG;
+    if (p->totals_reset_pending) {
+        GC_TRY(order_after_scatters(p));
+        GC_TRY(gc_apply_totals_reset(p, p->s));
+    }
     *totals_dev = (const double *)p->d_totals;
     return GC_OK;
 }
 
+// The zeroing is deferred to the next consumer of the totals: the next
+// batch's scatter (on its own stream, after the previous batch's scatter),
+// a read, a graph replay or a kick-drift.  Work issued meanwhile (uploads,
+// task builds) therefore does not wait for the batches in flight.
 int gc_reset_totals(gc_pool_t *p)
 {
     if (!p) return GC_ERR_ARG;
-    GC_TRY(order_after_scatters(p));
-    GC_CUDA_TRY(cudaMemsetAsync(p->d_totals, 0, sizeof(gcd4) * p->cfg.id_capacity, p->s));
+    p->totals_reset_pending = true;
     return GC_OK;
 }
 

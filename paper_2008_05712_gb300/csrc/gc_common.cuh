@@ -172,6 +172,7 @@ struct gc_pool {
     DBuf tasks, tgt_ids, src_ids;
     uint64_t submitted_batches = 0;   // index of the pending batch
     bool md_pending = false;          // the pending batch began with an MD build
+    bool totals_reset_pending = false;   // gc_reset_totals not yet applied on the device
     int md_pend_m = 0, md_pend_dim = 3;
 
     // two flush contexts: batch k runs on ctx[k % 2]; `cur` takes the next
@@ -242,6 +243,9 @@ int order_after_scatters(gc_pool *p);
 // Clear the status bits `mask` of the pool's flag word, stream-ordered and
 // atomically (kernels of another batch may be setting other bits meanwhile).
 int gc_clear_flags(gc_pool *p, cudaStream_t s, unsigned long long mask);
+// Apply a pending reset of the per-id totals on stream s (the caller orders
+// s after every scatter already issued).
+int gc_apply_totals_reset(gc_pool *p, cudaStream_t s);
 int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
                        std::vector<uint32_t> &lj_off);
 int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,

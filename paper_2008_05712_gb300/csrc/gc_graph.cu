@@ -267,6 +267,7 @@ extern "C" int gc_graph_launch(gc_graph_t *g)
     // totals accumulate in admission order: after every scatter in flight;
     // the pool's issue stream then waits for this replay
     GC_TRY(order_after_scatters(p));
+    GC_TRY(gc_apply_totals_reset(p, p->s));
     cudaEvent_t issue = nullptr;
     GC_CUDA_TRY(cudaEventCreateWithFlags(&issue, cudaEventDisableTiming));
     int rc = GC_OK;

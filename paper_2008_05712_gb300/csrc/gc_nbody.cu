@@ -702,6 +702,7 @@ extern "C" int gc_nbody_kick_drift(gc_pool_t *p, const double *acc_dev, float *x
         ((uintptr_t)acc_dev) % 32)
         return GC_ERR_ARG;
     GC_TRY(order_after_scatters(p));   // the accelerations of batches in flight
+    GC_TRY(gc_apply_totals_reset(p, p->s));
     ++p->stats.kernel_launches;
     k_kick_drift<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
         (const gcd4 *)acc_dev, (float4 *)xyzm_dev, (float4 *)vel_dev, n, dt);

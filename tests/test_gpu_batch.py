@@ -250,3 +250,33 @@ def test_wait_expiry_reported_and_pool_stays_usable(gc, orc):
             pool.check_wait_expiry(bad)
         assert e.value.code == gc.GC_ERR_ARG
     pool.close()
+
+
+def test_reset_totals_semantics(gc):
+    """A reset zeroes the per-id totals for every later reader: a read right
+    after it sees zeros, the next batch's totals hold that batch alone, and
+    batches flushed back to back without a reset accumulate."""
+    x, to, tg, so, sr = uneven(n_ids=3000, n_tasks=20, seed=51, s_range=(1, 300))
+    n = x.shape[0]
+    ids = np.arange(n, dtype=np.uint32)
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(ids, x)
+    b = submit_gravity(pool, to, tg, so, sr)
+    pool.flush()
+    pool.wait(b)
+    one = pool.totals(ids)
+    assert np.abs(one).sum() > 0
+    pool.reset_totals()
+    assert not pool.totals(ids).any()
+    pool.reset_totals()
+    for _ in range(2):                  # two batches in flight, one reset before them
+        b = submit_gravity(pool, to, tg, so, sr)
+        pool.flush()
+    pool.wait(b)
+    np.testing.assert_allclose(pool.totals(ids), 2 * one, rtol=1e-12, atol=1e-300)
+    pool.reset_totals()
+    b = submit_gravity(pool, to, tg, so, sr)
+    pool.flush()
+    pool.wait(b)
+    assert np.array_equal(pool.totals(ids), one)
+    pool.close()
