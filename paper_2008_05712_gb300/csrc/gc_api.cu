@@ -567,6 +567,9 @@ static int flush_impl(gc_pool *p, int per_task)
     c.md_m = p->md_pend_m;
     c.md_dim = p->md_pend_dim;
     p->md_pending = false;
+    // one N-body build alone: its rows are the bucket particles, each once
+    c.unique_rows = p->nb_pend_tasks != 0 && c.n_tasks == p->nb_pend_tasks;
+    p->nb_pend_tasks = 0;
     c.valid = false;
     c.host_tasks_valid = false;
     c.timing_valid = false;

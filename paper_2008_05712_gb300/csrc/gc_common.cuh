@@ -141,6 +141,7 @@ struct FlushCtx {
     uint64_t max_list = 0;                 // longest target or source list
     bool md_struct = false;                // the batch is one MD build: rows reduced per cell
     int md_m = 0, md_dim = 3;
+    bool unique_rows = false;              // every row id occurs once (one N-body build)
     std::vector<TaskRec> host_tasks;       // for gc_read_results
     std::unordered_map<uint64_t, uint64_t> task_index;
     bool host_tasks_valid = false;
@@ -172,6 +173,7 @@ struct gc_pool {
     DBuf tasks, tgt_ids, src_ids;
     uint64_t submitted_batches = 0;   // index of the pending batch
     bool md_pending = false;          // the pending batch began with an MD build
+    uint64_t nb_pend_tasks = 0;       // tasks of an N-body build that began the pending batch
     bool totals_reset_pending = false;   // gc_reset_totals not yet applied on the device
     int md_pend_m = 0, md_pend_dim = 3;
 

@@ -197,6 +197,7 @@ extern "C" int gc_graph_capture(gc_pool_t *p, gc_graph_t **out)
     c.md_struct = src.md_struct;
     c.md_m = src.md_m;
     c.md_dim = src.md_dim;
+    c.unique_rows = src.unique_rows;
     c.n_waves = src.n_waves;
     c.valid = true;
     src.valid = false;    // its arrays now belong to the graph

@@ -1409,6 +1409,23 @@ __global__ void k_iota(uint32_t *v, uint64_t n)
     GRID_STRIDE(i, n) v[i] = (uint32_t)i;
 }
 
+// Rows whose ids are distinct: each row is its id's only contribution, so
+// the sorted path's result is one FP64 add per component, done in place.
+__global__ void k_reduce_unique(uint64_t n_rows, const uint32_t *row_id, const float4 *res,
+                                gcd4 *totals)
+{
+    GRID_STRIDE(r, n_rows) {
+        const uint32_t id = row_id[r];
+        const float4 sv = res[2 * r], cv = res[2 * r + 1];
+        gcd4 acc = totals[id];
+        acc.x += gc_f2d(sv.x) - gc_f2d(cv.x);
+        acc.y += gc_f2d(sv.y) - gc_f2d(cv.y);
+        acc.z += gc_f2d(sv.z) - gc_f2d(cv.z);
+        acc.w += gc_f2d(sv.w) - gc_f2d(cv.w);
+        totals[id] = acc;
+    }
+}
+
 __global__ void k_reduce_runs(const uint32_t *runs, const unsigned long long *n_runs_dev,
                               uint64_t n_rows, const uint32_t *rid, const uint32_t *row,
                               const float4 *res, gcd4 *totals)
@@ -1802,6 +1819,13 @@ int gc_scatter(gc_pool *p, FlushCtx &c)
     const uint64_t n_rows = c.n_rows;
     if (n_rows == 0) return GC_OK;
     if (c.md_struct) return gc_md_reduce(p, c);
+    if (c.unique_rows) {
+        ++p->stats.kernel_launches;
+        k_reduce_unique<<<grid_for(n_rows, 256, p->num_sms * 16), 256, 0, c.s>>>(
+            n_rows, c.row_id.as<uint32_t>(), c.res.as<float4>(), p->d_totals);
+        GC_CUDA_TRY(cudaGetLastError());
+        return GC_OK;
+    }
     GC_TRY(c.rows_tmp.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(c.rid_sorted.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(c.row_sorted.reserve(n_rows * sizeof(uint32_t)));
@@ -1832,6 +1856,7 @@ int gc_scatter_replay(gc_pool *p, FlushCtx &c)
 {
     if (c.n_rows == 0) return GC_OK;
     if (c.md_struct) return gc_md_reduce(p, c);
+    if (c.unique_rows) return gc_scatter(p, c);   // no sorted state to replay
     ++p->stats.kernel_launches;
     k_reduce_runs<<<grid_for(c.n_rows, 256, p->num_sms * 16), 256, 0, c.s>>>(
         c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, c.n_rows, c.rid_sorted.as<uint32_t>(),

@@ -210,13 +210,6 @@ struct M4 {
     double m, mx, my, mz;
 };
 
-struct M4Add {
-    __device__ __forceinline__ M4 operator()(const M4 &a, const M4 &b) const
-    {
-        return M4{a.m + b.m, a.mx + b.mx, a.my + b.my, a.mz + b.mz};
-    }
-};
-
 __global__ void k_mono_input(const uint32_t *sorted_ids, const float4 *x, uint64_t n, M4 *out)
 {
     GRID_STRIDE(i, n + 1) {
@@ -227,6 +220,121 @@ __global__ void k_mono_input(const uint32_t *sorted_ids, const float4 *x, uint64
             v = M4{w, w * (double)p.x, w * (double)p.y, w * (double)p.z};
         }
         out[i] = v;
+    }
+}
+
+// Exclusive scan of the M4 values with a fixed association, so that the node
+// values -- and every result computed from them -- repeat bit for bit from
+// run to run (a decoupled look-back scan groups floating-point sums by
+// timing).  Tiles of M4_TILE values: (1) each tile's sum, (2) an exclusive
+// scan of the tile sums in one block, (3) each tile's exclusive scan offset
+// by its tile prefix.  Within a tile every thread owns M4_PER consecutive
+// values; thread sums are combined by a shuffle scan per warp and then
+// across the warps in warp order.
+constexpr int M4_THREADS = 256, M4_PER = 8, M4_TILE = M4_THREADS * M4_PER;
+
+__device__ __forceinline__ M4 m4_add(const M4 &a, const M4 &b)
+{
+    return M4{a.m + b.m, a.mx + b.mx, a.my + b.my, a.mz + b.mz};
+}
+
+__device__ __forceinline__ M4 m4_shfl_up(const M4 &v, int o)
+{
+    return M4{__shfl_up_sync(0xffffffffu, v.m, o), __shfl_up_sync(0xffffffffu, v.mx, o),
+              __shfl_up_sync(0xffffffffu, v.my, o), __shfl_up_sync(0xffffffffu, v.mz, o)};
+}
+
+// Exclusive block scan of one M4 per thread (M4_THREADS threads); *total
+// receives the block's sum.
+__device__ M4 m4_block_excl_scan(M4 v, M4 *wsum, M4 *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    M4 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const M4 y = m4_shfl_up(x, o);
+        if (lane >= o) x = m4_add(y, x);
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    M4 before{0, 0, 0, 0};
+    for (int q = 0; q < w; ++q) before = m4_add(before, wsum[q]);
+    if (total) {
+        M4 t{0, 0, 0, 0};
+        for (int q = 0; q < M4_THREADS / 32; ++q) t = m4_add(t, wsum[q]);
+        *total = t;
+    }
+    __syncthreads();
+    // exclusive: the sum of the earlier warps plus the earlier lanes of this warp
+    M4 ex = m4_shfl_up(x, 1);
+    if (lane == 0) ex = M4{0, 0, 0, 0};
+    return m4_add(before, ex);
+}
+
+__device__ __forceinline__ M4 m4_thread_sum(const M4 *in, uint64_t n, uint64_t i0)
+{
+    M4 acc{0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < M4_PER; ++j)
+        if (i0 + j < n) acc = m4_add(acc, in[i0 + j]);
+    return acc;
+}
+
+__global__ void __launch_bounds__(M4_THREADS) k_m4_tile_sum(const M4 *in, uint64_t n, M4 *tile_sum)
+{
+    __shared__ M4 wsum[M4_THREADS / 32];
+    const uint64_t i0 = (uint64_t)blockIdx.x * M4_TILE + (uint64_t)threadIdx.x * M4_PER;
+    M4 total;
+    m4_block_excl_scan(m4_thread_sum(in, n, i0), wsum, &total);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// one block: tile sums -> exclusive tile prefixes, M4_PER tiles per thread and round
+__global__ void __launch_bounds__(M4_THREADS) k_m4_scan_tiles(M4 *tile, uint64_t nt)
+{
+    __shared__ M4 wsum[M4_THREADS / 32];
+    __shared__ M4 carry;
+    if (threadIdx.x == 0) carry = M4{0, 0, 0, 0};
+    __syncthreads();
+    for (uint64_t r0 = 0; r0 < nt; r0 += M4_TILE) {
+        const uint64_t i0 = r0 + (uint64_t)threadIdx.x * M4_PER;
+        M4 v[M4_PER];
+        M4 acc{0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < M4_PER; ++j) {
+            v[j] = i0 + j < nt ? tile[i0 + j] : M4{0, 0, 0, 0};
+            acc = m4_add(acc, v[j]);
+        }
+        M4 total;
+        M4 run = m4_add(carry, m4_block_excl_scan(acc, wsum, &total));
+#pragma unroll
+        for (int j = 0; j < M4_PER; ++j) {
+            if (i0 + j < nt) tile[i0 + j] = run;
+            run = m4_add(run, v[j]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry = m4_add(carry, total);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(M4_THREADS) k_m4_tile_scan(const M4 *in, uint64_t n,
+                                                            const M4 *tile_pre, M4 *out)
+{
+    __shared__ M4 wsum[M4_THREADS / 32];
+    const uint64_t i0 = (uint64_t)blockIdx.x * M4_TILE + (uint64_t)threadIdx.x * M4_PER;
+    M4 v[M4_PER];
+    M4 acc{0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < M4_PER; ++j) {
+        v[j] = i0 + j < n ? in[i0 + j] : M4{0, 0, 0, 0};
+        acc = m4_add(acc, v[j]);
+    }
+    M4 run = m4_add(tile_pre[blockIdx.x], m4_block_excl_scan(acc, wsum, nullptr));
+#pragma unroll
+    for (int j = 0; j < M4_PER; ++j) {
+        if (i0 + j < n) out[i0 + j] = run;
+        run = m4_add(run, v[j]);
     }
 }
 
@@ -531,22 +639,15 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     k_emit_nodes<<<grid_for(n, 256, maxb), 256, 0, s>>>(
         K, n, S.lcp.as<int8_t>(), S.dmax.as<int8_t>(), S.node_off.as<uint32_t>(),
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), bcnt, B);
-    GC_TRY(S.mono.reserve((n + 1) * sizeof(M4) * 2));
-    M4 *mono_in = S.mono.as<M4>(), *mono_pre = mono_in + (n + 1);
+    const uint64_t n_m4 = n + 1, n_tiles = (n_m4 + M4_TILE - 1) / M4_TILE;
+    GC_TRY(S.mono.reserve((n_m4 * 2 + n_tiles) * sizeof(M4)));
+    M4 *mono_in = S.mono.as<M4>(), *mono_pre = mono_in + n_m4, *tiles = mono_pre + n_m4;
     ++p->stats.kernel_launches;
     k_mono_input<<<grid_for(n + 1, 256, maxb), 256, 0, s>>>(sid, x, n, mono_in);
-    {
-        size_t bytes = 0;
-        if (cub::DeviceScan::ExclusiveScan(nullptr, bytes, mono_in, mono_pre, M4Add(),
-                                           M4{0, 0, 0, 0}, (int64_t)(n + 1), s) != cudaSuccess)
-            return GC_ERR_CUDA;
-        GC_TRY(S.cub_tmp.reserve(bytes + 16));
-        size_t have = S.cub_tmp.cap;
-        ++p->stats.primitive_calls;
-        if (cub::DeviceScan::ExclusiveScan(S.cub_tmp.p, have, mono_in, mono_pre, M4Add(),
-                                           M4{0, 0, 0, 0}, (int64_t)(n + 1), s) != cudaSuccess)
-            return GC_ERR_CUDA;
-    }
+    p->stats.kernel_launches += 3;
+    k_m4_tile_sum<<<(unsigned)n_tiles, M4_THREADS, 0, s>>>(mono_in, n_m4, tiles);
+    k_m4_scan_tiles<<<1, M4_THREADS, 0, s>>>(tiles, n_tiles);
+    k_m4_tile_scan<<<(unsigned)n_tiles, M4_THREADS, 0, s>>>(mono_in, n_m4, tiles, mono_pre);
     ++p->stats.kernel_launches;
     k_mono_nodes<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, mono_pre,
                                                          S.node_val.as<float4>());
@@ -596,6 +697,7 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     GC_CUDA_TRY(cudaStreamSynchronize(s));
 
     // append the tasks to the pending batch
+    const bool batch_start = p->nb_tasks == 0;
     GC_TRY(gc_reserve_batch(p, NB, n, NL));
     uint32_t *dt = p->tgt_ids.as<uint32_t>() + p->nb_tgt;
     uint32_t *ds = p->src_ids.as<uint32_t>() + p->nb_src;
@@ -613,6 +715,8 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     p->nb_tasks += NB;
     p->nb_tgt += n;
     p->nb_src += NL;
+    // a batch that holds exactly this build has one row per particle
+    p->nb_pend_tasks = batch_start ? NB : 0;
     S.n = n;
     S.n_nodes = NN;
     S.n_buckets = NB;

@@ -145,3 +145,57 @@ def test_drift_step_reuses_slots(gc, orc):
     errs = per_task_errors(gc.value(pool.results()), ref, to)
     assert errs.max() <= TOL
     pool.close()
+
+
+def test_unique_row_scatter_matches_sorted_path(gc):
+    """A batch holding exactly one N-body build has one row per particle and
+    adds each row to its id's total directly; the same tasks submitted from
+    the host go through the sorted path.  Rows and totals agree bit for
+    bit, over two batches (totals accumulate)."""
+    n = 6000
+    x = inputs.plummer(n, inputs.SEED_BASE + 7)
+    pool, info, g = build_and_flush(gc, x)
+    NN, NB = info["n_nodes"], info["n_buckets"]
+    ids = np.arange(n, dtype=np.uint32)
+    tg = g["sorted_ids"]
+    to = np.zeros(NB + 1, np.uint64)
+    to[1:] = np.cumsum(g["bucket_count"])
+    so, sr = g["list_off"], g["list_ids"]
+    other = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    other.upload(ids, x)
+    other.upload(np.arange(n, n + NN, dtype=np.uint32), g["node_xyzm"])
+    b = other.submit_csr(np.zeros(NB, np.uint32), to, tg, so, sr)
+    other.flush()
+    other.wait(b)
+    assert np.array_equal(pool.results(), other.results())
+    assert np.array_equal(pool.totals(ids), other.totals(ids))
+    # second batch on both: totals accumulate identically
+    pool.build_nbody(torch.from_numpy(x).cuda(), 32, 7, 10)
+    pool.flush()
+    b = other.submit_csr(np.zeros(NB, np.uint32), to, tg, so, sr)
+    other.flush()
+    other.wait(b)
+    assert np.array_equal(pool.totals(ids), other.totals(ids))
+    pool.close()
+    other.close()
+
+
+def test_build_repeats_bit_for_bit(gc):
+    """Building the same system twice gives the same node values and the
+    same rows, bit for bit (the monopole prefix sums use a fixed order)."""
+    n = 20000
+    x = inputs.plummer(n, inputs.SEED_BASE + 8)
+    xd = torch.from_numpy(x).cuda()
+    pool = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    out = []
+    for _ in range(3):
+        info = pool.build_nbody(xd, 32, 7, 10)
+        g = pool.nbody_tree(n, info["n_nodes"], info["n_buckets"], info["list_entries"])
+        pool.flush()
+        pool.wait(pool.stats()["flushes"] - 1)
+        out.append((g["node_xyzm"].copy(), pool.results().copy()))
+    for node_val, rows in out[1:]:
+        assert np.array_equal(node_val, out[0][0])
+        assert np.array_equal(rows, out[0][1])
+    pool.close()
