@@ -52,8 +52,8 @@ PACK_BYTES_PER_ENTRY = 40
 # k_gravity per interaction, the pack kernels per list entry.
 # profiles/k_gravity_nbody262k.md: 506.6 MB for 2.949e8 interactions (262,144-particle step)
 GRAVITY_DRAM_BYTES_PER_INTERACTION = 506.6e6 / 2.949e8
-# profiles/k_pack_mid_nbody262k.md: 643.1 MB for 3.07e7 entries (262,144-particle step)
-PACK_DRAM_BYTES_PER_ENTRY = 643.1e6 / 3.07e7
+# profiles/k_pack_mid_nbody262k.md: 634.1 MB for 3.07e7 entries (262,144-particle step)
+PACK_DRAM_BYTES_PER_ENTRY = 634.1e6 / 3.07e7
 
 
 # Uneven batch and serving workload: a two-Plummer merger of 4,194,304
