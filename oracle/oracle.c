@@ -11,8 +11,8 @@
  * What each function follows:
  *   orc_morton_keys / orc_build_tree  -- Section 4.1: particles grouped into
  *       buckets by a Barnes-Hut octree; buckets share one interaction list.
- *       Quantisation, octant order and bucket size are this build's fixed
- *       reading (the paper gives none): 21-bit grid per axis, Morton key with
+ *       Quantisation, octant order and bucket size are a fixed reading
+ *       (the paper gives none): 21-bit grid per axis, Morton key with
  *       x in bit 0, split while a cell holds more than bucket_max particles.
  *   orc_walk         -- Section 4.1: tree walks produce per-bucket
  *       interaction lists of tree nodes and particles; opening criterion is
@@ -28,7 +28,7 @@
  *       are kept sorted by inserting each new index with a binary search, so
  *       threads read data in sorted index order.
  *   orc_reduce       -- per-id FP64 sum of the per-task contributions in
- *       admission order (this build's cross-task reduction).
+ *       admission order (the engine's cross-task reduction).
  *
  * Precision: every accumulation is FP64; inputs are FP32 values promoted
  * exactly.  Compile with -ffp-contract=off so that no FMA is formed.

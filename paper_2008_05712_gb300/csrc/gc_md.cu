@@ -301,7 +301,7 @@ static int build_md(gc_pool_t *p, const uint32_t *cell_dev, uint64_t n, int m, i
     p->nb_tasks += nt;
     p->nb_tgt += tot_t;
     p->nb_src += tot_s;
-    // a batch that holds exactly this build is reduced per cell at its flush
+    // a batch that holds exactly these tasks is reduced per cell at its flush
     p->md_pending = batch_start;
     p->md_pend_m = m;
     p->md_pend_dim = dim;

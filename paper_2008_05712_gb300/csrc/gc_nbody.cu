@@ -715,7 +715,7 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     p->nb_tasks += NB;
     p->nb_tgt += n;
     p->nb_src += NL;
-    // a batch that holds exactly this build has one row per particle
+    // a batch that holds exactly these tasks has one row per particle
     p->nb_pend_tasks = batch_start ? NB : 0;
     S.n = n;
     S.n_nodes = NN;
