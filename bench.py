@@ -281,11 +281,13 @@ MD_WORKLOAD = ("lj_fcc_1M: 1,048,576 Lennard-Jones atoms, jittered FCC at densit
 RC2 = 6.25
 
 
-def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True):
+def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True, cells=64, ncell=42):
     """The MD workload (Section 4.2 on the 3-D FCC system): task build from
     device-resident cell indices and one batched flush per step, timed with
-    events; candidate pairs per second; parity on a seeded task sample."""
-    sysm = inputs.fcc_lj(64, seed, ncell=42)
+    events; candidate pairs per second; parity on a seeded task sample.
+    cells / ncell: FCC unit cells and MD cells per axis (64 / 42: 1,048,576
+    atoms; smaller systems serve profiling)."""
+    sysm = inputs.fcc_lj(cells, seed, ncell=ncell)
     n, m = sysm.n, sysm.ncell
     pool = gcharm.Pool(id_capacity=n, pool_capacity=n, eps2=EPS2, lj_rc2=RC2,
                        md_edge=sysm.edge, stream=stream.cuda_stream)
@@ -425,16 +427,13 @@ def ewald_section(gcharm, torch, seed, stream, reps=5, with_oracle=True):
     return out
 
 
-def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=True):
-    """The 200k-task uneven batch (device-resident task arrays, timed with
-    events) and the serving loop at three arrival rates (host task arrays,
-    host clock, latency from each task's scheduled arrival)."""
+def uneven_setup(gcharm, torch, seed, stream):
+    """Pool, merger and the 200k uneven tasks (host arrays)."""
     x = inputs.merger(*C4_N, seed)
     n = x.shape[0]
-    ids = np.arange(n, dtype=np.uint32)
     pool = gcharm.Pool(id_capacity=2 * n + 1024, pool_capacity=2 * n + 1024, eps2=EPS2,
                        staging_budget_bytes=C4_BUDGET, stream=stream.cuda_stream)
-    pool.upload(ids, x)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
     # Morton order of the merger from the library's own tree build (the
     # built N-body step is flushed: it doubles as a warm-up)
     pool.build_nbody(x, BUCKET, *THETA)
@@ -442,6 +441,33 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=Tr
     order = pool.nbody_sorted_ids(n)
     to, tg, so, sr = inputs.uneven_tasks(n, C4_TASKS, seed + 1, C4_T_RANGE, C4_S_RANGE,
                                          order=order)
+    return x, pool, to, tg, so, sr
+
+
+def uneven_plain(gcharm, torch, seed, stream, batches=2):
+    """The uneven batch alone, flushed `batches` times from device-resident
+    task arrays (no tuning, no graph, no serving): the profiling form."""
+    x, pool, to, tg, so, sr = uneven_setup(gcharm, torch, seed, stream)
+    dev = [torch.from_numpy(a.view(t)).cuda() for a, t in
+           [(np.zeros(C4_TASKS, np.uint32), np.int32), (to, np.int64), (tg, np.int32),
+            (so, np.int64), (sr, np.int32)]]
+    torch.cuda.synchronize()
+    out = {"workload": C4_WORKLOAD, "batches": []}
+    for _ in range(batches):
+        pool.submit_csr_device(*dev, tg.shape[0], sr.shape[0])
+        pool.flush()
+        stream.synchronize()
+        out["batches"].append(pool.timings())
+    pool.close()
+    return out
+
+
+def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=True):
+    """The 200k-task uneven batch (device-resident task arrays, timed with
+    events) and the serving loop at three arrival rates (host task arrays,
+    host clock, latency from each task's scheduled arrival)."""
+    x, pool, to, tg, so, sr = uneven_setup(gcharm, torch, seed, stream)
+    n = x.shape[0]
     kinds = np.zeros(C4_TASKS, np.uint32)
     nt = (to[1:] - to[:-1]).astype(np.float64)
     ns = (so[1:] - so[:-1]).astype(np.float64)
@@ -548,6 +574,22 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=Tr
     return uneven, serving
 
 
+def run_section(args):
+    """One workload alone on one GPU: the form the profiles capture."""
+    import torch
+
+    from paper_2008_05712_gb300 import gcharm
+
+    gcharm.load()
+    stream = torch.cuda.Stream()
+    if args.section == "md":
+        out = md_section(gcharm, torch, inputs.SEED_BASE + 3, stream, with_oracle=False,
+                         cells=args.md_cells, ncell=args.md_ncell)
+    else:
+        out = uneven_plain(gcharm, torch, inputs.SEED_BASE + 4, stream)
+    print(json.dumps({"section": args.section, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,9 +602,16 @@ def main():
     ap.add_argument("--no-md", action="store_true", help="skip the MD measurement")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the uneven-batch and serving measurements")
+    ap.add_argument("--section", choices=["md", "uneven"],
+                    help="run one workload alone and print its figures (profiling form)")
+    ap.add_argument("--md-cells", type=int, default=64, help="FCC unit cells per axis")
+    ap.add_argument("--md-ncell", type=int, default=42, help="MD cells per axis")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.section:
+        run_section(args)
         return
 
     import torch
