@@ -66,11 +66,23 @@ __global__ void k_bbox(const float4 *x, uint64_t n, uint32_t *bounds)
             mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
             mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
+    // warps -> block in shared memory, then one set of atomics per block (one
+    // set per warp made the six global words a serial hot spot)
+    __shared__ uint32_t wb[32][6];
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if ((threadIdx.x & 31) == 0)
         for (int a = 0; a < 3; ++a) {
-            atomicMin(&bounds[a], mn[a]);
-            atomicMax(&bounds[3 + a], mx[a]);
+            wb[w][a] = mn[a];
+            wb[w][3 + a] = mx[a];
         }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        uint32_t v = wb[0][a];
+        for (int q = 1; q < nw; ++q) v = a < 3 ? min(v, wb[q][a]) : max(v, wb[q][a]);
+        if (a < 3) atomicMin(&bounds[a], v);
+        else atomicMax(&bounds[a], v);
+    }
 }
 
 __global__ void k_grid_params(const uint32_t *bounds, GridParams *gp)
