@@ -579,9 +579,12 @@ static int flush_impl(gc_pool *p, int per_task)
     clear_last_stats(p);
 
     uint64_t info[5];
+    // the task-flag word travels with the preparation's read-back (one host
+    // round trip for both; the task records were written on this stream)
+    GC_CUDA_TRY(cudaMemcpyAsync(p->h_ctr + CTR_FLAGS, p->d_ctr + CTR_FLAGS,
+                                sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.s));
     int rc = gc_prepare(p, c, info);
     if (rc != GC_OK) return rc;
-    GC_CUDA_TRY(cudaMemcpy(p->h_ctr, p->d_ctr, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     if (p->h_ctr[CTR_FLAGS] & GC_FLAG_BAD_TASK) {
         gc_clear_flags(p, c.s, GC_FLAG_BAD_TASK);
         return GC_ERR_ARG;

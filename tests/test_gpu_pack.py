@@ -46,8 +46,8 @@ def csr(lists):
 @pytest.mark.parametrize("warm", [False, True])
 def test_pack_permutation_adversarial(gc, orc, warm):
     """warm: a first batch references every id, so ids take slots 0..N-1 and
-    the lists below span a 20-bit slot range (four 6-bit radix passes);
-    otherwise only the referenced ids take slots (a 16-bit range)."""
+    the lists below span a 20-bit slot range; otherwise only the referenced
+    ids take slots (a 16-bit range)."""
     n = 1 << 20
     x = inputs.plummer(n, 91)
     srcs = adversarial_lists(n, 92)
