@@ -90,10 +90,61 @@ def test_pack_perm_is_stable_sort(orc):
     assert orc.pack_perm_batch(off, s).tolist() == [1, 0, 2, 2, 0, 1, 4, 3]
 
 
-def test_reduce_matches_add_at(orc):
-    g = inputs.rng(8)
-    ids = g.integers(0, 50, 400).astype(np.uint32)
-    c = g.normal(size=(400, 4))
-    ref = np.zeros((50, 4))
-    np.add.at(ref, ids, c)
-    np.testing.assert_allclose(orc.reduce(ids, c, 50), ref, rtol=1e-14, atol=1e-14)
+def test_reduce_order_and_stride(orc):
+    """Cross-task reduction (Section 2.2: the results of the combined kernel
+    go back to each chare): per id, an FP64 sum taken in admission order.
+
+    Hand-worked values.  In binary64 the spacing of numbers near 1e16 is 2, so
+    1e16 + 1 is a tie that rounds to the even neighbour 1e16: admitted as
+    (1e16, 1, -1e16) the total is exactly 0, admitted as (1e16, -1e16, 1) it
+    is exactly 1.  A reversed or reassociated order, an FP32 accumulator or
+    a compensated sum would each give the other value for one of the two ids.
+    """
+    big = 1e16
+    id_cap = 9
+    # rows in admission order: (id, 4 components)
+    rows = [
+        (3, [big, 0.5, 0.0, -2.0]),
+        (8, [big, 1.0, 0.0, 0.0]),       # the top id of the range
+        (3, [1.0, 0.25, 0.0, -2.0]),
+        (8, [-big, 2.0, 0.0, 0.0]),
+        (3, [-big, 0.125, 7.0, -2.0]),
+        (8, [1.0, 4.0, 0.0, 3.0]),
+        (0, [0.0, 0.0, -1.5, 0.0]),
+    ]
+    ids = np.array([r[0] for r in rows], np.uint32)
+    c = np.array([r[1] for r in rows], np.float64)
+    tot = orc.reduce(ids, c, id_cap)
+    assert tot.shape == (id_cap, 4)
+    assert tot[3].tolist() == [0.0, 0.875, 7.0, -6.0]
+    assert tot[8].tolist() == [1.0, 7.0, 0.0, 3.0]
+    assert tot[0].tolist() == [0.0, 0.0, -1.5, 0.0]
+    for i in (1, 2, 4, 5, 6, 7):                 # never referenced
+        assert tot[i].tolist() == [0.0, 0.0, 0.0, 0.0]
+    # the same rows admitted in another order (rows 2 <-> 4 and 3 <-> 5, so
+    # id 3 sees 1e16, -1e16, 1 and id 8 sees 1e16, 1, -1e16) swap the two
+    # outcomes; the other components are exact in any order
+    order = [0, 1, 4, 5, 2, 3, 6]
+    tot_r = orc.reduce(ids[order].copy(), c[order].copy(), id_cap)
+    assert tot_r[3].tolist() == [1.0, 0.875, 7.0, -6.0]
+    assert tot_r[8].tolist() == [0.0, 7.0, 0.0, 3.0]
+    # no rows: all zero
+    assert not orc.reduce(np.zeros(0, np.uint32), np.zeros((0, 4)), 4).any()
+
+
+def test_reduce_three_tasks_one_id(orc):
+    """One id referenced by three tasks, each contributing distinct powers of
+    two per component (exact in FP64), next to a neighbour id: the totals
+    show each component landing in its own column and no row leaking into
+    the neighbouring id."""
+    ids = np.array([5, 4, 5, 6, 5], np.uint32)
+    c = np.array([[1, 2, 4, 8],
+                  [16, 32, 64, 128],
+                  [256, 512, 1024, 2048],
+                  [4096, 8192, 16384, 32768],
+                  [65536, 131072, 262144, 524288]], np.float64)
+    tot = orc.reduce(ids, c, 7)
+    assert tot[5].tolist() == [65793.0, 131586.0, 263172.0, 526344.0]
+    assert tot[4].tolist() == [16.0, 32.0, 64.0, 128.0]
+    assert tot[6].tolist() == [4096.0, 8192.0, 16384.0, 32768.0]
+    assert not tot[[0, 1, 2, 3]].any()
