@@ -873,7 +873,9 @@ struct GravSmem {
 // as compensated FP32 pairs in lane order.  Work units come from a device queue (persistent
 // kernel); with a null queue each warp takes a fixed share
 // (one-launch-per-task mode).  A bulk copy that does not complete within the
-// polling limit sets GC_FLAG_TIMEOUT and the warp stops.
+// polling limit sets GC_FLAG_TIMEOUT and the warp stops; the lanes poll
+// together and take that decision as one, so no lane is left waiting at a
+// later warp-wide shuffle.
 __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -926,7 +928,7 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
         uint32_t failed_at = 0;
         for (uint32_t i = 0; i < ntiles; ++i) {
             const uint32_t b = i & 1u;
-            if (!gc_mbar_wait_bounded(&bar[b], (parity >> b) & 1u, WAIT_LIMIT)) {
+            if (!gc_mbar_wait_bounded_warp(&bar[b], (parity >> b) & 1u, WAIT_LIMIT)) {
                 ok = false;
                 failed_at = i;
                 break;
@@ -978,7 +980,7 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
             if (lane == 0) atomicOr(a.flags, (unsigned long long)GC_FLAG_TIMEOUT);
             if (failed_at + 1 < ntiles) {
                 const uint32_t ob = (failed_at + 1) & 1u;
-                gc_mbar_wait_bounded(&bar[ob], (parity >> ob) & 1u, WAIT_LIMIT);
+                gc_mbar_wait_bounded_warp(&bar[ob], (parity >> ob) & 1u, WAIT_LIMIT);
             }
             return;
         }

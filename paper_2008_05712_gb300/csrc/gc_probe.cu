@@ -32,14 +32,20 @@ __global__ void __launch_bounds__(PR_THREADS) k_ffma2_probe(float *sink, int ite
     if (acc == 12345.678f) sink[blockIdx.x] = acc;   // keeps the chains live
 }
 
-// One thread waits on a barrier that nothing arrives at; the bounded wait
-// gives up after `polls` polls and records the timeout status.
+// One warp waits on a barrier that nothing arrives at, with the warp-wide
+// bounded wait of the interaction kernel; it gives up after `polls` polls and
+// records the timeout status.
 __global__ void k_wait_expiry(unsigned long long *flags, uint32_t polls)
 {
     __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x != 0) return;
-    gc_mbar_init(&bar, 1);
-    if (!gc_mbar_wait_bounded(&bar, 0, polls)) atomicOr(flags, (unsigned long long)GC_FLAG_TIMEOUT);
+    if (threadIdx.x >= 32) return;
+    if (threadIdx.x == 0) {
+        gc_mbar_init(&bar, 1);
+        gc_fence_mbar_init();
+    }
+    __syncwarp();
+    const bool ok = gc_mbar_wait_bounded_warp(&bar, 0, polls);
+    if (!ok && threadIdx.x == 0) atomicOr(flags, (unsigned long long)GC_FLAG_TIMEOUT);
 }
 
 }  // namespace

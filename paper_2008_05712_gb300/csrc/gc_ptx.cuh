@@ -59,12 +59,18 @@ __device__ __forceinline__ bool gc_mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false if the limit ran out.
-__device__ __forceinline__ bool gc_mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                     uint32_t limit)
+// Bounded wait for phase `parity` of `bar`, taken by a whole warp (all 32
+// lanes call it with the same barrier and parity); false if the limit ran
+// out.  The lanes agree after every poll, so they all
+// return true together or all false together, and a warp that gives up
+// leaves no lane behind at a later full-mask shuffle or __syncwarp.  Once the
+// phase has completed every lane's poll sees it, so the agreement costs at
+// most one extra poll.
+__device__ __forceinline__ bool gc_mbar_wait_bounded_warp(uint64_t *bar, uint32_t parity,
+                                                          uint32_t limit)
 {
     for (uint32_t i = 0; i < limit; ++i)
-        if (gc_mbar_try_wait(bar, parity)) return true;
+        if (__all_sync(0xffffffffu, gc_mbar_try_wait(bar, parity))) return true;
     return false;
 }
 
