@@ -330,7 +330,7 @@ def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True, cells=64, 
         ta, tb, td, ts = O.md_tasks(m)
         cnt = (start[1:] - start[:-1]).astype(np.int64)
         roff = np.concatenate([[0], np.cumsum(cnt[ta] + np.where(ts != 0, 0, cnt[tb]))])
-        rows = gcharm.value(pool.results())
+        rows = pool.values()
         pick = np.sort(inputs.rng(seed + 1).choice(len(ta), 2000, replace=False))
         got, ref, off = [], [], [0]
         t0 = time.perf_counter()
@@ -414,7 +414,7 @@ def ewald_section(gcharm, torch, seed, stream, reps=5, with_oracle=True):
            "stage_ms_avg": stage}
     if with_oracle:
         from oracle import oracle as O
-        rows = gcharm.value(pool.results())
+        rows = pool.values()
         pick = np.sort(inputs.rng(seed + 1).choice(nb, 200, replace=False))
         tab = np.concatenate([x, np.zeros((1, 4), np.float32)])
         got, ref, off = [], [], [0]
@@ -741,13 +741,13 @@ def main():
     for k in range(K):
         pool.upload(ids_pin, hx[k])              # ids + values H2D
         pool.reset_totals()
-        pool.build_nbody(hx[k], BUCKET, *THETA)  # values H2D again
+        pool.build_nbody_resident(n, BUCKET, *THETA)   # tree from the pool's values
         pool.flush()
         tot = pool.totals(ids_pin, out=tot_pin)  # ids H2D, totals D2H
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": interactions / K * K / e2e_s if K else 0.0, "unit": "interactions/s",
-           "h2d_bytes_per_step": int(n * (4 + 16 + 16 + 4)),
+           "h2d_bytes_per_step": int(n * (4 + 16 + 4)),
            "d2h_bytes_per_step": int(tot.nbytes)}
     if ws > 1:
         e2e_max, _ = reduce_over_ranks(e2e_s, 0, "cuda")
@@ -799,7 +799,7 @@ def main():
         pool.flush()
         counts = pool.nbody_bucket_counts(keep["n_buckets"])
         boff = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
-        rows_gpu = gcharm.value(pool.results())
+        rows_gpu = pool.values()
         got = np.concatenate([rows_gpu[boff[b]:boff[b + 1]] for b in keep["buckets"]])
         cpu["parity_on_sample"] = error_stats(got, keep["rows"], keep["tgt_off"])
         cores = os.cpu_count() or 1

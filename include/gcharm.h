@@ -230,6 +230,21 @@ int gc_result_rows(gc_pool_t *pool, uint64_t *rows_out);
 int gc_read_batch_results(gc_pool_t *pool, uint64_t first_row, uint64_t n_rows,
                           float *out);
 
+/* The FP64 values of the same rows: 4 doubles per row, value = (double)s -
+ * (double)c per component (the compensated partial of Section 2.2's result
+ * of one work request, read as the number it stands for), computed on the
+ * device and copied to values4 (host, caller-owned).  Waits for the batch.
+ * Errors: GC_ERR_ARG (range outside the batch), GC_ERR_CUDA. */
+int gc_read_batch_values(gc_pool_t *pool, uint64_t first_row, uint64_t n_rows,
+                         double *values4);
+
+/* The same conversion for rows already in host memory (rows read through
+ * gc_read_results, gc_graph_results, gc_serve or written by
+ * gc_gravity_noalloc): values4[4i + k] = (double)rows[8i + k] -
+ * (double)rows[8i + 4 + k].  Host pointers, caller-owned.  Errors:
+ * GC_ERR_ARG (null pointer with n_rows > 0). */
+int gc_row_values(const float *rows, uint64_t n_rows, double *values4);
+
 /* As gc_read_batch_results, for batch `batch` (one of the two most recently
  * flushed batches).  Waits for that batch.  Errors: GC_ERR_ARG (batch no
  * longer held, range outside the batch). */
@@ -307,6 +322,17 @@ int gc_read_evicted(gc_pool_t *pool, uint32_t *ids, uint64_t cap, uint64_t *n_ou
 int gc_build_nbody_tasks(gc_pool_t *pool, const float *xyzm_dev, uint64_t n,
                          int bucket_max, int theta_num, int theta_den,
                          uint64_t task_id_base, uint64_t info_out[4]);
+
+/* As gc_build_nbody_tasks, with the positions of particles 0..n-1 taken
+ * from the pool itself: the values most recently uploaded for ids 0..n-1
+ * (gc_pool_upload, gc_pool_upload_device, gc_nbody_kick_drift), read on the
+ * device from their slots (or, for an id not resident, from the host
+ * mirror), so a caller that has just uploaded a step's positions does not
+ * copy them to the device a second time.  Every id 0..n-1 must have been
+ * uploaded.  Stream-ordered after those uploads.  Errors as
+ * gc_build_nbody_tasks. */
+int gc_build_nbody_tasks_resident(gc_pool_t *pool, uint64_t n, int bucket_max, int theta_num,
+                                  int theta_den, uint64_t task_id_base, uint64_t info_out[4]);
 
 /* One time step around the force computation (Section 4.1): for particles
  * i = 0..n-1, leapfrog kick then drift,
@@ -583,13 +609,16 @@ int gc_check_wait_expiry(gc_pool_t *pool, uint32_t polls);
  * already in device memory, without allocating anything: no cudaMalloc, no
  * cudaFree, no allocating library call.  The paper has no counterpart; this
  * is for callers that cannot allocate when they need the result -- code
- * running during stream capture, code inside a framework whose allocator
- * owns device memory, latency-critical threads that must not take the
- * device-wide synchronisation of cudaMalloc/cudaFree.
+ * inside a framework whose caching allocator already holds the device
+ * memory budget (a cudaMalloc beside it can fail or fragment that budget),
+ * latency-critical threads that must not take the device-wide
+ * synchronisation of cudaMalloc/cudaFree.
  *   tgt_off, src_off : device, n_tasks + 1 offsets each, starting at 0 and
- *                      not decreasing; tgt_off[n_tasks] must equal
- *                      n_tgt_total (checked on the device: otherwise
- *                      nothing is computed)
+ *                      not decreasing, fewer than 2^32 sources per task;
+ *                      tgt_off[n_tasks] must equal n_tgt_total.  Checked on
+ *                      the device: a call that breaks any of these computes
+ *                      nothing and writes NaN into all n_tgt_total rows of
+ *                      out_rows
  *   tgt_xyzm         : device, 4 floats per target (x, y, z, m), 16-byte aligned
  *   src_xyzm         : device, 4 floats per source, 16-byte aligned
  *   out_rows         : device, 8 floats per target, in target order: the
@@ -603,7 +632,9 @@ int gc_check_wait_expiry(gc_pool_t *pool, uint32_t polls);
  * (symbol lookup); make it before any stream capture.  Errors:
  * GC_ERR_TOO_LARGE (n_tasks > GC_NOALLOC_MAX_TASKS or n_tgt_total >
  * GC_NOALLOC_MAX_TARGETS), GC_ERR_ARG (eps2 <= 0, null or misaligned
- * pointers), GC_ERR_CUDA.  Asynchronous: returns after queueing. */
+ * pointers), GC_ERR_CUDA (a launch failed, or a CUDA error was already
+ * pending when the call began: that error is left pending for its owner and
+ * nothing is launched).  Asynchronous: returns after queueing. */
 int gc_gravity_noalloc(uint64_t n_tasks, const uint64_t *tgt_off, const float *tgt_xyzm,
                        const uint64_t *src_off, const float *src_xyzm, uint64_t n_tgt_total,
                        float eps2, float *out_rows, void *cuda_stream);

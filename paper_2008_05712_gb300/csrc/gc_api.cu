@@ -100,6 +100,18 @@ __global__ void k_gather_totals(const gcd4 *totals, const uint32_t *ids, uint64_
     }
 }
 
+// FP64 value s - c of compensated result rows (sum float4, compensation
+// float4 per row), one row per thread
+__global__ void k_row_values(const float4 *res, uint64_t n, gcd4 *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float4 s = res[2 * i], c = res[2 * i + 1];
+        out[i] = gcd4{(double)s.x - (double)c.x, (double)s.y - (double)c.y,
+                      (double)s.z - (double)c.z, (double)s.w - (double)c.w};
+    }
+}
+
 }  // namespace
 
 void free_ctx(FlushCtx &c)
@@ -828,6 +840,35 @@ int gc_read_batch_results(gc_pool_t *p, uint64_t first_row, uint64_t n_rows, flo
     GC_CUDA_TRY(cudaEventSynchronize(c->ev_done));
     GC_CUDA_TRY(cudaMemcpy(out, c->res.as<float4>() + 2 * first_row, n_rows * 2 * sizeof(float4),
                            cudaMemcpyDeviceToHost));
+    return GC_OK;
+}
+
+int gc_read_batch_values(gc_pool_t *p, uint64_t first_row, uint64_t n_rows, double *values4)
+{
+    if (!p || (n_rows && !values4)) return GC_ERR_ARG;
+    FlushCtx *c = result_ctx(p);
+    if (!c || first_row + n_rows > c->n_rows) return GC_ERR_ARG;
+    if (n_rows == 0) return GC_OK;
+    GC_TRY(grow_keep(p->io_b, n_rows * sizeof(gcd4) + 32, 0, p->s));
+    GC_CUDA_TRY(cudaStreamWaitEvent(p->s, c->ev_done, 0));
+    unsigned g = (unsigned)((n_rows + 255) / 256);
+    if (g > 65535u * 8) g = 65535u * 8;
+    ++p->stats.kernel_launches;
+    k_row_values<<<g, 256, 0, p->s>>>(c->res.as<float4>() + 2 * first_row, n_rows,
+                                      p->io_b.as<gcd4>());
+    GC_CUDA_TRY(cudaGetLastError());
+    GC_CUDA_TRY(cudaMemcpyAsync(values4, p->io_b.p, n_rows * sizeof(gcd4),
+                                cudaMemcpyDeviceToHost, p->s));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    return GC_OK;
+}
+
+int gc_row_values(const float *rows, uint64_t n_rows, double *values4)
+{
+    if (n_rows && (!rows || !values4)) return GC_ERR_ARG;
+    for (uint64_t i = 0; i < n_rows; ++i)
+        for (int k = 0; k < 4; ++k)
+            values4[4 * i + k] = (double)rows[8 * i + k] - (double)rows[8 * i + 4 + k];
     return GC_OK;
 }
 

@@ -579,7 +579,34 @@ __global__ void k_kick_drift(const gcd4 *acc, float4 *x, float4 *v, uint64_t n, 
     }
 }
 
+// Current values of ids 0..n-1 in id order: a resident id's pool slot, else
+// its entry of the host mirror (mapped memory, read over the host link).
+__global__ void k_values_of_ids(const uint32_t *slot_of_id, const float4 *pool,
+                                const float4 *mirror, uint64_t n, float4 *out)
+{
+    GRID_STRIDE(i, n) {
+        const uint32_t s = slot_of_id[i];
+        out[i] = s != GC_NONE ? pool[s] : mirror[i];
+    }
+}
+
 }  // namespace
+
+extern "C" int gc_build_nbody_tasks_resident(gc_pool_t *p, uint64_t n, int bucket_max,
+                                             int theta_num, int theta_den,
+                                             uint64_t task_id_base, uint64_t info_out[4])
+{
+    if (!p || n == 0 || n > 0x7FFFFFFFull) return GC_ERR_ARG;
+    if (n >= p->cfg.id_capacity) return GC_ERR_POOL_FULL;
+    NBodyState &S = p->nb;
+    GC_TRY(S.hostcopy.reserve(n * sizeof(float4)));
+    ++p->stats.kernel_launches;
+    k_values_of_ids<<<grid_for(n, 256, p->num_sms * 16), 256, 0, p->s>>>(
+        p->d_slot_of_id, p->d_pool, p->d_mirror, n, S.hostcopy.as<float4>());
+    GC_CUDA_TRY(cudaGetLastError());
+    return gc_build_nbody_tasks(p, S.hostcopy.as<float>(), n, bucket_max, theta_num, theta_den,
+                                task_id_base, info_out);
+}
 
 extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_t n,
                                     int bucket_max, int theta_num, int theta_den,

@@ -3,11 +3,11 @@
 // no allocation of any kind.
 //
 // Why it exists: some callers cannot allocate device memory at the moment
-// they need the result -- code running while a CUDA stream is being
-// captured into a graph, code inside another framework whose allocator owns
-// the device memory budget, and latency-critical serving threads where the
-// implicit device-wide synchronisation of cudaMalloc/cudaFree is not
-// acceptable.  The regular path (gc_pool_*/gc_flush) grows its buffers with
+// they need the result -- code inside another framework whose caching
+// allocator already holds the device memory budget (a cudaMalloc beside it
+// can fail or fragment that budget), and latency-critical serving threads
+// where the implicit device-wide synchronisation of cudaMalloc/cudaFree is
+// not acceptable.  The regular path (gc_pool_*/gc_flush) grows its buffers with
 // cudaMalloc; this entry point instead keeps all of its scratch (work-unit
 // table, per-task counts and offsets, work-queue head) in one fixed-size
 // file-scope device array.
@@ -20,6 +20,11 @@
 // it uses and zeroes its queue head.  Two calls whose work overlaps on the
 // GPU (different streams, or the same stream from different host threads
 // without ordering) race on the array.
+//
+// Bad offsets (not starting at 0, decreasing, not ending at n_tgt_total, a
+// task with 2^32 or more sources) are found on the device: such a call
+// computes nothing and writes NaN into every one of its n_tgt_total output
+// rows, so stale rows are never mistaken for results.
 //
 // Set-up: the first call on a device (with that device current) looks up
 // the array's device address with cudaGetSymbolAddress -- the array's name
@@ -44,7 +49,8 @@ struct NaUnit {
 struct NaScratch {
     unsigned long long queue;          // work-queue head (zeroed by every call)
     unsigned long long n_units;        // work units of the current call
-    unsigned int bad;                  // offsets of this call decrease somewhere
+    unsigned int bad;                  // a task of this call has bad offsets
+    unsigned int status;               // 0: consistent call; 1: bad offsets (NaN rows)
     uint32_t unit_cnt[NA_MAX_TASKS + 1];
     uint32_t unit_off[NA_MAX_TASKS + 1];
     NaUnit unit[NA_MAX_TARGETS];       // <= one unit per target
@@ -88,7 +94,8 @@ __global__ void k_na_count(uint64_t n_tasks, const uint64_t *tgt_off, const uint
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n_tasks;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t a = tgt_off[t], b = tgt_off[t + 1];
-        if (b < a || src_off[t + 1] < src_off[t] || b - a > NA_MAX_TARGETS) {
+        const uint64_t sa = src_off[t], sb = src_off[t + 1];
+        if (b < a || sb < sa || sb - sa > 0xFFFFFFFFull || b - a > NA_MAX_TARGETS) {
             S->bad = 1u;
             S->unit_cnt[t] = 0u;
             continue;
@@ -98,7 +105,8 @@ __global__ void k_na_count(uint64_t n_tasks, const uint64_t *tgt_off, const uint
 }
 
 // single block: exclusive scan of the unit counts, unit total, queue reset;
-// a call whose target total disagrees with its offsets runs no unit
+// a call whose target total disagrees with its offsets runs no unit and is
+// marked for NaN output
 __global__ void k_na_scan(uint64_t n_tasks, const uint64_t *tgt_off, uint64_t n_tgt_total,
                           NaScratch *S)
 {
@@ -128,6 +136,7 @@ __global__ void k_na_scan(uint64_t n_tasks, const uint64_t *tgt_off, uint64_t n_
                                 S->bad == 0u && carry <= NA_MAX_TARGETS;
         S->unit_off[n_tasks] = carry;
         S->n_units = consistent ? carry : 0ull;
+        S->status = consistent ? 0u : 1u;
         S->queue = 0ull;
         S->bad = 0u;
     }
@@ -165,17 +174,26 @@ __device__ __forceinline__ void na_kahan(float &s, float &c, float v)
 // S = 32 / T source lanes, sources read in place (float4 x, y, z, m), the
 // same softened-gravity terms and compensated accumulation as the batched
 // kernel; lane results combined in FP64 in lane order; row r of target
-// tgt_off[task] + k gets (s0..s3, c0..c3) with value s - c.
+// tgt_off[task] + k gets (s0..s3, c0..c3) with value s - c.  A call with
+// bad offsets instead fills its n_tgt_total rows with NaN.
 __global__ void __launch_bounds__(NA_THREADS) k_na_gravity(const NaScratch *S,
                                                            const uint64_t *tgt_off,
                                                            const float4 *tgt,
                                                            const uint64_t *src_off,
                                                            const float4 *src, float eps2,
-                                                           float4 *out,
+                                                           float4 *out, uint64_t n_tgt_total,
                                                            unsigned long long *queue)
 {
     __shared__ double red[NA_WARPS][32][4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (S->status != 0u) {
+        const float q = __int_as_float(0x7fc00000);
+        const float4 nan4 = make_float4(q, q, q, q);
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < 2 * n_tgt_total;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            out[i] = nan4;
+        return;
+    }
     const unsigned long long n_units = S->n_units;
     for (;;) {
         unsigned long long w = 0;
@@ -245,6 +263,9 @@ extern "C" int gc_gravity_noalloc(uint64_t n_tasks, const uint64_t *tgt_off, con
     if (n_tasks == 0) return GC_OK;
     if (!tgt_off || !src_off || !tgt_xyzm || !src_xyzm || !out_rows) return GC_ERR_ARG;
     if (((uintptr_t)tgt_xyzm | (uintptr_t)src_xyzm | (uintptr_t)out_rows) % 16) return GC_ERR_ARG;
+    // an error left pending by earlier work is the caller's: report it
+    // without clearing it and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return GC_ERR_CUDA;
     NaScratch *S = nullptr;
     int sms = 0;
     int rc = na_setup(&S, &sms);
@@ -253,11 +274,14 @@ extern "C" int gc_gravity_noalloc(uint64_t n_tasks, const uint64_t *tgt_off, con
     const unsigned g = (unsigned)((n_tasks + 255) / 256 < (uint64_t)sms * 8 ? (n_tasks + 255) / 256
                                                                           : (uint64_t)sms * 8);
     k_na_count<<<g, 256, 0, s>>>(n_tasks, tgt_off, src_off, S);
+    if (cudaGetLastError() != cudaSuccess) return GC_ERR_CUDA;
     k_na_scan<<<1, 1024, 0, s>>>(n_tasks, tgt_off, n_tgt_total, S);
+    if (cudaGetLastError() != cudaSuccess) return GC_ERR_CUDA;
     k_na_fill<<<g, 256, 0, s>>>(n_tasks, tgt_off, S);
+    if (cudaGetLastError() != cudaSuccess) return GC_ERR_CUDA;
     k_na_gravity<<<(unsigned)sms * 4, NA_THREADS, 0, s>>>(
         S, tgt_off, (const float4 *)tgt_xyzm, src_off, (const float4 *)src_xyzm, eps2,
-        (float4 *)out_rows, &S->queue);
+        (float4 *)out_rows, n_tgt_total, &S->queue);
     if (cudaGetLastError() != cudaSuccess) return GC_ERR_CUDA;
     return GC_OK;
 }

@@ -133,12 +133,15 @@ _SIGS = {
     "gc_read_residency": [P, P, P, P],
     "gc_read_evicted": [P, P, U64, U64P],
     "gc_build_nbody_tasks": [P, P, U64, C.c_int, C.c_int, C.c_int, U64, P],
+    "gc_build_nbody_tasks_resident": [P, U64, C.c_int, C.c_int, C.c_int, U64, P],
     "gc_read_nbody_tree": [P] + [P] * 14,
     "gc_build_md_tasks": [P, P, U64, C.c_int, U64, P],
     "gc_build_md_tasks_2d": [P, P, U64, C.c_int, U64, P],
     "gc_read_md_cells": [P, P, P],
     "gc_last_timings": [P, P],
     "gc_gravity_noalloc": [U64, P, P, P, P, U64, C.c_float, P, P],
+    "gc_read_batch_values": [P, U64, U64, P],
+    "gc_row_values": [P, U64, P],
     "gc_combiner_create": [C.c_int, U64, U64, U64, C.POINTER(P)],
     "gc_combiner_destroy": [P],
     "gc_combiner_arrive": [P, U64, U64],
@@ -323,6 +326,16 @@ class Pool:
         out = np.empty((n, 8), np.float32)
         _check(self.lib.gc_read_batch_results(self.h, first, n, _p(out)),
                "gc_read_batch_results")
+        return out
+
+    def values(self, first=0, n=None):
+        """(rows, 4) float64 values s - c of the last batch's rows, computed
+        on the device (gc_read_batch_values)."""
+        if n is None:
+            n = self.result_rows() - first
+        out = np.empty((n, 4), np.float64)
+        _check(self.lib.gc_read_batch_values(self.h, first, n, _p(out)),
+               "gc_read_batch_values")
         return out
 
     def batch_rows(self, batch, first=0, n=None):
@@ -516,6 +529,16 @@ class Pool:
                "gc_build_nbody_tasks")
         return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]))
 
+    def build_nbody_resident(self, n, bucket_max=32, theta_num=7, theta_den=10,
+                             task_id_base=0):
+        """As build_nbody, with the positions of particles 0..n-1 read from
+        the pool's current values (no second host-to-device copy)."""
+        info = np.zeros(4, np.uint64)
+        _check(self.lib.gc_build_nbody_tasks_resident(self.h, int(n), bucket_max, theta_num,
+                                                      theta_den, task_id_base, _p(info)),
+               "gc_build_nbody_tasks_resident")
+        return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]))
+
     def nbody_tree(self, n, n_nodes, n_buckets, n_list):
         out = dict(sorted_ids=np.empty(n, np.uint32), sorted_keys=np.empty(n, np.uint64),
                    level=np.empty(n_nodes, np.uint8), cell=np.empty((n_nodes, 3), np.uint32),
@@ -621,21 +644,52 @@ class Graph:
 
 
 def value(res):
-    """FP64 value s - c of result rows (rows, 8) -> (rows, 4)."""
-    return res[:, :4].astype(np.float64) - res[:, 4:].astype(np.float64)
+    """FP64 values of compensated result rows (rows, 8) float32 -> (rows, 4)
+    float64, computed by the library (gc_row_values)."""
+    rows = np.ascontiguousarray(res, np.float32)
+    if rows.ndim != 2 or rows.shape[1] != 8:
+        raise ValueError("expected result rows of shape (n, 8)")
+    out = np.empty((rows.shape[0], 4), np.float64)
+    _check(load().gc_row_values(_p(rows), rows.shape[0], _p(out)), "gc_row_values")
+    return out
 
 
 def gravity_noalloc(tgt_off, tgt_xyzm, src_off, src_xyzm, n_tgt_total, eps2, out_rows,
                     stream=None):
     """Softened gravity of a CSR batch already in device memory, without any
-    allocation (for callers that cannot allocate at that point: stream
-    capture, foreign allocators, latency-critical threads).  All arguments
-    are CUDA tensors (offsets as 64-bit integers, values (n, 4) float32, out
-    (n_tgt_total, 8) float32); the call is queued on ``stream`` (a raw
-    cudaStream_t handle; None = the legacy default stream)."""
+    allocation, for callers that cannot allocate when they need the result
+    (a framework whose allocator already holds the device memory budget,
+    latency-critical threads that must not take cudaMalloc/cudaFree's
+    device-wide synchronisation).  Offsets are int64 CUDA tensors of
+    n_tasks + 1 entries, values float32 (n, 4) CUDA tensors, out a float32
+    (n_tgt_total, 8) CUDA tensor, all on the current device; the call is
+    queued on ``stream`` (a raw cudaStream_t handle; None = the legacy
+    default stream).  Shapes and types are checked here, before the library
+    is called, because the library cannot see the tensors' sizes."""
+    import torch
+    dev = torch.cuda.current_device()
+    n_tgt_total = int(n_tgt_total)
+    for name, t in (("tgt_off", tgt_off), ("src_off", src_off), ("tgt_xyzm", tgt_xyzm),
+                    ("src_xyzm", src_xyzm), ("out_rows", out_rows)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name}: on cuda:{t.device.index}, not the current device cuda:{dev}")
+    for name, t in (("tgt_off", tgt_off), ("src_off", src_off)):
+        if t.dtype != torch.int64 or t.dim() != 1 or t.numel() < 1:
+            raise ValueError(f"{name}: expected a 1-D int64 tensor of n_tasks + 1 offsets")
+    if src_off.numel() != tgt_off.numel():
+        raise ValueError("tgt_off and src_off must hold the same number of offsets")
+    for name, t in (("tgt_xyzm", tgt_xyzm), ("src_xyzm", src_xyzm)):
+        if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 4:
+            raise ValueError(f"{name}: expected a float32 tensor of shape (n, 4)")
+    if tgt_xyzm.shape[0] < n_tgt_total:
+        raise ValueError("tgt_xyzm holds fewer than n_tgt_total rows")
+    if out_rows.dtype != torch.float32 or tuple(out_rows.shape) != (n_tgt_total, 8):
+        raise ValueError("out_rows: expected a float32 tensor of shape (n_tgt_total, 8)")
     lib = load()
     _check(lib.gc_gravity_noalloc(tgt_off.numel() - 1, _dptr(tgt_off), _dptr(tgt_xyzm),
-                                  _dptr(src_off), _dptr(src_xyzm), int(n_tgt_total),
+                                  _dptr(src_off), _dptr(src_xyzm), n_tgt_total,
                                   float(eps2), _dptr(out_rows), stream),
            "gc_gravity_noalloc")
 

@@ -86,3 +86,19 @@ def test_missing_library_fails_loudly(tmp_path):
             gcharm.load(str(tmp_path / "nope.so"))
     finally:
         gcharm._lib = saved
+
+
+def test_row_values_on_the_host():
+    """gc_row_values (a host function, no GPU needed): the FP64 value s - c of
+    each compensated row, component by component, with hand-worked values
+    that an FP32 subtraction or swapped halves would get wrong."""
+    import numpy as np
+    from paper_2008_05712_gb300 import gcharm
+    gcharm.load()
+    rows = np.array([[1.0, -2.0, 0.5, 3.0, 2.0 ** -30, 0.0, -0.25, 3.0],
+                     [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]], np.float32)
+    v = gcharm.value(rows)
+    assert v.dtype == np.float64 and v.shape == (2, 4)
+    assert v[0].tolist() == [1.0 - 2.0 ** -30, -2.0, 0.75, 0.0]
+    assert v[1].tolist() == [0.0, 0.0, 0.0, 0.0]
+    assert gcharm.value(np.zeros((0, 8), np.float32)).shape == (0, 4)

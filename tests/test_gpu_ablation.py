@@ -30,14 +30,14 @@ def test_ablation_modes_agree_with_oracle(gc, orc):
     pool.flush()
     pool.wait(b)
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-    packed = gc.value(pool.results())
+    packed = pool.values()
     assert per_task_errors(packed, ref, to).max() <= TOL
     r = pool.reuse_ablation(reps=1)
     for k in ["kernel_pack_ms", "kernel_indirect_ms", "kernel_sorted_indirect_ms",
               "redundant_h2d_ms"]:
         assert r[k] > 0, k
     # rows now hold the last device mode's run (sorted slots)
-    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    assert per_task_errors(pool.values(), ref, to).max() <= TOL
     assert r["redundant_bytes"] == 16 * (len(sr) + len(to) - 1)
     assert r["reuse_fetch_bytes"] == 16 * len(np.unique(np.concatenate([tg, sr])))
     pool.close()
@@ -60,5 +60,5 @@ def test_ablation_list_order_run(gc, orc):
     pool.wait(b)
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
     pool.reuse_ablation(reps=1)
-    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    assert per_task_errors(pool.values(), ref, to).max() <= TOL
     pool.close()

@@ -38,7 +38,7 @@ def test_uneven_tasks_vs_oracle(gc, orc):
     pool.flush()
     pool.wait(b)
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-    got = gc.value(pool.results())
+    got = pool.values()
     errs = per_task_errors(got, ref, to)
     assert errs.max() <= TOL, errs.max()
     # totals: ids repeat across tasks; FP64 sums in admission order
@@ -72,7 +72,7 @@ def test_results_by_task_id(gc, orc):
     pick = [1013, 1002]
     rows = int((to[14] - to[13]) + (to[3] - to[2]))
     got = gc.value(pool.read_results(np.array(pick, np.uint64), rows))
-    all_rows = gc.value(pool.results())
+    all_rows = pool.values()
     exp = np.concatenate([all_rows[to[13]:to[14]], all_rows[to[2]:to[3]]])
     assert np.array_equal(got, exp)
     pool.close()
@@ -104,7 +104,7 @@ def test_eviction_sequence_matches_oracle(gc, orc):
         assert np.array_equal(o2s, R.id_of_slot), epoch
         assert np.array_equal(pool.evicted(), r["evicted"]), epoch
         ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-        errs = per_task_errors(gc.value(pool.results()), ref, to)
+        errs = per_task_errors(pool.values(), ref, to)
         assert errs.max() <= TOL
     assert pool.stats()["evictions"] > 0
     pool.close()
@@ -210,7 +210,7 @@ def test_edge_cases(gc, orc):
                        dict(task_id=2, kind=0, targets=tg[3:4], sources=sr[5:9]),
                        dict(task_id=3, kind=0, targets=tg[4:5], sources=sr[9:10])])
     pool.flush()
-    got = gc.value(pool.results())
+    got = pool.values()
     assert got.shape[0] == 5
     assert np.all(got[:3] == 0)
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
@@ -240,11 +240,11 @@ def test_wait_expiry_reported_and_pool_stays_usable(gc, orc):
         pool.wait(b1)
     assert e.value.code == gc.GC_ERR_TIMEOUT
     pool.wait(b1)                       # the status was cleared by the report
-    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    assert per_task_errors(pool.values(), ref, to).max() <= TOL
     b2 = submit_gravity(pool, to, tg, so, sr)
     pool.flush()
     pool.wait(b2)
-    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    assert per_task_errors(pool.values(), ref, to).max() <= TOL
     for bad in (0, (1 << 24) + 1):
         with pytest.raises(gc.GcError) as e:
             pool.check_wait_expiry(bad)

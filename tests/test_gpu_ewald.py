@@ -56,7 +56,7 @@ def test_ewald_batch_vs_oracle(gc, orc):
     b = pool.submit_csr(kinds, to, tg, so, sr)
     pool.flush()
     pool.wait(b)
-    got = gc.value(pool.results())
+    got = pool.values()
     ref = oracle_rows(orc, x, to, tg, so, sr)
     errs = per_task_errors(got, ref, to)
     assert errs.max() <= TOL, errs.max()
@@ -69,7 +69,7 @@ def test_ewald_batch_vs_oracle(gc, orc):
     b = pool.submit_csr(kinds, to, tg, so, sr)
     pool.flush_per_task()
     pool.wait(b)
-    assert np.array_equal(gc.value(pool.results()), got)
+    assert np.array_equal(pool.values(), got)
     pool.close()
 
 
@@ -101,7 +101,7 @@ def test_ewald_in_a_mixed_batch(gc, orc):
     b = pool.submit_tasks(tasks)
     pool.flush()
     pool.wait(b)
-    got = gc.value(pool.results())
+    got = pool.values()
     row = 0
     for t, d in enumerate(tasks):
         tg = np.asarray(d["targets"], np.uint32)

@@ -89,7 +89,7 @@ def test_nbody_1m(gc, orc):
     to_all, tg_all = np.zeros(tr.n_buckets + 1, np.uint64), g["sorted_ids"]
     to_all[1:] = np.cumsum(g["bucket_count"])
     assert np.array_equal(g["bucket_first"], to_all[:-1])   # buckets partition in order
-    rows = gc.value(pool.results())
+    rows = pool.values()
     got = np.concatenate([rows[int(to_all[b]):int(to_all[b + 1])] for b in sample])
     errs = per_task_errors(got, ref, to_s)
     assert errs.max() <= TOL, errs.max()
@@ -120,7 +120,7 @@ def test_md_1m(gc, orc):
     rows_per = cnt[ta] + np.where(ts != 0, 0, cnt[tb])
     roff = np.zeros(len(ta) + 1, np.int64)
     roff[1:] = np.cumsum(rows_per)
-    rows = gc.value(pool.results())
+    rows = pool.values()
     assert rows.shape[0] == roff[-1]
     # sampled tasks against the oracle, Newton III inside each
     rng = np.random.default_rng(12)

@@ -46,7 +46,7 @@ def test_kick_drift_bit_exact(gc, orc):
     pool.wait(b)
     ref = orc.gravity_batch(x_ref, to, np.array([0], np.uint32), so, np.array([1], np.uint32),
                             EPS2)
-    assert rel_l2(gc.value(pool.results())[:, :3], ref[:, :3]) <= TOL
+    assert rel_l2(pool.values()[:, :3], ref[:, :3]) <= TOL
     pool.close()
 
 

@@ -55,7 +55,7 @@ def test_cells_bit_exact(gc, orc, small_md):
 def test_forces_vs_oracle(gc, orc, small_md):
     sysm = small_md
     pool, info = run_md(gc, sysm)
-    got = gc.value(pool.results())
+    got = pool.values()
     start, atoms, ta, tb, td, ts = oracle_tasks(orc, sysm)
     row = 0
     errs = []

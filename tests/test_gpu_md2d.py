@@ -33,7 +33,7 @@ def test_planar_md_vs_oracle(gc, orc, side, ncell):
     assert np.array_equal(start, s0) and np.array_equal(atoms, a0)
     ta, tb, td, ts = orc.md_tasks_2d(m)
     assert info["tasks"] == len(ta) == 5 * m * m
-    got = gc.value(pool.results())
+    got = pool.values()
     row, errs, inside = 0, [], 0
     tot_ref = np.zeros((n, 4))
     for k in range(len(ta)):

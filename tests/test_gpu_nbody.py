@@ -67,7 +67,7 @@ def test_forces_vs_oracle(gc, orc, n):
     to, tg = tr.bucket_targets()
     lo, li = tr.lists(7, 10)
     ref = orc.gravity_batch(tab, to, tg, lo, li, EPS2)
-    got = gc.value(pool.results())
+    got = pool.values()
     errs = per_task_errors(got, ref, to)
     assert errs.max() <= TOL, (errs.max(), np.argmax(errs))
     # per-id FP64 totals: each particle is the target of exactly one bucket
@@ -142,7 +142,7 @@ def test_drift_step_reuses_slots(gc, orc):
     to, tg = tr.bucket_targets()
     lo, li = tr.lists(7, 10)
     ref = orc.gravity_batch(tab, to, tg, lo, li, EPS2)
-    errs = per_task_errors(gc.value(pool.results()), ref, to)
+    errs = per_task_errors(pool.values(), ref, to)
     assert errs.max() <= TOL
     pool.close()
 
@@ -199,3 +199,31 @@ def test_build_repeats_bit_for_bit(gc):
         assert np.array_equal(node_val, out[0][0])
         assert np.array_equal(rows, out[0][1])
     pool.close()
+
+
+def test_build_from_resident_values_matches_build_from_positions(gc):
+    """gc_build_nbody_tasks_resident reads the positions of ids 0..n-1 from
+    the pool (from the host mirror before any flush has placed them, from
+    their slots after) and builds the same tree and rows as the build that is
+    handed the positions, over two drift steps."""
+    n = 6000
+    x0 = inputs.plummer(n, inputs.SEED_BASE + 9)
+    x1 = inputs.drift(x0, inputs.SEED_BASE + 10)
+    ids = np.arange(n, dtype=np.uint32)
+    a = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    b = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    for x in (x0, x1):
+        a.upload(ids, x)
+        ia = a.build_nbody(torch.from_numpy(x).cuda(), 32, 7, 10)
+        a.flush()
+        b.upload(ids, x)
+        ib = b.build_nbody_resident(n, 32, 7, 10)
+        b.flush()
+        assert ia == ib
+        ta = a.nbody_tree(n, ia["n_nodes"], ia["n_buckets"], ia["list_entries"])
+        tb = b.nbody_tree(n, ib["n_nodes"], ib["n_buckets"], ib["list_entries"])
+        for k in ta:
+            assert np.array_equal(ta[k], tb[k]), k
+        assert np.array_equal(a.results(), b.results())
+    a.close()
+    b.close()

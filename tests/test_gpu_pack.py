@@ -75,7 +75,7 @@ def test_pack_permutation_adversarial(gc, orc, warm):
     assert np.array_equal(ps, orc.pack_perm_batch(so, ss))
     assert np.array_equal(pt, orc.pack_perm_batch(to, st))
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-    errs = per_task_errors(gc.value(pool.results()), ref, to)
+    errs = per_task_errors(pool.values(), ref, to)
     assert errs.max() <= TOL, errs.max()
     pool.close()
 
@@ -107,6 +107,6 @@ def test_pack_permutation_small_lists(gc, orc):
     assert np.array_equal(pt, orc.pack_perm_batch(to, st))
     assert np.array_equal(ps, orc.pack_perm_batch(so, ss))
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-    errs = per_task_errors(gc.value(pool.results()), ref, to)
+    errs = per_task_errors(pool.values(), ref, to)
     assert errs.max() <= TOL, errs.max()
     pool.close()

@@ -71,7 +71,7 @@ def test_serve_mix_equals_alone_and_oracle(gc, orc):
         bi = pool.submit_csr(np.zeros(1, np.uint32), one_to, tg[a:b], one_so, sr[c:d])
         pool.flush()
         pool.wait(bi)
-        alone = gc.value(pool.results())
+        alone = pool.values()
         assert rel_l2(mix[a:b, :3], alone[:, :3]) <= TOL
         assert rel_l2(alone[:, :3], ref[a:b, :3]) <= TOL
     pool.close()

@@ -81,12 +81,12 @@ def test_autotune_keeps_fastest_and_caches(gc, orc, batch, tmp_path):
     assert pool.tuning() == choice
     # the re-run rows of the tuned batch still match the oracle
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    assert per_task_errors(pool.values(), ref, to).max() <= TOL
     # the next flush runs under the choice
     b = pool.submit_csr(np.zeros(len(to) - 1, np.uint32), to, tg, so, sr)
     pool.flush()
     pool.wait(b)
-    assert per_task_errors(gc.value(pool.results()), ref, to).max() <= TOL
+    assert per_task_errors(pool.values(), ref, to).max() <= TOL
     # JSON cache: stored on the first call, applied without tuning on the next
     cache = str(tmp_path / "tuning.json")
     c1, t1 = pool.autotune(reps=1, cache=cache, key="uneven300")
