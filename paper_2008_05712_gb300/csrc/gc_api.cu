@@ -119,7 +119,7 @@ void free_ctx(FlushCtx &c)
     DBuf *bufs[] = {&c.tasks, &c.tgt_ids, &c.src_ids, &c.tgt_perm, &c.src_perm, &c.stg_tgt,
                     &c.stg_src, &c.wu, &c.wu_cnt, &c.wu_off, &c.rowcnt, &c.lj_list, &c.res,
                     &c.row_id, &c.rid_sorted, &c.row_sorted, &c.rows_tmp, &c.runs, &c.tiles,
-                    &c.merge_a, &c.merge_b, &c.cub_tmp, &c.lpt};
+                    &c.merge_a, &c.merge_b, &c.cub_tmp, &c.lpt, &c.ent};
     for (DBuf *b : bufs) b->release();
     for (int i = 0; i < 6; ++i)
         if (c.ev_stage[i]) cudaEventDestroy(c.ev_stage[i]);
@@ -648,6 +648,10 @@ static int flush_impl(gc_pool *p, int per_task)
     }
     GC_TRY(c.stg_tgt.reserve((max_wt + 1) * sizeof(float4)));
     GC_TRY(c.stg_src.reserve((max_ws + 1) * sizeof(float4)));
+    uint64_t max_we = 0;   // entries of the largest wave (entry slots)
+    for (const Wave &w : waves)
+        if (w.tg1 - w.tg0 + w.s1 - w.s0 > max_we) max_we = w.tg1 - w.tg0 + w.s1 - w.s0;
+    GC_TRY(c.ent.reserve((max_we + 1) * sizeof(uint32_t)));
     if (max_list > 16384) {   // lists beyond one shared-memory sort: chunk + merge
         GC_TRY(c.merge_a.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
         GC_TRY(c.merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
@@ -671,10 +675,12 @@ static int flush_impl(gc_pool *p, int per_task)
     for (size_t k = 0; k < waves.size(); ++k) {
         const Wave &w = waves[k];
         if (k > 0) GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
-        rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0);
+        rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0,
+                          c.ent.as<uint32_t>());
         if (rc != GC_OK) return rc;
         GC_CUDA_TRY(cudaEventRecord(c.ev_stage[1], c.s));
-        GC_TRY(gc_pack(p, c, w.t0, w.t1, w.tg0, w.s0, max_wt + 1));
+        GC_TRY(gc_pack(p, c, w.t0, w.t1, w.tg0, w.s0, max_wt + 1, c.ent.as<uint32_t>(),
+                       w.tg1 - w.tg0));
         GC_CUDA_TRY(cudaEventRecord(c.ev_stage[2], c.s));
         uint64_t w0 = 0, w1 = W, l0 = 0, l1 = L;
         if (need_offsets) {

@@ -130,6 +130,7 @@ struct FlushCtx {
     DBuf wu, wu_cnt, wu_off, rowcnt, lj_list, res, row_id;
     DBuf lpt;                          // longest-first ordering scratch
     DBuf rid_sorted, row_sorted, rows_tmp, runs, tiles, merge_a, merge_b, cub_tmp;
+    DBuf ent;                          // the current wave's entry slots
     cudaEvent_t ev_stage[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_done = nullptr, ev_packed = nullptr, ev_scattered = nullptr;
     bool timing_valid = false;
@@ -228,11 +229,13 @@ int gc_exclusive_scan_u32(DBuf &tmp, const uint32_t *in, uint32_t *out, uint64_t
 
 // ---- residency (gc_residency.cu) -----------------------------------------------
 // Runs the chare-table step for the entries tgt[0..nt) and src[0..ns): after
-// it every referenced id is resident.  Returns GC_OK, GC_ERR_UNKNOWN_ID or
+// it every referenced id is resident.  With `ent` (nt + ns words, may be
+// null) it also records each entry's slot as found before any miss was
+// placed (NONE for a miss).  Returns GC_OK, GC_ERR_UNKNOWN_ID or
 // GC_ERR_POOL_FULL.
 int gc_entry_slots(gc_pool *p, cudaStream_t s, const uint32_t *ids, uint64_t n, uint32_t *out);
 int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
-                 uint64_t ns);
+                 uint64_t ns, uint32_t *ent);
 int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64_t n,
                      int write_mirror);
 
@@ -250,8 +253,10 @@ int gc_clear_flags(gc_pool *p, cudaStream_t s, unsigned long long mask);
 int gc_apply_totals_reset(gc_pool *p, cudaStream_t s);
 int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
                        std::vector<uint32_t> &lj_off);
+// `ent` (may be null): the wave's entry slots (as gc_residency records
+// them), the wave's ent_nt target entries first, then its source entries.
 int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,
-            uint64_t src_base, uint64_t msrc);
+            uint64_t src_base, uint64_t msrc, const uint32_t *ent, uint64_t ent_nt);
 int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,
                       uint64_t l1, uint64_t tgt_base, uint64_t src_base, uint64_t task_base);
 int gc_interact_one_task(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_t l0,

@@ -18,6 +18,7 @@ struct gc_graph {
     gc_pool *p = nullptr;
     FlushCtx c;                       // the graph's own batch buffers and stream
     DBuf uniq;                        // distinct ids of the batch
+    DBuf ent;                         // slot of every entry (targets, then sources)
     uint64_t n_uniq = 0;
     uint32_t *d_epoch = nullptr;      // epoch of the current replay (device)
     uint32_t *h_epoch = nullptr;      // pinned staging of it
@@ -66,6 +67,7 @@ void destroy_graph(gc_graph *g)
     if (g->d_epoch) cudaFree(g->d_epoch);
     if (g->h_epoch) cudaFreeHost(g->h_epoch);
     g->uniq.release();
+    g->ent.release();
     free_ctx(g->c);
     delete g;
 }
@@ -214,6 +216,18 @@ extern "C" int gc_graph_capture(gc_pool_t *p, gc_graph_t **out)
         destroy_graph(g);
         return rc;
     }
+    // the slot of every entry, fixed for the graph's lifetime (a replay is
+    // refused once any slot has been assigned or freed)
+    if (rc == GC_OK) rc = g->ent.reserve((g->entries + 1) * sizeof(uint32_t));
+    if (rc == GC_OK && c.n_tgt)
+        rc = gc_entry_slots(p, c.s, c.tgt_ids.as<uint32_t>(), c.n_tgt, g->ent.as<uint32_t>());
+    if (rc == GC_OK && c.n_src)
+        rc = gc_entry_slots(p, c.s, c.src_ids.as<uint32_t>(), c.n_src,
+                            g->ent.as<uint32_t>() + c.n_tgt);
+    if (rc != GC_OK) {
+        destroy_graph(g);
+        return rc;
+    }
     {
         // interactions of the batch, as the flush counted them
         unsigned long long inter = 0;
@@ -236,7 +250,13 @@ extern "C" int gc_graph_capture(gc_pool_t *p, gc_graph_t **out)
         k_touch_epoch<<<grid_for(g->n_uniq, 256, maxb), 256, 0, c.s>>>(
             g->uniq.as<uint32_t>(), g->n_uniq, p->d_slot_of_id, p->d_last_use, g->d_epoch);
     for (const WaveRange &w : c.waves) {
-        if (rc == GC_OK) rc = gc_pack(p, c, w.t0, w.t1, w.tg0, w.s0, c.msrc);
+        if (rc == GC_OK) {
+            // per-wave views of the batch-wide entry slots: targets of the
+            // wave, then (at ent_t + ent_nt) its sources
+            const uint32_t *et = g->ent.as<uint32_t>() + w.tg0;
+            const uint32_t *es = g->ent.as<uint32_t>() + c.n_tgt + w.s0;
+            rc = gc_pack(p, c, w.t0, w.t1, w.tg0, w.s0, c.msrc, et, (uint64_t)(es - et));
+        }
         if (rc == GC_OK) rc = gc_interact_range(p, c, w.w0, w.w1, w.l0, w.l1, w.tg0, w.s0, w.t0);
     }
     if (rc == GC_OK) rc = gc_scatter_replay(p, c);

@@ -131,15 +131,13 @@ __global__ void k_wu_gather(const GravWU *wu, const uint32_t *idx, uint64_t n, G
 
 constexpr int PK_CAP = 4096;          // entries sorted in shared memory at once
 constexpr int PK_CAP_HUGE = 16384;    // the same, one block per SM (about 200 KB)
-constexpr int PK_CAP_SMALL = 2048;    // lists up to this size use half the shared memory
-constexpr int PK_THREADS = 256;
-constexpr int PK_WARPS = PK_THREADS / 32;
 
 struct PackArgs {
     const TaskRec *tasks;
     uint64_t t0, n_lists;
     const uint32_t *tgt_ids, *src_ids;   // batch-global entry index
     const uint32_t *slot_of_id;
+    const uint32_t *ent_t, *ent_s;       // entry slots (wave-local index; NONE: look up), or null
     uint32_t *perm_t, *perm_s;           // batch-global entry index
     float4 *stg_t, *stg_s;               // wave-local staging
     uint64_t tgt_base, src_base, task_base;
@@ -156,6 +154,7 @@ struct PackList {
     bool src;
     bool paired;      // gravity source list
     uint64_t stg;     // first staging float4 (wave-local)
+    const uint32_t *es;   // entry slots of the list, or null
 };
 
 __device__ __forceinline__ PackList list_of(const PackArgs &a, uint64_t L)
@@ -168,6 +167,8 @@ __device__ __forceinline__ PackList list_of(const PackArgs &a, uint64_t L)
     l.off = l.src ? r->src_off : r->tgt_off;
     l.paired = l.src && r->kind == GC_GRAVITY;
     l.stg = l.src ? (l.off - a.src_base) + (t - a.task_base) : l.off - a.tgt_base;
+    l.es = !a.ent_t ? nullptr
+                    : (l.src ? a.ent_s + (l.off - a.src_base) : a.ent_t + (l.off - a.tgt_base));
     return l;
 }
 
@@ -175,6 +176,18 @@ __device__ __forceinline__ uint32_t list_n(const PackArgs &a, uint64_t L)
 {
     const TaskRec *r = a.tasks + a.t0 + (L >> 1);
     return (L & 1) ? r->ns : r->nt;
+}
+
+// Slot of entry k of list l: the slot recorded by the chare-table step, or
+// (a miss placed after it, or no record) a lookup.
+__device__ __forceinline__ uint32_t entry_slot(const PackArgs &a, const PackList &l,
+                                               const uint32_t *ids, uint32_t k)
+{
+    if (l.es) {
+        const uint32_t s = __ldg(l.es + k);
+        if (s != GC_NONE) return s;
+    }
+    return __ldg(a.slot_of_id + __ldg(ids + k));
 }
 
 // The block-per-list kernels claim lists dynamically, PK_CHUNK at a time
@@ -285,7 +298,7 @@ __global__ void k_pack_small(PackArgs a)
             const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
             uint64_t key = ~0ull;
             if ((uint32_t)hl < l.n)
-                key = ((uint64_t)a.slot_of_id[ids[hl]] << 32) | (uint64_t)hl;
+                key = ((uint64_t)entry_slot(a, l, ids, (uint32_t)hl) << 32) | (uint64_t)hl;
             key = bitonic_lanes<16>(key, hl);
             if ((uint32_t)hl < l.n)
                 emit(a, l, hl, (uint32_t)(key >> 32), (uint32_t)(key & 0xFFFFFFFFu));
@@ -298,7 +311,7 @@ __global__ void k_pack_small(PackArgs a)
             const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
             uint64_t key = ~0ull;
             if ((uint32_t)lane < l.n)
-                key = ((uint64_t)a.slot_of_id[ids[lane]] << 32) | (uint64_t)lane;
+                key = ((uint64_t)entry_slot(a, l, ids, (uint32_t)lane) << 32) | (uint64_t)lane;
             key = bitonic_lanes<32>(key, lane);
             if ((uint32_t)lane < l.n)
                 emit(a, l, lane, (uint32_t)(key >> 32), (uint32_t)(key & 0xFFFFFFFFu));
@@ -322,16 +335,10 @@ __device__ __forceinline__ uint32_t warp_match(uint32_t d, uint32_t valid)
     return m;
 }
 
-template <int CAP, int NW = PK_WARPS>
-struct PackSmem {
-    uint32_t ka[CAP], kb[CAP];           // slots
-    uint16_t pa[CAP], pb[CAP];           // list positions (within a chunk)
-    uint32_t hist[NW][256];              // per (warp, digit) counts, then offsets
-    uint32_t wsum[NW];
-    int skip;
-};
-
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *wsum)
+// Exclusive prefix sum over the block's NW warps (one value per thread);
+// barriers before and after the use of wsum, so it can be called again.
+template <int NW>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t x = v;
@@ -348,125 +355,323 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t *wsu
     return before + x - v;
 }
 
-// Stable LSD radix sort of n <= PK_CAP (slot, pos) entries held in ka/pa,
-// 8-bit digits, `passes` passes.  Warp w owns a contiguous range of the
-// items; inside a warp, 32 items at a time are ranked among equal digits
-// by label ballots, so equal digits keep their order (warp by warp,
-// chunk by chunk, lane by lane).  Returns 0 if the result is in ka/pa, 1 if
-// in kb/pb.
-// NW warps (256 threads or more); threads 0..255 own one digit each in the
-// scans.
-template <int CAP, int NW>
-__device__ int block_radix_sort(PackSmem<CAP, NW> &sm, int n, int passes)
+// Stable LSD radix sort of n (slot, position) entries held in (ka, pa) by
+// slot - kmin, 8-bit digits, `passes` passes, alternating with (kb, pb).
+// Warp w owns a contiguous range of the current layout; inside a warp, 32
+// items at a time are ranked among equal digits by label ballots, so equal
+// digits keep their order (warp by warp, chunk by chunk, lane by lane).  A
+// pass whose digits are all equal is skipped.  hist: NW x 256 counters.
+// Returns true if the result ends in (kb, pb).
+template <int NW>
+__device__ __forceinline__ bool radix_lsd(uint32_t *ka, uint16_t *pa, uint32_t *kb, uint16_t *pb,
+                          uint32_t *hist, uint32_t *wsum, int *skip, int n, int passes,
+                          uint32_t kmin)
 {
-    static_assert(NW >= 8, "one thread per digit");
+    constexpr int NT = NW * 32;
+    constexpr int DPT = NT >= 256 ? 1 : 256 / NT;   // digits per thread in the offset scan
+    static_assert(DPT * NT >= 256, "every digit has an owner");
+    const bool owner = threadIdx.x * DPT < 256;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const bool digit_owner = threadIdx.x < 256;
     const int per = (((n + NW - 1) / NW) + 31) & ~31;
     const int b0 = min(n, w * per), b1 = min(n, b0 + per);
-    uint32_t *ka = sm.ka, *kb = sm.kb;
-    uint16_t *pa = sm.pa, *pb = sm.pb;
-    int flip = 0;
+    bool flip = false;
     for (int pass = 0; pass < passes; ++pass) {
         const int sh = 8 * pass;
-        for (int i = threadIdx.x; i < 256 * NW; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
-        if (threadIdx.x == 0) sm.skip = 0;
+        for (int i = threadIdx.x; i < 256 * NW; i += NT) hist[i] = 0;
+        if (threadIdx.x == 0) *skip = 0;
         __syncthreads();
-        for (int c = b0; c < b1; c += 32) {
-            const int k = c + lane;
-            const bool v = k < b1;
-            if (v) atomicAdd(&sm.hist[w][(ka[k] >> sh) & 255u], 1u);
-        }
+        for (int k = b0 + lane; k < b1; k += 32)
+            atomicAdd(&hist[w * 256 + (((ka[k] - kmin) >> sh) & 255u)], 1u);
         __syncthreads();
         uint32_t s = 0;
-        if (digit_owner)
-            for (int q = 0; q < NW; ++q) s += sm.hist[q][threadIdx.x];
-        if (digit_owner && s == (uint32_t)n) sm.skip = 1;   // one digit value: identity pass
-        uint32_t run = block_excl_scan256(s, sm.wsum);
-        if (digit_owner)
-            for (int q = 0; q < NW; ++q) {
-                uint32_t c = sm.hist[q][threadIdx.x];
-                sm.hist[q][threadIdx.x] = run;
-                run += c;
+        if (owner) {
+#pragma unroll
+            for (int i = 0; i < DPT; ++i) {
+                uint32_t c = 0;
+                for (int q = 0; q < NW; ++q) c += hist[q * 256 + DPT * threadIdx.x + i];
+                if (c == (uint32_t)n) *skip = 1;       // one digit value: identity pass
+                s += c;
             }
-        __syncthreads();
-        if (sm.skip) continue;
-        for (int c = b0; c < b1; c += 32) {
-            const int k = c + lane;
-            const bool v = k < b1;
-            const uint32_t key = v ? ka[k] : 0u;
-            const uint32_t d = (key >> sh) & 255u;
-            const uint32_t m = warp_match<8>(d, __ballot_sync(0xffffffffu, v));
-            if (v) {
-                const uint32_t dst = sm.hist[w][d] + (uint32_t)__popc(m & lt);
-                kb[dst] = key;
-                pb[dst] = pa[k];
-            }
-            __syncwarp();
-            if (v && (m & lt) == 0) sm.hist[w][d] += (uint32_t)__popc(m);
-            __syncwarp();
+        }
+        uint32_t run = block_excl_scan<NW>(s, wsum);
+        if (owner) {
+#pragma unroll
+            for (int i = 0; i < DPT; ++i)
+                for (int q = 0; q < NW; ++q) {
+                    const uint32_t c = hist[q * 256 + DPT * threadIdx.x + i];
+                    hist[q * 256 + DPT * threadIdx.x + i] = run;
+                    run += c;
+                }
         }
         __syncthreads();
-        uint32_t *tk = ka; ka = kb; kb = tk;
-        uint16_t *tp = pa; pa = pb; pb = tp;
-        flip ^= 1;
+        const bool skip_pass = *skip != 0;
+        if (!skip_pass) {
+            for (int c = b0; c < b1; c += 32) {
+                const int k = c + lane;
+                const bool v = k < b1;
+                const uint32_t key = v ? ka[k] : 0u;
+                const uint32_t d = ((key - kmin) >> sh) & 255u;
+                const uint32_t m = warp_match<8>(d, __ballot_sync(0xffffffffu, v));
+                if (v) {
+                    const uint32_t dst = hist[w * 256 + d] + (uint32_t)__popc(m & lt);
+                    kb[dst] = key;
+                    pb[dst] = pa[k];
+                }
+                __syncwarp();
+                if (v && (m & lt) == 0) hist[w * 256 + d] += (uint32_t)__popc(m);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (!skip_pass) {
+            uint32_t *tk = ka; ka = kb; kb = tk;
+            uint16_t *tp = pa; pa = pb; pb = tp;
+            flip = !flip;
+        }
     }
     return flip;
 }
 
-// Lists of 33..2048 entries: one block of 4 warps per list, LSD radix sort
-// of (slot, pos) with 8-bit digits in shared memory.  Two size classes
-// (33..1024 and 1025..2048) with their own shared-memory footprint, so the
-// common short lists keep twice as many blocks resident.
+// Insertion sort of entries [s, e) of (k, p) by (slot, position), one thread.
+__device__ __forceinline__ void insertion_sort(uint32_t *k, uint16_t *p, int s, int e)
+{
+    for (int i = s + 1; i < e; ++i) {
+        const uint32_t kv = k[i];
+        const uint16_t pv = p[i];
+        int j = i - 1;
+        while (j >= s) {
+            const uint32_t kj = k[j];
+            const uint16_t pj = p[j];
+            if (kj < kv || (kj == kv && pj < pv)) break;
+            k[j + 1] = kj;
+            p[j + 1] = pj;
+            --j;
+        }
+        k[j + 1] = kv;
+        p[j + 1] = pv;
+    }
+}
+
+// Lists of 33..2048 entries: one block of 4 warps per list, sorted in shared
+// memory by (slot, position) in three steps that all lead to that one order:
 //
-// The pool lookups are latency-bound random reads (id -> slot -> value):
-// each thread first issues PM_U of them before using any, for the slot
-// lookups while loading and for the value gathers while writing staging.
-// Sorting: warp w owns a contiguous range of the current layout; within a
-// warp, 32 items at a time are ranked among equal digits with
-// label ballots (stable: warp by warp, chunk by chunk, lane by lane).
-// Each scatter also counts the next pass's per-warp histogram (shared-memory
-// atomics) from the destinations it writes, so a pass is one sweep between
-// two barriers.
+//   1. the ordered tail of the key range: P = 1 + the largest slot that
+//      follows a larger slot in list order (a prefix-maximum scan), so the
+//      entries with slot >= P are already in ascending order -- in the
+//      N-body lists these are the tree nodes, about two thirds of every
+//      list, whose slots follow their depth-first numbering;
+//   2. a stable split: entries below P first, in list order, then the
+//      ordered tail (every tail slot is >= P, so the tail goes last as is);
+//   3. the part below P: one distribution pass into 256 buckets of equal
+//      slot range (shared-memory atomics), then each bucket finished by an
+//      insertion sort on (slot, position).  If a bucket would hold more than
+//      PM_BUCKET_MAX entries, 8-bit LSD radix passes sort that part instead.
+//
+// The lookups are latency-bound reads: each thread issues PM_U of them
+// before using any; the 1025..2048 class also reads the next list of its
+// claim while the current one is sorted.
 constexpr int PM_THREADS = 128;
 constexpr int PM_W = PM_THREADS / 32;
 constexpr int PM_U = 8;             // lookups in flight per thread
 constexpr int PM_CAP = 2048;        // largest list of the mid class
-static_assert(PM_W == 4, "the destination-warp test below assumes four warps");
+constexpr int PM_NB = 256;          // buckets of the distribution pass
+constexpr int PM_BUCKET_MAX = 48;   // largest bucket finished by insertion
+static_assert(PM_NB == 2 * PM_THREADS, "two buckets per thread in the bucket scan");
 
 template <int CAP>
 struct PackSmemMid {
     uint32_t ka[CAP], kb[CAP];
     uint16_t pa[CAP], pb[CAP];
-    uint32_t hist[2][PM_W][256];
+    uint32_t hist[PM_W * 256];          // LSD passes: per (warp, digit)
+    uint32_t bcur[PM_NB];               // bucket counts, then scatter cursors
     uint32_t wsum[PM_W];
-    int skip;
+    uint32_t wmax[PM_W], wmin[PM_W], winv[PM_W], wsmall[PM_W];
+    int flag, skip;
 };
 
-__device__ __forceinline__ uint32_t block_excl_scan128(uint32_t v, uint32_t *wsum)
+// Slots of entries c0 .. c0+cn-1 of list l into ka (positions 0..cn-1 in
+// pa): PM_U reads in flight per thread (entry slots, or ids then slots).
+template <int NT>
+__device__ __forceinline__ void load_slots(const PackArgs &a, const PackList &l, uint32_t c0,
+                                           int cn, uint32_t *ka, uint16_t *pa)
 {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = v;
+    const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off + c0;
+    const uint32_t *es = l.es ? l.es + c0 : nullptr;
+    for (int base = 0; base < cn; base += NT * PM_U) {
+        uint32_t s[PM_U];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        for (int j = 0; j < PM_U; ++j) {
+            const int k = base + threadIdx.x + NT * j;
+            s[j] = k < cn ? __ldg((es ? es : ids) + k) : 0u;
+        }
+        if (!es) {
+#pragma unroll
+            for (int j = 0; j < PM_U; ++j) {
+                const int k = base + threadIdx.x + NT * j;
+                if (k < cn) s[j] = __ldg(a.slot_of_id + s[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < PM_U; ++j) {
+                const int k = base + threadIdx.x + NT * j;
+                if (k < cn && s[j] == GC_NONE) s[j] = __ldg(a.slot_of_id + __ldg(ids + k));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PM_U; ++j) {
+            const int k = base + threadIdx.x + NT * j;
+            if (k < cn) {
+                ka[k] = s[j];
+                pa[k] = (uint16_t)k;
+            }
+        }
     }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    uint32_t before = 0;
-    for (int q = 0; q < w; ++q) before += wsum[q];
-    return before + x - v;
 }
 
-// Write sorted entries 0..n-1 (slots ka, positions pa) of list l: permutation
-// and staging.  Entries k = threadIdx.x + PM_THREADS * j, so the lanes of a
-// warp hold consecutive k: in the paired source layout lanes 2i and 2i+1
-// swap halves with one shuffle pair and each writes a whole float4.
+// The crowded-bucket fallback of mid_sort, kept out of line: it is rare, and
+// inlined beside the insertion sort it costs the common path registers.
+template <int CAP>
+__device__ __noinline__ bool mid_radix_fallback(PackSmemMid<CAP> &sm, int ns, int passes,
+                                                uint32_t kmin)
+{
+    return radix_lsd<PM_W>(sm.kb, sm.pb, sm.ka, sm.pa, sm.hist, sm.wsum, &sm.skip, ns, passes,
+                           kmin);
+}
+
+// Sort entries 0..n-1 of a list (slots in ka, positions pa = 0..n-1) by
+// (slot, position), steps 1-3 above.  Result: entries [0, split) in (ka, pa)
+// if *low_in_a, else in (kb, pb); entries [split, n) in (kb, pb).
+template <int CAP>
+__device__ __forceinline__ int mid_sort(PackSmemMid<CAP> &sm, int n, bool &low_in_a)
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int per = (((n + PM_W - 1) / PM_W) + 31) & ~31;
+    const int b0 = min(n, w * per), b1 = min(n, b0 + per);
+    // 1. largest and smallest slot of each warp's range, then the running
+    //    maximum in list order: P = 1 + the largest slot below it
+    uint32_t mx = 0u, mn = 0xFFFFFFFFu;
+    for (int k = b0 + lane; k < b1; k += 32) {
+        const uint32_t v = sm.ka[k];
+        mx = max(mx, v);
+        mn = min(mn, v);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    mn = __reduce_min_sync(0xffffffffu, mn);
+    if (lane == 0) {
+        sm.wmax[w] = mx;
+        sm.wmin[w] = mn;
+    }
+    __syncthreads();
+    uint32_t carry = 0u, kmin = 0xFFFFFFFFu;
+    for (int q = 0; q < PM_W; ++q) {
+        if (q < w) carry = max(carry, sm.wmax[q]);
+        kmin = min(kmin, sm.wmin[q]);
+    }
+    uint32_t inv = 0u;
+    for (int c = b0; c < b1; c += 32) {
+        const int k = c + lane;
+        const bool v = k < b1;
+        const uint32_t key = v ? sm.ka[k] : 0u;
+        uint32_t incl = key;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, y);
+        }
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, incl, 1);
+        const uint32_t before = lane ? max(prev, carry) : carry;
+        if (v && before > key) inv = max(inv, key + 1u);
+        carry = max(carry, __shfl_sync(0xffffffffu, incl, 31));
+    }
+    inv = __reduce_max_sync(0xffffffffu, inv);
+    if (lane == 0) sm.winv[w] = inv;
+    __syncthreads();
+    uint32_t P = 0u;
+    for (int q = 0; q < PM_W; ++q) P = max(P, sm.winv[q]);
+    if (P == 0u) {           // the list is in order already
+        low_in_a = true;
+        return n;
+    }
+    // 2. stable split: slots below P to kb[0, ns), the ordered tail to kb[ns, n)
+    uint32_t cs = 0;
+    for (int c = b0; c < b1; c += 32) {
+        const int k = c + lane;
+        cs += (uint32_t)__popc(__ballot_sync(0xffffffffu, k < b1 && sm.ka[k] < P));
+    }
+    if (lane == 0) sm.wsmall[w] = cs;
+    __syncthreads();
+    uint32_t run = 0, ns = 0;
+    for (int q = 0; q < PM_W; ++q) {
+        if (q < w) run += sm.wsmall[q];
+        ns += sm.wsmall[q];
+    }
+    for (int c = b0; c < b1; c += 32) {
+        const int k = c + lane;
+        const bool v = k < b1;
+        const uint32_t key = v ? sm.ka[k] : 0u;
+        const bool low = v && key < P;
+        const uint32_t bal = __ballot_sync(0xffffffffu, low);
+        const uint32_t nlow = run + (uint32_t)__popc(bal & lt);   // low entries before k
+        if (v) {
+            const uint32_t dst = low ? nlow : ns + (uint32_t)k - nlow;
+            sm.kb[dst] = key;
+            sm.pb[dst] = sm.pa[k];
+        }
+        run += (uint32_t)__popc(bal);
+    }
+    __syncthreads();
+    if (ns <= 1u) {
+        low_in_a = false;
+        return (int)ns;
+    }
+    // 3. distribution over [kmin, P - 1] into PM_NB buckets, kb -> ka
+    const uint32_t r = P - 1u - kmin;
+    const int bits = 32 - __clz((int)r);          // 0 when every low slot is kmin
+    const int shift = bits > 8 ? bits - 8 : 0;
+    for (int i = threadIdx.x; i < PM_NB; i += PM_THREADS) sm.bcur[i] = 0u;
+    if (threadIdx.x == 0) sm.flag = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < (int)ns; k += PM_THREADS)
+        atomicAdd(&sm.bcur[(sm.kb[k] - kmin) >> shift], 1u);
+    __syncthreads();
+    const int d0 = 2 * threadIdx.x;
+    const uint32_t c0 = sm.bcur[d0], c1 = sm.bcur[d0 + 1];
+    if (c0 > (uint32_t)PM_BUCKET_MAX || c1 > (uint32_t)PM_BUCKET_MAX) sm.flag = 1;
+    const uint32_t st = block_excl_scan<PM_W>(c0 + c1, sm.wsum);
+    sm.bcur[d0] = st;
+    sm.bcur[d0 + 1] = st + c0;
+    __syncthreads();
+    if (sm.flag == 0) {
+        for (int k = threadIdx.x; k < (int)ns; k += PM_THREADS) {
+            const uint32_t key = sm.kb[k];
+            const uint32_t dst = atomicAdd(&sm.bcur[(key - kmin) >> shift], 1u);
+            sm.ka[dst] = key;
+            sm.pa[dst] = sm.pb[k];
+        }
+        __syncthreads();
+        insertion_sort(sm.ka, sm.pa, (int)st, (int)(st + c0));
+        insertion_sort(sm.ka, sm.pa, (int)(st + c0), (int)(st + c0 + c1));
+        __syncthreads();
+        low_in_a = true;
+        return (int)ns;
+    }
+    // a crowded bucket: LSD radix passes over the low part (kb -> ka -> ...)
+    const int passes = (bits + 7) / 8;
+    low_in_a = mid_radix_fallback(sm, (int)ns, passes, kmin);
+    return (int)ns;
+}
+
+// Write sorted entries 0..n-1 of list l: permutation and staging.  Entry k
+// comes from (ka, pa) if k < split, else from (kb, pb).  Entries k =
+// threadIdx.x + NT * j, so the lanes of a warp hold consecutive k: in the
+// paired source layout lanes 2i and 2i+1 swap halves with one shuffle pair
+// and each writes a whole float4.
 template <int NT = PM_THREADS>
 __device__ __forceinline__ void emit_block(const PackArgs &a, const PackList &l, int n,
-                                           const uint32_t *ka, const uint16_t *pa)
+                                           const uint32_t *ka, const uint16_t *pa, int split,
+                                           const uint32_t *kb, const uint16_t *pb)
 {
     const int lane = threadIdx.x & 31;
     const int h = lane & 1;
@@ -478,13 +683,13 @@ __device__ __forceinline__ void emit_block(const PackArgs &a, const PackList &l,
         for (int j = 0; j < PM_U; ++j) {
             const int k = base + threadIdx.x + NT * j;
             v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (k < n) v[j] = a.pool[ka[k]];
+            if (k < n) v[j] = a.pool[k < split ? ka[k] : kb[k]];
         }
 #pragma unroll
         for (int j = 0; j < PM_U; ++j) {
             const int k = base + threadIdx.x + NT * j;
             if (base + NT * j >= n_run) break;      // uniform over the block
-            if (k < n) (l.src ? a.perm_s : a.perm_t)[l.off + k] = pa[k];
+            if (k < n) (l.src ? a.perm_s : a.perm_t)[l.off + k] = k < split ? pa[k] : pb[k];
             if (!l.paired) {
                 if (k < n) (l.src ? a.stg_s : a.stg_t)[l.stg + k] = v[j];
                 continue;
@@ -508,155 +713,63 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
     PackSmemMid<CAP> &sm = *reinterpret_cast<PackSmemMid<CAP> *>(smem_raw);
     constexpr uint32_t LO = CAP == PM_CAP ? (uint32_t)(PM_CAP / 2) : 32u;
     __shared__ ListClaim cl;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
     unsigned long long *ctr = a.work + (CAP == PM_CAP ? 1 : 0);
     // The 1025..2048 class reads the next list of the claim while this one
-    // is sorted: its ids before the first radix pass, its slots after it,
-    // into registers that the sort does not touch; the dependent reads'
-    // latency then overlaps the sort instead of following it (pack of the
-    // 1M-particle step 2.89 -> 2.60 ms; the shorter class gains nothing
-    // from it and keeps its registers).
+    // is sorted: its entry slots (or ids) before the sort, the lookups it
+    // still needs after it, into registers that the sort does not touch.
     constexpr int PF = CAP / PM_THREADS;     // entries per thread of a full list
     constexpr bool PREFETCH = CAP == PM_CAP;
     uint32_t pf[PF];
     while (claim_lists(a, ctr, LO, (uint32_t)CAP, cl)) {
-    bool have_pf = false;
-    for (uint32_t ci = 0; ci < cl.cnt; ++ci) {
-        const PackList l = list_of(a, cl.base + cl.off[ci]);
-        const int n = (int)l.n;
-        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
-        const int per = (((n + PM_W - 1) / PM_W) + 31) & ~31;
-        const int b0 = min(n, w * per), b1 = min(n, b0 + per);
-        for (int i = threadIdx.x; i < 2 * PM_W * 256; i += PM_THREADS) (&sm.hist[0][0][0])[i] = 0;
-        if (have_pf) {
-#pragma unroll
-            for (int j = 0; j < PF; ++j) {
-                const int k = threadIdx.x + PM_THREADS * j;
-                if (k < n) {
-                    sm.ka[k] = pf[j];
-                    sm.pa[k] = (uint16_t)k;
-                }
-            }
-        } else
-        // load: PM_U id reads, then PM_U slot lookups, in flight per thread
-        for (int base = 0; base < n; base += PM_THREADS * PM_U) {
-            uint32_t s[PM_U];
-#pragma unroll
-            for (int j = 0; j < PM_U; ++j) {
-                const int k = base + threadIdx.x + PM_THREADS * j;
-                s[j] = k < n ? __ldg(ids + k) : 0u;
-            }
-#pragma unroll
-            for (int j = 0; j < PM_U; ++j) {
-                const int k = base + threadIdx.x + PM_THREADS * j;
-                if (k < n) s[j] = __ldg(a.slot_of_id + s[j]);
-            }
-#pragma unroll
-            for (int j = 0; j < PM_U; ++j) {
-                const int k = base + threadIdx.x + PM_THREADS * j;
-                if (k < n) {
-                    sm.ka[k] = s[j];
-                    sm.pa[k] = (uint16_t)k;
-                }
-            }
-        }
-        __syncthreads();
-        // the next list's ids
-        const bool pf_next = PREFETCH && ci + 1 < cl.cnt;
-        int nn = 0;
-        if (pf_next) {
-            const PackList ln = list_of(a, cl.base + cl.off[ci + 1]);
-            const uint32_t *idn = (ln.src ? a.src_ids : a.tgt_ids) + ln.off;
-            nn = (int)ln.n;
-#pragma unroll
-            for (int j = 0; j < PF; ++j) {
-                const int k = threadIdx.x + PM_THREADS * j;
-                pf[j] = k < nn ? __ldg(idn + k) : 0u;
-            }
-        }
-        // digit-0 histogram per warp range
-        for (int c = b0; c < b1; c += 32) {
-            const int k = c + lane;
-            const bool v = k < b1;
-            if (v) atomicAdd(&sm.hist[0][w][sm.ka[k] & 255u], 1u);
-        }
-        __syncthreads();
-        uint32_t *ka = sm.ka, *kb = sm.kb;
-        uint16_t *pa = sm.pa, *pb = sm.pb;
-        int cur = 0;
-        for (int pass = 0; pass < a.passes; ++pass) {
-            const int sh = 8 * pass;
-            const bool last = pass + 1 == a.passes;
-            // exclusive offsets over (digit, warp); thread t owns digits 2t, 2t+1
-            const int d0 = 2 * threadIdx.x, d1 = d0 + 1;
-            uint32_t c0 = 0, c1 = 0;
-            for (int q = 0; q < PM_W; ++q) {
-                c0 += sm.hist[cur][q][d0];
-                c1 += sm.hist[cur][q][d1];
-            }
-            if (threadIdx.x == 0) sm.skip = 0;
-            __syncthreads();
-            if (c0 == (uint32_t)n || c1 == (uint32_t)n) sm.skip = 1;
-            uint32_t run = block_excl_scan128(c0 + c1, sm.wsum);
-            for (int q = 0; q < PM_W; ++q) {
-                uint32_t c = sm.hist[cur][q][d0];
-                sm.hist[cur][q][d0] = run;
-                run += c;
-            }
-            for (int q = 0; q < PM_W; ++q) {
-                uint32_t c = sm.hist[cur][q][d1];
-                sm.hist[cur][q][d1] = run;
-                run += c;
-            }
-            for (int i = threadIdx.x; i < PM_W * 256; i += PM_THREADS)
-                (&sm.hist[cur ^ 1][0][0])[i] = 0;
-            __syncthreads();
-            const bool skip = sm.skip != 0;
-            for (int c = b0; c < b1; c += 32) {
-                const int k = c + lane;
-                const bool v = k < b1;
-                const uint32_t vm = __ballot_sync(0xffffffffu, v);
-                const uint32_t key = v ? ka[k] : 0u;
-                int dst = k;
-                if (!skip) {
-                    const uint32_t d = (key >> sh) & 255u;
-                    const uint32_t m = warp_match<8>(d, vm);
-                    if (v) {
-                        dst = (int)(sm.hist[cur][w][d] + (uint32_t)__popc(m & lt));
-                        kb[dst] = key;
-                        pb[dst] = pa[k];
-                    }
-                    __syncwarp();
-                    if (v && (m & lt) == 0) sm.hist[cur][w][d] += (uint32_t)__popc(m);
-                }
-                if (!last && v) {
-                    // next pass: count (warp range of dst, next digit)
-                    const uint32_t wd = (uint32_t)(dst >= per) + (uint32_t)(dst >= 2 * per) +
-                                        (uint32_t)(dst >= 3 * per);
-                    atomicAdd(&sm.hist[cur ^ 1][0][0] + wd * 256u + ((key >> (sh + 8)) & 255u),
-                              1u);
-                }
-            }
-            __syncthreads();
-            if (!skip) {
-                uint32_t *tk = ka; ka = kb; kb = tk;
-                uint16_t *tp = pa; pa = pb; pb = tp;
-            }
-            cur ^= 1;
-            if (pass == 0 && pf_next) {
-                // the next list's slots (its ids have arrived meanwhile)
+        bool have_pf = false;
+        for (uint32_t ci = 0; ci < cl.cnt; ++ci) {
+            const PackList l = list_of(a, cl.base + cl.off[ci]);
+            const int n = (int)l.n;
+            if (have_pf) {
 #pragma unroll
                 for (int j = 0; j < PF; ++j) {
                     const int k = threadIdx.x + PM_THREADS * j;
-                    if (k < nn) pf[j] = __ldg(a.slot_of_id + pf[j]);
+                    if (k < n) {
+                        sm.ka[k] = pf[j];
+                        sm.pa[k] = (uint16_t)k;
+                    }
+                }
+            } else {
+                load_slots<PM_THREADS>(a, l, 0, n, sm.ka, sm.pa);
+            }
+            __syncthreads();
+            const bool pf_next = PREFETCH && ci + 1 < cl.cnt;
+            PackList ln;
+            int nn = 0;
+            if (pf_next) {
+                ln = list_of(a, cl.base + cl.off[ci + 1]);
+                nn = (int)ln.n;
+                const uint32_t *src = ln.es ? ln.es : (ln.src ? a.src_ids : a.tgt_ids) + ln.off;
+#pragma unroll
+                for (int j = 0; j < PF; ++j) {
+                    const int k = threadIdx.x + PM_THREADS * j;
+                    pf[j] = k < nn ? __ldg(src + k) : 0u;
                 }
             }
+            bool low_in_a = true;
+            const int split = mid_sort(sm, n, low_in_a);
+            if (pf_next) {
+                // the lookups the next list still needs (its reads have arrived)
+                const uint32_t *idn = (ln.src ? a.src_ids : a.tgt_ids) + ln.off;
+#pragma unroll
+                for (int j = 0; j < PF; ++j) {
+                    const int k = threadIdx.x + PM_THREADS * j;
+                    if (k < nn) {
+                        if (!ln.es) pf[j] = __ldg(a.slot_of_id + pf[j]);
+                        else if (pf[j] == GC_NONE) pf[j] = __ldg(a.slot_of_id + __ldg(idn + k));
+                    }
+                }
+            }
+            emit_block(a, l, n, low_in_a ? sm.ka : sm.kb, low_in_a ? sm.pa : sm.pb, split,
+                       sm.kb, sm.pb);
+            __syncthreads();
+            have_pf = pf_next;
         }
-        emit_block(a, l, n, ka, pa);
-        __syncthreads();
-        have_pf = pf_next;
-    }
     }
 }
 
@@ -667,39 +780,20 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
 // sorted in chunks of PK_CAP_HUGE that are merged pairwise in global scratch
 // (keys (slot << 32 | pos) are unique, so an element's output index is its
 // rank in its own run plus its rank in the other run).
-// Slots of entries c0 .. c0+cn-1 of a list into ka (positions 0..cn-1 in
-// pa): PM_U id reads, then PM_U slot lookups, in flight per thread.
-template <int NT>
-__device__ __forceinline__ void load_slots(const PackArgs &a, const uint32_t *ids, int cn,
-                                           uint32_t *ka, uint16_t *pa)
-{
-    for (int base = 0; base < cn; base += NT * PM_U) {
-        uint32_t s[PM_U];
-#pragma unroll
-        for (int j = 0; j < PM_U; ++j) {
-            const int k = base + threadIdx.x + NT * j;
-            s[j] = k < cn ? __ldg(ids + k) : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < PM_U; ++j) {
-            const int k = base + threadIdx.x + NT * j;
-            if (k < cn) s[j] = __ldg(a.slot_of_id + s[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < PM_U; ++j) {
-            const int k = base + threadIdx.x + NT * j;
-            if (k < cn) {
-                ka[k] = s[j];
-                pa[k] = (uint16_t)k;
-            }
-        }
-    }
-}
 
 // Warps of each block-sort class: the largest lists take a whole SM.
 constexpr int PK_NW_MID = 16, PK_NW_HUGE = 16;
 template <int CAP> struct PackLargeWarps { static constexpr int value = PK_NW_MID; };
 template <> struct PackLargeWarps<PK_CAP_HUGE> { static constexpr int value = PK_NW_HUGE; };
+
+template <int CAP, int NW>
+struct PackSmem {
+    uint32_t ka[CAP], kb[CAP];           // slots
+    uint16_t pa[CAP], pb[CAP];           // list positions (within a chunk)
+    uint32_t hist[NW * 256];             // per (warp, digit) counts, then offsets
+    uint32_t wsum[NW];
+    int skip;
+};
 
 template <int CAP>
 __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(PackArgs a)
@@ -714,12 +808,13 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
     while (claim_lists(a, a.work + (CAP == PK_CAP ? 2 : 3), lo_n, hi_n, cl))
     for (uint32_t ci = 0; ci < cl.cnt; ++ci) {
         PackList l = list_of(a, cl.base + cl.off[ci]);
-        const uint32_t *ids = (l.src ? a.src_ids : a.tgt_ids) + l.off;
         if (l.n <= (uint32_t)CAP) {
-            load_slots<NW * 32>(a, ids, (int)l.n, sm.ka, sm.pa);
+            load_slots<NW * 32>(a, l, 0, (int)l.n, sm.ka, sm.pa);
             __syncthreads();
-            int f = block_radix_sort(sm, (int)l.n, a.passes);
-            emit_block<NW * 32>(a, l, (int)l.n, f ? sm.kb : sm.ka, f ? sm.pb : sm.pa);
+            const bool f = radix_lsd<NW>(sm.ka, sm.pa, sm.kb, sm.pb, sm.hist, sm.wsum, &sm.skip,
+                                         (int)l.n, a.passes, 0u);
+            emit_block<NW * 32>(a, l, (int)l.n, f ? sm.kb : sm.ka, f ? sm.pb : sm.pa,
+                                (int)l.n, nullptr, nullptr);
             __syncthreads();
             continue;
         }
@@ -729,9 +824,10 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
         const uint32_t n = l.n;
         for (uint32_t c0 = 0; c0 < n; c0 += CAP) {
             const int cn = (int)min((uint32_t)CAP, n - c0);
-            load_slots<NW * 32>(a, ids + c0, cn, sm.ka, sm.pa);
+            load_slots<NW * 32>(a, l, c0, cn, sm.ka, sm.pa);
             __syncthreads();
-            int f = block_radix_sort(sm, cn, a.passes);
+            const bool f = radix_lsd<NW>(sm.ka, sm.pa, sm.kb, sm.pb, sm.hist, sm.wsum, &sm.skip,
+                                         cn, a.passes, 0u);
             const uint32_t *kk = f ? sm.kb : sm.ka;
             const uint16_t *pp = f ? sm.pb : sm.pa;
             for (int k = threadIdx.x; k < cn; k += blockDim.x)
@@ -1561,7 +1657,7 @@ int gc_read_wu_offsets(gc_pool *p, FlushCtx &c, std::vector<uint32_t> &wu_off,
 }
 
 int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base,
-            uint64_t src_base, uint64_t msrc)
+            uint64_t src_base, uint64_t msrc, const uint32_t *ent, uint64_t ent_nt)
 {
     if (t1 <= t0) return GC_OK;
     static bool attr_set = false;
@@ -1587,6 +1683,8 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     a.tgt_ids = c.tgt_ids.as<uint32_t>();
     a.src_ids = c.src_ids.as<uint32_t>();
     a.slot_of_id = p->d_slot_of_id;
+    a.ent_t = ent;
+    a.ent_s = ent ? ent + ent_nt : nullptr;
     a.task_base = t0;
     int bits = 1;
     while (bits < 32 && ((uint64_t)1 << bits) < p->cfg.pool_capacity) ++bits;

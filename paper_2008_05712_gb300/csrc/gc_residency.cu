@@ -145,13 +145,19 @@ __global__ void k_compact_write(CompactArgs a, const uint32_t *tile_off, uint32_
 // entries (neighbouring tasks share many ids: the far tree nodes appear in
 // almost every list), aggregates reference counts in a small shared-memory
 // hash table and adds them to the global counters once per block; ids that
-// do not find a table slot fall back to global atomics.
+// do not find a table slot fall back to global atomics.  With `ent` set, the
+// entry's current slot is recorded too (wave-local entry order: targets,
+// then sources; NONE for an id not resident yet): the slot is read beside
+// the reference word, in parallel with it, so the pack that follows reads
+// the slots of its entries in order instead of looking each one up.  A hit
+// keeps its slot through the rest of the chare-table step (only ids not
+// referenced now are evicted); a miss is looked up again by the pack.
 constexpr int MARK_HASH = 2048;
 
 __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, uint64_t ns,
                        uint64_t id_cap, uint32_t *ref_epoch,
                        uint32_t *ref_count, uint32_t epoch, unsigned long long *ctr,
-                       uint64_t chunk)
+                       uint64_t chunk, const uint32_t *slot_of_id, uint32_t *ent)
 {
     __shared__ uint32_t hkey[MARK_HASH];
     __shared__ uint32_t hcnt[MARK_HASH];
@@ -171,6 +177,7 @@ __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, ui
             continue;
         }
         const uint32_t e0 = ref_epoch[id];   // one word: uploaded? referenced this wave?
+        if (ent) ent[e] = slot_of_id[id];
         if (e0 == GC_EPOCH_UNKNOWN) {
             bad = true;
             continue;
@@ -383,7 +390,7 @@ int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint6
 }
 
 int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
-                 uint64_t ns)
+                 uint64_t ns, uint32_t *ent)
 {
     const uint64_t id_cap = p->cfg.id_capacity, cap = p->cfg.pool_capacity;
     const uint64_t n = nt + ns;
@@ -399,7 +406,7 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         ++p->stats.kernel_launches;
         k_mark<<<(unsigned)((n + chunk - 1) / chunk), 512, 0, p->s>>>(
             tgt, nt, src, ns, id_cap, p->d_ref_epoch, p->d_ref_count, p->epoch, ctr,
-            chunk);
+            chunk, p->d_slot_of_id, ent);
     }
     uint64_t ubound = n < id_cap ? n : id_cap;
     GC_TRY(p->uniq.reserve((ubound + 1) * sizeof(uint32_t)));

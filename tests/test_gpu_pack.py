@@ -3,7 +3,10 @@ stress the sort: every size-class boundary (32/33, 1024/1025, 2048/2049,
 4096/4097, 16384/16385 and a list merged from three sorted chunks),
 lists of one repeated id (no radix pass needed), lists with heavy
 duplication (stability decides the order), lists spanning the whole slot
-range and lists confined to a narrow one.  The pack permutation must equal a
+range and lists confined to a narrow one, lists already in order, lists in
+order but for one low slot at the end, and lists shaped like the N-body
+interaction lists (an ascending tail of high slots interleaved with short
+runs of random low ones).  The pack permutation must equal a
 stable argsort of the entry slots, bit for bit, and the staged forces must
 match the FP64 oracle."""
 import numpy as np
@@ -34,7 +37,32 @@ def adversarial_lists(n_ids, seed):
         base = int(rng.integers(0, n_ids - 70))
         lists.append(base + rng.integers(0, 64, size))                 # narrow range
         lists.append(np.sort(rng.integers(0, n_ids, size))[::-1])      # descending
+        lists.append(tree_like(rng, n_ids, size))                      # ordered tail
+        asc = np.sort(rng.integers(1, n_ids, size))
+        lists.append(asc.copy())                                       # in order already
+        asc[-1] = 0
+        lists.append(asc)                                              # one low slot last
     return [a.astype(np.uint32) for a in lists]
+
+
+def tree_like(rng, n_ids, size):
+    """The shape of an N-body interaction list: about two thirds ascending
+    high ids (tree nodes in depth-first order) interleaved with runs of up
+    to 9 random lower ids (the particles of opened leaves)."""
+    cut = int(0.9 * n_ids)
+    n_hi = size - size // 3
+    hi = np.sort(rng.integers(cut, n_ids, n_hi))
+    lo = rng.integers(0, cut, size - n_hi)
+    out, i, j = [], 0, 0
+    while i < len(hi) or j < len(lo):
+        if j < len(lo) and (i == len(hi) or rng.random() < 0.1):
+            k = min(len(lo), j + int(rng.integers(1, 10)))
+            out.extend(lo[j:k])
+            j = k
+        else:
+            out.append(hi[i])
+            i += 1
+    return np.array(out)
 
 
 def csr(lists):
