@@ -151,7 +151,8 @@ static void free_pool(gc_pool *p)
                     &p->nb.win, &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a,
                     &p->nb.node_b, &p->nb.node_val, &p->nb.bucket, &p->nb.bbox,
                     &p->nb.list_off, &p->nb.list_len, &p->nb.list, &p->nb.bounds,
-                    &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->md.hostcopy, &p->md.keys,
+                    &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->nb.wnode, &p->md.hostcopy,
+                    &p->md.keys,
                     &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
                     &p->md.cnt_s, &p->md.cub_tmp};
     for (DBuf *b : bufs) b->release();

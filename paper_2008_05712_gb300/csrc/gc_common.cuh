@@ -85,7 +85,8 @@ struct GravWU {
 struct NBodyState {
     uint64_t n = 0, n_nodes = 0, n_buckets = 0, n_list = 0, max_list = 0;
     DBuf keys, keys2, ids, ids2, lcp, win, dmax, nnode, node_off;
-    DBuf node_a, node_b, node_val, bucket, bbox, list_off, list_len, list;
+    DBuf node_a, node_b, node_val, bucket, bbox, list_off, list_len, list, wnode;
+    uint64_t n_walk_items = 0;       // (bucket, walk range) pairs of the last build
     DBuf bounds, cub_tmp, mono, hostcopy;
 };
 

@@ -23,8 +23,10 @@
 // sorted keys and its subtree size from the same prefix sum.
 //
 // The walk visits nodes in preorder with skips (no stack): an accepted or
-// leaf node continues at k + size(k), an opened internal node at k + 1.
+// leaf node continues at k + size(k), an opened internal node at k + 1; the
+// node array is split into preorder ranges walked independently (k_walk).
 #include <cub/device/device_scan.cuh>
+#include <algorithm>
 #include <climits>
 
 #include "gc_common.cuh"
@@ -393,8 +395,6 @@ __global__ void k_emit_buckets(const uint4 *node_a, uint64_t nn, const uint32_t 
     }
 }
 
-constexpr int WALK_ITEMS = 8;   // independent sub-walks per bucket
-
 // Acceptance thresholds per level: a node of edge s (doubled units) is
 // accepted iff td^2 s^2 < tn^2 d^2, i.e. (integers, tn > 0) iff
 // d^2 > floor(td^2 s^2 / tn^2); with tn = 0 nothing is accepted.
@@ -402,127 +402,144 @@ struct WalkThresholds {
     int64_t t[22];
 };
 
-// Stackless preorder walk of one preorder range [k0, k_end) for one bucket.
-// FILL = false: count list entries; true: write them.  Each step loads both
-// possible successors of the current node (the next node in preorder and the
-// node after its subtree) ahead of the decision, so the dependent chain per
-// visited node is one decision.
-template <bool FILL>
-__device__ __forceinline__ uint32_t walk_range(const uint4 *node_a, const uint4 *node_b,
-                                               uint32_t k0, uint32_t k_end, uint32_t bf,
-                                               int4 lo, int4 hi, const uint32_t *sorted_ids,
-                                               uint32_t n_part, const WalkThresholds &th,
-                                               uint32_t *o)
+// The walk's view of node k, 16 bytes: W[k] = {subtree size | leaf << 31,
+// centre x | level << 22, centre y, centre z} (centre in doubled grid units,
+// below 2^22), and for a leaf LF[k] = {first particle, count}.  W[nn] is a
+// sentinel.  Whether a node contains a bucket is a preorder test against the
+// bucket's own leaf (k <= leaf < k + size), so the per-node record needs no
+// particle range; the acceptance thresholds come per level from a table.
+__global__ void k_walk_nodes(const uint4 *node_a, const uint4 *node_b, uint32_t nn, uint4 *W,
+                             uint2 *LF)
 {
-    uint32_t cnt = 0;
-    uint32_t k = k0;
-    uint4 A = node_a[k0], C = node_b[k0];
-    while (k < k_end) {
-        const uint32_t k_open = k + 1, k_skip = k + A.z;
-        uint4 An = make_uint4(0, 0, 1, 0), Cn = make_uint4(0, 0, 0, 0);
-        uint4 As = An, Cs = Cn;
-        if (k_open < k_end) {
-            An = node_a[k_open];
-            Cn = node_b[k_open];
+    GRID_STRIDE(k, (uint64_t)nn + 1) {
+        if (k == nn) {
+            W[k] = make_uint4(1u, 0u, 0u, 0u);
+            continue;
         }
-        if (k_skip == k_open) {
-            As = An;
-            Cs = Cn;
-        } else if (k_skip < k_end) {
-            As = node_a[k_skip];
-            Cs = node_b[k_skip];
+        const uint4 A = node_a[k], C = node_b[k];
+        const uint32_t lvl = A.w & 255u;
+        const uint32_t s = 1u << (22 - lvl), h = s >> 1;
+        W[k] = make_uint4(A.z | ((A.w & 256u) << 23), (C.x * s + h) | (lvl << 22), C.y * s + h,
+                          C.z * s + h);
+        LF[k] = make_uint2(A.x, A.y);
+    }
+}
+
+constexpr int WALK_ANC = 24;      // > tree depth (21 levels below the root)
+constexpr int WALK_RANGES = 16;   // preorder ranges of the walk (at most)
+
+// The preorder ranges of the walk: range r = [klo[r], klo[r + 1]), equal
+// node counts; for each range start its strict ancestors (root first), so a
+// walk of the range knows where in it a bucket's own walk resumes.
+__global__ void k_walk_ranges(const uint4 *W, uint32_t nn, uint32_t M, uint32_t *klo,
+                              uint32_t *anc, uint32_t *nanc)
+{
+    GRID_STRIDE(r, (uint64_t)M + 1) {
+        const uint32_t k0 = (uint32_t)((uint64_t)r * nn / M);
+        klo[r] = k0;
+        if (r == M) continue;
+        uint32_t j = 0, d = 0;
+        while (j != k0 && d < WALK_ANC) {
+            anc[r * WALK_ANC + d++] = j;
+            uint32_t c = j + 1;          // the child of j whose subtree holds k0
+            while (c + (W[c].x & 0x7FFFFFFFu) <= k0) c += W[c].x & 0x7FFFFFFFu;
+            j = c;
         }
-        const bool contains = (A.x <= bf) && (bf < A.x + A.y);
-        bool skip = false;
-        if (!contains) {
-            const int lvl = (int)(A.w & 255u);
-            const int s = 1 << (22 - lvl), h = s >> 1;
-            const int cx = (int)C.x * s + h, cy = (int)C.y * s + h, cz = (int)C.z * s + h;
-            const uint32_t dx = (uint32_t)max(0, max(lo.x - cx, cx - hi.x));
-            const uint32_t dy = (uint32_t)max(0, max(lo.y - cy, cy - hi.y));
-            const uint32_t dz = (uint32_t)max(0, max(lo.z - cz, cz - hi.z));
-            const uint64_t d2 = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
-            if ((int64_t)d2 > th.t[lvl]) {
+        nanc[r] = d;
+    }
+}
+
+// Does the bucket (its leaf node lf, box lo..hi) accept node k (record R)
+// as a whole?  Nodes containing the bucket are always opened.
+__device__ __forceinline__ bool walk_accepts(uint32_t k, const uint4 &R, uint32_t lf,
+                                             const int4 &lo, const int4 &hi, const int64_t *th)
+{
+    const uint32_t size = R.x & 0x7FFFFFFFu;
+    if (k <= lf && lf < k + size) return false;
+    const int cx = (int)(R.y & 0x3FFFFFu), cy = (int)R.z, cz = (int)R.w;
+    const uint32_t dx = (uint32_t)max(0, max(lo.x - cx, cx - hi.x));
+    const uint32_t dy = (uint32_t)max(0, max(lo.y - cy, cy - hi.y));
+    const uint32_t dz = (uint32_t)max(0, max(lo.z - cz, cz - hi.z));
+    const uint64_t d2 = (uint64_t)dx * dx + (uint64_t)dy * dy + (uint64_t)dz * dz;
+    return (int64_t)d2 > th[R.y >> 22];
+}
+
+// Walk of one preorder range [klo[r], klo[r + 1]) for one bucket, one thread
+// per (bucket, range) item.  Items run range-major, so a warp walks the same
+// range for 32 consecutive buckets (neighbours in Morton order, similar
+// paths).  The walk visits nodes in preorder with skips (no stack): an
+// accepted node or an opened leaf continues after its subtree (k + size),
+// an opened internal node (containing the bucket or failing the acceptance
+// test) at k + 1.  Before the range, the strict ancestors of its first node
+// are tested, root first: if the bucket accepts one, its walk resumes only
+// where that ancestor's subtree ends (which may be inside the range or
+// beyond it).  A node is emitted by the range that holds it, so the ranges'
+// lists, concatenated in range order, are the depth-first list of the
+// bucket's own walk.  The walk is bound by the L1 traffic of its node reads
+// (lanes read different nodes): one 16-byte record per visited node, read
+// after the decision; the many resident warps hide its latency.  FILL =
+// false: lengths into len[b M + r]; true: entries written at off[b M + r].
+template <bool FILL>
+__global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF, uint32_t M,
+                                                 const uint32_t *klo, const uint32_t *anc,
+                                                 const uint32_t *nanc, WalkThresholds thg,
+                                                 const uint4 *bucket, const int4 *blo,
+                                                 const int4 *bhi, uint64_t nb,
+                                                 const uint32_t *sorted_ids, uint32_t n_part,
+                                                 uint32_t *len, const uint64_t *off,
+                                                 uint32_t *out)
+{
+    __shared__ int64_t th[22];
+    if (threadIdx.x < 22) th[threadIdx.x] = thg.t[threadIdx.x];
+    __syncthreads();
+    GRID_STRIDE(t, nb * M) {
+        const uint32_t r = (uint32_t)(t / nb);
+        const uint64_t b = t - (uint64_t)r * nb;
+        const uint32_t lf = bucket[b].z;
+        const int4 lo = blo[b], hi = bhi[b];
+        uint32_t k = klo[r];
+        const uint32_t k1 = klo[r + 1];
+        const uint32_t na = nanc[r];
+        for (uint32_t j = 0; j < na; ++j) {
+            const uint32_t a = anc[r * WALK_ANC + j];
+            const uint4 R = W[a];
+            if (walk_accepts(a, R, lf, lo, hi, th)) {
+                k = max(k, a + (R.x & 0x7FFFFFFFu));
+                break;
+            }
+        }
+        uint32_t cnt = 0;
+        uint32_t *o = FILL ? out + off[b * M + r] : nullptr;
+        while (k < k1) {
+            const uint4 R = W[k];
+            const uint32_t size = R.x & 0x7FFFFFFFu;
+            if (walk_accepts(k, R, lf, lo, hi, th)) {
                 if (FILL) o[cnt] = n_part + k;
                 ++cnt;
-                skip = true;
-            }
-        }
-        if (!skip && (A.w & 256u)) {
-            if (FILL) {
-                const uint32_t *src = sorted_ids + A.x;
-                uint32_t *dst = o + cnt;
-                uint32_t q = 0;
-                for (; q + 4 <= A.y; q += 4) {
-                    const uint32_t v0 = src[q], v1 = src[q + 1], v2 = src[q + 2], v3 = src[q + 3];
-                    dst[q] = v0;
-                    dst[q + 1] = v1;
-                    dst[q + 2] = v2;
-                    dst[q + 3] = v3;
+                k += size;
+            } else if (R.x >> 31) {      // leaf: its particles
+                const uint2 L = LF[k];
+                if (FILL) {
+                    const uint32_t *src = sorted_ids + L.x;
+                    uint32_t *dst = o + cnt;
+                    uint32_t q = 0;
+                    for (; q + 4 <= L.y; q += 4) {
+                        const uint32_t v0 = src[q], v1 = src[q + 1], v2 = src[q + 2],
+                                       v3 = src[q + 3];
+                        dst[q] = v0;
+                        dst[q + 1] = v1;
+                        dst[q + 2] = v2;
+                        dst[q + 3] = v3;
+                    }
+                    for (; q < L.y; ++q) dst[q] = src[q];
                 }
-                for (; q < A.y; ++q) dst[q] = src[q];
+                cnt += L.y;
+                k += size;
+            } else {
+                k += 1;
             }
-            cnt += A.y;
-            skip = true;   // a leaf's subtree is itself
         }
-        if (skip) {
-            k = k_skip;
-            A = As;
-            C = Cs;
-        } else {
-            k = k_open;
-            A = An;
-            C = Cn;
-        }
-    }
-    return cnt;
-}
-
-// Preorder ranges of the walk items: the subtrees of the root's children in
-// octant order (the root always contains the bucket and is opened), or the
-// whole tree when the root is a leaf.  The lists of the items, concatenated
-// in item order, are the depth-first list.
-__global__ void k_walk_items(const uint4 *node_a, uint32_t nn, uint32_t *item_lo,
-                             uint32_t *item_hi)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const uint4 root = node_a[0];
-    for (int j = 0; j < WALK_ITEMS; ++j) item_lo[j] = item_hi[j] = 0;
-    if (root.w & 256u) {
-        item_lo[0] = 0;
-        item_hi[0] = nn;
-        return;
-    }
-    uint32_t k = 1;
-    int j = 0;
-    while (k < root.z && j < WALK_ITEMS) {
-        item_lo[j] = k;
-        item_hi[j] = k + node_a[k].z;
-        k = item_hi[j];
-        ++j;
-    }
-}
-
-// One thread per (bucket, item).  Threads run item-major (a warp walks the
-// same subtree for 32 consecutive buckets, which take similar paths); the
-// lengths and offsets are stored bucket-major (the order of the lists).
-template <bool FILL>
-__global__ void k_walk(const uint4 *node_a, const uint4 *node_b, const uint32_t *item_lo,
-                       const uint32_t *item_hi, const uint4 *bucket, const int4 *blo,
-                       const int4 *bhi, uint64_t nb, const uint32_t *sorted_ids,
-                       uint32_t n_part, WalkThresholds th, uint32_t *len, const uint64_t *off,
-                       uint32_t *out)
-{
-    GRID_STRIDE(t, nb * WALK_ITEMS) {
-        const uint64_t b = t % nb;
-        const int j = (int)(t / nb);
-        const uint64_t it = b * WALK_ITEMS + (uint64_t)j;
-        const uint32_t k0 = item_lo[j], k1 = item_hi[j];
-        uint32_t cnt = 0;
-        if (k1 > k0)
-            cnt = walk_range<FILL>(node_a, node_b, k0, k1, bucket[b].x, blo[b], bhi[b],
-                                   sorted_ids, n_part, th, FILL ? out + off[it] : nullptr);
-        if (!FILL) len[it] = cnt;
+        if (!FILL) len[b * M + r] = cnt;
     }
 }
 
@@ -531,15 +548,11 @@ __global__ void k_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t n)
     GRID_STRIDE(i, n) out[i] = in[i];
 }
 
-// per-bucket list offsets from the per-item offsets (items of a bucket are
-// adjacent); also the per-bucket lengths
-__global__ void k_bucket_offsets(const uint64_t *ioff, uint64_t nb, uint64_t *loff,
-                                 uint64_t *blen)
+// per-bucket list offsets from the per-(bucket, range) offsets (the ranges
+// of a bucket are adjacent)
+__global__ void k_bucket_offsets(const uint64_t *ioff, uint64_t nb, uint32_t M, uint64_t *loff)
 {
-    GRID_STRIDE(b, nb + 1) {
-        loff[b] = ioff[b * WALK_ITEMS];
-        if (b < nb) blen[b] = ioff[(b + 1) * WALK_ITEMS] - ioff[b * WALK_ITEMS];
-    }
+    GRID_STRIDE(b, nb + 1) loff[b] = ioff[b * M];
 }
 
 __global__ void k_nbody_tasks(const uint4 *bucket, uint64_t nb, const uint64_t *list_off,
@@ -703,33 +716,44 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     ++p->stats.kernel_launches;
     k_emit_buckets<<<grid_for(NN, 256, maxb), 256, 0, s>>>(S.node_a.as<uint4>(), NN, boff, K, B,
                                                            S.bucket.as<uint4>(), blo, bhi);
-    const uint64_t NI = (uint64_t)NB * WALK_ITEMS;           // walk items
-    GC_TRY(S.list_off.reserve((NI + 1) * 8 * 2 + (NB + 1) * 8));
-    GC_TRY(S.win.reserve((NI + 1) * 4 + 2 * WALK_ITEMS * 4));   // reused: item lengths + ranges
-    uint32_t *llen = S.win.as<uint32_t>();
-    uint32_t *item_lo = llen + (NI + 1), *item_hi = item_lo + WALK_ITEMS;
-    uint64_t *llen64 = S.list_off.as<uint64_t>();
-    uint64_t *ioff = llen64 + (NI + 1);                       // per-item offsets
-    uint64_t *loff = ioff + (NI + 1);                         // per-bucket offsets
     const int64_t tn2 = (int64_t)theta_num * theta_num, td2 = (int64_t)theta_den * theta_den;
     WalkThresholds th;
     for (int l = 0; l < 22; ++l) {
         const int64_t sz = (int64_t)1 << (22 - l);
         th.t[l] = tn2 ? (td2 * sz * sz) / tn2 : INT64_MAX;
     }
+    // walk records and ranges (about 512 nodes per range or more)
+    const uint32_t M = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(WALK_RANGES, NN / 512));
+    const uint64_t NI = (uint64_t)NB * M;                      // (bucket, range) lists
+    GC_TRY(S.wnode.reserve(((uint64_t)NN + 1) * 24 + (uint64_t)(M + 1) * 4 +
+                           (uint64_t)M * (WALK_ANC + 1) * 4));
+    uint4 *W = S.wnode.as<uint4>();
+    uint2 *LF = (uint2 *)(W + ((uint64_t)NN + 1));
+    uint32_t *klo = (uint32_t *)(LF + ((uint64_t)NN + 1));
+    uint32_t *anc = klo + (M + 1), *nanc = anc + (uint64_t)M * WALK_ANC;
     ++p->stats.kernel_launches;
-    k_walk_items<<<1, 32, 0, s>>>(S.node_a.as<uint4>(), NN, item_lo, item_hi);
+    k_walk_nodes<<<grid_for((uint64_t)NN + 1, 256, maxb), 256, 0, s>>>(
+        S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, W, LF);
     ++p->stats.kernel_launches;
-    k_walk<false><<<grid_for(NI, 128, 1 << 20), 128, 0, s>>>(
-        S.node_a.as<uint4>(), S.node_b.as<uint4>(), item_lo, item_hi, S.bucket.as<uint4>(), blo,
-        bhi, NB, sid, (uint32_t)n, th, llen, nullptr, nullptr);
+    k_walk_ranges<<<grid_for((uint64_t)M + 1, 64, maxb), 64, 0, s>>>(W, NN, M, klo, anc, nanc);
+    GC_TRY(S.list_off.reserve((NI + 1) * 8 * 2 + ((uint64_t)NB + 1) * 8));
+    GC_TRY(S.win.reserve((NI + 1) * 4));   // reused: (bucket, range) list lengths
+    uint32_t *llen = S.win.as<uint32_t>();
+    uint64_t *llen64 = S.list_off.as<uint64_t>();
+    uint64_t *ioff = llen64 + (NI + 1);                       // per-(bucket, range) offsets
+    uint64_t *loff = ioff + (NI + 1);                         // per-bucket offsets
+    const unsigned walk_blocks = grid_for(NI, 128, 1 << 20);
+    ++p->stats.kernel_launches;
+    k_walk<false><<<walk_blocks, 128, 0, s>>>(W, LF, M, klo, anc, nanc, th, S.bucket.as<uint4>(),
+                                              blo, bhi, NB, sid, (uint32_t)n, llen, nullptr,
+                                              nullptr);
     GC_CUDA_TRY(cudaMemsetAsync(llen + NI, 0, 4, s));
     ++p->stats.kernel_launches;
     k_u32_to_u64<<<grid_for(NI + 1, 256, maxb), 256, 0, s>>>(llen, llen64, NI + 1);
     ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u64(S.cub_tmp, llen64, ioff, NI + 1, s));
     ++p->stats.kernel_launches;
-    k_bucket_offsets<<<grid_for(NB + 1, 256, maxb), 256, 0, s>>>(ioff, NB, loff, llen64);
+    k_bucket_offsets<<<grid_for((uint64_t)NB + 1, 256, maxb), 256, 0, s>>>(ioff, NB, M, loff);
     uint64_t NL = 0;
     uint32_t maxlen = 0;
     GC_CUDA_TRY(cudaMemcpyAsync(&NL, loff + NB, 8, cudaMemcpyDeviceToHost, s));
@@ -742,9 +766,8 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     uint32_t *ds = p->src_ids.as<uint32_t>() + p->nb_src;
     TaskRec *recs = p->tasks.as<TaskRec>() + p->nb_tasks;
     ++p->stats.kernel_launches;
-    k_walk<true><<<grid_for(NI, 128, 1 << 20), 128, 0, s>>>(
-        S.node_a.as<uint4>(), S.node_b.as<uint4>(), item_lo, item_hi, S.bucket.as<uint4>(), blo,
-        bhi, NB, sid, (uint32_t)n, th, nullptr, ioff, ds);
+    k_walk<true><<<walk_blocks, 128, 0, s>>>(W, LF, M, klo, anc, nanc, th, S.bucket.as<uint4>(),
+                                             blo, bhi, NB, sid, (uint32_t)n, nullptr, ioff, ds);
     GC_CUDA_TRY(cudaMemcpyAsync(dt, sid, n * 4, cudaMemcpyDeviceToDevice, s));
     ++p->stats.kernel_launches;
     k_nbody_tasks<<<grid_for(NB, 256, maxb), 256, 0, s>>>(S.bucket.as<uint4>(), NB, loff,
@@ -760,6 +783,7 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     S.n_nodes = NN;
     S.n_buckets = NB;
     S.n_list = NL;
+    S.n_walk_items = NI;
     (void)maxlen;
     if (info_out) {
         info_out[0] = NN;
@@ -810,8 +834,7 @@ extern "C" int gc_read_nbody_tree(gc_pool_t *p, uint32_t *sorted_ids, uint64_t *
             if (bucket_node) bucket_node[b] = bk[b].z;
         }
     }
-    const uint64_t NI = NB * WALK_ITEMS;
-    const uint64_t *loff = S.list_off.as<uint64_t>() + 2 * (NI + 1);
+    const uint64_t *loff = S.list_off.as<uint64_t>() + 2 * (S.n_walk_items + 1);
     if (list_off) GC_CUDA_TRY(cudaMemcpy(list_off, loff, (NB + 1) * 8, cudaMemcpyDeviceToHost));
     if (list_ids) {
         // the lists live in the batch source array (pending, or last flushed)

@@ -34,9 +34,13 @@ def build_and_flush(gc, x, theta=(7, 10), bucket=32, per_task=False):
     return pool, info, tree
 
 
+# the larger cases split the walk into several preorder ranges (one per
+# 512 nodes, up to 64): 65,536 particles use 16, the others 3-12
 @pytest.mark.parametrize("n,theta,bucket", [(4096, (7, 10), 32), (3000, (0, 1), 32),
                                             (5000, (255, 1), 16), (33, (7, 10), 32),
-                                            (1, (7, 10), 32)])
+                                            (1, (7, 10), 32), (65536, (7, 10), 32),
+                                            (12000, (0, 1), 16), (40000, (255, 1), 16),
+                                            (30000, (7, 10), 4)])
 def test_tree_and_lists_bit_exact(gc, orc, n, theta, bucket):
     x = inputs.plummer(n, inputs.SEED_BASE + 1)
     pool, info, g = build_and_flush(gc, x, theta, bucket)
