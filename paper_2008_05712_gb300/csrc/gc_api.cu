@@ -145,7 +145,8 @@ static void free_pool(gc_pool *p)
     if (p->d_ewald_h) cudaFree(p->d_ewald_h);
     if (p->h_mirror) cudaFreeHost(p->h_mirror);
     if (p->h_ctr) cudaFreeHost(p->h_ctr);
-    DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->uniq, &p->miss, &p->freel,
+    DBuf *bufs[] = {&p->tasks, &p->tgt_ids, &p->src_ids, &p->uniq, &p->miss, &p->miss_sorted,
+                    &p->freel,
                     &p->tiles, &p->ekeys, &p->ekeys2, &p->evicted, &p->cub_tmp, &p->io_a,
                     &p->io_b, &p->nb.keys, &p->nb.keys2, &p->nb.ids, &p->nb.ids2, &p->nb.lcp,
                     &p->nb.win, &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a,
@@ -171,7 +172,7 @@ int init_ctx(FlushCtx &c, cudaStream_t given)
         c.owns_stream = true;
     }
     if (cudaMalloc((void **)&c.d_ctr, sizeof(unsigned long long) * FC_COUNT) != cudaSuccess ||
-        cudaHostAlloc((void **)&c.h_ctr, sizeof(unsigned long long) * FC_COUNT,
+        cudaHostAlloc((void **)&c.h_ctr, sizeof(unsigned long long) * FH_COUNT,
                       cudaHostAllocDefault) != cudaSuccess)
         return GC_ERR_OOM;
     for (int i = 0; i < 6; ++i)
@@ -366,6 +367,7 @@ int gc_pool_create(const gc_config *cfg, gc_pool_t **out)
     if (rc == GC_OK) {
         cudaMemsetAsync(p->d_slot_of_id, 0xFF, sizeof(uint32_t) * idc, p->s);
         cudaMemsetAsync(p->d_id_of_slot, 0xFF, sizeof(uint32_t) * cap, p->s);
+        p->free_slots = cap;
         cudaMemsetAsync(p->d_last_use, 0, sizeof(uint32_t) * cap, p->s);
         cudaMemsetAsync(p->d_ref_epoch, 0xFF, sizeof(uint32_t) * idc, p->s);   // unknown
         cudaMemsetAsync(p->d_ref_count, 0, sizeof(uint32_t) * idc, p->s);
@@ -592,11 +594,25 @@ static int flush_impl(gc_pool *p, int per_task)
     clear_last_stats(p);
 
     uint64_t info[5];
-    // the task-flag word travels with the preparation's read-back (one host
-    // round trip for both; the task records were written on this stream)
+    const uint64_t budget = p->cfg.staging_budget_bytes;
+    // A batch that fits the staging budget runs as one wave: its chare-table
+    // step is issued with the preparation, and the task-flag word, the
+    // preparation's sizes and the chare-table counters come back in one host
+    // round trip (the task records were written on this stream).
+    const bool one_wave = !(budget && (NT + NS) * sizeof(float4) > budget);
     GC_CUDA_TRY(cudaMemcpyAsync(p->h_ctr + CTR_FLAGS, p->d_ctr + CTR_FLAGS,
                                 sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.s));
-    int rc = gc_prepare(p, c, info);
+    int rc = gc_prepare_issue(p, c);
+    if (rc != GC_OK) return rc;
+    if (one_wave) {
+        GC_TRY(c.ent.reserve((NT + NS + 1) * sizeof(uint32_t)));
+        GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
+        rc = gc_residency_issue(p, c.tgt_ids.as<uint32_t>(), NT, c.src_ids.as<uint32_t>(), NS,
+                                c.ent.as<uint32_t>());
+        if (rc != GC_OK) return rc;
+    }
+    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
+    rc = gc_prepare_finish(p, c, info);
     if (rc != GC_OK) return rc;
     if (p->h_ctr[CTR_FLAGS] & GC_FLAG_BAD_TASK) {
         gc_clear_flags(p, c.s, GC_FLAG_BAD_TASK);
@@ -614,10 +630,9 @@ static int flush_impl(gc_pool *p, int per_task)
     // waves under the staging budget
     struct Wave { uint64_t t0, t1, tg0, tg1, s0, s1; };
     std::vector<Wave> waves;
-    const uint64_t budget = p->cfg.staging_budget_bytes;
     std::vector<uint32_t> wu_off, lj_off;
     bool need_offsets = per_task != 0;
-    if (budget && (NT + NS) * sizeof(float4) > budget) {
+    if (!one_wave) {
         std::vector<TaskRec> h(T);
         GC_CUDA_TRY(cudaMemcpy(h.data(), c.tasks.p, T * sizeof(TaskRec), cudaMemcpyDeviceToHost));
         uint64_t t0 = 0;
@@ -652,7 +667,7 @@ static int flush_impl(gc_pool *p, int per_task)
     uint64_t max_we = 0;   // entries of the largest wave (entry slots)
     for (const Wave &w : waves)
         if (w.tg1 - w.tg0 + w.s1 - w.s0 > max_we) max_we = w.tg1 - w.tg0 + w.s1 - w.s0;
-    GC_TRY(c.ent.reserve((max_we + 1) * sizeof(uint32_t)));
+    if (!one_wave) GC_TRY(c.ent.reserve((max_we + 1) * sizeof(uint32_t)));
     if (max_list > 16384) {   // lists beyond one shared-memory sort: chunk + merge
         GC_TRY(c.merge_a.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
         GC_TRY(c.merge_b.reserve((max_wt + max_ws + 1) * sizeof(uint64_t)));
@@ -672,12 +687,15 @@ static int flush_impl(gc_pool *p, int per_task)
     float ms_res = 0, ms_pack = 0, ms_int = 0;
     const uint32_t *tgt_ids = c.tgt_ids.as<uint32_t>();
     const uint32_t *src_ids = c.src_ids.as<uint32_t>();
-    GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
     for (size_t k = 0; k < waves.size(); ++k) {
         const Wave &w = waves[k];
-        if (k > 0) GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
-        rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0,
-                          c.ent.as<uint32_t>());
+        if (one_wave) {
+            rc = gc_residency_finish(p);   // issued with the preparation
+        } else {
+            GC_CUDA_TRY(cudaEventRecord(c.ev_stage[0], c.s));
+            rc = gc_residency(p, tgt_ids + w.tg0, w.tg1 - w.tg0, src_ids + w.s0, w.s1 - w.s0,
+                              c.ent.as<uint32_t>());
+        }
         if (rc != GC_OK) return rc;
         GC_CUDA_TRY(cudaEventRecord(c.ev_stage[1], c.s));
         GC_TRY(gc_pack(p, c, w.t0, w.t1, w.tg0, w.s0, max_wt + 1, c.ent.as<uint32_t>(),

@@ -52,6 +52,10 @@ enum {
     FC_PACK_WORK,       // list claims of the block-per-list pack kernels (4 counters)
     FC_COUNT = FC_PACK_WORK + 4
 };
+// Host-only words after the FC_COUNT counters of a context's pinned block:
+// the batch sizes the preparation reads back (rows, gravity work units, LJ
+// tasks; 4-byte values land in the low half of a zeroed word).
+enum { FH_ROWS = FC_COUNT, FH_WU, FH_LJ, FH_COUNT };
 
 // One task as the kernels see it (48 bytes).
 struct TaskRec {
@@ -161,6 +165,9 @@ struct gc_pool {
     float4 *d_pool = nullptr;          // [pool_capacity]
     uint32_t *d_slot_of_id = nullptr;  // [id_capacity]
     uint32_t *d_id_of_slot = nullptr;  // [pool_capacity]
+    uint64_t free_slots = 0;           // slots holding no id (kept on the host)
+    uint64_t res_n = 0;                // entries of the chare-table step issued last
+    bool res_few = false;              // it listed its distinct ids while marking
     uint32_t *d_last_use = nullptr;    // [pool_capacity]
     uint32_t *d_ref_epoch = nullptr;   // [id_capacity]
     uint32_t *d_ref_count = nullptr;   // [id_capacity]
@@ -185,7 +192,7 @@ struct gc_pool {
     int cur = 0, last = -1;
 
     // residency work buffers (the chare-table step is serialised)
-    DBuf uniq, miss, freel, tiles, ekeys, ekeys2, evicted, cub_tmp;
+    DBuf uniq, miss, miss_sorted, freel, tiles, ekeys, ekeys2, evicted, cub_tmp;
     DBuf io_a, io_b;                  // host <-> device staging of uploads and reads
     uint64_t n_evicted_last = 0;
     uint32_t epoch = 0;
@@ -221,6 +228,8 @@ int gc_sort_pairs_u64(DBuf &tmp, const uint64_t *kin, uint64_t *kout, const uint
                       uint32_t *vout, uint64_t n, int end_bit, cudaStream_t s);
 int gc_sort_pairs_u32(DBuf &tmp, const uint32_t *kin, uint32_t *kout, const uint32_t *vin,
                       uint32_t *vout, uint64_t n, int end_bit, cudaStream_t s);
+int gc_sort_keys_u32(DBuf &tmp, const uint32_t *kin, uint32_t *kout, uint64_t n, int end_bit,
+                     cudaStream_t s);
 int gc_sort_keys_u64(DBuf &tmp, const uint64_t *kin, uint64_t *kout, uint64_t n,
                      cudaStream_t s);
 int gc_exclusive_scan_u64(DBuf &tmp, const uint64_t *in, uint64_t *out, uint64_t n,
@@ -237,11 +246,22 @@ int gc_exclusive_scan_u32(DBuf &tmp, const uint32_t *in, uint32_t *out, uint64_t
 int gc_entry_slots(gc_pool *p, cudaStream_t s, const uint32_t *ids, uint64_t n, uint32_t *out);
 int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
                  uint64_t ns, uint32_t *ent);
+// The same in two halves around a wait for the pool's stream (so that the
+// wait can serve other read-backs too): the device steps and the counters'
+// copy, then what follows from the counters.
+int gc_residency_issue(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
+                       uint64_t ns, uint32_t *ent);
+int gc_residency_finish(gc_pool *p);
 int gc_launch_upload(gc_pool *p, const uint32_t *ids, const float4 *vals, uint64_t n,
                      int write_mirror);
 
 // ---- pack / interaction / scatter (gc_kernels.cu) -----------------------------
 int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5]);
+// The same in two halves around a wait for the context's stream: the
+// counting kernels and the sizes' copy into the context's pinned words,
+// then the buffers and work lists sized from them.
+int gc_prepare_issue(gc_pool *p, FlushCtx &c);
+int gc_prepare_finish(gc_pool *p, FlushCtx &c, uint64_t info[5]);
 int gc_scatter_replay(gc_pool *p, FlushCtx &c);
 int init_ctx(FlushCtx &c, cudaStream_t given);
 void free_ctx(FlushCtx &c);

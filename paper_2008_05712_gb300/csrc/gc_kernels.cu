@@ -466,7 +466,7 @@ __device__ __forceinline__ void insertion_sort(uint32_t *k, uint16_t *p, int s, 
 //   3. the part below P: one distribution pass into 256 buckets of equal
 //      slot range (shared-memory atomics), then each bucket finished by an
 //      insertion sort on (slot, position).  If a bucket would hold more than
-//      PM_BUCKET_MAX entries, 8-bit LSD radix passes sort that part instead.
+//      PK_BUCKET_MAX entries, 8-bit LSD radix passes sort that part instead.
 //
 // The lookups are latency-bound reads: each thread issues PM_U of them
 // before using any; the 1025..2048 class also reads the next list of its
@@ -476,19 +476,26 @@ constexpr int PM_W = PM_THREADS / 32;
 constexpr int PM_U = 8;             // lookups in flight per thread
 constexpr int PM_CAP = 2048;        // largest list of the mid class
 constexpr int PM_NB = 256;          // buckets of the distribution pass
-constexpr int PM_BUCKET_MAX = 48;   // largest bucket finished by insertion
-static_assert(PM_NB == 2 * PM_THREADS, "two buckets per thread in the bucket scan");
+constexpr int PK_BUCKET_MAX = 48;   // largest bucket finished by insertion
 
-template <int CAP>
-struct PackSmemMid {
+// Shared memory of a block sort of up to CAP entries by NW warps with NB
+// distribution buckets (the crowded-bucket LSD fallback reuses the bucket
+// words for its per-warp digit counts).
+template <int CAP, int NW, int NB>
+struct SortSmem {
     uint32_t ka[CAP], kb[CAP];
     uint16_t pa[CAP], pb[CAP];
-    uint32_t hist[PM_W * 256];          // LSD passes: per (warp, digit)
-    uint32_t bcur[PM_NB];               // bucket counts, then scatter cursors
-    uint32_t wsum[PM_W];
-    uint32_t wmax[PM_W], wmin[PM_W], winv[PM_W], wsmall[PM_W];
+    union {
+        uint32_t hist[NW * 256];        // LSD passes: per (warp, digit)
+        uint32_t bcur[NB];              // bucket counts, then scatter cursors
+    };
+    uint32_t wsum[NW];
+    uint32_t wmax[NW], wmin[NW], winv[NW], wsmall[NW];
     int flag, skip;
 };
+template <int CAP> using PackSmemMid = SortSmem<CAP, PM_W, PM_NB>;
+
+__host__ __device__ constexpr int ilog2(int v) { return v > 1 ? 1 + ilog2(v / 2) : 0; }
 
 // Slots of entries c0 .. c0+cn-1 of list l into ka (positions 0..cn-1 in
 // pa): PM_U reads in flight per thread (entry slots, or ids then slots).
@@ -529,25 +536,30 @@ __device__ __forceinline__ void load_slots(const PackArgs &a, const PackList &l,
     }
 }
 
-// The crowded-bucket fallback of mid_sort, kept out of line: it is rare, and
-// inlined beside the insertion sort it costs the common path registers.
-template <int CAP>
-__device__ __noinline__ bool mid_radix_fallback(PackSmemMid<CAP> &sm, int ns, int passes,
-                                                uint32_t kmin)
+// The crowded-bucket fallback of block_sort, kept out of line: it is rare,
+// and inlined beside the insertion sort it costs the common path registers.
+template <int CAP, int NW, int NB>
+__device__ __noinline__ bool sort_radix_fallback(SortSmem<CAP, NW, NB> &sm, int ns, int passes,
+                                                 uint32_t kmin)
 {
-    return radix_lsd<PM_W>(sm.kb, sm.pb, sm.ka, sm.pa, sm.hist, sm.wsum, &sm.skip, ns, passes,
-                           kmin);
+    return radix_lsd<NW>(sm.kb, sm.pb, sm.ka, sm.pa, sm.hist, sm.wsum, &sm.skip, ns, passes,
+                         kmin);
 }
 
 // Sort entries 0..n-1 of a list (slots in ka, positions pa = 0..n-1) by
-// (slot, position), steps 1-3 above.  Result: entries [0, split) in (ka, pa)
-// if *low_in_a, else in (kb, pb); entries [split, n) in (kb, pb).
-template <int CAP>
-__device__ __forceinline__ int mid_sort(PackSmemMid<CAP> &sm, int n, bool &low_in_a)
+// (slot, position), steps 1-3 above, with NW warps and NB distribution
+// buckets.  Result: entries [0, split) in (ka, pa) if low_in_a, else in
+// (kb, pb); entries [split, n) in (kb, pb).
+template <int CAP, int NW, int NB>
+__device__ __forceinline__ int block_sort(SortSmem<CAP, NW, NB> &sm, int n, bool &low_in_a)
 {
+    constexpr int NT = NW * 32;
+    constexpr int BPT = NB / NT;        // buckets per thread in the bucket scan
+    constexpr int NBB = ilog2(NB);
+    static_assert(BPT >= 1 && BPT * NT == NB && (1 << NBB) == NB, "bucket layout");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
-    const int per = (((n + PM_W - 1) / PM_W) + 31) & ~31;
+    const int per = (((n + NW - 1) / NW) + 31) & ~31;
     const int b0 = min(n, w * per), b1 = min(n, b0 + per);
     // 1. largest and smallest slot of each warp's range, then the running
     //    maximum in list order: P = 1 + the largest slot below it
@@ -565,7 +577,7 @@ __device__ __forceinline__ int mid_sort(PackSmemMid<CAP> &sm, int n, bool &low_i
     }
     __syncthreads();
     uint32_t carry = 0u, kmin = 0xFFFFFFFFu;
-    for (int q = 0; q < PM_W; ++q) {
+    for (int q = 0; q < NW; ++q) {
         if (q < w) carry = max(carry, sm.wmax[q]);
         kmin = min(kmin, sm.wmin[q]);
     }
@@ -589,7 +601,7 @@ __device__ __forceinline__ int mid_sort(PackSmemMid<CAP> &sm, int n, bool &low_i
     if (lane == 0) sm.winv[w] = inv;
     __syncthreads();
     uint32_t P = 0u;
-    for (int q = 0; q < PM_W; ++q) P = max(P, sm.winv[q]);
+    for (int q = 0; q < NW; ++q) P = max(P, sm.winv[q]);
     if (P == 0u) {           // the list is in order already
         low_in_a = true;
         return n;
@@ -603,7 +615,7 @@ __device__ __forceinline__ int mid_sort(PackSmemMid<CAP> &sm, int n, bool &low_i
     if (lane == 0) sm.wsmall[w] = cs;
     __syncthreads();
     uint32_t run = 0, ns = 0;
-    for (int q = 0; q < PM_W; ++q) {
+    for (int q = 0; q < NW; ++q) {
         if (q < w) run += sm.wsmall[q];
         ns += sm.wsmall[q];
     }
@@ -626,40 +638,57 @@ __device__ __forceinline__ int mid_sort(PackSmemMid<CAP> &sm, int n, bool &low_i
         low_in_a = false;
         return (int)ns;
     }
-    // 3. distribution over [kmin, P - 1] into PM_NB buckets, kb -> ka
+    // 3. distribution over [kmin, P - 1] into NB buckets, kb -> ka
     const uint32_t r = P - 1u - kmin;
     const int bits = 32 - __clz((int)r);          // 0 when every low slot is kmin
-    const int shift = bits > 8 ? bits - 8 : 0;
-    for (int i = threadIdx.x; i < PM_NB; i += PM_THREADS) sm.bcur[i] = 0u;
+    const int shift = bits > NBB ? bits - NBB : 0;
+    for (int i = threadIdx.x; i < NB; i += NT) sm.bcur[i] = 0u;
     if (threadIdx.x == 0) sm.flag = 0;
     __syncthreads();
-    for (int k = threadIdx.x; k < (int)ns; k += PM_THREADS)
+    for (int k = threadIdx.x; k < (int)ns; k += NT)
         atomicAdd(&sm.bcur[(sm.kb[k] - kmin) >> shift], 1u);
     __syncthreads();
-    const int d0 = 2 * threadIdx.x;
-    const uint32_t c0 = sm.bcur[d0], c1 = sm.bcur[d0 + 1];
-    if (c0 > (uint32_t)PM_BUCKET_MAX || c1 > (uint32_t)PM_BUCKET_MAX) sm.flag = 1;
-    const uint32_t st = block_excl_scan<PM_W>(c0 + c1, sm.wsum);
-    sm.bcur[d0] = st;
-    sm.bcur[d0 + 1] = st + c0;
+    // thread t owns buckets BPT t .. BPT t + BPT - 1
+    uint32_t cnt[BPT], tot = 0;
+    bool crowded = false;
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        cnt[i] = sm.bcur[BPT * threadIdx.x + i];
+        tot += cnt[i];
+        crowded |= cnt[i] > (uint32_t)PK_BUCKET_MAX;
+    }
+    if (crowded) sm.flag = 1;
+    const uint32_t st = block_excl_scan<NW>(tot, sm.wsum);
+    {
+        uint32_t at = st;
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            sm.bcur[BPT * threadIdx.x + i] = at;
+            at += cnt[i];
+        }
+    }
     __syncthreads();
     if (sm.flag == 0) {
-        for (int k = threadIdx.x; k < (int)ns; k += PM_THREADS) {
+        for (int k = threadIdx.x; k < (int)ns; k += NT) {
             const uint32_t key = sm.kb[k];
             const uint32_t dst = atomicAdd(&sm.bcur[(key - kmin) >> shift], 1u);
             sm.ka[dst] = key;
             sm.pa[dst] = sm.pb[k];
         }
         __syncthreads();
-        insertion_sort(sm.ka, sm.pa, (int)st, (int)(st + c0));
-        insertion_sort(sm.ka, sm.pa, (int)(st + c0), (int)(st + c0 + c1));
+        uint32_t at = st;
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            insertion_sort(sm.ka, sm.pa, (int)at, (int)(at + cnt[i]));
+            at += cnt[i];
+        }
         __syncthreads();
         low_in_a = true;
         return (int)ns;
     }
     // a crowded bucket: LSD radix passes over the low part (kb -> ka -> ...)
     const int passes = (bits + 7) / 8;
-    low_in_a = mid_radix_fallback(sm, (int)ns, passes, kmin);
+    low_in_a = sort_radix_fallback(sm, (int)ns, passes, kmin);
     return (int)ns;
 }
 
@@ -752,7 +781,7 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
                 }
             }
             bool low_in_a = true;
-            const int split = mid_sort(sm, n, low_in_a);
+            const int split = block_sort(sm, n, low_in_a);
             if (pf_next) {
                 // the lookups the next list still needs (its reads have arrived)
                 const uint32_t *idn = (ln.src ? a.src_ids : a.tgt_ids) + ln.off;
@@ -773,34 +802,33 @@ __global__ void __launch_bounds__(PM_THREADS) k_pack_mid(PackArgs a)
     }
 }
 
-// Lists of more than 2048 entries: one block per list, radix-sorted in
-// shared memory.  CAP = PK_CAP takes lists of 2049..4096 entries (about 56 KB
-// of shared memory, three blocks per SM); CAP = PK_CAP_HUGE every longer
-// list (about 200 KB, one block per SM), and a list beyond PK_CAP_HUGE is
+// Lists of more than 2048 entries: one block of 16 warps per list, sorted in
+// shared memory by the same block sort (ordered-tail split, distribution
+// pass, insertion).  CAP = PK_CAP takes lists of 2049..4096 entries (about
+// 64 KB of shared memory, three blocks per SM); CAP = PK_CAP_HUGE every
+// longer list (about 224 KB, one block per SM), and a list beyond PK_CAP_HUGE is
 // sorted in chunks of PK_CAP_HUGE that are merged pairwise in global scratch
 // (keys (slot << 32 | pos) are unique, so an element's output index is its
 // rank in its own run plus its rank in the other run).
 
-// Warps of each block-sort class: the largest lists take a whole SM.
+// Warps and distribution buckets of each block-sort class: the largest lists
+// take a whole SM; one bucket per entry at full size for 4096 entries, one
+// per two for 16384 (its shared memory, about 224 KB, is then full).  Fewer
+// entries per bucket shorten the insertion sorts, chains of dependent
+// shared-memory accesses.
 constexpr int PK_NW_MID = 16, PK_NW_HUGE = 16;
 template <int CAP> struct PackLargeWarps { static constexpr int value = PK_NW_MID; };
 template <> struct PackLargeWarps<PK_CAP_HUGE> { static constexpr int value = PK_NW_HUGE; };
-
-template <int CAP, int NW>
-struct PackSmem {
-    uint32_t ka[CAP], kb[CAP];           // slots
-    uint16_t pa[CAP], pb[CAP];           // list positions (within a chunk)
-    uint32_t hist[NW * 256];             // per (warp, digit) counts, then offsets
-    uint32_t wsum[NW];
-    int skip;
-};
+template <int CAP>
+using PackSmemLarge = SortSmem<CAP, PackLargeWarps<CAP>::value,
+                               CAP == PK_CAP_HUGE ? CAP / 2 : CAP>;
 
 template <int CAP>
 __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(PackArgs a)
 {
     constexpr int NW = PackLargeWarps<CAP>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PackSmem<CAP, NW> &sm = *reinterpret_cast<PackSmem<CAP, NW> *>(smem_raw);
+    PackSmemLarge<CAP> &sm = *reinterpret_cast<PackSmemLarge<CAP> *>(smem_raw);
     static_assert(CAP == PK_CAP || CAP == PK_CAP_HUGE, "two block-sort classes");
     const uint32_t lo_n = (CAP == PK_CAP) ? (uint32_t)PM_CAP : (uint32_t)PK_CAP;
     const uint32_t hi_n = (CAP == PK_CAP) ? (uint32_t)PK_CAP : 0xFFFFFFFFu;
@@ -811,10 +839,10 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
         if (l.n <= (uint32_t)CAP) {
             load_slots<NW * 32>(a, l, 0, (int)l.n, sm.ka, sm.pa);
             __syncthreads();
-            const bool f = radix_lsd<NW>(sm.ka, sm.pa, sm.kb, sm.pb, sm.hist, sm.wsum, &sm.skip,
-                                         (int)l.n, a.passes, 0u);
-            emit_block<NW * 32>(a, l, (int)l.n, f ? sm.kb : sm.ka, f ? sm.pb : sm.pa,
-                                (int)l.n, nullptr, nullptr);
+            bool low_in_a = true;
+            const int split = block_sort(sm, (int)l.n, low_in_a);
+            emit_block<NW * 32>(a, l, (int)l.n, low_in_a ? sm.ka : sm.kb,
+                                low_in_a ? sm.pa : sm.pb, split, sm.kb, sm.pb);
             __syncthreads();
             continue;
         }
@@ -826,12 +854,15 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
             const int cn = (int)min((uint32_t)CAP, n - c0);
             load_slots<NW * 32>(a, l, c0, cn, sm.ka, sm.pa);
             __syncthreads();
-            const bool f = radix_lsd<NW>(sm.ka, sm.pa, sm.kb, sm.pb, sm.hist, sm.wsum, &sm.skip,
-                                         cn, a.passes, 0u);
-            const uint32_t *kk = f ? sm.kb : sm.ka;
-            const uint16_t *pp = f ? sm.pb : sm.pa;
-            for (int k = threadIdx.x; k < cn; k += blockDim.x)
-                A[c0 + k] = ((uint64_t)kk[k] << 32) | (uint64_t)(c0 + pp[k]);
+            bool low_in_a = true;
+            const int split = block_sort(sm, cn, low_in_a);
+            const uint32_t *kl = low_in_a ? sm.ka : sm.kb;
+            const uint16_t *pl = low_in_a ? sm.pa : sm.pb;
+            for (int k = threadIdx.x; k < cn; k += blockDim.x) {
+                const uint32_t key = k < split ? kl[k] : sm.kb[k];
+                const uint32_t pos = k < split ? pl[k] : sm.pb[k];
+                A[c0 + k] = ((uint64_t)key << 32) | (uint64_t)(c0 + pos);
+            }
             __syncthreads();
         }
         for (uint32_t w = CAP; w < n; w <<= 1) {
@@ -1588,7 +1619,7 @@ int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
 
 // Result rows, work units and LJ task list of the batch in context c.  Reads
 // back {rows, gravity work units, LJ tasks, interactions, longest list}.
-int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
+int gc_prepare_issue(gc_pool *p, FlushCtx &c)
 {
     const uint64_t n = c.n_tasks;
     TaskRec *tasks = c.tasks.as<TaskRec>();
@@ -1615,14 +1646,28 @@ int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
     GC_TRY(gc_exclusive_scan_u32(c.cub_tmp, wu_g, wu_off, n + 1, c.s));
     ++p->stats.primitive_calls;
     GC_TRY(gc_exclusive_scan_u32(c.cub_tmp, lj, lj_off, n + 1, c.s));
-    uint64_t h_rows = 0;
-    uint32_t h_wu = 0, h_lj = 0;
-    GC_CUDA_TRY(cudaMemcpyAsync(&h_rows, row_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, c.s));
-    GC_CUDA_TRY(cudaMemcpyAsync(&h_wu, wu_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
-    GC_CUDA_TRY(cudaMemcpyAsync(&h_lj, lj_off + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.s));
+    // sizes into the context's pinned words (the copies do not block)
+    c.h_ctr[FH_ROWS] = c.h_ctr[FH_WU] = c.h_ctr[FH_LJ] = 0;
+    GC_CUDA_TRY(cudaMemcpyAsync(c.h_ctr + FH_ROWS, row_off + n, sizeof(uint64_t),
+                                cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaMemcpyAsync(c.h_ctr + FH_WU, wu_off + n, sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, c.s));
+    GC_CUDA_TRY(cudaMemcpyAsync(c.h_ctr + FH_LJ, lj_off + n, sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, c.s));
     GC_CUDA_TRY(cudaMemcpyAsync(c.h_ctr, c.d_ctr, sizeof(unsigned long long) * FC_COUNT,
                                 cudaMemcpyDeviceToHost, c.s));
-    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
+    return GC_OK;
+}
+
+int gc_prepare_finish(gc_pool *p, FlushCtx &c, uint64_t info[5])
+{
+    const uint64_t n = c.n_tasks;
+    TaskRec *tasks = c.tasks.as<TaskRec>();
+    uint64_t *row_off = c.rowcnt.as<uint64_t>() + (n + 1);
+    uint32_t *wu_off = c.wu_off.as<uint32_t>();
+    uint32_t *lj_off = wu_off + (n + 1);
+    const uint64_t h_rows = c.h_ctr[FH_ROWS];
+    const uint32_t h_wu = (uint32_t)c.h_ctr[FH_WU], h_lj = (uint32_t)c.h_ctr[FH_LJ];
     GC_TRY(c.wu.reserve(((uint64_t)h_wu + 1) * sizeof(GravWU)));
     GC_TRY(c.lj_list.reserve(((uint64_t)h_lj + 1) * sizeof(uint32_t)));
     ++p->stats.kernel_launches;
@@ -1636,6 +1681,13 @@ int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
     info[3] = c.h_ctr[FC_INTER];
     info[4] = c.h_ctr[FC_MAXLIST];
     return GC_OK;
+}
+
+int gc_prepare(gc_pool *p, FlushCtx &c, uint64_t info[5])
+{
+    GC_TRY(gc_prepare_issue(p, c));
+    GC_CUDA_TRY(cudaStreamSynchronize(c.s));
+    return gc_prepare_finish(p, c, info);
 }
 
 // Host copies of the per-task work-unit offsets (for waves and per-task
@@ -1664,10 +1716,10 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     if (!attr_set) {
         GC_CUDA_TRY(cudaFuncSetAttribute(
             k_pack_large<PK_CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            (int)sizeof(PackSmem<PK_CAP, PackLargeWarps<PK_CAP>::value>)));
+            (int)sizeof(PackSmemLarge<PK_CAP>)));
         GC_CUDA_TRY(cudaFuncSetAttribute(
             k_pack_large<PK_CAP_HUGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-            (int)sizeof(PackSmem<PK_CAP_HUGE, PackLargeWarps<PK_CAP_HUGE>::value>)));
+            (int)sizeof(PackSmemLarge<PK_CAP_HUGE>)));
         GC_CUDA_TRY(cudaFuncSetAttribute(k_pack_mid<PM_CAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(PackSmemMid<PM_CAP>)));
@@ -1718,13 +1770,13 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
         ++p->stats.kernel_launches;
         constexpr int nw = PackLargeWarps<PK_CAP>::value;
         k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), nw * 32,
-                               sizeof(PackSmem<PK_CAP, nw>), c.s>>>(a);
+                               sizeof(PackSmemLarge<PK_CAP>), c.s>>>(a);
     }
     if (c.max_list > PK_CAP) {
         ++p->stats.kernel_launches;
         constexpr int nw = PackLargeWarps<PK_CAP_HUGE>::value;
         k_pack_large<PK_CAP_HUGE><<<grid_for(a.n_lists, 1, p->num_sms), nw * 32,
-                                    sizeof(PackSmem<PK_CAP_HUGE, nw>), c.s>>>(a);
+                                    sizeof(PackSmemLarge<PK_CAP_HUGE>), c.s>>>(a);
     }
     GC_CUDA_TRY(cudaGetLastError());
     return GC_OK;

@@ -4,16 +4,22 @@
 //
 // Per flush wave (all steps on the device, one small counter read-back):
 //   1. mark every referenced id with the wave's epoch and count references,
-//   2. list the distinct ids in ascending order (order-preserving compaction
-//      over the id space; no sort needed),
-//   3. split them into hits (resident) and misses,
-//   4. list free slots in ascending order; if misses exceed them, evict the
+//   2. list the distinct ids: for a wave of many entries, in ascending order
+//      by an order-preserving compaction over the id space; for a wave of
+//      few entries (fewer than a sixteenth of the id range), as the marking
+//      finds them, so the wave costs its entries and not the id range,
+//   3. split them into hits (resident) and misses (read back with the
+//      counters: one host round trip), misses then in ascending id order,
+//   4. if misses exceed the free slots (counted on the host), evict the
 //      resident ids not referenced now in ascending (last use, slot) order,
-//      writing their values back to the host mirror,
+//      writing their values back to the host mirror; list the free slots in
+//      ascending order,
 //   5. give the i-th smallest missing id the i-th smallest free slot and
 //      fetch its value from the pinned host mirror (mapped memory, read by
 //      the kernel over the CPU-GPU link),
-//   6. stamp last use and write the slot of every entry.
+//   6. stamp last use.
+#include <algorithm>
+
 #include "gc_common.cuh"
 
 namespace {
@@ -151,13 +157,17 @@ __global__ void k_compact_write(CompactArgs a, const uint32_t *tile_off, uint32_
 // the reference word, in parallel with it, so the pack that follows reads
 // the slots of its entries in order instead of looking each one up.  A hit
 // keeps its slot through the rest of the chare-table step (only ids not
-// referenced now are evicted); a miss is looked up again by the pack.
+// referenced now are evicted); a miss is looked up again by the pack.  With
+// `first` set, the thread that moves an id's reference word to the wave's
+// epoch appends the id to `first` (the distinct ids of the wave, in no
+// particular order, counted in ctr[CTR_UNIQUE]).
 constexpr int MARK_HASH = 2048;
 
 __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, uint64_t ns,
                        uint64_t id_cap, uint32_t *ref_epoch,
                        uint32_t *ref_count, uint32_t epoch, unsigned long long *ctr,
-                       uint64_t chunk, const uint32_t *slot_of_id, uint32_t *ent)
+                       uint64_t chunk, const uint32_t *slot_of_id, uint32_t *ent,
+                       uint32_t *first)
 {
     __shared__ uint32_t hkey[MARK_HASH];
     __shared__ uint32_t hcnt[MARK_HASH];
@@ -182,7 +192,23 @@ __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, ui
             bad = true;
             continue;
         }
-        if (e0 != epoch) ref_epoch[id] = epoch;
+        bool is_first = false;
+        if (e0 != epoch) {
+            if (first) is_first = atomicExch(&ref_epoch[id], epoch) != epoch;
+            else ref_epoch[id] = epoch;
+        }
+        if (first) {
+            // one counter add per warp for the ids it sees first
+            const unsigned am = __activemask();
+            const unsigned fm = __ballot_sync(am, is_first);
+            if (fm) {
+                const int lane = threadIdx.x & 31, leader = __ffs((int)fm) - 1;
+                unsigned long long at = 0;
+                if (lane == leader) at = atomicAdd(&ctr[CTR_UNIQUE], (unsigned long long)__popc(fm));
+                at = __shfl_sync(am, at, leader);
+                if (is_first) first[at + __popc(fm & ((1u << lane) - 1u))] = id;
+            }
+        }
         uint32_t h = (id * 2654435761u) & (MARK_HASH - 1);
         bool done = false;
         for (int probe = 0; probe < 8; ++probe) {
@@ -389,10 +415,11 @@ int gc_launch_upload_seq(gc_pool *p, uint32_t id_base, const float4 *vals, uint6
     return GC_OK;
 }
 
-int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
-                 uint64_t ns, uint32_t *ent)
+// Steps 1-3 on the device and the counters' copy to the host (no wait).
+int gc_residency_issue(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
+                       uint64_t ns, uint32_t *ent)
 {
-    const uint64_t id_cap = p->cfg.id_capacity, cap = p->cfg.pool_capacity;
+    const uint64_t id_cap = p->cfg.id_capacity;
     const uint64_t n = nt + ns;
     unsigned long long *ctr = p->d_ctr;
     p->epoch += 1;
@@ -401,29 +428,46 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
 
     GC_CUDA_TRY(cudaMemsetAsync(ctr + CTR_UNIQUE, 0,
                                 sizeof(unsigned long long) * (CTR_COUNT - CTR_UNIQUE), p->s));
-    if (n > 0) {
-        const uint64_t chunk = 8192;
-        ++p->stats.kernel_launches;
-        k_mark<<<(unsigned)((n + chunk - 1) / chunk), 512, 0, p->s>>>(
-            tgt, nt, src, ns, id_cap, p->d_ref_epoch, p->d_ref_count, p->epoch, ctr,
-            chunk, p->d_slot_of_id, ent);
-    }
+    // a wave of few entries lists its distinct ids while marking them
+    const bool few = n * 16 < id_cap;
     uint64_t ubound = n < id_cap ? n : id_cap;
     GC_TRY(p->uniq.reserve((ubound + 1) * sizeof(uint32_t)));
     GC_TRY(p->miss.reserve((ubound + 1) * sizeof(uint32_t)));
-    GC_TRY(p->freel.reserve((cap + 1) * sizeof(uint32_t)));
-    GC_TRY(gc_compact(p, p->tiles, p->s, CK_REF_EPOCH, id_cap, nullptr, nullptr, p->uniq.as<uint32_t>(),
-                      ctr + CTR_UNIQUE));
+    if (n > 0) {
+        // chunks of 8192 entries (neighbouring lists share ids, so a block's
+        // table aggregates well); a small wave in chunks of at least 1024
+        // spread over more SMs
+        uint64_t chunk = (n + (uint64_t)p->num_sms * 4 - 1) / ((uint64_t)p->num_sms * 4);
+        chunk = std::min<uint64_t>(8192, std::max<uint64_t>(1024, (chunk + 511) / 512 * 512));
+        ++p->stats.kernel_launches;
+        k_mark<<<(unsigned)((n + chunk - 1) / chunk), 512, 0, p->s>>>(
+            tgt, nt, src, ns, id_cap, p->d_ref_epoch, p->d_ref_count, p->epoch, ctr,
+            chunk, p->d_slot_of_id, ent, few ? p->uniq.as<uint32_t>() : nullptr);
+    }
+    if (!few)
+        GC_TRY(gc_compact(p, p->tiles, p->s, CK_REF_EPOCH, id_cap, nullptr, nullptr,
+                          p->uniq.as<uint32_t>(), ctr + CTR_UNIQUE));
     ++p->stats.kernel_launches;
     k_classify<<<grid_for(ubound, 256, maxb), 256, 0, p->s>>>(
         p->uniq.as<uint32_t>(), ctr + CTR_UNIQUE, p->d_slot_of_id, p->d_ref_count, ctr);
     GC_TRY(gc_compact(p, p->tiles, p->s, CK_MISS, ubound, (const uint64_t *)(ctr + CTR_UNIQUE),
                       p->uniq.as<uint32_t>(), p->miss.as<uint32_t>(), ctr + CTR_MISSES));
-    GC_TRY(gc_compact(p, p->tiles, p->s, CK_FREE, cap, nullptr, nullptr, p->freel.as<uint32_t>(),
-                      ctr + CTR_FREE));
     GC_CUDA_TRY(cudaMemcpyAsync(p->h_ctr, ctr, sizeof(unsigned long long) * CTR_COUNT,
                                 cudaMemcpyDeviceToHost, p->s));
-    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    p->res_n = n;
+    p->res_few = few;
+    return GC_OK;
+}
+
+// Steps 3-6 once the counters issued by gc_residency_issue have reached the
+// host (the caller has waited for the stream).
+int gc_residency_finish(gc_pool *p)
+{
+    const uint64_t id_cap = p->cfg.id_capacity, cap = p->cfg.pool_capacity;
+    const uint64_t n = p->res_n;
+    const bool few = p->res_few;
+    unsigned long long *ctr = p->d_ctr;
+    const int maxb = p->num_sms * 16;
     GC_CUDA_TRY(cudaGetLastError());
 
     // this step's own status bits; a timeout of an earlier batch stays for
@@ -434,9 +478,20 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         return GC_ERR_UNKNOWN_ID;
     }
     const uint64_t U = p->h_ctr[CTR_UNIQUE], H = p->h_ctr[CTR_HITS];
-    const uint64_t M = p->h_ctr[CTR_MISSES], F = p->h_ctr[CTR_FREE];
+    const uint64_t M = p->h_ctr[CTR_MISSES], F = p->free_slots;
     uint64_t need = M > F ? M - F : 0;
     p->n_evicted_last = 0;
+    const uint32_t *miss = p->miss.as<uint32_t>();
+    if (few && M > 1) {
+        // misses take free slots in ascending id order
+        GC_TRY(p->miss_sorted.reserve((M + 1) * sizeof(uint32_t)));
+        int bits = 1;
+        while (bits < 32 && ((uint64_t)1 << bits) < id_cap) ++bits;
+        ++p->stats.primitive_calls;
+        GC_TRY(gc_sort_keys_u32(p->cub_tmp, miss, p->miss_sorted.as<uint32_t>(), M, bits, p->s));
+        miss = p->miss_sorted.as<uint32_t>();
+    }
+    if (M) GC_TRY(p->freel.reserve((cap + 1) * sizeof(uint32_t)));
     if (need) {
         uint64_t resident = cap - F;
         uint64_t candidates = resident - H;
@@ -455,17 +510,18 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
         k_evict_apply<<<grid_for(need, 256, maxb), 256, 0, p->s>>>(
             p->ekeys2.as<uint64_t>(), need, p->d_id_of_slot, p->d_slot_of_id, p->d_pool,
             p->d_mirror, p->evicted.as<uint32_t>());
-        GC_TRY(gc_compact(p, p->tiles, p->s, CK_FREE, cap, nullptr, nullptr, p->freel.as<uint32_t>(),
-                          ctr + CTR_FREE));
         p->n_evicted_last = need;
     }
     if (M || need) ++p->table_version;   // slots assigned or freed: captured graphs stale
     if (M) {
+        GC_TRY(gc_compact(p, p->tiles, p->s, CK_FREE, cap, nullptr, nullptr,
+                          p->freel.as<uint32_t>(), ctr + CTR_FREE));
         ++p->stats.kernel_launches;
         k_assign<<<grid_for(M, 256, maxb), 256, 0, p->s>>>(
-            p->miss.as<uint32_t>(), M, p->freel.as<uint32_t>(), p->d_slot_of_id,
-            p->d_id_of_slot, p->d_pool, p->d_mirror);
+            miss, M, p->freel.as<uint32_t>(), p->d_slot_of_id, p->d_id_of_slot, p->d_pool,
+            p->d_mirror);
     }
+    p->free_slots = F + need - M;
     if (U) {
         ++p->stats.kernel_launches;
         k_touch<<<grid_for(U, 256, maxb), 256, 0, p->s>>>(p->uniq.as<uint32_t>(), U,
@@ -487,4 +543,12 @@ int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *s
     st.last_evictions += need;
     for (int b = 0; b < 8; ++b) st.reuse_hist[b] += p->h_ctr[CTR_HIST0 + b];
     return GC_OK;
+}
+
+int gc_residency(gc_pool *p, const uint32_t *tgt, uint64_t nt, const uint32_t *src,
+                 uint64_t ns, uint32_t *ent)
+{
+    GC_TRY(gc_residency_issue(p, tgt, nt, src, ns, ent));
+    GC_CUDA_TRY(cudaStreamSynchronize(p->s));
+    return gc_residency_finish(p);
 }

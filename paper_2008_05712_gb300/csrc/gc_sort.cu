@@ -40,6 +40,15 @@ int gc_sort_pairs_u32(DBuf &tmp, const uint32_t *kin, uint32_t *kout, const uint
     });
 }
 
+int gc_sort_keys_u32(DBuf &tmp, const uint32_t *kin, uint32_t *kout, uint64_t n, int end_bit,
+                     cudaStream_t s)
+{
+    if (n == 0) return GC_OK;
+    return run_twice(tmp, [&](void *t, size_t &b) {
+        return cub::DeviceRadixSort::SortKeys(t, b, kin, kout, (int64_t)n, 0, end_bit, s);
+    });
+}
+
 int gc_sort_keys_u64(DBuf &tmp, const uint64_t *kin, uint64_t *kout, uint64_t n,
                      cudaStream_t s)
 {
