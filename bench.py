@@ -50,10 +50,19 @@ PACK_BYTES_PER_ENTRY = 40
 # DRAM bytes (read + write) per unit of work from ncu captures of the current
 # kernels (None until captured again after a kernel change):
 # k_gravity per interaction, the pack kernels per list entry.
-# profiles/k_gravity_nbody262k.md: 506.6 MB for 2.949e8 interactions (262,144-particle step)
-GRAVITY_DRAM_BYTES_PER_INTERACTION = 506.6e6 / 2.949e8
-# profiles/k_pack_mid_nbody262k.md: 634.1 MB for 3.07e7 entries (262,144-particle step)
-PACK_DRAM_BYTES_PER_ENTRY = 634.1e6 / 3.07e7
+GRAVITY_DRAM_BYTES_PER_INTERACTION = None
+PACK_DRAM_BYTES_PER_ENTRY = None
+# Algorithmic bytes of the per-id accumulation: a row's 32-byte compensated
+# partial and its 4-byte id read, the id's FP64 total (32 B) read and written;
+# the per-cell MD form derives ids from the task structure (no id read).
+SCATTER_BYTES_PER_ROW = 32 + 4 + 32 + 32
+MD_SCATTER_BYTES_PER_ROW = 32
+MD_SCATTER_BYTES_PER_ID = 32 + 32
+# FP32 instructions of one LJ candidate pair: about 6 when rejected (the
+# displacement, |r|^2, the compare) and 40 when inside the cutoff (plus the
+# force, the energy and the compensated sums)
+LJ_INSTR_REJECTED = 6
+LJ_INSTR_INSIDE = 40
 
 
 # Uneven batch and serving workload: a two-Plummer merger of 4,194,304
@@ -71,8 +80,15 @@ C4_WORKLOAD = ("uneven_200k: 200,000 gravity tasks over a 4,194,304-particle two
 # Interaction schedules chosen by the autotuner on this GPU, per workload
 # (written on the first run, then reused).
 TUNE_CACHE = os.path.join(ROOT, "paper_2008_05712_gb300", "tuning.json")
-# serving: (aggregate Poisson rate of 16 producers in tasks/s, schedule seconds)
-SERVE_RATES = ((1e4, 1.0), (1e5, 1.0), (1e6, 0.2))
+# serving: aggregate Poisson rates of 16 producers (tasks/s); every rate runs
+# under each combining policy for SERVE_WARMUP_S + SERVE_SECONDS of arrivals
+# (latency statistics from the arrivals after the warm-up; the 200k tasks
+# replayed cyclically), with at most SERVE_DRAIN_S after the schedule for the
+# queue an overloaded policy leaves behind
+SERVE_RATES = (1e4, 1e5, 1e6)
+SERVE_SECONDS = 10.0
+SERVE_WARMUP_S = 1.0
+SERVE_DRAIN_S = 2.0
 
 
 def peaks():
@@ -281,6 +297,33 @@ MD_WORKLOAD = ("lj_fcc_1M: 1,048,576 Lennard-Jones atoms, jittered FCC at densit
 RC2 = 6.25
 
 
+def md_rooflines(md, fp32_tflops, hbm_gbs, hbm_basis):
+    """LJ interaction against the FP32 pipe (instructions per candidate pair)
+    and the per-cell accumulation of the MD step against HBM."""
+    cand, inside = md["candidate_pairs_per_step"], md["pairs_in_cutoff"]
+    instr = LJ_INSTR_REJECTED * (cand - inside) + LJ_INSTR_INSIDE * inside
+    ms_lj, ms_sc = md["stage_ms_avg"]["interact"], md["stage_ms_avg"]["scatter"]
+    lj = {"kernel": "k_lj (interaction)", "bound": "alu",
+          "achieved": instr / (ms_lj / 1e3) / 1e12, "peak": fp32_tflops / 2,
+          "unit": "T FP32 lane-instructions/s",
+          "peak_basis": "measured paired-FP32 FMA probe (gc_fp32_peak), one lane-instruction "
+                        "per FMA",
+          "work_per_unit": f"{LJ_INSTR_REJECTED} instructions per rejected candidate, "
+                           f"{LJ_INSTR_INSIDE} per pair inside the cutoff",
+          "units_per_launch": cand, "ms_per_launch": ms_lj, "traffic": None}
+    lj["frac"] = lj["achieved"] / lj["peak"]
+    rows, ids = md["rows_per_step"], md["atoms"]
+    by = MD_SCATTER_BYTES_PER_ROW * rows + MD_SCATTER_BYTES_PER_ID * ids
+    sc = {"kernel": "k_reduce_md (per-cell accumulation)", "bound": "hbm",
+          "achieved": by / (ms_sc / 1e3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+          "peak_basis": hbm_basis,
+          "work_per_unit": f"{MD_SCATTER_BYTES_PER_ROW} B per row, "
+                           f"{MD_SCATTER_BYTES_PER_ID} B per atom (FP64 total read and written)",
+          "units_per_launch": rows, "ms_per_launch": ms_sc, "traffic": None}
+    sc["frac"] = sc["achieved"] / sc["peak"]
+    return {"lj": lj, "scatter": sc}
+
+
 def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True, cells=64, ncell=42):
     """The MD workload (Section 4.2 on the 3-D FCC system): task build from
     device-resident cell indices and one batched flush per step, timed with
@@ -320,7 +363,8 @@ def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True, cells=64, 
     nb = s1["timed_batches"] - s0["timed_batches"]
     stage = {k: (s1["stage_ms_sum"][k] - s0["stage_ms_sum"][k]) / max(nb, 1)
              for k in s1["stage_ms_sum"]}
-    out = {"workload": label, "ms_per_step": ms, "candidate_pairs_per_step": int(pairs),
+    out = {"workload": label, "atoms": n, "rows_per_step": int(pool.result_rows()),
+           "ms_per_step": ms, "candidate_pairs_per_step": int(pairs),
            "value": pairs / (ms / 1e3), "unit": "candidate pairs/s",
            "pairs_in_cutoff": s1["lj_pairs_in_cutoff"], "stage_ms_avg": stage,
            "tasks_per_step": int((s1["tasks"] - s0["tasks"]) / reps)}
@@ -353,6 +397,92 @@ def md_section(gcharm, torch, seed, stream, reps=5, with_oracle=True, cells=64, 
                                "sample": "2000 seeded-random cell-pair tasks of the step "
                                          "(FP64 LJ, one thread; includes Python call overhead "
                                          "per task)"}
+    pool.close()
+    return out
+
+
+C1_WORKLOAD = ("plummer_4096: 4,096 Plummer particles, theta=0.7, buckets<=32, eps=0.01, "
+               "every bucket's task in one batch")
+
+
+def c1_section(gcharm, torch, seed, stream, reps=200, with_oracle=True):
+    """The small case: one batch of every bucket of a 4096-particle tree, as
+    a step (tree build and flush), as the flush of the built tasks alone,
+    with one interaction launch per task, and replayed as a CUDA graph."""
+    n = 4096
+    x = inputs.plummer(n, seed)
+    pool = gcharm.Pool(id_capacity=4 * n, pool_capacity=4 * n, eps2=EPS2,
+                       stream=stream.cuda_stream)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    xd = torch.from_numpy(x).cuda()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        pool.join(stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    def step():
+        pool.build_nbody(xd, BUCKET, *THETA)
+        pool.flush()
+
+    for _ in range(5):
+        step()
+    s0 = pool.stats()
+    ms_step = timed(step, reps)
+    s1 = pool.stats()
+    inter = (s1["interactions"] - s0["interactions"]) / reps
+    tasks = int((s1["tasks"] - s0["tasks"]) / reps)
+    nbt = s1["timed_batches"] - s0["timed_batches"]
+    flush_ms = (s1["stage_ms_sum"]["total"] - s0["stage_ms_sum"]["total"]) / max(nbt, 1)
+    inter_ms = (s1["stage_ms_sum"]["interact"] - s0["stage_ms_sum"]["interact"]) / max(nbt, 1)
+    out = {"workload": C1_WORKLOAD, "tasks": tasks, "interactions": int(inter),
+           "step": {"ms": ms_step, "value": inter / (ms_step / 1e3), "unit": "interactions/s",
+                    "note": "tree build, walk and one batched flush per step"},
+           "batched_flush": {"ms": flush_ms, "value": inter / (flush_ms / 1e3),
+                             "interaction_ms": inter_ms,
+                             "interaction_value": inter / (inter_ms / 1e3),
+                             "unit": "interactions/s"}}
+    # one interaction launch per task (the uncombined form of Section 3.1)
+    per = []
+    for _ in range(5):
+        pool.build_nbody(xd, BUCKET, *THETA)
+        pool.flush_per_task()
+        torch.cuda.synchronize()
+        per.append(pool.timings())
+    per_flush = statistics.median(t["total"] for t in per)
+    per_inter = statistics.median(t["interact"] for t in per)
+    out["per_task_launch"] = {"ms": per_flush, "value": inter / (per_flush / 1e3),
+                              "interaction_ms": per_inter,
+                              "interaction_value": inter / (per_inter / 1e3),
+                              "unit": "interactions/s",
+                              "speedup_batched_flush": per_flush / flush_ms,
+                              "speedup_interaction": per_inter / inter_ms}
+    # the batch captured once and replayed as a CUDA graph
+    pool.build_nbody(xd, BUCKET, *THETA)
+    graph = gcharm.Graph(pool)
+    graph.launch()
+    graph.wait()
+    ms_graph = timed(graph.launch, reps)
+    graph.wait()
+    if with_oracle:
+        from oracle import oracle as O
+        tr = O.Tree(x)
+        tab = np.concatenate([x, tr.node_table()])
+        to, tg = tr.bucket_targets()
+        lo, li = tr.lists(*THETA)
+        ref = O.gravity_batch(tab, to, tg, lo, li, EPS2)
+        out["parity_on_graph_rows"] = error_stats(gcharm.value(graph.results()), ref, to)
+    graph.close()
+    out["graph_replay"] = {"ms": ms_graph, "value": inter / (ms_graph / 1e3),
+                           "unit": "interactions/s",
+                           "note": "same tasks and chare table each replay (no tree build)"}
     pool.close()
     return out
 
@@ -465,7 +595,8 @@ def uneven_plain(gcharm, torch, seed, stream, batches=2):
     return out
 
 
-def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=True):
+def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=True,
+                       serve_seconds=SERVE_SECONDS, serve_warmup=SERVE_WARMUP_S):
     """The 200k-task uneven batch (device-resident task arrays, timed with
     events) and the serving loop at three arrival rates (host task arrays,
     host clock, latency from each task's scheduled arrival)."""
@@ -551,28 +682,41 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=Tr
     graph.close()
     del dk, dto, dso, dtg, dsr
 
-    # serving: open-loop Poisson arrivals (16 producers merged)
+    # serving: open-loop Poisson arrivals (16 producers merged), every rate
+    # under every combining policy
     serving = {"workload": C4_WORKLOAD + "; tasks arrive as open-loop Poisson streams of "
-                                         "16 producers, in task order",
-               "latency": "host CLOCK_MONOTONIC, scheduled arrival -> completion observed",
-               "runs": []}
-    runs = [(r, d, gcharm.GC_COMBINE_GREEDY) for r, d in SERVE_RATES]
-    runs.append((1e5, 1.0, gcharm.GC_COMBINE_ADAPTIVE_WINDOW))
-    names = {gcharm.GC_COMBINE_GREEDY: "greedy (continuous batching)",
-             gcharm.GC_COMBINE_ADAPTIVE_WINDOW: "adaptive, windowed running max (Section 3.1)"}
-    for k, (rate, dur, policy) in enumerate(runs):
-        m = min(C4_TASKS, int(rate * dur))
+                                         "16 producers, the 200k tasks replayed cyclically",
+               "latency": "host CLOCK_MONOTONIC, scheduled arrival -> completion observed; "
+                          f"statistics over the arrivals after a {serve_warmup:g} s warm-up",
+               "seconds_per_run": serve_seconds, "warmup_s": serve_warmup,
+               "drain_limit_s": SERVE_DRAIN_S, "runs": []}
+    policies = [
+        (gcharm.GC_COMBINE_GREEDY, "greedy (continuous batching)"),
+        (gcharm.GC_COMBINE_ADAPTIVE, "adaptive, running max of the arrival gaps (Section 3.1)"),
+        (gcharm.GC_COMBINE_ADAPTIVE_WINDOW, "adaptive, running max over the last 1024 gaps"),
+        (gcharm.GC_COMBINE_STATIC, "static, every 100 arrivals (Section 4.3)"),
+        (gcharm.GC_COMBINE_PER_TASK, "per task (no combining)"),
+    ]
+    for k, rate in enumerate(SERVE_RATES):
+        m = int(rate * (serve_warmup + serve_seconds))
         arr = inputs.poisson_arrivals(m, rate, seed + 10 + k)
-        a, b = int(to[m]), int(so[m])
-        rep, lat, _ = pool.serve(arr, kinds[:m], to[:m + 1], tg[:a], so[:m + 1], sr[:b],
-                                 policy=policy)
-        serving["runs"].append({
-            "rate_tasks_per_s": rate, "policy": names[policy], "tasks": m,
-            "p50_us": rep["lat_p50_us"], "p99_us": rep["lat_p99_us"],
-            "max_us": rep["lat_max_us"], "mean_us": rep["lat_mean_us"],
-            "interactions_per_s": rep["interactions_per_s"], "wall_s": rep["wall_s"],
-            "batches": rep["batches"], "mean_batch": rep["mean_batch"],
-            "max_size": rep["max_size"], "busy_s": rep["busy_s"]})
+        for policy, name in policies:
+            rep, lat, _ = pool.serve(arr, kinds, to, tg, so, sr, policy=policy,
+                                     task_set=C4_TASKS, warmup_ns=int(serve_warmup * 1e9),
+                                     drain_ns=int(SERVE_DRAIN_S * 1e9))
+            served = m - rep["unserved"]
+            lat_ok = rep["measured"] > 0     # else no arrival after the warm-up was served
+            serving["runs"].append({
+                "rate_tasks_per_s": rate, "policy": name, "arrivals": m,
+                "measured": rep["measured"], "unserved": rep["unserved"],
+                "served_tasks_per_s": served / rep["wall_s"],
+                "p50_us": rep["lat_p50_us"] if lat_ok else None,
+                "p99_us": rep["lat_p99_us"] if lat_ok else None,
+                "max_us": rep["lat_max_us"] if lat_ok else None,
+                "mean_us": rep["lat_mean_us"] if lat_ok else None,
+                "interactions_per_s": rep["interactions_per_s"], "wall_s": rep["wall_s"],
+                "batches": rep["batches"], "mean_batch": rep["mean_batch"],
+                "max_size": rep["max_size"], "busy_s": rep["busy_s"]})
     pool.close()
     return uneven, serving
 
@@ -609,6 +753,10 @@ def main():
                     help="run one workload alone and print its figures (profiling form)")
     ap.add_argument("--md-cells", type=int, default=64, help="FCC unit cells per axis")
     ap.add_argument("--md-ncell", type=int, default=42, help="MD cells per axis")
+    ap.add_argument("--serve-seconds", type=float, default=SERVE_SECONDS,
+                    help="measured seconds of arrivals per serving run")
+    ap.add_argument("--serve-warmup", type=float, default=SERVE_WARMUP_S,
+                    help="warm-up seconds of arrivals per serving run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -719,6 +867,14 @@ def main():
             "traffic": (PACK_DRAM_BYTES_PER_ENTRY * per_step_entries
                         if PACK_DRAM_BYTES_PER_ENTRY else None)}
     pack["frac"] = pack["achieved"] / pack["peak"]
+    scatter = {"kernel": "k_reduce_unique (scatter: one row per particle, no sort)",
+               "bound": "hbm",
+               "achieved": SCATTER_BYTES_PER_ROW * n / (stage["scatter"] / 1e3) / 1e9,
+               "peak": pack["peak"], "unit": "GB/s", "peak_basis": pack["peak_basis"],
+               "work_per_unit": f"{SCATTER_BYTES_PER_ROW} B per row (32 B partial, 4 B id, "
+                                "32 B FP64 total read and written)",
+               "units_per_launch": n, "ms_per_launch": stage["scatter"], "traffic": None}
+    scatter["frac"] = scatter["achieved"] / scatter["peak"]
     dominant = pack if stage["pack"] >= stage["interact"] else grav
 
     # reuse ablation (Section 3.2, Fig. 3) on the last timed batch
@@ -815,6 +971,11 @@ def main():
     if rank == 0 and not args.no_md:
         md = md_section(gcharm, torch, inputs.SEED_BASE + 3, stream,
                         with_oracle=not args.no_cpu_baseline)
+        md["rooflines"] = md_rooflines(md, fp32_measured, pack["peak"], pack["peak_basis"])
+    c1 = None
+    if rank == 0:
+        c1 = c1_section(gcharm, torch, inputs.SEED_BASE + 1, stream,
+                        with_oracle=not args.no_cpu_baseline)
     ewald = None
     if rank == 0 and not args.no_md:
         ewald = ewald_section(gcharm, torch, inputs.SEED_BASE + 8, stream,
@@ -825,7 +986,9 @@ def main():
         del X
         torch.cuda.empty_cache()
         uneven, serving = uneven_and_serving(gcharm, torch, inputs.SEED_BASE + 4, stream,
-                                             with_oracle=not args.no_cpu_baseline)
+                                             with_oracle=not args.no_cpu_baseline,
+                                             serve_seconds=args.serve_seconds,
+                                             serve_warmup=args.serve_warmup)
 
     if rank == 0:
         line = {
@@ -837,7 +1000,7 @@ def main():
                        "l2": "inputs larger than L2 (staging ~4 GB per step)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": dominant,
-            "rooflines": {"interaction": grav, "pack": pack},
+            "rooflines": {"interaction": grav, "pack": pack, "scatter": scatter},
             "stage_ms_avg": stage,
             "tuning": {"wu_max_targets": tuning["wu_max_targets"],
                        "schedule": "lpt" if tuning["schedule"] else "fifo",
@@ -851,6 +1014,7 @@ def main():
             "per_task_launch": per_task,
             "reuse_ablation": ablation,
             "md": md,
+            "c1_small": c1,
             "ewald": ewald,
             "uneven_batch": uneven,
             "serving": serving,

@@ -402,10 +402,10 @@ int gc_last_timings(gc_pool_t *pool, float ms_out[5]);
 #define GC_COMBINE_STATIC 2          /* paper's baseline: all pending every static_n
                                         arrivals (100 in Section 4.3)                    */
 #define GC_COMBINE_PER_TASK 3        /* no combining: one task per batch                */
-#define GC_COMBINE_GREEDY 4          /* every poll: all pending, up to maxSize (no
-                                        counterpart in the paper; work-conserving form
-                                        for a caller that polls when the device has
-                                        room for another batch)                          */
+#define GC_COMBINE_GREEDY 4          /* every poll: all pending (no counterpart in the
+                                        paper; work-conserving form for a caller that
+                                        polls when the device has room for another
+                                        batch; batches grow with the queue)              */
 
 typedef struct gc_combiner gc_combiner_t;
 
@@ -416,8 +416,8 @@ typedef struct gc_combiner gc_combiner_t;
  * pending once the time since the last arrival exceeds 2 x maxInterval.
  * GC_COMBINE_STATIC combines all pending after every static_n arrivals
  * (the paper's static strategy, Section 4.3).  GC_COMBINE_GREEDY combines
- * min(pending, maxSize) at every poll.  Host-side, no device work.
- * Errors: GC_ERR_ARG (unknown policy, max_size 0 for the adaptive and greedy rules,
+ * everything pending at every poll.  Host-side, no device work.
+ * Errors: GC_ERR_ARG (unknown policy, max_size 0 for the adaptive rules,
  * static_n 0 for the static rule, window 0 for the windowed rule). */
 int gc_combiner_create(int policy, uint64_t max_size, uint64_t static_n, uint64_t window,
                        gc_combiner_t **out);
@@ -454,6 +454,13 @@ typedef struct {
     uint64_t poll_ns;         /* longest idle sleep while nothing is queued    */
     uint64_t timeout_ns;      /* a batch not complete after this long fails the
                                  call with GC_ERR_TIMEOUT; 0 = 60 s           */
+    uint64_t task_set;        /* tasks in the CSR arrays; arrival k is task
+                                 k mod task_set (0 = n: arrival k is task k)  */
+    uint64_t warmup_ns;       /* arrivals scheduled before this are served but
+                                 left out of the latency statistics           */
+    uint64_t drain_ns;        /* no batch is started later than this after the
+                                 last scheduled arrival; tasks still queued
+                                 then are counted as unserved (0 = no limit)  */
 } gc_serve_config;
 
 typedef struct {
@@ -466,6 +473,8 @@ typedef struct {
     double mean_batch;        /* tasks per batch                               */
     double busy_s;            /* time with requests queued and no free batch
                                  slot (both flush contexts busy)              */
+    uint64_t measured;        /* tasks in the latency statistics               */
+    uint64_t unserved;        /* arrivals not served within the drain limit    */
 } gc_serve_report;
 
 /* Replay an open-loop arrival schedule in real time on this thread: task t
@@ -479,9 +488,15 @@ typedef struct {
  * interaction of the batch before it.  The static rule drains what is left
  * once the schedule has ended.  Latency of a task = completion observed by
  * the loop - its scheduled arrival (CLOCK_MONOTONIC), so queueing behind a
- * busy device is counted.  latency_ns_out (n values) and results_out (8
- * floats per result row, rows of task after task as gc_read_batch_results
- * gives them) may be NULL.  tgt_ids and src_ids are page-locked for the
+ * busy device is counted.  latency_ns_out (n values; UINT64_MAX for an
+ * unserved arrival) and results_out (8 floats per result row, rows of task
+ * after task as gc_read_batch_results gives them; only with task_set = 0 or
+ * n) may be NULL.  With task_set = m < n the m tasks are replayed cyclically
+ * (a batch of consecutive arrivals is then at most a few contiguous runs of
+ * the task arrays), so a long schedule needs no more than one task set.  An
+ * offered load the engine cannot sustain leaves a queue behind: drain_ns
+ * bounds the time spent after the schedule, and what is still queued then
+ * is reported as unserved instead of delaying the call without end.  tgt_ids and src_ids are page-locked for the
  * duration of the call (cudaHostRegister) unless they already are, so that
  * the per-batch copies run as direct DMA.  The pool must have no pending tasks; per-id
  * totals accumulate as for any flush.  Errors: GC_ERR_ARG (bad pointers,

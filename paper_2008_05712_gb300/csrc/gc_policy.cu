@@ -10,8 +10,11 @@
 // The paper's static baseline (Section 4.3) combines whatever is pending
 // after every 100 requests.  The greedy rule (no counterpart in the paper)
 // is the work-conserving form for a caller that polls only when it has room
-// for another batch on the device: combine everything pending, up to
-// maxSize, at every poll.  Host-side logic only (no device work).
+// for another batch on the device: combine everything pending at every
+// poll (the caller's admission still bounds a batch by the staging budget),
+// so under a load above what maxSize-request batches sustain the batches
+// grow with the queue instead of the queue growing without end.  Host-side
+// logic only (no device work).
 #include <cmath>
 #include <deque>
 
@@ -25,7 +28,10 @@ struct gc_combiner {
     bool have_arrival = false;
     uint64_t last_arrival = 0;
     uint64_t max_interval = 0;
-    std::deque<uint64_t> recent;     // windowed variant: last `window` intervals
+    // windowed variant: the last `window` intervals as a decreasing deque of
+    // (arrival number, interval), so the front is their maximum
+    std::deque<std::pair<uint64_t, uint64_t>> recent;
+    uint64_t n_gaps = 0;
     uint64_t since_combine = 0;      // arrivals since the last combine (static rule)
 };
 
@@ -37,8 +43,8 @@ int gc_combiner_create(int policy, uint64_t max_size, uint64_t static_n, uint64_
     if (!out) return GC_ERR_ARG;
     *out = nullptr;
     if (policy < GC_COMBINE_ADAPTIVE || policy > GC_COMBINE_GREEDY) return GC_ERR_ARG;
-    if ((policy == GC_COMBINE_ADAPTIVE || policy == GC_COMBINE_ADAPTIVE_WINDOW ||
-         policy == GC_COMBINE_GREEDY) && max_size == 0)
+    if ((policy == GC_COMBINE_ADAPTIVE || policy == GC_COMBINE_ADAPTIVE_WINDOW) &&
+        max_size == 0)
         return GC_ERR_ARG;
     if (policy == GC_COMBINE_STATIC && static_n == 0) return GC_ERR_ARG;
     if (policy == GC_COMBINE_ADAPTIVE_WINDOW && window == 0) return GC_ERR_ARG;
@@ -65,11 +71,13 @@ int gc_combiner_arrive(gc_combiner_t *c, uint64_t t_ns, uint64_t count)
         if (c->have_arrival) {
             const uint64_t gap = t_ns >= c->last_arrival ? t_ns - c->last_arrival : 0;
             if (c->policy == GC_COMBINE_ADAPTIVE_WINDOW) {
-                c->recent.push_back(gap);
-                if (c->recent.size() > c->window) c->recent.pop_front();
-                uint64_t m = 0;
-                for (uint64_t g : c->recent) m = g > m ? g : m;
-                c->max_interval = m;
+                // maximum of the last `window` intervals, amortised O(1)
+                const uint64_t k = c->n_gaps++;
+                while (!c->recent.empty() && c->recent.back().second <= gap)
+                    c->recent.pop_back();
+                c->recent.emplace_back(k, gap);
+                while (c->recent.front().first + c->window <= k) c->recent.pop_front();
+                c->max_interval = c->recent.front().second;
             } else if (gap > c->max_interval) {
                 c->max_interval = gap;
             }
@@ -101,7 +109,7 @@ int gc_combiner_poll(gc_combiner_t *c, uint64_t t_ns, uint64_t queued, uint64_t 
             if (c->since_combine >= c->static_n) take = queued;
             break;
         case GC_COMBINE_GREEDY:
-            take = queued < c->max_size ? queued : c->max_size;
+            take = queued;
             break;
         default:   // GC_COMBINE_PER_TASK
             take = 1;

@@ -63,6 +63,10 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     for (uint64_t i = 1; i < n; ++i)
         if (arrival_ns[i] < arrival_ns[i - 1]) return GC_ERR_ARG;
     if (p->nb_tasks) return GC_ERR_STATE;   // a pending batch would mix in
+    // arrival k is task k mod m
+    const uint64_t m = (cfg->task_set && cfg->task_set < n) ? cfg->task_set : n;
+    if (m < n && results_out) return GC_ERR_ARG;
+    auto task_of = [m](uint64_t k) { return k % m; };
 
     uint64_t max_size = cfg->max_size;
     if (!max_size) GC_TRY(gc_max_combine_size(p, &max_size));
@@ -70,8 +74,8 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     GC_TRY(gc_combiner_create(cfg->policy, max_size, cfg->static_n, cfg->window, &comb));
 
     // result rows of each task (targets, plus sources of LJ pair tasks)
-    std::vector<uint64_t> row_off(n + 1, 0);
-    for (uint64_t t = 0; t < n; ++t) {
+    std::vector<uint64_t> row_off(m + 1, 0);
+    for (uint64_t t = 0; t < m; ++t) {
         const uint64_t nt = tgt_off[t + 1] - tgt_off[t], ns = src_off[t + 1] - src_off[t];
         row_off[t + 1] = row_off[t] + nt + (kinds[t] == GC_LJ_PAIR ? ns : 0);
     }
@@ -92,15 +96,17 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
         else
             cudaGetLastError();   // stays pageable: slower copies, same results
     };
-    pin(tgt_ids, tgt_off[n] * sizeof(uint32_t));
-    pin(src_ids, src_off[n] * sizeof(uint32_t));
+    pin(tgt_ids, tgt_off[m] * sizeof(uint32_t));
+    pin(src_ids, src_off[m] * sizeof(uint32_t));
     const uint64_t budget = p->cfg.staging_budget_bytes;
-    std::vector<uint64_t> lat(n, 0);
+    const uint64_t none = ~0ull;
+    std::vector<uint64_t> lat(n, none);
     std::vector<uint64_t> to, so;
     std::deque<InFlight> inflight;
     uint64_t next = 0, head = 0, done = 0;   // arrivals [0,next) queued from `head`
     uint64_t batches = 0, taken_total = 0, busy_ns = 0, last_iter = 0;
     const uint64_t limit = cfg->timeout_ns ? cfg->timeout_ns : 60000000000ull;
+    const uint64_t last_arrival = arrival_ns[n - 1];
     gc_stats_t s0;
     int rc = gc_stats(p, &s0);
     const uint64_t start = now_ns();
@@ -134,9 +140,12 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
             inflight.pop_front();
         }
         if (rc != GC_OK) break;
+        // past the drain limit: start nothing more, finish what runs
+        const bool closed = cfg->drain_ns && next == n && now > last_arrival + cfg->drain_ns;
+        if (closed && inflight.empty()) break;
         const uint64_t queued = next - head;
         bool acted = false;
-        if (queued && inflight.size() < cfg->max_in_flight) {
+        if (!closed && queued && inflight.size() < cfg->max_in_flight) {
             uint64_t take = 0;
             gc_combiner_poll(comb, now, queued, &take);
             // the static rule fires only on arrivals: drain what is left once
@@ -147,32 +156,39 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
                 // admission by staging memory: the oldest requests that fit
                 uint64_t t1 = head, bytes = 0;
                 while (t1 < head + take) {
-                    const uint64_t b = ((tgt_off[t1 + 1] - tgt_off[t1]) +
-                                        (src_off[t1 + 1] - src_off[t1])) * sizeof(float4);
+                    const uint64_t q = task_of(t1);
+                    const uint64_t b = ((tgt_off[q + 1] - tgt_off[q]) +
+                                        (src_off[q + 1] - src_off[q])) * sizeof(float4);
                     if (budget && bytes + b > budget && t1 > head) break;
                     bytes += b;
                     ++t1;
                 }
-                const uint64_t m = t1 - head;
-                to.assign(m + 1, 0);
-                so.assign(m + 1, 0);
-                for (uint64_t k = 0; k <= m; ++k) {
-                    to[k] = tgt_off[head + k] - tgt_off[head];
-                    so[k] = src_off[head + k] - src_off[head];
-                }
+                // arrivals head .. t1-1: contiguous runs of the task arrays
                 uint64_t b_idx = 0;
-                rc = gc_submit_csr(p, m, nullptr, kinds + head, shifts ? shifts + 3 * head : nullptr,
-                                   to.data(), tgt_ids + tgt_off[head], so.data(),
-                                   src_ids + src_off[head], 0, 0, 0, &b_idx);
+                for (uint64_t k = head; k < t1 && rc == GC_OK;) {
+                    const uint64_t q0 = task_of(k);
+                    const uint64_t len = std::min(t1 - k, m - q0);
+                    to.assign(len + 1, 0);
+                    so.assign(len + 1, 0);
+                    for (uint64_t j = 0; j <= len; ++j) {
+                        to[j] = tgt_off[q0 + j] - tgt_off[q0];
+                        so[j] = src_off[q0 + j] - src_off[q0];
+                    }
+                    rc = gc_submit_csr(p, len, nullptr, kinds + q0,
+                                       shifts ? shifts + 3 * q0 : nullptr, to.data(),
+                                       tgt_ids + tgt_off[q0], so.data(), src_ids + src_off[q0],
+                                       0, 0, 0, &b_idx);
+                    k += len;
+                }
                 if (rc == GC_OK) rc = gc_flush(p);
                 if (rc != GC_OK) break;
                 inflight.push_back(InFlight{b_idx, head, t1, now_ns() - start});
+                taken_total += t1 - head;
                 head = t1;
                 ++batches;
-                taken_total += m;
                 acted = true;
             }
-        } else if (queued) {
+        } else if (queued && !closed) {
             busy_ns += now - last_iter;   // requests ready, no free flush context
         }
         last_iter = now;
@@ -195,17 +211,26 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     if (rc != GC_OK) return rc;
     gc_stats_t s1;
     GC_TRY(gc_stats(p, &s1));
+    // latency statistics over the served arrivals after the warm-up
+    std::vector<uint64_t> meas;
+    meas.reserve(n);
+    for (uint64_t k = 0; k < n; ++k)
+        if (lat[k] != none && arrival_ns[k] >= cfg->warmup_ns) meas.push_back(lat[k]);
     report->tasks = n;
     report->batches = batches;
     report->interactions = s1.interactions - s0.interactions;
     report->wall_s = (double)wall * 1e-9;
     report->interactions_per_s = (double)report->interactions / report->wall_s;
-    report->lat_p50_us = percentile(lat, 0.50) * 1e-3;
-    report->lat_p99_us = percentile(lat, 0.99) * 1e-3;
-    report->lat_max_us = (double)*std::max_element(lat.begin(), lat.end()) * 1e-3;
-    double sum = 0;
-    for (uint64_t v : lat) sum += (double)v;
-    report->lat_mean_us = sum / (double)n * 1e-3;
+    report->measured = meas.size();
+    report->unserved = n - done;
+    if (!meas.empty()) {
+        report->lat_p50_us = percentile(meas, 0.50) * 1e-3;
+        report->lat_p99_us = percentile(meas, 0.99) * 1e-3;
+        report->lat_max_us = (double)*std::max_element(meas.begin(), meas.end()) * 1e-3;
+        double sum = 0;
+        for (uint64_t v : meas) sum += (double)v;
+        report->lat_mean_us = sum / (double)meas.size() * 1e-3;
+    }
     report->mean_batch = batches ? (double)taken_total / (double)batches : 0.0;
     report->busy_s = (double)busy_ns * 1e-9;
     report->max_size = max_size;

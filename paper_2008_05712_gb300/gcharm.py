@@ -75,17 +75,20 @@ class GcStats(C.Structure):
 class GcServeConfig(C.Structure):
     _fields_ = [("policy", C.c_int), ("max_size", C.c_uint64), ("static_n", C.c_uint64),
                 ("window", C.c_uint64), ("max_in_flight", C.c_uint32),
-                ("poll_ns", C.c_uint64), ("timeout_ns", C.c_uint64)]
+                ("poll_ns", C.c_uint64), ("timeout_ns", C.c_uint64),
+                ("task_set", C.c_uint64), ("warmup_ns", C.c_uint64), ("drain_ns", C.c_uint64)]
 
 
 _SERVE_FIELDS = ["tasks", "batches", "interactions", "max_size"]
 _SERVE_DFIELDS = ["wall_s", "interactions_per_s", "lat_mean_us", "lat_p50_us", "lat_p99_us",
                   "lat_max_us", "mean_batch", "busy_s"]
+_SERVE_TAIL = ["measured", "unserved"]
 
 
 class GcServeReport(C.Structure):
     _fields_ = ([(f, C.c_uint64) for f in _SERVE_FIELDS]
-                + [(f, C.c_double) for f in _SERVE_DFIELDS])
+                + [(f, C.c_double) for f in _SERVE_DFIELDS]
+                + [(f, C.c_uint64) for f in _SERVE_TAIL])
 
 
 class GcTuning(C.Structure):
@@ -349,11 +352,13 @@ class Pool:
 
     def serve(self, arrival_ns, kinds, tgt_off, tgt_ids, src_off, src_ids, shifts=None,
               policy=GC_COMBINE_GREEDY, max_size=0, static_n=100, window=1024,
-              max_in_flight=2, poll_ns=50_000, timeout_ns=0, want_results=False):
+              max_in_flight=2, poll_ns=50_000, timeout_ns=0, want_results=False,
+              task_set=0, warmup_ns=0, drain_ns=0):
         """Replay an arrival schedule through the serving loop (gc_serve).
 
         Returns (report dict, latency_ns array, rows or None); rows are the
-        result rows of every task in task order, (n_rows, 8) float32."""
+        result rows of every task in task order, (n_rows, 8) float32.  With
+        task_set = m > 0 the CSR arrays hold m tasks, replayed cyclically."""
         arr = np.ascontiguousarray(arrival_ns, np.uint64)
         kinds = np.ascontiguousarray(kinds, np.uint32)
         to = np.ascontiguousarray(tgt_off, np.uint64)
@@ -363,7 +368,8 @@ class Pool:
         sh = None if shifts is None else np.ascontiguousarray(shifts, np.int8)
         n = arr.shape[0]
         cfg = GcServeConfig(policy=policy, max_size=max_size, static_n=static_n, window=window,
-                            max_in_flight=max_in_flight, poll_ns=poll_ns, timeout_ns=timeout_ns)
+                            max_in_flight=max_in_flight, poll_ns=poll_ns, timeout_ns=timeout_ns,
+                            task_set=task_set, warmup_ns=warmup_ns, drain_ns=drain_ns)
         lat = np.zeros(n, np.uint64)
         rows = None
         if want_results:
@@ -373,7 +379,7 @@ class Pool:
         _check(self.lib.gc_serve(self.h, n, _p(arr), _p(kinds), _p(sh), _p(to), _p(tg), _p(so),
                                  _p(sr), C.byref(cfg), _p(lat), _p(rows), C.byref(rep)),
                "gc_serve")
-        d = {f: getattr(rep, f) for f in _SERVE_FIELDS + _SERVE_DFIELDS}
+        d = {f: getattr(rep, f) for f in _SERVE_FIELDS + _SERVE_DFIELDS + _SERVE_TAIL}
         return d, lat, rows
 
     def read_results(self, task_ids, n_rows):

@@ -91,13 +91,28 @@ def test_per_task_and_bad_arguments():
             g.Combiner(*args)
 
 
-def test_greedy_takes_everything_up_to_max_size():
+def test_greedy_takes_everything_pending():
     c = g.Combiner(g.GC_COMBINE_GREEDY, max_size=5)
     assert c.poll(0, 0) == 0
     assert c.poll(0, 3) == 3              # no waiting: all pending
-    assert c.poll(0, 12) == 5             # capped at maxSize
-    with pytest.raises(g.GcError):
-        g.Combiner(g.GC_COMBINE_GREEDY, max_size=0)
+    assert c.poll(0, 12) == 12            # not capped: batches grow with the queue
+    assert g.Combiner(g.GC_COMBINE_GREEDY, max_size=0).poll(0, 7) == 7
+
+
+def test_windowed_max_is_the_max_of_the_last_gaps():
+    """The windowed rule's maxInterval equals the largest of the last
+    `window` arrival gaps (checked against a direct maximum on a random
+    arrival stream)."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    t = np.cumsum(rng.integers(1, 1000, 3000)).astype(np.uint64)
+    for window in (1, 3, 64):
+        c = g.Combiner(g.GC_COMBINE_ADAPTIVE_WINDOW, max_size=10, window=window)
+        for k, tk in enumerate(t):
+            c.arrive(int(tk))
+            if k >= 1:
+                gaps = np.diff(t[:k + 1].astype(np.int64))
+                assert c.max_interval() == int(gaps[-window:].max()), (window, k)
 
 
 def test_adaptive_rule_under_poisson_arrivals_waits_for_max_size():

@@ -147,3 +147,39 @@ def test_serve_rejects(gc):
     rep, lat, _ = pool.serve(np.zeros(0, np.uint64), kinds[:0], to[:1], tg[:0], so[:1], sr[:0])
     assert rep["tasks"] == 0 and lat.shape[0] == 0
     pool.close()
+
+
+def test_serve_cycled_task_set_warmup_and_drain(gc):
+    """A task set replayed cyclically (arrival k runs task k mod m), the
+    warm-up arrivals left out of the latency statistics, and an overloaded
+    run (one task per batch at 1e6 tasks/s) cut off by the drain limit with
+    the rest reported unserved."""
+    x, to, tg, so, sr = workload(n_tasks=200)
+    n_ids = x.shape[0]
+    pool = make_pool(gc, torch, n_ids, n_ids)
+    pool.upload(np.arange(n_ids, dtype=np.uint32), x)
+    m, n = 200, 1000
+    kinds = np.zeros(m, np.uint32)
+    nt = (to[1:] - to[:-1]).astype(np.int64)
+    ns = (so[1:] - so[:-1]).astype(np.int64)
+    arr = inputs.poisson_arrivals(n, 5e4, 9)
+    warm = int(arr[199])
+    rep, lat, _ = pool.serve(arr, kinds, to, tg, so, sr, policy=gc.GC_COMBINE_GREEDY,
+                             task_set=m, warmup_ns=warm)
+    k = np.arange(n) % m
+    assert rep["interactions"] == int((nt[k] * ns[k]).sum())
+    assert rep["unserved"] == 0
+    assert rep["measured"] == int((arr >= warm).sum())
+    assert (lat != np.iinfo(np.uint64).max).all()
+    # results of a cycled set are refused (rows would repeat)
+    with pytest.raises(gc.GcError):
+        pool.serve(arr, kinds, to, tg, so, sr, task_set=m, want_results=True)
+    # overload: the queue left after the schedule is not drained past the limit
+    arr2 = inputs.poisson_arrivals(20000, 1e6, 10)          # about 20 ms of arrivals
+    rep2, lat2, _ = pool.serve(arr2, kinds, to, tg, so, sr, policy=gc.GC_COMBINE_PER_TASK,
+                               task_set=m, drain_ns=50_000_000)
+    served = lat2 != np.iinfo(np.uint64).max
+    assert rep2["unserved"] > 0 and int((~served).sum()) == rep2["unserved"]
+    assert rep2["wall_s"] < 2.0
+    assert rep2["measured"] == int(served.sum()) and rep2["batches"] == int(served.sum())
+    pool.close()
