@@ -811,6 +811,7 @@ def main():
     if ws > 1:
         dist.barrier()
     s0 = pool.stats()
+    nb0 = pool.nbody_stats()
     clocks = ClockSampler(local)
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -827,6 +828,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     s1 = pool.stats()
+    nb1 = pool.nbody_stats()
     interactions = s1["interactions"] - s0["interactions"]
     launches = s1["kernel_launches"] - s0["kernel_launches"]
     prims = s1["primitive_calls"] - s0["primitive_calls"]
@@ -941,6 +943,35 @@ def main():
             "speedup_flush": tp["total"] / tb["total"],
         }
 
+    # tree stage: the timed steps (Morton order seeded by the previous
+    # step's), then the same drift steps with every build sorted from
+    # scratch and seeded again, each measured step preceded by its
+    # predecessor so that the seeded build starts from a one-step-old order
+    nbt = max(nb1["timed_builds"] - nb0["timed_builds"], 1)
+    tree = {"timed_steps": {
+        "order": "seeded",
+        "order_ms": (nb1["order_ms_sum"] - nb0["order_ms_sum"]) / nbt,
+        "tree_ms": (nb1["tree_ms_sum"] - nb0["tree_ms_sum"]) / nbt,
+        "seeded_builds": nb1["seeded_builds"] - nb0["seeded_builds"], "builds": nbt}}
+    J = min(K, 8)
+    for mode, name in ((gcharm.GC_ORDER_FULL, "full"), (gcharm.GC_ORDER_SEEDED, "seeded")):
+        pool.set_order(mode)
+        om, tm, rs = [], [], []
+        for k in range(W, W + J):
+            step(k - 1)
+            step(k)
+            st = pool.nbody_stats()
+            om.append(st["last_order_ms"])
+            tm.append(st["last_tree_ms"])
+            rs.append(st["last_resorted"] / n)
+        tree[name] = {"order_ms": float(np.median(om)), "tree_ms": float(np.median(tm)),
+                      "resorted_frac": float(np.median(rs)), "steps": J}
+    pool.set_order(gcharm.GC_ORDER_SEEDED)
+    tree["note"] = ("order_ms: bounding box to sorted Morton order; tree_ms: the whole build "
+                    "(order, nodes, monopoles, buckets, list walk, tasks), CUDA events on the "
+                    "build stream including the build's own host read-backs; medians over "
+                    f"{J} drift steps")
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         keep = {}
@@ -1004,6 +1035,7 @@ def main():
             "roofline": dominant,
             "rooflines": {"interaction": grav, "pack": pack, "scatter": scatter},
             "stage_ms_avg": stage,
+            "tree": tree,
             "tuning": {"wu_max_targets": tuning["wu_max_targets"],
                        "schedule": "lpt" if tuning["schedule"] else "fifo",
                        "autotune_ms": tune_ms or tuning.get("times_ms"),

@@ -317,11 +317,47 @@ int gc_read_evicted(gc_pool_t *pool, uint32_t *ids, uint64_t cap, uint64_t *n_ou
  * opened leaves contribute their particles.  theta_num, theta_den in
  * [0, 255], theta_den >= 1.  Requires id_capacity >= n + node count.
  * task_id of bucket b = task_id_base + b.  info_out (may be NULL) receives
- * {n_nodes, n_buckets, list entries, max list length}.  Errors: GC_ERR_ARG,
- * GC_ERR_POOL_FULL (ids would exceed id_capacity), GC_ERR_OOM. */
+ * {n_nodes, n_buckets, list entries, particles sorted afresh}: n after a
+ * full sort, the movers after a seeded one (gc_nbody_set_order).  Errors:
+ * GC_ERR_ARG, GC_ERR_POOL_FULL (ids would exceed id_capacity), GC_ERR_OOM.
+ *
+ * Morton order.  The tree is rebuilt at every step of an integration
+ * (Section 4.1), and a step moves the particles little.  When the previous
+ * build on this pool had the same n, the build (GC_ORDER_SEEDED, the
+ * default) computes the new keys in the previous sorted order, keeps a
+ * sorted subsequence of it in place, sorts only the other particles (the
+ * movers, gathered in id order) and merges the two.  The order, and so
+ * every output, is the same as the full stable sort's, for any positions;
+ * only the cost depends on how far the particles moved. */
 int gc_build_nbody_tasks(gc_pool_t *pool, const float *xyzm_dev, uint64_t n,
                          int bucket_max, int theta_num, int theta_den,
                          uint64_t task_id_base, uint64_t info_out[4]);
+
+/* Morton order of the next N-body builds: GC_ORDER_FULL sorts every build's
+ * keys from scratch; GC_ORDER_SEEDED (default) starts from the previous
+ * build's order when it had the same n.  Both give identical trees.
+ * Errors: GC_ERR_ARG (unknown mode). */
+#define GC_ORDER_FULL 0
+#define GC_ORDER_SEEDED 1
+int gc_nbody_set_order(gc_pool_t *pool, int mode);
+
+/* N-body build statistics.  Times are CUDA-event intervals on the pool's
+ * stream and include the host's waits inside a build (the node, bucket and
+ * list counts are read back mid-build). */
+typedef struct {
+    uint64_t builds;          /* N-body builds completed                    */
+    uint64_t seeded_builds;   /* of which started from the previous order   */
+    uint64_t last_resorted;   /* particles the last build sorted afresh     */
+    uint64_t timed_builds;    /* builds counted in the time sums            */
+    double last_order_ms;     /* last build: bounding box to sorted order   */
+    double last_tree_ms;      /* last build: whole build, tasks appended    */
+    double order_ms_sum;      /* sums over timed builds                     */
+    double tree_ms_sum;
+} gc_nbody_stats_t;
+
+/* Statistics of this pool's N-body builds (waits for the last build's end
+ * event).  Errors: GC_ERR_ARG, GC_ERR_CUDA. */
+int gc_nbody_stats(gc_pool_t *pool, gc_nbody_stats_t *out);
 
 /* As gc_build_nbody_tasks, with the positions of particles 0..n-1 taken
  * from the pool itself: the values most recently uploaded for ids 0..n-1

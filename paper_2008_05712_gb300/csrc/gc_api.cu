@@ -152,11 +152,14 @@ static void free_pool(gc_pool *p)
                     &p->nb.win, &p->nb.dmax, &p->nb.nnode, &p->nb.node_off, &p->nb.node_a,
                     &p->nb.node_b, &p->nb.node_val, &p->nb.bucket, &p->nb.bbox,
                     &p->nb.list_off, &p->nb.list_len, &p->nb.list, &p->nb.bounds,
-                    &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->nb.wnode, &p->md.hostcopy,
+                    &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->nb.wnode, &p->nb.seed_tiles,
+                    &p->nb.seed_a, &p->nb.seed_m, &p->nb.seed_key, &p->md.hostcopy,
                     &p->md.keys,
                     &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
                     &p->md.cnt_s, &p->md.cub_tmp};
     for (DBuf *b : bufs) b->release();
+    for (cudaEvent_t &e : p->nb.ev)
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < 2; ++i) free_ctx(p->ctx[i]);
     delete p;
 }

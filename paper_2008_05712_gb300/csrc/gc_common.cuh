@@ -92,6 +92,17 @@ struct NBodyState {
     DBuf node_a, node_b, node_val, bucket, bbox, list_off, list_len, list, wnode;
     uint64_t n_walk_items = 0;       // (bucket, walk range) pairs of the last build
     DBuf bounds, cub_tmp, mono, hostcopy;
+    // Morton order: seeded from the previous build's order (ids2) when it
+    // holds a permutation of the same n particles
+    int order_mode = 1;              // GC_ORDER_SEEDED
+    uint64_t order_n = 0;            // particles of the permutation in ids2 (0: none)
+    DBuf seed_tiles, seed_a, seed_m, seed_key;
+    // build timing: events {start, order done, end}, folded into the sums
+    // once the end event has completed
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool ev_pending = false, pending_seeded = false;
+    uint64_t builds = 0, seeded_builds = 0, timed_builds = 0, last_resorted = 0;
+    double last_order_ms = 0, last_tree_ms = 0, order_ms_sum = 0, tree_ms_sum = 0;
 };
 
 struct MDState {

@@ -37,7 +37,11 @@ namespace {
 
 struct GridParams {
     double lo[3];
-    double scale;   // 2^21 / L, L = smallest power of two >= largest extent
+    double scale;   // 2^21 / L = 2^sh, L = smallest power of two >= largest extent
+    float lof[3];   // lo as float (the minima are float values)
+    float scalef;   // 2^sh
+    float tiny;     // 2^-(sh+6): smallest nonzero |coordinate| of the FP32 path
+    int fast;       // the FP32 path applies (sh in [-100, 100])
 };
 
 __device__ __forceinline__ uint32_t ord_key(float f)
@@ -102,6 +106,11 @@ __global__ void k_grid_params(const uint32_t *bounds, GridParams *gp)
         while (L * 0.5 >= ext) L *= 0.5;
     }
     gp->scale = 2097152.0 / L;
+    const int sh = ilogb(gp->scale);
+    for (int a = 0; a < 3; ++a) gp->lof[a] = (float)gp->lo[a];
+    gp->fast = sh >= -100 && sh <= 100;
+    gp->scalef = gp->fast ? ldexpf(1.0f, sh) : 0.0f;
+    gp->tiny = gp->fast ? ldexpf(1.0f, -(sh + 6)) : 0.0f;
 }
 
 __device__ __forceinline__ uint32_t quant(float x, double lo, double scale)
@@ -111,6 +120,35 @@ __device__ __forceinline__ uint32_t quant(float x, double lo, double scale)
     f = fmax(f, 0.0);
     f = fmin(f, 2097151.0);
     return (uint32_t)f;
+}
+
+// quant() in FP32, exact.  With x, lo floats, d = x - lo >= 0 and
+// d <= L = 2^(21-sh), the FP64 subtraction rounds d only below
+// 2^-(sh+31) (half an FP64 ulp of a number below 2^(22-sh)).  If x and lo
+// are each zero or at least 2^-(sh+6) in magnitude, both are multiples of
+// 2^-(sh+29) (23 fraction bits below their exponent), so d is at least
+// 2^-(sh+29) away from any multiple of 2^-sh it does not equal, and the FP64
+// rounding cannot carry it across one: floor(RN64(d) 2^sh) = floor(d 2^sh).
+// Knuth's TwoSum gives d = s + e exactly in FP32 (s = RN32(x - lo),
+// |e| <= half an ulp of s); scaled by 2^sh (exact), floor(S + E) is floor(S)
+// unless S is an integer and E < 0.  Other inputs take the FP64 expression.
+__device__ __forceinline__ uint32_t quant_exact(float x, int a, const GridParams &g)
+{
+    const float lo = g.lof[a];
+    const float ax = fabsf(x), al = fabsf(lo);
+    if (g.fast && (x == 0.f || ax >= g.tiny) && (lo == 0.f || al >= g.tiny) && ax < 1e37f &&
+        al < 1e37f) {
+        const float s = __fsub_rn(x, lo);
+        const float bp = __fsub_rn(s, x);       // TwoSum of x and -lo
+        const float ap = __fsub_rn(s, bp);
+        const float e = __fadd_rn(__fsub_rn(x, ap), __fsub_rn(-lo, bp));
+        const float S = __fmul_rn(s, g.scalef), E = __fmul_rn(e, g.scalef);
+        float f = floorf(S);
+        if (f == S && E < 0.f) f -= 1.f;
+        f = fminf(fmaxf(f, 0.f), 2097151.f);
+        return (uint32_t)f;
+    }
+    return quant(x, g.lo[a], g.scale);
 }
 
 // spread the 21 low bits of v to every third bit
@@ -136,17 +174,443 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x)
     return (uint32_t)x;
 }
 
+__device__ __forceinline__ uint64_t morton_of(float4 v, const GridParams &g)
+{
+    return spread3(quant_exact(v.x, 0, g)) | (spread3(quant_exact(v.y, 1, g)) << 1) |
+           (spread3(quant_exact(v.z, 2, g)) << 2);
+}
+
 __global__ void k_keys(const float4 *x, uint64_t n, const GridParams *gp, uint64_t *keys,
                        uint32_t *ids)
 {
     const GridParams g = *gp;
     GRID_STRIDE(i, n) {
-        float4 v = x[i];
-        uint32_t qx = quant(v.x, g.lo[0], g.scale);
-        uint32_t qy = quant(v.y, g.lo[1], g.scale);
-        uint32_t qz = quant(v.z, g.lo[2], g.scale);
-        keys[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+        keys[i] = morton_of(x[i], g);
         ids[i] = (uint32_t)i;
+    }
+}
+
+// ---- Morton order seeded by the previous build's order -------------------
+//
+// The tree is rebuilt at every step (Section 4.1), and between two steps the
+// particles move little, so the previous step's sorted order is close to the
+// new one.  The seeded order computes the new keys in the previous order and
+// keeps most of it in place; the order compared is (key, id), the order of
+// the stable key sort.
+//   1. Tiles of SEED_TILE consecutive particles (previous order): one or
+//      both particles of every descent are dropped, round after round, until
+//      the tile's remainder rem_t is ascending.  The part of rem_t above U_t,
+//      the median of the first 32 keys of tile t+1, is dropped too; b_t
+//      elements stay (k_seed_tiles).
+//   2. P_t = the largest of the last remaining elements rem_u[b_u - 1] of the
+//      tiles u < t (k_seed_scan); tile t drops its elements below P_t, a_t of
+//      them (k_seed_low).  A kept element of tile t is then at most
+//      rem_t[b_t - 1] <= P_u < every kept element of a later tile u: the kept
+//      elements, in slot order (slot = tile * SEED_TILE + index), ascend.
+//      The inclusive maximum P'_t is the largest kept element of tiles <= t.
+//   3. Every dropped particle ("mover") x finds the slot of the smallest kept
+//      element above it (k_mover_slot: the first tile with P'_t > x, then
+//      within that tile), or the end slot n.  W[q] counts the kept element of
+//      slot q plus the movers assigned to it; with E the exclusive prefix sum
+//      of W, the kept element of slot q lands at E[q] + W[q] - 1 and the
+//      movers of slot q at E[q] + their rank by (key, id) among themselves
+//      (k_mover_scatter, k_seed_place).
+// The result is the stable key sort, element for element.  Which particles
+// are dropped decides only the cost; if some slot collects more than
+// SEED_GROUP_MAX movers the build sorts all keys instead.
+constexpr int SEED_TILE = 2048, SEED_THREADS = 512, SEED_PER = SEED_TILE / SEED_THREADS;
+constexpr int SEED_ROUNDS = 64;       // descent-removal rounds before a tile gives up
+constexpr int SEED_GROUP_MAX = 64;    // movers per slot ranked pairwise
+
+struct KidMax {
+    uint64_t k;
+    uint32_t i, h;   // h = 0: no element (below everything)
+};
+
+struct SeedTile {
+    KidMax last;     // rem[b - 1]
+    KidMax pe, pi;   // largest kept element of the tiles before / up to this one
+    uint32_t b, a;   // remainder [0, b) after step 1; kept range [a, b)
+};
+
+struct SeedCtr {
+    unsigned long long movers;
+    unsigned int max_group;
+    unsigned int pad;
+};
+
+__device__ __forceinline__ bool kid_gt(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib)
+{
+    return ka > kb || (ka == kb && ia > ib);
+}
+
+__device__ __forceinline__ KidMax kid_max(KidMax a, KidMax b)
+{
+    if (!a.h) return b;
+    if (!b.h) return a;
+    return kid_gt(a.k, a.i, b.k, b.i) ? a : b;
+}
+
+// (k, i) is above m (every (k, i) is above "no element")
+__device__ __forceinline__ bool above(uint64_t k, uint32_t i, const KidMax &m)
+{
+    return !m.h || kid_gt(k, i, m.k, m.i);
+}
+
+__device__ __forceinline__ KidMax shfl_up_kid(KidMax v, int o)
+{
+    KidMax r;
+    r.k = __shfl_up_sync(0xffffffffu, v.k, o);
+    r.i = __shfl_up_sync(0xffffffffu, v.i, o);
+    r.h = __shfl_up_sync(0xffffffffu, v.h, o);
+    return r;
+}
+
+// Append c movers per lane (the whole warp calls): returns this lane's
+// first index in the mover list.
+__device__ __forceinline__ unsigned long long mover_base(int c, SeedCtr *ctr)
+{
+    const int lane = threadIdx.x & 31;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(&ctr->movers, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (unsigned long long)(incl - c);
+}
+
+// One block per tile; thread t owns remainder positions 4t .. 4t+3.  Each
+// round every descent (p-1, p) is resolved from the four elements around
+// it: drop p-1 alone if p-2 (if any) does not exceed p (p-1 is a spike),
+// else drop p alone if p-1 does not exceed p+1 (if any; p is a dip), else
+// drop both.  A round with a descent drops at least one particle, so the
+// loop ends; after SEED_ROUNDS rounds a tile still out of order drops its
+// whole remainder.
+__global__ __launch_bounds__(SEED_THREADS) void k_seed_tiles(
+    const float4 *x, const uint32_t *prev, uint64_t n, const GridParams *gp, uint64_t *KT,
+    uint32_t *IT, uint32_t *W, SeedTile *tiles, SeedCtr *ctr, uint64_t *MK, uint32_t *MI,
+    uint32_t *MH)
+{
+    __shared__ uint64_t sk[SEED_TILE];
+    __shared__ uint32_t si[SEED_TILE];
+    __shared__ int wsum[SEED_THREADS / 32];
+    __shared__ int s_total, s_b;
+    __shared__ KidMax s_u;
+    const uint64_t t0 = (uint64_t)blockIdx.x * SEED_TILE;
+    const int size = (int)(n - t0 < (uint64_t)SEED_TILE ? n - t0 : (uint64_t)SEED_TILE);
+    int cnt = size;
+    const GridParams g = *gp;
+    const uint32_t tile = blockIdx.x;
+    for (int j = threadIdx.x; j < cnt; j += SEED_THREADS) {
+        const uint32_t id = prev[t0 + j];
+        sk[j] = morton_of(x[id], g);
+        si[j] = id;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {   // U: median of the first 32 keys of the next tile
+        const uint64_t t1 = t0 + SEED_TILE;
+        const int m = t1 < n ? (n - t1 < 32 ? (int)(n - t1) : 32) : 0;
+        KidMax v{0, 0, 0};
+        if (lane < m) {
+            const uint32_t id = prev[t1 + lane];
+            v.k = morton_of(x[id], g);
+            v.i = id;
+            v.h = 1;
+        }
+        int below = 0;   // elements of the sample below this lane's
+        for (int q = 0; q < m; ++q) {
+            const uint64_t k = __shfl_sync(0xffffffffu, v.k, q);
+            const uint32_t i = __shfl_sync(0xffffffffu, v.i, q);
+            below += (v.h && kid_gt(v.k, v.i, k, i)) ? 1 : 0;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, v.h && below == m / 2);
+        if (lane == 0) s_u = KidMax{0, 0, 0};
+        __syncwarp();
+        if (hit && lane == __ffs(hit) - 1) s_u = v;
+    }
+    __syncthreads();
+    const int base = threadIdx.x * SEED_PER;
+    constexpr int WIN = SEED_PER + 4;     // positions base-2 .. base+SEED_PER+1
+    for (int round = 0;; ++round) {
+        uint64_t k[WIN];
+        uint32_t id[WIN];
+#pragma unroll
+        for (int q = 0; q < WIN; ++q) {
+            const int pos = base - 2 + q;
+            const bool in = pos >= 0 && pos < cnt;
+            k[q] = in ? sk[pos] : 0;
+            id[q] = in ? si[pos] : 0;
+        }
+        // descents at p = base .. base+SEED_PER; drop-left / drop-right
+        bool dl[SEED_PER + 1], dr[SEED_PER + 1];
+        bool any = false;
+#pragma unroll
+        for (int e = 0; e <= SEED_PER; ++e) {
+            const int p = base + e, q = e + 2;
+            const bool d = p >= 1 && p < cnt && kid_gt(k[q - 1], id[q - 1], k[q], id[q]);
+            const bool spike = p == 1 || !kid_gt(k[q - 2], id[q - 2], k[q], id[q]);
+            const bool dip = p + 1 >= cnt || !kid_gt(k[q - 1], id[q - 1], k[q + 1], id[q + 1]);
+            dl[e] = d && (spike || !dip);
+            dr[e] = d && !spike;
+            if (e < SEED_PER) any |= d;
+        }
+        if (!__syncthreads_or(any)) break;
+        const bool give_up = round >= SEED_ROUNDS;
+        int c = 0, cd = 0;
+#pragma unroll
+        for (int e = 0; e < SEED_PER; ++e) {
+            if (base + e >= cnt) break;
+            if (!give_up && !dr[e] && !dl[e + 1]) ++c;
+            else ++cd;
+        }
+        unsigned long long mb = mover_base(cd, ctr);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int v = lane < SEED_THREADS / 32 ? wsum[lane] : 0;
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            if (lane < SEED_THREADS / 32) wsum[lane] = inc - v;
+            if (lane == SEED_THREADS / 32 - 1) s_total = inc;
+        }
+        __syncthreads();
+        int dst = wsum[w] + incl - c;
+#pragma unroll
+        for (int e = 0; e < SEED_PER; ++e) {
+            if (base + e >= cnt) break;
+            if (!give_up && !dr[e] && !dl[e + 1]) {
+                sk[dst] = k[e + 2];
+                si[dst] = id[e + 2];
+                ++dst;
+            } else {
+                MK[mb] = k[e + 2];
+                MI[mb] = id[e + 2];
+                MH[mb] = tile;
+                ++mb;
+            }
+        }
+        cnt = s_total;
+        __syncthreads();
+    }
+    // b = elements not above U (the remainder ascends: one boundary)
+    if (threadIdx.x == 0) s_b = (cnt && above(sk[0], si[0], s_u) && s_u.h) ? 0 : cnt;
+    __syncthreads();
+    if (s_u.h) {
+        for (int j = threadIdx.x; j < cnt; j += SEED_THREADS)
+            if (!kid_gt(sk[j], si[j], s_u.k, s_u.i) &&
+                (j + 1 == cnt || kid_gt(sk[j + 1], si[j + 1], s_u.k, s_u.i)))
+                s_b = j + 1;
+    }
+    __syncthreads();
+    const int b = s_b;
+    // drop [b, cnt); slots [0, b) hold the remainder
+#pragma unroll
+    for (int e = 0; e < SEED_PER; ++e) {
+        const int j = threadIdx.x + e * SEED_THREADS;
+        if (j < size) W[t0 + j] = j < b ? 1u : 0u;
+        if (j < b) {
+            KT[t0 + j] = sk[j];
+            IT[t0 + j] = si[j];
+        }
+    }
+    int cd = 0;
+#pragma unroll
+    for (int e = 0; e < SEED_PER; ++e) cd += (base + e >= b && base + e < cnt) ? 1 : 0;
+    unsigned long long mb = mover_base(cd, ctr);
+#pragma unroll
+    for (int e = 0; e < SEED_PER; ++e) {
+        const int j = base + e;
+        if (j >= b && j < cnt) {
+            MK[mb] = sk[j];
+            MI[mb] = si[j];
+            MH[mb] = tile;
+            ++mb;
+        }
+    }
+    if (threadIdx.x == 0) {
+        SeedTile T{};
+        T.b = (uint32_t)b;
+        if (b) T.last = KidMax{sk[b - 1], si[b - 1], 1};
+        tiles[tile] = T;
+    }
+}
+
+// One block of 1024 threads over all tiles, 1024 at a time: exclusive and
+// inclusive prefix maxima of the tiles' last remaining elements.
+__global__ __launch_bounds__(1024) void k_seed_scan(SeedTile *tiles, uint32_t nt)
+{
+    __shared__ KidMax wmax[32];
+    __shared__ KidMax carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry = KidMax{0, 0, 0};
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < nt; c0 += blockDim.x) {
+        const uint32_t t = c0 + threadIdx.x;
+        const KidMax last = t < nt ? tiles[t].last : KidMax{0, 0, 0};
+        KidMax inc = last;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const KidMax v = shfl_up_kid(inc, o);
+            if (lane >= o) inc = kid_max(inc, v);
+        }
+        KidMax exc = shfl_up_kid(inc, 1);
+        if (lane == 0) exc.h = 0;
+        if (lane == 31) wmax[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const KidMax v = lane < nw ? wmax[lane] : KidMax{0, 0, 0};
+            KidMax vi = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const KidMax u = shfl_up_kid(vi, o);
+                if (lane >= o) vi = kid_max(vi, u);
+            }
+            KidMax ve = shfl_up_kid(vi, 1);
+            if (lane == 0) ve.h = 0;
+            if (lane < nw) wmax[lane] = ve;
+        }
+        __syncthreads();
+        const KidMax pe = kid_max(carry, kid_max(wmax[w], exc));
+        const KidMax pi = kid_max(pe, last);
+        if (t < nt) {
+            tiles[t].pe = pe;
+            tiles[t].pi = pi;
+        }
+        __syncthreads();   // every thread has read the carry
+        if (threadIdx.x == blockDim.x - 1) carry = pi;
+        __syncthreads();
+    }
+}
+
+// One warp per tile: a = remainder elements below P (a prefix), dropped.
+__global__ __launch_bounds__(256) void k_seed_low(const uint64_t *KT, const uint32_t *IT,
+                                                  SeedTile *tiles, uint32_t nt, uint32_t *W,
+                                                  SeedCtr *ctr, uint64_t *MK, uint32_t *MI,
+                                                  uint32_t *MH)
+{
+    const uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= nt) return;   // whole warps leave together
+    const KidMax P = tiles[t].pe;
+    const uint32_t b = tiles[t].b;
+    const uint64_t t0 = (uint64_t)t * SEED_TILE;
+    uint32_t a = 0;
+    if (P.h) {
+        for (uint32_t j0 = 0; j0 < b; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const bool below = j < b && kid_gt(P.k, P.i, KT[t0 + j], IT[t0 + j]);
+            const unsigned bal = __ballot_sync(0xffffffffu, below);
+            unsigned long long mb = mover_base(below ? 1 : 0, ctr);
+            if (below) {
+                MK[mb] = KT[t0 + j];
+                MI[mb] = IT[t0 + j];
+                MH[mb] = t;
+                W[t0 + j] = 0;
+            }
+            a += __popc(bal);
+            if (bal != 0xffffffffu) break;
+        }
+    }
+    if (lane == 0) tiles[t].a = a;
+}
+
+// Slot of the smallest kept element above each mover, or n; the mover's
+// arrival index among the movers of that slot.
+__global__ __launch_bounds__(256) void k_mover_slot(
+    SeedCtr *ctr, const uint64_t *MK, const uint32_t *MI, const uint32_t *MH,
+    const uint64_t *KT, const uint32_t *IT, const SeedTile *tiles, uint32_t nt, uint64_t n,
+    uint32_t *W, uint32_t *MS, uint32_t *MA)
+{
+    const uint64_t m = ctr->movers;
+    GRID_STRIDE(v, m) {
+        const uint64_t k = MK[v];
+        const uint32_t i = MI[v], hint = MH[v];
+        // first tile u whose largest kept element so far is above (k, i)
+        uint32_t u;
+        if (!above(k, i, tiles[hint].pi) && (hint == 0 || above(k, i, tiles[hint - 1].pi))) {
+            u = hint;
+        } else {
+            uint32_t lo = 0, hi = nt;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (above(k, i, tiles[mid].pi)) lo = mid + 1;
+                else hi = mid;
+            }
+            u = lo;
+        }
+        uint64_t q = n;
+        if (u < nt) {   // within tile u: the remainder elements below (k, i)
+            const uint64_t t0 = (uint64_t)u * SEED_TILE;
+            uint32_t lo = 0, hi = tiles[u].b;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (kid_gt(k, i, KT[t0 + mid], IT[t0 + mid])) lo = mid + 1;
+                else hi = mid;
+            }
+            q = t0 + lo;
+        }
+        const uint32_t arr = atomicAdd(&W[q], 1u) - (q < n ? 1u : 0u);
+        MS[v] = (uint32_t)q;
+        MA[v] = arr;
+        atomicMax(&ctr->max_group, arr + 1);
+    }
+}
+
+// Movers to their slot's output range, in arrival order.
+__global__ void k_mover_scatter(const uint64_t *MK, const uint32_t *MI, const uint32_t *MS,
+                                const uint32_t *MA, uint64_t m, const uint32_t *E,
+                                uint64_t *TK, uint32_t *TI)
+{
+    GRID_STRIDE(v, m) {
+        const uint64_t pos = (uint64_t)E[MS[v]] + MA[v];
+        TK[pos] = MK[v];
+        TI[pos] = MI[v];
+    }
+}
+
+// Final order: kept elements of slots [0, n), then the m movers ranked by
+// (key, id) within their slot's range.
+__global__ void k_seed_place(const uint64_t *KT, const uint32_t *IT, const SeedTile *tiles,
+                             uint64_t n, const uint32_t *W, const uint32_t *E,
+                             const uint64_t *MK, const uint32_t *MI, const uint32_t *MS,
+                             uint64_t m, const uint64_t *TK, const uint32_t *TI, uint64_t *K,
+                             uint32_t *I)
+{
+    GRID_STRIDE(v, n + m) {
+        if (v < n) {
+            const uint32_t t = (uint32_t)(v / SEED_TILE), j = (uint32_t)(v % SEED_TILE);
+            const SeedTile &T = tiles[t];
+            if (j >= T.a && j < T.b) {
+                const uint64_t pos = (uint64_t)E[v] + W[v] - 1;
+                K[pos] = KT[v];
+                I[pos] = IT[v];
+            }
+        } else {
+            const uint64_t u = v - n;
+            const uint64_t k = MK[u];
+            const uint32_t i = MI[u], q = MS[u];
+            const uint32_t grp = W[q] - (q < n ? 1u : 0u);
+            const uint64_t g0 = E[q];
+            uint32_t r = 0;
+            for (uint32_t c = 0; c < grp; ++c) r += kid_gt(k, i, TK[g0 + c], TI[g0 + c]) ? 1 : 0;
+            K[g0 + r] = k;
+            I[g0 + r] = i;
+        }
     }
 }
 
@@ -603,6 +1067,83 @@ __global__ void k_values_of_ids(const uint32_t *slot_of_id, const float4 *pool,
     }
 }
 
+// Sorted keys and ids (keys2, ids2) of the n particles x, seeded by the
+// permutation ids2 holds from the previous build of the same n.  *done is
+// false (nothing written) when a slot collected more than SEED_GROUP_MAX
+// movers; *movers receives the number of particles placed afresh.
+int seeded_order(gc_pool *p, const float4 *x, uint64_t n, const GridParams *gp,
+                 uint64_t *movers, bool *done)
+{
+    NBodyState &S = p->nb;
+    cudaStream_t s = p->s;
+    const int maxb = p->num_sms * 16;
+    const uint64_t nt = (n + SEED_TILE - 1) / SEED_TILE;
+    *done = false;
+    GC_TRY(S.seed_tiles.reserve(nt * sizeof(SeedTile) + sizeof(SeedCtr) + 64));
+    GC_TRY(S.seed_a.reserve((n + 1) * 8 + 64));
+    GC_TRY(S.seed_m.reserve(n * 24 + 64));
+    GC_TRY(S.seed_key.reserve(n * 12 + 64));
+    SeedTile *tiles = S.seed_tiles.as<SeedTile>();
+    SeedCtr *ctr = reinterpret_cast<SeedCtr *>(tiles + nt);
+    uint64_t *KT = S.keys.as<uint64_t>();       // tile remainders, slot = tile * SEED_TILE + j
+    uint32_t *IT = S.ids.as<uint32_t>();
+    uint32_t *W = S.seed_a.as<uint32_t>(), *E = W + (n + 1);
+    uint64_t *MK = S.seed_m.as<uint64_t>();     // movers: key, id, tile, slot, arrival
+    uint32_t *MI = reinterpret_cast<uint32_t *>(MK + n);
+    uint32_t *MH = MI + n, *MS = MH + n, *MA = MS + n;
+    uint64_t *TK = S.seed_key.as<uint64_t>();   // movers in their slots' ranges
+    uint32_t *TI = reinterpret_cast<uint32_t *>(TK + n);
+
+    GC_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(SeedCtr), s));
+    GC_CUDA_TRY(cudaMemsetAsync(W + n, 0, 4, s));
+    p->stats.kernel_launches += 4;
+    k_seed_tiles<<<(unsigned)nt, SEED_THREADS, 0, s>>>(x, S.ids2.as<uint32_t>(), n, gp, KT, IT,
+                                                       W, tiles, ctr, MK, MI, MH);
+    k_seed_scan<<<1, 1024, 0, s>>>(tiles, (uint32_t)nt);
+    k_seed_low<<<(unsigned)((nt + 7) / 8), 256, 0, s>>>(KT, IT, tiles, (uint32_t)nt, W, ctr, MK,
+                                                        MI, MH);
+    k_mover_slot<<<(unsigned)(p->num_sms * 8), 256, 0, s>>>(ctr, MK, MI, MH, KT, IT, tiles,
+                                                            (uint32_t)nt, n, W, MS, MA);
+    SeedCtr h{};
+    GC_CUDA_TRY(cudaMemcpyAsync(&h, ctr, sizeof h, cudaMemcpyDeviceToHost, s));
+    GC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h.movers > n) return GC_ERR_CUDA;          // every particle is kept or moved, once
+    if (h.max_group > SEED_GROUP_MAX) return GC_OK;   // sort all keys instead
+    const uint64_t m = h.movers;
+    ++p->stats.primitive_calls;
+    GC_TRY(gc_exclusive_scan_u32(S.cub_tmp, W, E, n + 1, s));
+    if (m) {
+        ++p->stats.kernel_launches;
+        k_mover_scatter<<<grid_for(m, 256, maxb), 256, 0, s>>>(MK, MI, MS, MA, m, E, TK, TI);
+    }
+    S.order_n = 0;   // ids2 is rewritten below
+    ++p->stats.kernel_launches;
+    k_seed_place<<<grid_for(n + m, 256, maxb), 256, 0, s>>>(
+        KT, IT, tiles, n, W, E, MK, MI, MS, m, TK, TI, S.keys2.as<uint64_t>(),
+        S.ids2.as<uint32_t>());
+    GC_CUDA_TRY(cudaGetLastError());
+    *movers = m;
+    *done = true;
+    return GC_OK;
+}
+
+// Fold a completed build's event times into the sums.
+int nbody_timing_fold(NBodyState &S)
+{
+    if (!S.ev_pending) return GC_OK;
+    GC_CUDA_TRY(cudaEventSynchronize(S.ev[2]));
+    float a = 0.f, b = 0.f;
+    GC_CUDA_TRY(cudaEventElapsedTime(&a, S.ev[0], S.ev[1]));
+    GC_CUDA_TRY(cudaEventElapsedTime(&b, S.ev[0], S.ev[2]));
+    S.last_order_ms = a;
+    S.last_tree_ms = b;
+    S.order_ms_sum += a;
+    S.tree_ms_sum += b;
+    ++S.timed_builds;
+    S.ev_pending = false;
+    return GC_OK;
+}
+
 }  // namespace
 
 extern "C" int gc_build_nbody_tasks_resident(gc_pool_t *p, uint64_t n, int bucket_max,
@@ -631,6 +1172,10 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     if (((uintptr_t)xyzm_dev) % 16) return GC_ERR_ARG;
     if (n >= p->cfg.id_capacity) return GC_ERR_POOL_FULL;
     NBodyState &S = p->nb;
+    GC_TRY(nbody_timing_fold(S));
+    for (cudaEvent_t &e : S.ev)
+        if (!e) GC_CUDA_TRY(cudaEventCreate(&e));
+    GC_CUDA_TRY(cudaEventRecord(S.ev[0], p->s));
     int vrc = GC_OK;
     xyzm_dev = (const float *)gc_device_view(p, xyzm_dev, n * sizeof(float4), S.hostcopy, &vrc);
     if (vrc != GC_OK) return vrc;
@@ -658,12 +1203,24 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     k_bbox<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, bounds);
     ++p->stats.kernel_launches;
     k_grid_params<<<1, 1, 0, s>>>(bounds, gp);
-    ++p->stats.kernel_launches;
-    k_keys<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, gp, S.keys.as<uint64_t>(),
-                                                  S.ids.as<uint32_t>());
-    ++p->stats.primitive_calls;
-    GC_TRY(gc_sort_pairs_u64(S.cub_tmp, S.keys.as<uint64_t>(), S.keys2.as<uint64_t>(),
-                             S.ids.as<uint32_t>(), S.ids2.as<uint32_t>(), n, 63, s));
+    // Morton order: seeded by the previous build's order of the same n
+    // particles, else a full stable radix sort of the keys
+    bool seeded = false;
+    uint64_t resorted = n;
+    if (S.order_mode == GC_ORDER_SEEDED && S.order_n == n)
+        GC_TRY(seeded_order(p, x, n, gp, &resorted, &seeded));
+    if (!seeded) {
+        resorted = n;
+        ++p->stats.kernel_launches;
+        k_keys<<<grid_for(n, 256, maxb), 256, 0, s>>>(x, n, gp, S.keys.as<uint64_t>(),
+                                                      S.ids.as<uint32_t>());
+        S.order_n = 0;
+        ++p->stats.primitive_calls;
+        GC_TRY(gc_sort_pairs_u64(S.cub_tmp, S.keys.as<uint64_t>(), S.keys2.as<uint64_t>(),
+                                 S.ids.as<uint32_t>(), S.ids2.as<uint32_t>(), n, 63, s));
+    }
+    S.order_n = n;
+    GC_CUDA_TRY(cudaEventRecord(S.ev[1], s));
     const uint64_t *K = S.keys2.as<uint64_t>();
     const uint32_t *sid = S.ids2.as<uint32_t>();
     ++p->stats.kernel_launches;
@@ -755,7 +1312,6 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     ++p->stats.kernel_launches;
     k_bucket_offsets<<<grid_for((uint64_t)NB + 1, 256, maxb), 256, 0, s>>>(ioff, NB, M, loff);
     uint64_t NL = 0;
-    uint32_t maxlen = 0;
     GC_CUDA_TRY(cudaMemcpyAsync(&NL, loff + NB, 8, cudaMemcpyDeviceToHost, s));
     GC_CUDA_TRY(cudaStreamSynchronize(s));
 
@@ -784,13 +1340,40 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     S.n_buckets = NB;
     S.n_list = NL;
     S.n_walk_items = NI;
-    (void)maxlen;
+    GC_CUDA_TRY(cudaEventRecord(S.ev[2], s));
+    S.ev_pending = true;
+    ++S.builds;
+    if (seeded) ++S.seeded_builds;
+    S.last_resorted = resorted;
     if (info_out) {
         info_out[0] = NN;
         info_out[1] = NB;
         info_out[2] = NL;
-        info_out[3] = 0;
+        info_out[3] = resorted;
     }
+    return GC_OK;
+}
+
+extern "C" int gc_nbody_set_order(gc_pool_t *p, int mode)
+{
+    if (!p || (mode != GC_ORDER_FULL && mode != GC_ORDER_SEEDED)) return GC_ERR_ARG;
+    p->nb.order_mode = mode;
+    return GC_OK;
+}
+
+extern "C" int gc_nbody_stats(gc_pool_t *p, gc_nbody_stats_t *out)
+{
+    if (!p || !out) return GC_ERR_ARG;
+    NBodyState &S = p->nb;
+    GC_TRY(nbody_timing_fold(S));
+    out->builds = S.builds;
+    out->seeded_builds = S.seeded_builds;
+    out->last_resorted = S.last_resorted;
+    out->timed_builds = S.timed_builds;
+    out->last_order_ms = S.last_order_ms;
+    out->last_tree_ms = S.last_tree_ms;
+    out->order_ms_sum = S.order_ms_sum;
+    out->tree_ms_sum = S.tree_ms_sum;
     return GC_OK;
 }
 

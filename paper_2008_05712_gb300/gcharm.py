@@ -42,6 +42,8 @@ GC_COMBINE_PER_TASK = 3
 GC_COMBINE_GREEDY = 4
 GC_SCHED_FIFO = 0
 GC_SCHED_LPT = 1
+GC_ORDER_FULL = 0
+GC_ORDER_SEEDED = 1
 
 NONE32 = 0xFFFFFFFF
 
@@ -91,6 +93,15 @@ class GcServeReport(C.Structure):
                 + [(f, C.c_uint64) for f in _SERVE_TAIL])
 
 
+_NBODY_FIELDS = ["builds", "seeded_builds", "last_resorted", "timed_builds"]
+_NBODY_DFIELDS = ["last_order_ms", "last_tree_ms", "order_ms_sum", "tree_ms_sum"]
+
+
+class GcNbodyStats(C.Structure):
+    _fields_ = ([(f, C.c_uint64) for f in _NBODY_FIELDS]
+                + [(f, C.c_double) for f in _NBODY_DFIELDS])
+
+
 class GcTuning(C.Structure):
     _fields_ = [("wu_max_targets", C.c_uint32), ("schedule", C.c_uint32)]
 
@@ -136,6 +147,8 @@ _SIGS = {
     "gc_read_residency": [P, P, P, P],
     "gc_read_evicted": [P, P, U64, U64P],
     "gc_build_nbody_tasks": [P, P, U64, C.c_int, C.c_int, C.c_int, U64, P],
+    "gc_nbody_set_order": [P, C.c_int],
+    "gc_nbody_stats": [P, C.POINTER(GcNbodyStats)],
     "gc_build_nbody_tasks_resident": [P, U64, C.c_int, C.c_int, C.c_int, U64, P],
     "gc_read_nbody_tree": [P] + [P] * 14,
     "gc_build_md_tasks": [P, P, U64, C.c_int, U64, P],
@@ -533,7 +546,19 @@ class Pool:
         _check(self.lib.gc_build_nbody_tasks(self.h, ptr, xyzm.shape[0], bucket_max,
                                              theta_num, theta_den, task_id_base, _p(info)),
                "gc_build_nbody_tasks")
-        return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]))
+        return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]),
+                    resorted=int(info[3]))
+
+    def set_order(self, mode):
+        """GC_ORDER_SEEDED (default): a build of the same n starts from the
+        previous build's Morton order; GC_ORDER_FULL: every build sorts all
+        keys.  Both give identical trees (gc_nbody_set_order)."""
+        _check(self.lib.gc_nbody_set_order(self.h, int(mode)), "gc_nbody_set_order")
+
+    def nbody_stats(self):
+        s = GcNbodyStats()
+        _check(self.lib.gc_nbody_stats(self.h, C.byref(s)), "gc_nbody_stats")
+        return {f: getattr(s, f) for f in _NBODY_FIELDS + _NBODY_DFIELDS}
 
     def build_nbody_resident(self, n, bucket_max=32, theta_num=7, theta_den=10,
                              task_id_base=0):
@@ -543,7 +568,8 @@ class Pool:
         _check(self.lib.gc_build_nbody_tasks_resident(self.h, int(n), bucket_max, theta_num,
                                                       theta_den, task_id_base, _p(info)),
                "gc_build_nbody_tasks_resident")
-        return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]))
+        return dict(n_nodes=int(info[0]), n_buckets=int(info[1]), list_entries=int(info[2]),
+                    resorted=int(info[3]))
 
     def nbody_tree(self, n, n_nodes, n_buckets, n_list):
         out = dict(sorted_ids=np.empty(n, np.uint32), sorted_keys=np.empty(n, np.uint64),
