@@ -983,19 +983,18 @@ __global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF
                 k += size;
             } else if (R.x >> 31) {      // leaf: its particles
                 const uint2 L = LF[k];
-                if (FILL) {
+                if (FILL) {   // 16 loads in flight before their stores
                     const uint32_t *src = sorted_ids + L.x;
                     uint32_t *dst = o + cnt;
-                    uint32_t q = 0;
-                    for (; q + 4 <= L.y; q += 4) {
-                        const uint32_t v0 = src[q], v1 = src[q + 1], v2 = src[q + 2],
-                                       v3 = src[q + 3];
-                        dst[q] = v0;
-                        dst[q + 1] = v1;
-                        dst[q + 2] = v2;
-                        dst[q + 3] = v3;
+                    for (uint32_t q0 = 0; q0 < L.y; q0 += 16) {
+                        uint32_t v[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (q0 + u < L.y) v[u] = src[q0 + u];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (q0 + u < L.y) dst[q0 + u] = v[u];
                     }
-                    for (; q < L.y; ++q) dst[q] = src[q];
                 }
                 cnt += L.y;
                 k += size;
