@@ -647,6 +647,8 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=Tr
               "reps": batch_reps,
               "tuning": {"wu_max_targets": tuning["wu_max_targets"],
                          "schedule": "lpt" if tuning["schedule"] else "fifo",
+                         "tile_pairs": tuning["tile_pairs"],
+                         "comp_block": tuning["comp_block"],
                          "autotune_ms": tune_ms or tuning.get("times_ms")}}
     if with_oracle:
         # parity on 300 seeded tasks of the batch against the FP64 oracle
@@ -1038,6 +1040,8 @@ def main():
             "tree": tree,
             "tuning": {"wu_max_targets": tuning["wu_max_targets"],
                        "schedule": "lpt" if tuning["schedule"] else "fifo",
+                       "tile_pairs": tuning["tile_pairs"],
+                       "comp_block": tuning["comp_block"],
                        "autotune_ms": tune_ms or tuning.get("times_ms"),
                        "cache": os.path.relpath(TUNE_CACHE, ROOT)},
             "reuse": {"last_hits": hits, "last_unique": uniq},

@@ -590,24 +590,34 @@ typedef struct {
                                  ceil(nT / wu_max_targets) units of near-equal
                                  size, each run by T targets x 32/T source lanes */
     uint32_t schedule;        /* GC_SCHED_FIFO | GC_SCHED_LPT                  */
+    uint32_t tile_pairs;      /* source pairs per tile staged in shared memory
+                                 by a bulk copy: 64, 128 or 256 (32 B each;
+                                 a block holds 16 tiles, so the size sets
+                                 the resident blocks per SM)                   */
+    uint32_t comp_block;      /* source pairs summed in plain FP32 before each
+                                 compensated add: 4, 8 or 16                   */
 } gc_tuning;
 
-/* Set / read the interaction schedule used by later flushes (default 16,
- * FIFO).  The results change only by FP32 summation order (within the
- * per-result tolerance).  Errors: GC_ERR_ARG (other values). */
+/* Set / read the interaction schedule and tile shape used by later flushes
+ * (default 16, FIFO, 128, 8).  The results change only by FP32 summation
+ * order (within the per-result tolerance).  Errors: GC_ERR_ARG (other
+ * values). */
 int gc_set_tuning(gc_pool_t *pool, const gc_tuning *t);
 int gc_get_tuning(gc_pool_t *pool, gc_tuning *t);
 
 /* Autotuner: re-run the interaction stage of the last flushed batch (one
- * wave, gravity tasks) under every schedule {8, 16, 32} x {FIFO, LPT}, timing
- * each with CUDA events (best of `reps`), and keep the fastest for later
- * flushes.  ms_out (may be NULL) receives the 6 times, in the order
- * (8,FIFO), (8,LPT), (16,FIFO), (16,LPT), (32,FIFO), (32,LPT); *best_out (may
+ * wave, gravity tasks) under every schedule and tile shape, work-unit size
+ * {8, 16, 32} x {FIFO, LPT} x tile pairs {64, 128, 256} x compensation block
+ * {4, 8, 16}, timing each with CUDA events (best of `reps`), and keep the
+ * fastest for later flushes.  ms_out (may be NULL) receives the
+ * GC_TUNE_COUNT times, entry ((w * 2 + s) * 3 + t) * 3 + k for the w-th
+ * work-unit size, schedule s, t-th tile size and k-th block; *best_out (may
  * be NULL) the choice.  The batch's result rows are rewritten by the re-runs
  * (same values up to summation order); per-id totals are not touched.
  * Errors: GC_ERR_NOT_READY (no batch), GC_ERR_STATE (the batch ran in more
  * than one wave, or has no gravity task), GC_ERR_CUDA. */
-int gc_autotune(gc_pool_t *pool, int reps, gc_tuning *best_out, float ms_out[6]);
+#define GC_TUNE_COUNT 54
+int gc_autotune(gc_pool_t *pool, int reps, gc_tuning *best_out, float ms_out[GC_TUNE_COUNT]);
 
 /* ---- reuse ablation (Section 3.2, Fig. 3) --------------------------------- */
 

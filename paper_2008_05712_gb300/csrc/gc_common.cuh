@@ -212,6 +212,8 @@ struct gc_pool {
     // interaction schedule (gc_set_tuning / gc_autotune)
     uint32_t wu_max_targets = 16;      // targets per gravity work unit: 8, 16 or 32
     uint32_t wu_schedule = GC_SCHED_FIFO;
+    uint32_t wu_tile = 128;            // gravity tile shape: source pairs per staged tile
+    uint32_t wu_kb = 8;                // and pairs per plain partial sum
     uint64_t table_version = 0;        // bumped whenever a slot is assigned or freed
     // Ewald correction (GC_EWALD tasks): half of the reciprocal vectors
     // (hx, hy, hz, 2 exp(-pi^2 h^2 / (alpha L)^2) / h^2)

@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(PackLargeWarps<CAP>::value * 32) k_pack_large(
 
 constexpr int GRAV_THREADS = 256;
 constexpr int GRAV_WARPS = GRAV_THREADS / 32;
-constexpr int KB = 8;   // source pairs per plain FP32 partial before the compensated add
+constexpr int KB = 8;   // source pairs per plain FP32 partial (the indirect ablation kernel)
 
 struct InterArgs {
     const TaskRec *tasks;
@@ -980,9 +980,11 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float s2, float c2)
         bp = __ffma2_rn(mr, m1, bp);                                      \
     } while (0)
 
-constexpr int TP = 128;                 // source pairs per staged tile (4 KB)
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
 
+// TP source pairs per staged tile (32 TP bytes): shared memory of a block is
+// 512 TP bytes of tiles plus 8 KB, which sets the resident blocks per SM.
+template <int TP>
 struct GravSmem {
     float4 buf[GRAV_WARPS][2][2 * TP];  // per warp: two tiles of source pairs
     uint64_t bar[GRAV_WARPS][2];        // one mbarrier per tile buffer
@@ -995,18 +997,20 @@ struct GravSmem {
 // Source pairs stream through two shared-memory tile buffers per warp,
 // filled by 1-D bulk copies (TMA) that complete on mbarriers, one tile
 // ahead of the compute.  Every source pair is evaluated with paired FP32
-// instructions (two interactions per instruction); partial sums of KB pairs
-// are added with compensation; the S lane results of a target are combined
+// instructions (two interactions per instruction); plain FP32 partial sums
+// of KB pairs are added with compensation; the S lane results of a target are combined
 // as compensated FP32 pairs in lane order.  Work units come from a device queue (persistent
 // kernel); with a null queue each warp takes a fixed share
 // (one-launch-per-task mode).  A bulk copy that does not complete within the
 // polling limit sets GC_FLAG_TIMEOUT and the warp stops; the lanes poll
 // together and take that decision as one, so no lane is left waiting at a
 // later warp-wide shuffle.
+// The tile size TP and the block KB are the autotuner's tile shape.
+template <int TP, int KB>
 __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GravSmem &sm = *reinterpret_cast<GravSmem *>(smem_raw);
+    GravSmem<TP> &sm = *reinterpret_cast<GravSmem<TP> *>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1811,15 +1815,43 @@ static void fill_inter_args(gc_pool *p, FlushCtx &c, uint64_t tgt_base, uint64_t
     a.flags = p->d_ctr + CTR_FLAGS;
 }
 
-static int grav_setup()
+// Tile shapes of the gravity kernel: TP in {64, 128, 256} source pairs per
+// staged tile, KB in {4, 8, 16} pairs per plain partial sum.
+struct GravVariant {
+    void (*fn)(InterArgs);
+    uint32_t tp, kb;
+    size_t smem;
+    int ready;    // shared-memory limit raised
+    int per_sm;   // resident blocks per SM (0: not yet asked)
+};
+
+#define GRAV_V(tp, kb) {k_gravity<tp, kb>, tp, kb, sizeof(GravSmem<tp>), 0, 0}
+static GravVariant g_grav[9] = {GRAV_V(64, 4),  GRAV_V(64, 8),  GRAV_V(64, 16),
+                                GRAV_V(128, 4), GRAV_V(128, 8), GRAV_V(128, 16),
+                                GRAV_V(256, 4), GRAV_V(256, 8), GRAV_V(256, 16)};
+#undef GRAV_V
+
+static GravVariant *grav_variant(uint32_t tp, uint32_t kb)
 {
-    static int done = 0;
-    if (!done) {
-        if (cudaFuncSetAttribute(k_gravity, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(GravSmem)) != cudaSuccess)
+    for (GravVariant &v : g_grav)
+        if (v.tp == tp && v.kb == kb) return &v;
+    return nullptr;
+}
+
+static bool grav_shape_ok(uint32_t tp, uint32_t kb) { return grav_variant(tp, kb) != nullptr; }
+
+// The pool's variant, its shared-memory limit raised.
+static int grav_setup(gc_pool *p, GravVariant **out)
+{
+    GravVariant *v = grav_variant(p->wu_tile, p->wu_kb);
+    if (!v) return GC_ERR_STATE;
+    if (!v->ready) {
+        if (cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)v->smem) != cudaSuccess)
             return GC_ERR_CUDA;
-        done = 1;
+        v->ready = 1;
     }
+    *out = v;
     return GC_OK;
 }
 
@@ -1856,13 +1888,22 @@ static int ewald_blocks(gc_pool *p)
 
 int gc_grav_blocks(gc_pool *p)
 {
-    int per_sm = 0;
-    if (grav_setup() != GC_OK ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gravity, GRAV_THREADS,
-                                                      sizeof(GravSmem)) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    return per_sm * p->num_sms;
+    GravVariant *v = nullptr;
+    if (grav_setup(p, &v) != GC_OK) {
+        cudaGetLastError();
+        return p->num_sms;
+    }
+    if (v->per_sm == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v->fn, GRAV_THREADS,
+                                                          v->smem) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        v->per_sm = per_sm;
+    }
+    return v->per_sm * p->num_sms;
 }
 
 extern "C" int gc_max_combine_size(gc_pool_t *p, uint64_t *out)
@@ -1908,8 +1949,10 @@ int gc_interact_range(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint64_
         GC_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c.s));
         const uint64_t need = (a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS;
         const unsigned g = (unsigned)(need < (uint64_t)full ? need : (uint64_t)full);
+        GravVariant *v = nullptr;
+        GC_TRY(grav_setup(p, &v));
         ++p->stats.kernel_launches;
-        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), c.s>>>(a);
+        v->fn<<<g, GRAV_THREADS, v->smem, c.s>>>(a);
     }
     if (l1 > l0) {
         a.wu = nullptr;
@@ -1946,9 +1989,10 @@ int gc_interact_one_task(gc_pool *p, FlushCtx &c, uint64_t w0, uint64_t w1, uint
         a.lj_list = nullptr;
         a.n_lj = 0;
         const unsigned g = (unsigned)((a.n_wu + GRAV_WARPS - 1) / GRAV_WARPS);
-        GC_TRY(grav_setup());
+        GravVariant *v = nullptr;
+        GC_TRY(grav_setup(p, &v));
         ++p->stats.kernel_launches;
-        k_gravity<<<g, GRAV_THREADS, sizeof(GravSmem), c.s>>>(a);
+        v->fn<<<g, GRAV_THREADS, v->smem, c.s>>>(a);
     }
     if (l1 > l0) {
         a.wu = nullptr;
@@ -2027,8 +2071,11 @@ extern "C" int gc_set_tuning(gc_pool_t *p, const gc_tuning *t)
     if (t->wu_max_targets != 8 && t->wu_max_targets != 16 && t->wu_max_targets != 32)
         return GC_ERR_ARG;
     if (t->schedule != GC_SCHED_FIFO && t->schedule != GC_SCHED_LPT) return GC_ERR_ARG;
+    if (!grav_shape_ok(t->tile_pairs, t->comp_block)) return GC_ERR_ARG;
     p->wu_max_targets = t->wu_max_targets;
     p->wu_schedule = t->schedule;
+    p->wu_tile = t->tile_pairs;
+    p->wu_kb = t->comp_block;
     return GC_OK;
 }
 
@@ -2037,6 +2084,8 @@ extern "C" int gc_get_tuning(gc_pool_t *p, gc_tuning *t)
     if (!p || !t) return GC_ERR_ARG;
     t->wu_max_targets = p->wu_max_targets;
     t->schedule = p->wu_schedule;
+    t->tile_pairs = p->wu_tile;
+    t->comp_block = p->wu_kb;
     return GC_OK;
 }
 
@@ -2072,67 +2121,69 @@ static int rebuild_wus(gc_pool *p, FlushCtx &c, uint32_t wu_max, uint64_t *n_wu_
     return GC_OK;
 }
 
-extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out, float ms_out[6])
+extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
+                           float ms_out[GC_TUNE_COUNT])
 {
     if (!p || reps < 1) return GC_ERR_ARG;
     if (p->last < 0 || !p->ctx[p->last].valid) return GC_ERR_NOT_READY;
     FlushCtx &c = p->ctx[p->last];
     GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
     if (c.n_waves != 1) return GC_ERR_STATE;
-    const uint32_t saved_max = p->wu_max_targets, saved_sched = p->wu_schedule;
-    const uint32_t tiles[3] = {8, 16, 32};
+    const gc_tuning saved{p->wu_max_targets, p->wu_schedule, p->wu_tile, p->wu_kb};
+    const uint32_t wus[3] = {8, 16, 32}, tps[3] = {64, 128, 256}, kbs[3] = {4, 8, 16};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
         return GC_ERR_CUDA;
     }
     float best = 1e30f;
-    gc_tuning choice{saved_max, saved_sched};
+    gc_tuning choice = saved;
     int rc = GC_OK;
-    for (int ti = 0; ti < 3 && rc == GC_OK; ++ti) {
-        for (uint32_t sched = 0; sched < 2 && rc == GC_OK; ++sched) {
-            p->wu_max_targets = tiles[ti];
-            p->wu_schedule = sched;
-            float tbest = 1e30f;
-            for (int r = 0; r < reps && rc == GC_OK; ++r) {
-                uint64_t W = 0;
-                rc = rebuild_wus(p, c, tiles[ti], &W);
-                if (rc != GC_OK) break;
-                if (W == 0) {
-                    rc = GC_ERR_STATE;
-                    break;
-                }
-                // the ordering pass (LPT) is part of the schedule's cost
-                cudaEventRecord(e0, c.s);
-                rc = gc_interact_range(p, c, 0, W, 0, 0, 0, 0, 0);
-                cudaEventRecord(e1, c.s);
-                if (rc != GC_OK) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = GC_ERR_CUDA;
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < tbest) tbest = ms;
-            }
+    // index = ((wu * 2 + schedule) * 3 + tile) * 3 + block
+    for (int idx = 0; idx < GC_TUNE_COUNT && rc == GC_OK; ++idx) {
+        const gc_tuning t{wus[idx / 18], (uint32_t)((idx / 9) % 2), tps[(idx / 3) % 3],
+                          kbs[idx % 3]};
+        p->wu_max_targets = t.wu_max_targets;
+        p->wu_schedule = t.schedule;
+        p->wu_tile = t.tile_pairs;
+        p->wu_kb = t.comp_block;
+        float tbest = 1e30f;
+        for (int r = 0; r < reps && rc == GC_OK; ++r) {
+            uint64_t W = 0;
+            rc = rebuild_wus(p, c, t.wu_max_targets, &W);
             if (rc != GC_OK) break;
-            if (ms_out) ms_out[2 * ti + sched] = tbest;
-            if (tbest < best) {
-                best = tbest;
-                choice.wu_max_targets = tiles[ti];
-                choice.schedule = sched;
+            if (W == 0) {
+                rc = GC_ERR_STATE;
+                break;
             }
+            // the ordering pass (LPT) is part of the schedule's cost
+            cudaEventRecord(e0, c.s);
+            rc = gc_interact_range(p, c, 0, W, 0, 0, 0, 0, 0);
+            cudaEventRecord(e1, c.s);
+            if (rc != GC_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = GC_ERR_CUDA;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < tbest) tbest = ms;
+        }
+        if (rc != GC_OK) break;
+        if (ms_out) ms_out[idx] = tbest;
+        if (tbest < best) {
+            best = tbest;
+            choice = t;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc != GC_OK) {
-        p->wu_max_targets = saved_max;
-        p->wu_schedule = saved_sched;
-        return rc;
-    }
-    p->wu_max_targets = choice.wu_max_targets;
-    p->wu_schedule = choice.schedule;
+    const gc_tuning keep = rc == GC_OK ? choice : saved;
+    p->wu_max_targets = keep.wu_max_targets;
+    p->wu_schedule = keep.schedule;
+    p->wu_tile = keep.tile_pairs;
+    p->wu_kb = keep.comp_block;
+    if (rc != GC_OK) return rc;
     uint64_t W = 0;
     GC_TRY(rebuild_wus(p, c, choice.wu_max_targets, &W));   // context matches the choice
     GC_CUDA_TRY(cudaStreamSynchronize(c.s));

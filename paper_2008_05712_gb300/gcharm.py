@@ -103,7 +103,24 @@ class GcNbodyStats(C.Structure):
 
 
 class GcTuning(C.Structure):
-    _fields_ = [("wu_max_targets", C.c_uint32), ("schedule", C.c_uint32)]
+    _fields_ = [("wu_max_targets", C.c_uint32), ("schedule", C.c_uint32),
+                ("tile_pairs", C.c_uint32), ("comp_block", C.c_uint32)]
+
+
+GC_TUNE_COUNT = 54
+_TUNE_FIELDS = ["wu_max_targets", "schedule", "tile_pairs", "comp_block"]
+
+
+def tune_key(t):
+    """Name of a tuning in the autotuner's times: 'wu,fifo|lpt,tile,block'."""
+    return (f"{t['wu_max_targets']},{'lpt' if t['schedule'] else 'fifo'},"
+            f"{t['tile_pairs']},{t['comp_block']}")
+
+
+def tune_order():
+    """The autotuner's tunings in the order of its times (gc_autotune)."""
+    return [dict(wu_max_targets=w, schedule=s, tile_pairs=tp, comp_block=kb)
+            for w in (8, 16, 32) for s in (0, 1) for tp in (64, 128, 256) for kb in (4, 8, 16)]
 
 
 class GcError(RuntimeError):
@@ -433,14 +450,16 @@ class Pool:
         d["timed_batches"] = s.timed_batches
         return d
 
-    def set_tuning(self, wu_max_targets=16, schedule=GC_SCHED_FIFO):
-        t = GcTuning(wu_max_targets=wu_max_targets, schedule=schedule)
+    def set_tuning(self, wu_max_targets=16, schedule=GC_SCHED_FIFO, tile_pairs=128,
+                   comp_block=8):
+        t = GcTuning(wu_max_targets=wu_max_targets, schedule=schedule, tile_pairs=tile_pairs,
+                     comp_block=comp_block)
         _check(self.lib.gc_set_tuning(self.h, C.byref(t)), "gc_set_tuning")
 
     def tuning(self):
         t = GcTuning()
         _check(self.lib.gc_get_tuning(self.h, C.byref(t)), "gc_get_tuning")
-        return {"wu_max_targets": t.wu_max_targets, "schedule": t.schedule}
+        return {f: getattr(t, f) for f in _TUNE_FIELDS}
 
     def autotune(self, reps=3, cache=None, key=None):
         """Pick the interaction schedule on the last flushed batch (gc_autotune).
@@ -455,15 +474,14 @@ class Pool:
                     stored = json.load(f).get(key)
             except (OSError, ValueError):
                 stored = None
-            if stored:
-                self.set_tuning(stored["wu_max_targets"], stored["schedule"])
-                return stored, None
+            if stored and all(f in stored for f in _TUNE_FIELDS):
+                self.set_tuning(*[stored[f] for f in _TUNE_FIELDS])
+                return dict(stored), None
         best = GcTuning()
-        ms = np.zeros(6, np.float32)
+        ms = np.zeros(GC_TUNE_COUNT, np.float32)
         _check(self.lib.gc_autotune(self.h, int(reps), C.byref(best), _p(ms)), "gc_autotune")
-        choice = {"wu_max_targets": best.wu_max_targets, "schedule": best.schedule}
-        times = {f"{t},{'lpt' if k else 'fifo'}": float(ms[2 * i + k])
-                 for i, t in enumerate((8, 16, 32)) for k in (0, 1)}
+        choice = {f: getattr(best, f) for f in _TUNE_FIELDS}
+        times = {tune_key(t): float(ms[i]) for i, t in enumerate(tune_order())}
         if cache and key:
             try:
                 with open(cache) as f:

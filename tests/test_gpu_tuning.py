@@ -1,8 +1,10 @@
 """GPU tests of the interaction schedule (work-unit size 8 / 16 / 32 targets,
-admission-order or longest-first hand-out) and its autotuner: every schedule
-matches the FP64 oracle within the per-result tolerance, the work-unit order
-alone leaves every result bit-identical, and the autotuner keeps its fastest
-measured choice."""
+admission-order or longest-first hand-out) and tile shape (64 / 128 / 256
+source pairs per staged tile, 4 / 8 / 16 pairs per plain partial sum), and
+of the autotuner over all of them: every schedule and shape matches the FP64
+oracle within the per-result tolerance, the work-unit order alone leaves
+every result bit-identical, and the autotuner keeps its fastest measured
+choice."""
 import json
 
 import numpy as np
@@ -30,41 +32,58 @@ def batch():
     return x, to, tg, so, sr
 
 
-def run(gc, x, to, tg, so, sr, wu_max, sched):
-    n = x.shape[0]
-    pool = make_pool(gc, torch, n, n)
-    pool.upload(np.arange(n, dtype=np.uint32), x)
-    pool.set_tuning(wu_max, sched)
+def flush_under(gc, pool, to, tg, so, sr, tuning):
+    pool.set_tuning(**tuning)
     b = pool.submit_csr(np.zeros(len(to) - 1, np.uint32), to, tg, so, sr)
     pool.flush()
     pool.wait(b)
-    rows = pool.results()
+    return pool.results()
+
+
+def run(gc, x, to, tg, so, sr, wu_max, sched, tile=128, block=8):
+    n = x.shape[0]
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    rows = flush_under(gc, pool, to, tg, so, sr,
+                       dict(wu_max_targets=wu_max, schedule=sched, tile_pairs=tile,
+                            comp_block=block))
     return pool, rows
 
 
-def test_every_schedule_matches_oracle(gc, orc, batch):
+def test_every_schedule_and_tile_shape_matches_oracle(gc, orc, batch):
     x, to, tg, so, sr = batch
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
-    for wu_max in (8, 16, 32):
-        per_order = []
-        for sched in (gc.GC_SCHED_FIFO, gc.GC_SCHED_LPT):
-            pool, rows = run(gc, x, to, tg, so, sr, wu_max, sched)
-            assert pool.tuning() == {"wu_max_targets": wu_max, "schedule": sched}
-            errs = per_task_errors(gc.value(rows), ref, to)
-            assert errs.max() <= TOL, (wu_max, sched, errs.max())
-            per_order.append(rows)
-            pool.close()
-        # the hand-out order changes which warp runs a unit, not its sums
-        assert np.array_equal(per_order[0], per_order[1])
+    n = x.shape[0]
+    pool = make_pool(gc, torch, n, n)
+    pool.upload(np.arange(n, dtype=np.uint32), x)
+    rows = {}
+    for t in gc.tune_order():
+        r = flush_under(gc, pool, to, tg, so, sr, t)
+        assert pool.tuning() == t
+        errs = per_task_errors(gc.value(r), ref, to)
+        assert errs.max() <= TOL, (t, errs.max())
+        rows[gc.tune_key(t)] = r
+    assert len(rows) == gc.GC_TUNE_COUNT
+    # the hand-out order changes which warp runs a unit, not its sums
+    for t in gc.tune_order():
+        if t["schedule"] == gc.GC_SCHED_FIFO:
+            lpt = dict(t, schedule=gc.GC_SCHED_LPT)
+            assert np.array_equal(rows[gc.tune_key(t)], rows[gc.tune_key(lpt)]), t
+    pool.close()
 
 
 def test_bad_tuning_rejected(gc, batch):
     x = batch[0]
     pool = make_pool(gc, torch, x.shape[0], x.shape[0])
-    for wu_max, sched in [(12, 0), (64, 0), (16, 2)]:
+    for bad in [dict(wu_max_targets=12), dict(wu_max_targets=64), dict(schedule=2),
+                dict(tile_pairs=96), dict(tile_pairs=512), dict(comp_block=2),
+                dict(comp_block=32)]:
+        t = dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8)
+        t.update(bad)
         with pytest.raises(gc.GcError) as e:
-            pool.set_tuning(wu_max, sched)
+            pool.set_tuning(**t)
         assert e.value.code == gc.GC_ERR_ARG
+    assert pool.tuning() == dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8)
     with pytest.raises(gc.GcError) as e:
         pool.autotune()                      # nothing flushed yet
     assert e.value.code == gc.GC_ERR_NOT_READY
@@ -75,9 +94,8 @@ def test_autotune_keeps_fastest_and_caches(gc, orc, batch, tmp_path):
     x, to, tg, so, sr = batch
     pool, _ = run(gc, x, to, tg, so, sr, 16, gc.GC_SCHED_FIFO)
     choice, times = pool.autotune(reps=2)
-    assert len(times) == 6 and all(v > 0 for v in times.values())
-    key = f"{choice['wu_max_targets']},{'lpt' if choice['schedule'] else 'fifo'}"
-    assert times[key] == min(times.values())
+    assert len(times) == gc.GC_TUNE_COUNT and all(v > 0 for v in times.values())
+    assert times[gc.tune_key(choice)] == min(times.values())
     assert pool.tuning() == choice
     # the re-run rows of the tuned batch still match the oracle
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
@@ -92,8 +110,8 @@ def test_autotune_keeps_fastest_and_caches(gc, orc, batch, tmp_path):
     c1, t1 = pool.autotune(reps=1, cache=cache, key="uneven300")
     assert t1 is not None and json.load(open(cache))["uneven300"]["wu_max_targets"] == \
         c1["wu_max_targets"]
-    pool.set_tuning(8, gc.GC_SCHED_FIFO)
+    pool.set_tuning(8, gc.GC_SCHED_FIFO, 64, 4)
     c2, t2 = pool.autotune(cache=cache, key="uneven300")
     assert t2 is None and c2["wu_max_targets"] == c1["wu_max_targets"]
-    assert pool.tuning()["wu_max_targets"] == c1["wu_max_targets"]
+    assert pool.tuning() == c1
     pool.close()
