@@ -943,6 +943,18 @@ __device__ __forceinline__ bool walk_accepts(uint32_t k, const uint4 &R, uint32_
 // (lanes read different nodes): one 16-byte record per visited node, read
 // after the decision; the many resident warps hide its latency.  FILL =
 // false: lengths into len[b M + r]; true: entries written at off[b M + r].
+// Write out the entries a lane has gathered in its 16-byte group: slot q of
+// the group holds list entry (cnt - 1) - (last slot - q).
+__device__ __forceinline__ void walk_flush_group(uint32_t *o, uint32_t cnt, uint32_t a0,
+                                                 uint32_t &gmask, const uint32_t *g)
+{
+    const uint32_t sl = (a0 + cnt - 1) & 3u;
+    for (uint32_t q = 0; q < 4; ++q)
+        if ((gmask >> q) & 1u) o[cnt - 1 - (sl - q)] = g[q];
+    gmask = 0;
+}
+
+// Launched with 128 threads per block (the per-lane groups below).
 template <bool FILL>
 __global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF, uint32_t M,
                                                  const uint32_t *klo, const uint32_t *anc,
@@ -954,8 +966,10 @@ __global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF
                                                  uint32_t *out)
 {
     __shared__ int64_t th[22];
+    __shared__ __align__(16) uint32_t grp[128][4];
     if (threadIdx.x < 22) th[threadIdx.x] = thg.t[threadIdx.x];
     __syncthreads();
+    uint32_t *g = grp[threadIdx.x];
     GRID_STRIDE(t, nb * M) {
         const uint32_t r = (uint32_t)(t / nb);
         const uint64_t b = t - (uint64_t)r * nb;
@@ -974,15 +988,34 @@ __global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF
         }
         uint32_t cnt = 0;
         uint32_t *o = FILL ? out + off[b * M + r] : nullptr;
+        // Accepted-node entries gather in 16-byte groups aligned in the list
+        // (a lane's shared-memory row) and leave as one vector store: one
+        // scattered 4-byte store per entry was most of the fill pass's cost.
+        // A leaf copy and the end of the walk write out a partial group.
+        const uint32_t a0 = FILL ? (uint32_t)(((uintptr_t)o >> 2) & 3u) : 0u;
+        uint32_t gmask = 0;
         while (k < k1) {
             const uint4 R = W[k];
             const uint32_t size = R.x & 0x7FFFFFFFu;
             if (walk_accepts(k, R, lf, lo, hi, th)) {
-                if (FILL) o[cnt] = n_part + k;
+                if (FILL) {
+                    const uint32_t slot = (a0 + cnt) & 3u;
+                    g[slot] = n_part + k;
+                    gmask |= 1u << slot;
+                    if (slot == 3) {
+                        if (gmask == 0xFu)
+                            *reinterpret_cast<uint4 *>(o + cnt - 3) =
+                                *reinterpret_cast<const uint4 *>(g);
+                        else
+                            walk_flush_group(o, cnt + 1, a0, gmask, g);
+                        gmask = 0;
+                    }
+                }
                 ++cnt;
                 k += size;
             } else if (R.x >> 31) {      // leaf: its particles
                 const uint2 L = LF[k];
+                if (FILL && gmask) walk_flush_group(o, cnt, a0, gmask, g);
                 if (FILL) {   // 16 loads in flight before their stores
                     const uint32_t *src = sorted_ids + L.x;
                     uint32_t *dst = o + cnt;
@@ -1002,6 +1035,7 @@ __global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF
                 k += 1;
             }
         }
+        if (FILL && gmask) walk_flush_group(o, cnt, a0, gmask, g);
         if (!FILL) len[b * M + r] = cnt;
     }
 }
