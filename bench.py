@@ -50,8 +50,9 @@ PACK_BYTES_PER_ENTRY = 40
 # DRAM bytes (read + write) per unit of work from ncu captures of the current
 # kernels (None until captured again after a kernel change):
 # k_gravity per interaction, the pack kernels per list entry.
-# profiles/k_gravity_nbody262k.md: 503.5 MB for 2.949e8 interactions (262,144-particle step)
-GRAVITY_DRAM_BYTES_PER_INTERACTION = 503.5e6 / 2.949e8
+# profiles/k_gravity_nbody262k.md: 502.6 MB for 2.949e8 interactions (262,144-particle
+# step, k_gravity<128, 32>, the tuned tile shape)
+GRAVITY_DRAM_BYTES_PER_INTERACTION = 502.6e6 / 2.949e8
 # profiles/k_pack_mid_nbody262k.md: 629.7 MB for 3.07e7 entries (262,144-particle step)
 PACK_DRAM_BYTES_PER_ENTRY = 629.7e6 / 3.07e7
 # Algorithmic bytes of the per-id accumulation: a row's 32-byte compensated

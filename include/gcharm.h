@@ -595,7 +595,7 @@ typedef struct {
                                  a block holds 16 tiles, so the size sets
                                  the resident blocks per SM)                   */
     uint32_t comp_block;      /* source pairs summed in plain FP32 before each
-                                 compensated add: 4, 8 or 16                   */
+                                 compensated add: 8, 16 or 32                  */
 } gc_tuning;
 
 /* Set / read the interaction schedule and tile shape used by later flushes
@@ -608,7 +608,7 @@ int gc_get_tuning(gc_pool_t *pool, gc_tuning *t);
 /* Autotuner: re-run the interaction stage of the last flushed batch (one
  * wave, gravity tasks) under every schedule and tile shape, work-unit size
  * {8, 16, 32} x {FIFO, LPT} x tile pairs {64, 128, 256} x compensation block
- * {4, 8, 16}, timing each with CUDA events (best of `reps`), and keep the
+ * {8, 16, 32}, timing each with CUDA events (best of `reps`), and keep the
  * fastest for later flushes.  ms_out (may be NULL) receives the
  * GC_TUNE_COUNT times, entry ((w * 2 + s) * 3 + t) * 3 + k for the w-th
  * work-unit size, schedule s, t-th tile size and k-th block; *best_out (may

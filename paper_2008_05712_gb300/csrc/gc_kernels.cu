@@ -1816,7 +1816,7 @@ static void fill_inter_args(gc_pool *p, FlushCtx &c, uint64_t tgt_base, uint64_t
 }
 
 // Tile shapes of the gravity kernel: TP in {64, 128, 256} source pairs per
-// staged tile, KB in {4, 8, 16} pairs per plain partial sum.
+// staged tile, KB in {8, 16, 32} pairs per plain partial sum.
 struct GravVariant {
     void (*fn)(InterArgs);
     uint32_t tp, kb;
@@ -1826,9 +1826,9 @@ struct GravVariant {
 };
 
 #define GRAV_V(tp, kb) {k_gravity<tp, kb>, tp, kb, sizeof(GravSmem<tp>), 0, 0}
-static GravVariant g_grav[9] = {GRAV_V(64, 4),  GRAV_V(64, 8),  GRAV_V(64, 16),
-                                GRAV_V(128, 4), GRAV_V(128, 8), GRAV_V(128, 16),
-                                GRAV_V(256, 4), GRAV_V(256, 8), GRAV_V(256, 16)};
+static GravVariant g_grav[9] = {GRAV_V(64, 8),  GRAV_V(64, 16),  GRAV_V(64, 32),
+                                GRAV_V(128, 8), GRAV_V(128, 16), GRAV_V(128, 32),
+                                GRAV_V(256, 8), GRAV_V(256, 16), GRAV_V(256, 32)};
 #undef GRAV_V
 
 static GravVariant *grav_variant(uint32_t tp, uint32_t kb)
@@ -2130,7 +2130,7 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
     GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
     if (c.n_waves != 1) return GC_ERR_STATE;
     const gc_tuning saved{p->wu_max_targets, p->wu_schedule, p->wu_tile, p->wu_kb};
-    const uint32_t wus[3] = {8, 16, 32}, tps[3] = {64, 128, 256}, kbs[3] = {4, 8, 16};
+    const uint32_t wus[3] = {8, 16, 32}, tps[3] = {64, 128, 256}, kbs[3] = {8, 16, 32};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);

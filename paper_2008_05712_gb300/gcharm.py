@@ -120,7 +120,7 @@ def tune_key(t):
 def tune_order():
     """The autotuner's tunings in the order of its times (gc_autotune)."""
     return [dict(wu_max_targets=w, schedule=s, tile_pairs=tp, comp_block=kb)
-            for w in (8, 16, 32) for s in (0, 1) for tp in (64, 128, 256) for kb in (4, 8, 16)]
+            for w in (8, 16, 32) for s in (0, 1) for tp in (64, 128, 256) for kb in (8, 16, 32)]
 
 
 class GcError(RuntimeError):

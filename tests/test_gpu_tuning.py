@@ -1,6 +1,6 @@
 """GPU tests of the interaction schedule (work-unit size 8 / 16 / 32 targets,
 admission-order or longest-first hand-out) and tile shape (64 / 128 / 256
-source pairs per staged tile, 4 / 8 / 16 pairs per plain partial sum), and
+source pairs per staged tile, 8 / 16 / 32 pairs per plain partial sum), and
 of the autotuner over all of them: every schedule and shape matches the FP64
 oracle within the per-result tolerance, the work-unit order alone leaves
 every result bit-identical, and the autotuner keeps its fastest measured
@@ -76,8 +76,8 @@ def test_bad_tuning_rejected(gc, batch):
     x = batch[0]
     pool = make_pool(gc, torch, x.shape[0], x.shape[0])
     for bad in [dict(wu_max_targets=12), dict(wu_max_targets=64), dict(schedule=2),
-                dict(tile_pairs=96), dict(tile_pairs=512), dict(comp_block=2),
-                dict(comp_block=32)]:
+                dict(tile_pairs=96), dict(tile_pairs=512), dict(comp_block=4),
+                dict(comp_block=64)]:
         t = dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8)
         t.update(bad)
         with pytest.raises(gc.GcError) as e:
@@ -110,7 +110,7 @@ def test_autotune_keeps_fastest_and_caches(gc, orc, batch, tmp_path):
     c1, t1 = pool.autotune(reps=1, cache=cache, key="uneven300")
     assert t1 is not None and json.load(open(cache))["uneven300"]["wu_max_targets"] == \
         c1["wu_max_targets"]
-    pool.set_tuning(8, gc.GC_SCHED_FIFO, 64, 4)
+    pool.set_tuning(8, gc.GC_SCHED_FIFO, 64, 8)
     c2, t2 = pool.autotune(cache=cache, key="uneven300")
     assert t2 is None and c2["wu_max_targets"] == c1["wu_max_targets"]
     assert pool.tuning() == c1
