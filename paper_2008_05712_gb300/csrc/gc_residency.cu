@@ -161,7 +161,8 @@ __global__ void k_compact_write(CompactArgs a, const uint32_t *tile_off, uint32_
 // `first` set, the thread that moves an id's reference word to the wave's
 // epoch appends the id to `first` (the distinct ids of the wave, in no
 // particular order, counted in ctr[CTR_UNIQUE]).
-constexpr int MARK_HASH = 2048;
+constexpr int MARK_HASH_BITS = 12;
+constexpr int MARK_HASH = 1 << MARK_HASH_BITS;   // about twice the distinct ids of a chunk
 
 __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, uint64_t ns,
                        uint64_t id_cap, uint32_t *ref_epoch,
@@ -209,7 +210,7 @@ __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, ui
                 if (is_first) first[at + __popc(fm & ((1u << lane) - 1u))] = id;
             }
         }
-        uint32_t h = (id * 2654435761u) & (MARK_HASH - 1);
+        uint32_t h = (id * 2654435761u) >> (32 - MARK_HASH_BITS);   // top bits of the product
         bool done = false;
         for (int probe = 0; probe < 8; ++probe) {
             uint32_t k = hkey[h];
