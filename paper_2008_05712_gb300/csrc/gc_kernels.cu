@@ -558,44 +558,41 @@ __device__ __forceinline__ int block_sort(SortSmem<CAP, NW, NB> &sm, int n, bool
     constexpr int NBB = ilog2(NB);
     static_assert(BPT >= 1 && BPT * NT == NB && (1 << NBB) == NB, "bucket layout");
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    const int per = (((n + NW - 1) / NW) + 31) & ~31;
-    const int b0 = min(n, w * per), b1 = min(n, b0 + per);
-    // 1. largest and smallest slot of each warp's range, then the running
-    //    maximum in list order: P = 1 + the largest slot below it
-    uint32_t mx = 0u, mn = 0xFFFFFFFFu;
-    for (int k = b0 + lane; k < b1; k += 32) {
+    // Each thread takes a chunk of E consecutive entries (E odd, so the
+    // lanes' strided reads fall in distinct banks); running maxima and
+    // counts go sequentially within a chunk and by one scan across chunks.
+    const int E = ((n + NT - 1) / NT) | 1;
+    const int c0 = min(n, (int)threadIdx.x * E), c1 = min(n, c0 + E);
+    // 1. largest and smallest slot of each chunk; the running maximum in list
+    //    order: P = 1 + the largest slot below it
+    uint32_t tmax = 0u, tmin = 0xFFFFFFFFu;
+    for (int k = c0; k < c1; ++k) {
         const uint32_t v = sm.ka[k];
-        mx = max(mx, v);
-        mn = min(mn, v);
+        tmax = max(tmax, v);
+        tmin = min(tmin, v);
     }
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    mn = __reduce_min_sync(0xffffffffu, mn);
-    if (lane == 0) {
-        sm.wmax[w] = mx;
-        sm.wmin[w] = mn;
+    uint32_t incl = tmax;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = max(incl, y);
     }
+    tmin = __reduce_min_sync(0xffffffffu, tmin);
+    if (lane == 31) sm.wmax[w] = incl;
+    if (lane == 0) sm.wmin[w] = tmin;
     __syncthreads();
-    uint32_t carry = 0u, kmin = 0xFFFFFFFFu;
+    uint32_t carry = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) carry = 0u;
+    uint32_t kmin = 0xFFFFFFFFu;
     for (int q = 0; q < NW; ++q) {
         if (q < w) carry = max(carry, sm.wmax[q]);
         kmin = min(kmin, sm.wmin[q]);
     }
     uint32_t inv = 0u;
-    for (int c = b0; c < b1; c += 32) {
-        const int k = c + lane;
-        const bool v = k < b1;
-        const uint32_t key = v ? sm.ka[k] : 0u;
-        uint32_t incl = key;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl = max(incl, y);
-        }
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, incl, 1);
-        const uint32_t before = lane ? max(prev, carry) : carry;
-        if (v && before > key) inv = max(inv, key + 1u);
-        carry = max(carry, __shfl_sync(0xffffffffu, incl, 31));
+    for (int k = c0; k < c1; ++k) {
+        const uint32_t v = sm.ka[k];
+        if (carry > v) inv = max(inv, v + 1u);
+        carry = max(carry, v);
     }
     inv = __reduce_max_sync(0xffffffffu, inv);
     if (lane == 0) sm.winv[w] = inv;
@@ -607,31 +604,27 @@ __device__ __forceinline__ int block_sort(SortSmem<CAP, NW, NB> &sm, int n, bool
         return n;
     }
     // 2. stable split: slots below P to kb[0, ns), the ordered tail to kb[ns, n)
-    uint32_t cs = 0;
-    for (int c = b0; c < b1; c += 32) {
-        const int k = c + lane;
-        cs += (uint32_t)__popc(__ballot_sync(0xffffffffu, k < b1 && sm.ka[k] < P));
+    uint32_t cl = 0;
+    for (int k = c0; k < c1; ++k) cl += sm.ka[k] < P ? 1u : 0u;
+    uint32_t lincl = cl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, lincl, o);
+        if (lane >= o) lincl += y;
     }
-    if (lane == 0) sm.wsmall[w] = cs;
+    if (lane == 31) sm.wsmall[w] = lincl;
     __syncthreads();
-    uint32_t run = 0, ns = 0;
+    uint32_t nlow = lincl - cl, ns = 0;   // low entries before this chunk; in the list
     for (int q = 0; q < NW; ++q) {
-        if (q < w) run += sm.wsmall[q];
+        if (q < w) nlow += sm.wsmall[q];
         ns += sm.wsmall[q];
     }
-    for (int c = b0; c < b1; c += 32) {
-        const int k = c + lane;
-        const bool v = k < b1;
-        const uint32_t key = v ? sm.ka[k] : 0u;
-        const bool low = v && key < P;
-        const uint32_t bal = __ballot_sync(0xffffffffu, low);
-        const uint32_t nlow = run + (uint32_t)__popc(bal & lt);   // low entries before k
-        if (v) {
-            const uint32_t dst = low ? nlow : ns + (uint32_t)k - nlow;
-            sm.kb[dst] = key;
-            sm.pb[dst] = sm.pa[k];
-        }
-        run += (uint32_t)__popc(bal);
+    for (int k = c0; k < c1; ++k) {
+        const uint32_t v = sm.ka[k];
+        const uint16_t pos = sm.pa[k];
+        const uint32_t dst = v < P ? nlow++ : ns + (uint32_t)k - nlow;
+        sm.kb[dst] = v;
+        sm.pb[dst] = pos;
     }
     __syncthreads();
     if (ns <= 1u) {
