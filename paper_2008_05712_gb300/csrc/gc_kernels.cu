@@ -1594,6 +1594,53 @@ __global__ void k_reduce_runs(const uint32_t *runs, const unsigned long long *n_
     }
 }
 
+// Small batches (at most SCATTER_SMALL rows): the per-id accumulation in
+// one block.  The (id, row) keys -- distinct, one per row -- are sorted in
+// shared memory by a bitonic network, which orders rows by id and, within
+// an id, by row (the order of the stable sort of the general path); each
+// id's rows are then added to its total in that order with the same
+// arithmetic as k_reduce_runs, so both paths give the same totals.
+constexpr int SCATTER_SMALL = 2048;
+
+__global__ void __launch_bounds__(1024) k_scatter_small(uint32_t n_rows, const uint32_t *row_id,
+                                                        const float4 *res, gcd4 *totals)
+{
+    __shared__ unsigned long long sorted[SCATTER_SMALL];
+    uint32_t n2 = 1;
+    while (n2 < n_rows) n2 <<= 1;
+    for (uint32_t r = threadIdx.x; r < n2; r += blockDim.x)
+        sorted[r] = r < n_rows ? ((unsigned long long)row_id[r] << 32) | r : ~0ull;
+    __syncthreads();
+    for (uint32_t k = 2; k <= n2; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = sorted[i], b = sorted[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        sorted[i] = b;
+                        sorted[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (uint32_t q = threadIdx.x; q < n_rows; q += blockDim.x) {
+        const uint32_t id = (uint32_t)(sorted[q] >> 32);
+        if (q > 0 && (uint32_t)(sorted[q - 1] >> 32) == id) continue;   // not a run start
+        gcd4 acc = totals[id];
+        for (uint32_t e = q; e < n_rows && (uint32_t)(sorted[e] >> 32) == id; ++e) {
+            const uint32_t rw = (uint32_t)sorted[e];
+            const float4 sv = res[2 * (uint64_t)rw], cv = res[2 * (uint64_t)rw + 1];
+            acc.x += gc_f2d(sv.x) - gc_f2d(cv.x);
+            acc.y += gc_f2d(sv.y) - gc_f2d(cv.y);
+            acc.z += gc_f2d(sv.z) - gc_f2d(cv.z);
+            acc.w += gc_f2d(sv.w) - gc_f2d(cv.w);
+        }
+        totals[id] = acc;
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2015,6 +2062,13 @@ int gc_scatter(gc_pool *p, FlushCtx &c)
         GC_CUDA_TRY(cudaGetLastError());
         return GC_OK;
     }
+    if (n_rows <= (uint64_t)SCATTER_SMALL) {   // one block (no sorted state kept)
+        ++p->stats.kernel_launches;
+        k_scatter_small<<<1, 1024, 0, c.s>>>((uint32_t)n_rows, c.row_id.as<uint32_t>(),
+                                             c.res.as<float4>(), p->d_totals);
+        GC_CUDA_TRY(cudaGetLastError());
+        return GC_OK;
+    }
     GC_TRY(c.rows_tmp.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(c.rid_sorted.reserve(n_rows * sizeof(uint32_t)));
     GC_TRY(c.row_sorted.reserve(n_rows * sizeof(uint32_t)));
@@ -2046,6 +2100,7 @@ int gc_scatter_replay(gc_pool *p, FlushCtx &c)
     if (c.n_rows == 0) return GC_OK;
     if (c.md_struct) return gc_md_reduce(p, c);
     if (c.unique_rows) return gc_scatter(p, c);   // no sorted state to replay
+    if (c.n_rows <= (uint64_t)SCATTER_SMALL) return gc_scatter(p, c);   // the one-block path
     ++p->stats.kernel_launches;
     k_reduce_runs<<<grid_for(c.n_rows, 256, p->num_sms * 16), 256, 0, c.s>>>(
         c.runs.as<uint32_t>(), c.d_ctr + FC_RUNS, c.n_rows, c.rid_sorted.as<uint32_t>(),

@@ -280,3 +280,42 @@ def test_reset_totals_semantics(gc):
     pool.wait(b)
     assert np.array_equal(pool.totals(ids), one)
     pool.close()
+
+
+def test_per_id_totals_exact_small_and_large_batches(gc, orc):
+    """The per-id totals are the rows' FP64 values s - c summed per id in
+    admission order.  Batches of at most 2048 rows take a one-block path,
+    larger ones sort (id, row) first; both must give the oracle's reduction
+    of the same row values bit for bit, and so must a graph replay of a
+    small batch."""
+    n = 600                                   # few ids: they repeat across tasks
+    x = inputs.plummer(n, inputs.SEED_BASE + 21)
+    for n_tasks, t_range in [(40, (1, 60)), (300, (1, 40))]:
+        to, tg, so, sr = inputs.uneven_tasks(n, n_tasks, inputs.SEED_BASE + 22, t_range,
+                                             (1, 400))
+        rows = int(to[-1])
+        assert (rows <= 2048) == (n_tasks == 40)
+        pool = make_pool(gc, torch, n, n)
+        pool.upload(np.arange(n, dtype=np.uint32), x)
+        b = submit_gravity(pool, to, tg, so, sr)
+        pool.flush()
+        pool.wait(b)
+        vals = pool.values()                  # (rows, 4) FP64 s - c
+        ref = orc.reduce(tg, vals, n)
+        u = np.unique(tg)
+        got = pool.totals(u)
+        assert np.array_equal(got, ref[u]), n_tasks
+        pool.close()
+        if n_tasks == 40:   # the same batch captured: the capture run and a replay
+            pool = make_pool(gc, torch, n, n)
+            pool.upload(np.arange(n, dtype=np.uint32), x)
+            submit_gravity(pool, to, tg, so, sr)
+            g = gc.Graph(pool)
+            gref = orc.reduce(tg, gc.value(g.results()), n)
+            assert np.array_equal(pool.totals(u), gref[u])
+            pool.reset_totals()
+            g.launch()
+            g.wait()
+            assert np.array_equal(pool.totals(u), gref[u])
+            g.close()
+            pool.close()
