@@ -137,18 +137,22 @@ typedef struct {
 
 /* ---- pool lifetime and data -------------------------------------------- */
 
-/* Create a pool: device slots, the chare table (id -> slot), a pinned host
- * mirror holding the value of every id that is not resident (a slot's value
- * is written back to it when the id is evicted), and per-id FP64 totals.
+/* Create a pool (Section 2.2: the runtime keeps the data it has sent to the
+ * GPU; Section 3.2: the chare table maps chare buffers to device slots):
+ * device slots, the chare table (id -> slot), a pinned host mirror holding
+ * the value of every id that is not resident (a slot's value is written
+ * back to it when the id is evicted), and per-id FP64 totals.
  * *out receives the handle.  Errors: GC_ERR_ARG (zero capacities, eps2 <= 0, bad LJ values),
  * GC_ERR_OOM, GC_ERR_CUDA. */
 int gc_pool_create(const gc_config *cfg, gc_pool_t **out);
 
-/* Release everything the pool owns.  Waits for its stream first. */
+/* Release everything the pool owns (no counterpart in the paper: resource
+ * release).  Waits for its stream first. */
 int gc_pool_destroy(gc_pool_t *pool);
 
 /* Store values for ids (host arrays, n ids and 4n floats; copied before the
- * call returns).  A resident id is overwritten in its slot (an update, not a
+ * call returns) -- the chares' data regions (Section 3.2: data already on the
+ * GPU is not sent again).  A resident id is overwritten in its slot (an update, not a
  * miss); a non-resident id is stored in the host mirror and fetched at the
  * next flush that references it.  Duplicate ids in one call: one of the
  * values wins.  Runs on the pool's stream, after the pack of every batch
@@ -165,14 +169,16 @@ int gc_pool_upload_device(gc_pool_t *pool, const uint32_t *ids_dev,
 
 /* ---- batching ---------------------------------------------------------- */
 
-/* Append tasks to the pending batch (host descriptors; ids are copied).
+/* Append tasks to the pending batch (host descriptors; ids are copied): one
+ * workRequest per task, added to the list of combinable requests (Section
+ * 2.2's workGroupList; Section 3.1).
  * *batch_out (may be NULL) receives the index the next gc_flush will give
  * this batch.  Errors: GC_ERR_ARG (unknown kind, LJ_SELF with sources),
  * GC_ERR_BUDGET (one task's staging exceeds the budget), GC_ERR_OOM. */
 int gc_submit(gc_pool_t *pool, const gc_task *tasks, uint64_t n,
               uint64_t *batch_out);
 
-/* Append n_tasks tasks given as CSR arrays: task t has targets
+/* Append n_tasks workRequests (Sections 2.2, 3.1) given as CSR arrays: task t has targets
  * tgt_ids[tgt_off[t] .. tgt_off[t+1]) and sources src_ids[src_off[t] ..
  * src_off[t+1]), kind kinds[t], shift shifts[3t..3t+2] (may be NULL: all
  * zero), tag task_ids[t] (NULL: running task counter).  on_device = 0:
@@ -188,7 +194,9 @@ int gc_submit_csr(gc_pool_t *pool, uint64_t n_tasks, const uint64_t *task_ids,
                   uint64_t n_tgt_total, uint64_t n_src_total, int on_device,
                   uint64_t *batch_out);
 
-/* Run the pending batch: residency (chare-table lookup, slot allocation in
+/* Run the pending batch as one combined execution (Section 2.2's
+ * workRequestCombined; Section 3.1): residency (chare-table lookup, Section
+ * 3.2; slot allocation in
  * ascending id order, eviction of the least recently used unreferenced ids
  * when the pool is full, fetch of misses from the host mirror), pack
  * (per list, entries in ascending (slot, list position) order gathered into
@@ -201,14 +209,18 @@ int gc_submit_csr(gc_pool_t *pool, uint64_t n_tasks, const uint64_t *task_ids,
 int gc_flush(gc_pool_t *pool);
 
 /* Wait until batch `batch` (as returned by the submit calls) has completed,
- * for at most timeout_ns (0 = forever).  GC_ERR_TIMEOUT if it has not. */
+ * for at most timeout_ns (0 = forever) -- the runtime's monitoring of kernel
+ * status before it notifies the chares (Section 2.2).  GC_ERR_TIMEOUT if it
+ * has not. */
 int gc_wait(gc_pool_t *pool, uint64_t batch, uint64_t timeout_ns);
 
-/* Non-blocking completion check of batch `batch`: *done_out = 1 once it has
- * completed (0 while it runs or has not been flushed). */
+/* Non-blocking completion check of batch `batch` (Section 2.2: periodic
+ * monitoring of the kernels' status): *done_out = 1 once it has completed (0
+ * while it runs or has not been flushed). */
 int gc_batch_done(gc_pool_t *pool, uint64_t batch, int *done_out);
 
-/* Make `stream` (a cudaStream_t; NULL = the legacy default stream) wait for
+/* (No counterpart in the paper: stream interoperation.)  Make `stream` (a
+ * cudaStream_t; NULL = the legacy default stream) wait for
  * all work the pool has issued so far: every batch in flight and anything
  * queued on the pool's streams.  No host wait. */
 int gc_join(gc_pool_t *pool, void *stream);
@@ -219,7 +231,8 @@ int gc_join(gc_pool_t *pool, void *stream);
 
 /* ---- results ----------------------------------------------------------- */
 
-/* Number of result rows of the last completed batch: one per target, plus
+/* Results of a combined execution go back to the chares that issued the
+ * work requests (Section 2.2).  Number of result rows of the last completed batch: one per target, plus
  * one per source for GC_LJ_PAIR tasks (targets first), in admission order. */
 int gc_result_rows(gc_pool_t *pool, uint64_t *rows_out);
 
@@ -258,20 +271,24 @@ int gc_read_results(gc_pool_t *pool, const uint64_t *task_ids, uint64_t n,
                     float *partial_sum_comp);
 
 /* Per-id FP64 totals accumulated by every batch since the last reset:
- * 4 doubles per id (sum over the id's result rows of s - c). */
+ * 4 doubles per id (sum over the id's result rows of s - c) -- a particle's
+ * acceleration from all its buckets' work requests (Section 4.1), an atom's
+ * force from every cell-pair task that updates both patches (Section 4.2). */
 int gc_read_totals(gc_pool_t *pool, const uint32_t *ids, uint64_t n,
                    double *acc4);
 
 /* Device address of the totals array (double4 per id, id_capacity rows). */
 int gc_totals_device(gc_pool_t *pool, const double **totals_dev);
 
-/* Zero all per-id totals.  Takes effect before the next batch's scatter
+/* (No counterpart in the paper.)  Zero all per-id totals.  Takes effect before the next batch's scatter
  * (and before any read of the totals, graph replay or kick-drift), so work
  * issued in between -- uploads, task builds -- does not wait for the batches
  * still running. */
 int gc_reset_totals(gc_pool_t *pool);
 
-/* Counters since creation plus details of the last flush. */
+/* Counters since creation plus details of the last flush: among them the
+ * data-reuse figures of Section 3.2 (distinct ids, hits, misses, reuse
+ * histogram). */
 int gc_stats(gc_pool_t *pool, gc_stats_t *out);
 
 /* Human-readable text for a status code (static string). */
