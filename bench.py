@@ -53,8 +53,9 @@ PACK_BYTES_PER_ENTRY = 40
 # profiles/k_gravity_nbody262k.md: 502.6 MB for 2.949e8 interactions (262,144-particle
 # step, k_gravity<128, 32>, the tuned tile shape)
 GRAVITY_DRAM_BYTES_PER_INTERACTION = 502.6e6 / 2.949e8
-# profiles/k_pack_mid_nbody262k.md: 629.7 MB for 3.07e7 entries (262,144-particle step)
-PACK_DRAM_BYTES_PER_ENTRY = 629.7e6 / 3.07e7
+# profiles/k_pack_mid_nbody262k.md: 629.6 MB for 3.07e7 entries (262,144-particle step,
+# the chunked block sort)
+PACK_DRAM_BYTES_PER_ENTRY = 629.6e6 / 3.07e7
 # Algorithmic bytes of the per-id accumulation: a row's 32-byte compensated
 # partial and its 4-byte id read, the id's FP64 total (32 B) read and written;
 # the per-cell MD form derives ids from the task structure (no id read).

@@ -151,7 +151,10 @@ __global__ void k_compact_write(CompactArgs a, const uint32_t *tile_off, uint32_
 // entries (neighbouring tasks share many ids: the far tree nodes appear in
 // almost every list), aggregates reference counts in a small shared-memory
 // hash table and adds them to the global counters once per block; ids that
-// do not find a table slot fall back to global atomics.  With `ent` set, the
+// do not find a table slot fall back to global atomics.  Only the thread
+// that enters an id into the table (or finds no place for it) reads and
+// moves the id's reference word: a chunk of 8192 N-body entries holds about
+// 1900 distinct ids.  With `ent` set, the
 // entry's current slot is recorded too (wave-local entry order: targets,
 // then sources; NONE for an id not resident yet): the slot is read beside
 // the reference word, in parallel with it, so the pack that follows reads
@@ -187,16 +190,36 @@ __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, ui
             bad = true;
             continue;
         }
-        const uint32_t e0 = ref_epoch[id];   // one word: uploaded? referenced this wave?
         if (ent) ent[e] = slot_of_id[id];
-        if (e0 == GC_EPOCH_UNKNOWN) {
-            bad = true;
-            continue;
+        // count the reference in the block's table; the thread that puts the
+        // id there (or finds no place for it) marks it, the others skip it
+        uint32_t h = (id * 2654435761u) >> (32 - MARK_HASH_BITS);   // top bits of the product
+        bool counted = false, inserted = false;
+        for (int probe = 0; probe < 8; ++probe) {
+            uint32_t k = hkey[h];
+            if (k == GC_NONE) {
+                k = atomicCAS(&hkey[h], GC_NONE, id);
+                inserted = k == GC_NONE;
+            }
+            if (k == GC_NONE || k == id) {
+                atomicAdd(&hcnt[h], 1u);
+                counted = true;
+                break;
+            }
+            h = (h + 1) & (MARK_HASH - 1);
         }
         bool is_first = false;
-        if (e0 != epoch) {
-            if (first) is_first = atomicExch(&ref_epoch[id], epoch) != epoch;
-            else ref_epoch[id] = epoch;
+        bool known = true;
+        if (inserted || !counted) {
+            const uint32_t e0 = ref_epoch[id];   // one word: uploaded? referenced this wave?
+            if (e0 == GC_EPOCH_UNKNOWN) {
+                bad = true;
+                known = false;
+                if (counted) atomicOr(&hcnt[h], 0x80000000u);   // never uploaded: not counted
+            } else if (e0 != epoch) {
+                if (first) is_first = atomicExch(&ref_epoch[id], epoch) != epoch;
+                else ref_epoch[id] = epoch;
+            }
         }
         if (first) {
             // one counter add per warp for the ids it sees first
@@ -210,24 +233,12 @@ __global__ void k_mark(const uint32_t *tgt, uint64_t nt, const uint32_t *src, ui
                 if (is_first) first[at + __popc(fm & ((1u << lane) - 1u))] = id;
             }
         }
-        uint32_t h = (id * 2654435761u) >> (32 - MARK_HASH_BITS);   // top bits of the product
-        bool done = false;
-        for (int probe = 0; probe < 8; ++probe) {
-            uint32_t k = hkey[h];
-            if (k == GC_NONE) k = atomicCAS(&hkey[h], GC_NONE, id);
-            if (k == GC_NONE || k == id) {
-                atomicAdd(&hcnt[h], 1u);
-                done = true;
-                break;
-            }
-            h = (h + 1) & (MARK_HASH - 1);
-        }
-        if (!done) atomicAdd(&ref_count[id], 1u);
+        if (!counted && known) atomicAdd(&ref_count[id], 1u);
     }
     if (bad) atomicOr(&ctr[CTR_FLAGS], (unsigned long long)GC_FLAG_UNKNOWN_ID);
     __syncthreads();
     for (int i = threadIdx.x; i < MARK_HASH; i += blockDim.x)
-        if (hkey[i] != GC_NONE) atomicAdd(&ref_count[hkey[i]], hcnt[i]);
+        if (hkey[i] != GC_NONE && !(hcnt[i] & 0x80000000u)) atomicAdd(&ref_count[hkey[i]], hcnt[i]);
 }
 
 __device__ __forceinline__ int hist_bin(uint32_t c)
