@@ -895,21 +895,27 @@ constexpr int WALK_RANGES = 16;   // preorder ranges of the walk (at most)
 // The preorder ranges of the walk: range r = [klo[r], klo[r + 1]), equal
 // node counts; for each range start its strict ancestors (root first), so a
 // walk of the range knows where in it a bucket's own walk resumes.
+// Range r starts at node k0 = r nn / M; its strict ancestors, root first, at
+// most WALK_ANC of them.  Node j is a strict ancestor of k0 iff j < k0 <
+// j + size(j), and a node's level is its depth (children are one level
+// below their parent), so the ancestor at depth d is the one of level d and
+// k0 has level(k0) of them: every (range, node) pair is tested on its own.
 __global__ void k_walk_ranges(const uint4 *W, uint32_t nn, uint32_t M, uint32_t *klo,
                               uint32_t *anc, uint32_t *nanc)
 {
-    GRID_STRIDE(r, (uint64_t)M + 1) {
+    GRID_STRIDE(t, (uint64_t)M * nn) {
+        const uint32_t r = (uint32_t)(t / nn), j = (uint32_t)(t - (uint64_t)r * nn);
         const uint32_t k0 = (uint32_t)((uint64_t)r * nn / M);
-        klo[r] = k0;
-        if (r == M) continue;
-        uint32_t j = 0, d = 0;
-        while (j != k0 && d < WALK_ANC) {
-            anc[r * WALK_ANC + d++] = j;
-            uint32_t c = j + 1;          // the child of j whose subtree holds k0
-            while (c + (W[c].x & 0x7FFFFFFFu) <= k0) c += W[c].x & 0x7FFFFFFFu;
-            j = c;
+        if (j == 0) {
+            klo[r] = k0;
+            nanc[r] = min(W[k0].y >> 22, (uint32_t)WALK_ANC);
+            if (r == 0) klo[M] = nn;
         }
-        nanc[r] = d;
+        if (j < k0) {
+            const uint4 R = W[j];
+            const uint32_t l = R.y >> 22;
+            if (j + (R.x & 0x7FFFFFFFu) > k0 && l < (uint32_t)WALK_ANC) anc[r * WALK_ANC + l] = j;
+        }
     }
 }
 
@@ -1325,7 +1331,7 @@ extern "C" int gc_build_nbody_tasks(gc_pool_t *p, const float *xyzm_dev, uint64_
     k_walk_nodes<<<grid_for((uint64_t)NN + 1, 256, maxb), 256, 0, s>>>(
         S.node_a.as<uint4>(), S.node_b.as<uint4>(), NN, W, LF);
     ++p->stats.kernel_launches;
-    k_walk_ranges<<<grid_for((uint64_t)M + 1, 64, maxb), 64, 0, s>>>(W, NN, M, klo, anc, nanc);
+    k_walk_ranges<<<grid_for((uint64_t)M * NN, 256, maxb), 256, 0, s>>>(W, NN, M, klo, anc, nanc);
     GC_TRY(S.list_off.reserve((NI + 1) * 8 * 2 + ((uint64_t)NB + 1) * 8));
     GC_TRY(S.win.reserve((NI + 1) * 4));   // reused: (bucket, range) list lengths
     uint32_t *llen = S.win.as<uint32_t>();
