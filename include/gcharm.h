@@ -161,6 +161,15 @@ int gc_pool_destroy(gc_pool_t *pool);
 int gc_pool_upload(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
                    uint64_t n);
 
+/* As gc_pool_upload, in stream order: returns once the copies are queued
+ * (the ids are checked on the host first).  The host arrays must stay
+ * unchanged until the pool's stream has passed this point (gc_join, then a
+ * wait on the joined stream); with pinned host memory the copies overlap
+ * the pool's device work.  Errors: GC_ERR_ARG (id >= id_capacity; nothing
+ * is queued), GC_ERR_OOM, GC_ERR_CUDA. */
+int gc_pool_upload_async(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
+                         uint64_t n);
+
 /* As gc_pool_upload, with device arrays, in stream order (no host wait).
  * Ids are not checked on the host; an id >= id_capacity sets the pool's
  * device error flag and is skipped (reported by the next flush). */
@@ -276,6 +285,13 @@ int gc_read_results(gc_pool_t *pool, const uint64_t *task_ids, uint64_t n,
  * force from every cell-pair task that updates both patches (Section 4.2). */
 int gc_read_totals(gc_pool_t *pool, const uint32_t *ids, uint64_t n,
                    double *acc4);
+
+/* As gc_read_totals, in stream order: the totals as of every batch flushed
+ * so far are copied to acc4 once the pool's stream passes this point
+ * (gc_join, then a wait on the joined stream); ids and acc4 must stay valid
+ * until then (pinned host memory lets the copies overlap device work).
+ * Errors: GC_ERR_ARG, GC_ERR_OOM, GC_ERR_CUDA. */
+int gc_read_totals_async(gc_pool_t *pool, const uint32_t *ids, uint64_t n, double *acc4);
 
 /* Device address of the totals array (double4 per id, id_capacity rows). */
 int gc_totals_device(gc_pool_t *pool, const double **totals_dev);

@@ -153,13 +153,16 @@ static void free_pool(gc_pool *p)
                     &p->nb.node_b, &p->nb.node_val, &p->nb.bucket, &p->nb.bbox,
                     &p->nb.list_off, &p->nb.list_len, &p->nb.list, &p->nb.bounds,
                     &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->nb.wnode, &p->nb.seed_tiles,
-                    &p->nb.seed_a, &p->nb.seed_m, &p->nb.seed_key, &p->md.hostcopy,
+                    &p->nb.seed_a, &p->nb.seed_m, &p->nb.seed_key, &p->au_ids, &p->au_vals,
+                    &p->at_ids, &p->at_out, &p->md.hostcopy,
                     &p->md.keys,
                     &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
                     &p->md.cnt_s, &p->md.cub_tmp};
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t &e : p->nb.ev)
         if (e) cudaEventDestroy(e);
+    if (p->ev_au) cudaEventDestroy(p->ev_au);
+    if (p->ev_at) cudaEventDestroy(p->ev_at);
     for (int i = 0; i < 2; ++i) free_ctx(p->ctx[i]);
     delete p;
 }
@@ -418,6 +421,29 @@ int gc_pool_upload(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_
     if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
     p->stats.h2d_bytes += n * (sizeof(uint32_t) + sizeof(float4));
     return rc;
+}
+
+int gc_pool_upload_async(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_t n)
+{
+    if (!p || (n && (!ids || !xyzm))) return GC_ERR_ARG;
+    if (n == 0) return GC_OK;
+    uint32_t bad = 0;
+    for (uint64_t i = 0; i < n; ++i) bad |= (uint64_t)ids[i] >= p->cfg.id_capacity;
+    if (bad) return GC_ERR_ARG;
+    if (!p->ev_au) GC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_au, cudaEventDisableTiming));
+    // the previous asynchronous upload has read its device copies
+    if (p->au_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_au, 0));
+    GC_TRY(grow_keep(p->au_ids, n * sizeof(uint32_t) + 16, 0, p->s));
+    GC_TRY(grow_keep(p->au_vals, n * sizeof(float4) + 16, 0, p->s));
+    GC_CUDA_TRY(cudaMemcpyAsync(p->au_ids.p, ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                p->s));
+    GC_CUDA_TRY(cudaMemcpyAsync(p->au_vals.p, xyzm, n * sizeof(float4), cudaMemcpyHostToDevice,
+                                p->s));
+    GC_TRY(gc_launch_upload(p, p->au_ids.as<uint32_t>(), p->au_vals.as<float4>(), n, 1));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_au, p->s));
+    p->au_used = true;
+    p->stats.h2d_bytes += n * (sizeof(uint32_t) + sizeof(float4));
+    return GC_OK;
 }
 
 int gc_pool_upload_device(gc_pool_t *p, const uint32_t *ids_dev, const float *xyzm_dev,
@@ -973,6 +999,31 @@ int gc_read_totals(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
             rc = GC_ERR_CUDA;
     }
     return rc;
+}
+
+int gc_read_totals_async(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *acc4)
+{
+    if (!p || (n && (!ids || !acc4))) return GC_ERR_ARG;
+    if (n == 0) return GC_OK;
+    GC_TRY(order_after_scatters(p));
+    GC_TRY(gc_apply_totals_reset(p, p->s));
+    if (!p->ev_at) GC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_at, cudaEventDisableTiming));
+    // the previous asynchronous read has copied its results out
+    if (p->at_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_at, 0));
+    GC_TRY(grow_keep(p->at_ids, n * 4 + 16, 0, p->s));
+    GC_TRY(grow_keep(p->at_out, n * sizeof(gcd4) + 32, 0, p->s));
+    GC_CUDA_TRY(cudaMemcpyAsync(p->at_ids.p, ids, n * 4, cudaMemcpyHostToDevice, p->s));
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (g > 65535u * 8) g = 65535u * 8;
+    ++p->stats.kernel_launches;
+    k_gather_totals<<<g, 256, 0, p->s>>>(p->d_totals, p->at_ids.as<uint32_t>(), n,
+                                         p->cfg.id_capacity, p->at_out.as<gcd4>());
+    GC_CUDA_TRY(cudaGetLastError());
+    GC_CUDA_TRY(cudaMemcpyAsync(acc4, p->at_out.p, n * sizeof(gcd4), cudaMemcpyDeviceToHost,
+                                p->s));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_at, p->s));
+    p->at_used = true;
+    return GC_OK;
 }
 
 int gc_totals_device(gc_pool_t *p, const double **totals_dev)

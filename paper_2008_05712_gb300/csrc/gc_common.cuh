@@ -205,6 +205,12 @@ struct gc_pool {
     // residency work buffers (the chare-table step is serialised)
     DBuf uniq, miss, miss_sorted, freel, tiles, ekeys, ekeys2, evicted, cub_tmp;
     DBuf io_a, io_b;                  // host <-> device staging of uploads and reads
+    // stream-ordered uploads and totals reads (gc_pool_upload_async,
+    // gc_read_totals_async): own device buffers, and the event after each
+    // one's last use, which the next one's stream waits for
+    DBuf au_ids, au_vals, at_ids, at_out;
+    cudaEvent_t ev_au = nullptr, ev_at = nullptr;
+    bool au_used = false, at_used = false;
     uint64_t n_evicted_last = 0;
     uint32_t epoch = 0;
 

@@ -154,6 +154,8 @@ _SIGS = {
     "gc_read_batch_rows": [P, U64, U64, U64, P],
     "gc_read_results": [P, P, U64, P],
     "gc_read_totals": [P, P, U64, P],
+    "gc_read_totals_async": [P, P, U64, P],
+    "gc_pool_upload_async": [P, P, P, U64],
     "gc_totals_device": [P, C.POINTER(P)],
     "gc_reset_totals": [P],
     "gc_stats": [P, C.POINTER(GcStats)],
@@ -278,6 +280,20 @@ class Pool:
         x = np.ascontiguousarray(xyzm, np.float32)
         assert x.shape == (ids.shape[0], 4)
         _check(self.lib.gc_pool_upload(self.h, _p(ids), _p(x), ids.shape[0]), "gc_pool_upload")
+
+    def upload_async(self, ids, xyzm):
+        """gc_pool_upload_async: the copies are queued on the pool's stream and
+        read later, so the arrays (uint32 ids, float32 (n, 4) values, C-contiguous,
+        best in pinned memory) must stay alive and unchanged until the pool's
+        work is joined and waited for.  No temporary copies are made."""
+        if (not isinstance(ids, np.ndarray) or ids.dtype != np.uint32 or
+                not ids.flags["C_CONTIGUOUS"]):
+            raise ValueError("ids must be a C-contiguous uint32 array")
+        if (not isinstance(xyzm, np.ndarray) or xyzm.dtype != np.float32 or
+                xyzm.shape != (ids.shape[0], 4) or not xyzm.flags["C_CONTIGUOUS"]):
+            raise ValueError("xyzm must be a C-contiguous float32 array of shape (n, 4)")
+        _check(self.lib.gc_pool_upload_async(self.h, _p(ids), _p(xyzm), ids.shape[0]),
+               "gc_pool_upload_async")
 
     def upload_device(self, ids_t, xyzm_t):
         _check(self.lib.gc_pool_upload_device(self.h, _dptr(ids_t), _dptr(xyzm_t),
@@ -428,6 +444,20 @@ class Pool:
               not out.flags["C_CONTIGUOUS"]):
             raise ValueError("out must be a C-contiguous float64 array of shape (n, 4)")
         _check(self.lib.gc_read_totals(self.h, _p(ids), ids.shape[0], _p(out)), "gc_read_totals")
+        return out
+
+    def totals_async(self, ids, out):
+        """gc_read_totals_async: `out` (C-contiguous float64 (n, 4), best in
+        pinned memory) is filled once the pool's work is joined and waited
+        for; ids (C-contiguous uint32) and out must stay alive until then."""
+        if (not isinstance(ids, np.ndarray) or ids.dtype != np.uint32 or
+                not ids.flags["C_CONTIGUOUS"]):
+            raise ValueError("ids must be a C-contiguous uint32 array")
+        if (out.dtype != np.float64 or out.shape != (ids.shape[0], 4) or
+                not out.flags["C_CONTIGUOUS"]):
+            raise ValueError("out must be a C-contiguous float64 array of shape (n, 4)")
+        _check(self.lib.gc_read_totals_async(self.h, _p(ids), ids.shape[0], _p(out)),
+               "gc_read_totals_async")
         return out
 
     def totals_device_ptr(self):

@@ -319,3 +319,46 @@ def test_per_id_totals_exact_small_and_large_batches(gc, orc):
             assert np.array_equal(pool.totals(u), gref[u])
             g.close()
             pool.close()
+
+
+def test_async_upload_and_totals_read_match_sync(gc):
+    """Uploads and totals reads queued in stream order (the host waits once,
+    at the end) give the same per-id totals, step by step, as the
+    synchronous calls."""
+    n = 6000
+    ids = np.arange(n, dtype=np.uint32)
+    xs = [inputs.plummer(n, inputs.SEED_BASE + 31)]
+    for k in range(2):
+        xs.append(inputs.drift(xs[-1], inputs.SEED_BASE + 32 + k))
+    ps = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    pa = make_pool(gc, torch, 3 * n + 64, 3 * n + 64)
+    sync_tot = []
+    for x in xs:
+        ps.upload(ids, x)
+        ps.reset_totals()
+        ps.build_nbody_resident(n, 32, 7, 10)
+        ps.flush()
+        sync_tot.append(ps.totals(ids))
+    outs = [np.zeros((n, 4), np.float64) for _ in xs]
+    hx = [np.ascontiguousarray(x, np.float32) for x in xs]
+    for k, x in enumerate(hx):
+        pa.upload_async(ids, x)
+        pa.reset_totals()
+        pa.build_nbody_resident(n, 32, 7, 10)
+        pa.flush()
+        pa.totals_async(ids, outs[k])
+    pa.join(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for k in range(len(xs)):
+        assert np.array_equal(outs[k], sync_tot[k]), k
+    bad = ids.copy()
+    bad[7] = 10 * n
+    with pytest.raises(gc.GcError) as e:
+        pa.upload_async(bad, hx[0])
+    assert e.value.code == gc.GC_ERR_ARG
+    with pytest.raises(ValueError):
+        pa.upload_async(ids.astype(np.int64), hx[0])
+    with pytest.raises(ValueError):
+        pa.totals_async(ids, np.zeros((n, 4), np.float32))
+    ps.close()
+    pa.close()
