@@ -161,12 +161,13 @@ int gc_pool_destroy(gc_pool_t *pool);
 int gc_pool_upload(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
                    uint64_t n);
 
-/* As gc_pool_upload, in stream order: returns once the copies are queued
- * (the ids are checked on the host first).  The host arrays must stay
- * unchanged until the pool's stream has passed this point (gc_join, then a
- * wait on the joined stream); with pinned host memory the copies overlap
- * the pool's device work.  Errors: GC_ERR_ARG (id >= id_capacity; nothing
- * is queued), GC_ERR_OOM, GC_ERR_CUDA. */
+/* As gc_pool_upload, in stream order: returns once the copies are queued.
+ * The host arrays must stay unchanged until the pool's stream has passed
+ * this point (gc_join, then a wait on the joined stream); with pinned host
+ * memory the copies overlap the pool's device work.  Ids are checked on the
+ * device, as by gc_pool_upload_device: an id >= id_capacity is skipped and
+ * makes the next flush fail with GC_ERR_UNKNOWN_ID.  Errors: GC_ERR_ARG
+ * (null arrays), GC_ERR_OOM, GC_ERR_CUDA. */
 int gc_pool_upload_async(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
                          uint64_t n);
 

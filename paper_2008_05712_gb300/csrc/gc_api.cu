@@ -427,9 +427,6 @@ int gc_pool_upload_async(gc_pool_t *p, const uint32_t *ids, const float *xyzm, u
 {
     if (!p || (n && (!ids || !xyzm))) return GC_ERR_ARG;
     if (n == 0) return GC_OK;
-    uint32_t bad = 0;
-    for (uint64_t i = 0; i < n; ++i) bad |= (uint64_t)ids[i] >= p->cfg.id_capacity;
-    if (bad) return GC_ERR_ARG;
     if (!p->ev_au) GC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_au, cudaEventDisableTiming));
     // the previous asynchronous upload has read its device copies
     if (p->au_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_au, 0));
