@@ -902,8 +902,8 @@ def main():
     ids_pin, tot_pin = ids_pin_t.numpy(), tot_pin_t.numpy()
     torch.cuda.synchronize()
     # every step copies its inputs in and reads its totals out; the copies
-    # are queued on the pool's stream (pinned buffers, two alternating
-    # result buffers) and the host waits once, at the end
+    # are queued on the pool's two copy streams (pinned buffers, two
+    # alternating result buffers) and the host waits once, at the end
     t0 = time.perf_counter()
     for k in range(K):
         pool.upload_async(ids_pin, hx[k])        # ids + values H2D
@@ -918,8 +918,9 @@ def main():
     e2e = {"value": interactions / K * K / e2e_s if K else 0.0, "unit": "interactions/s",
            "h2d_bytes_per_step": int(n * (4 + 16 + 4)),
            "d2h_bytes_per_step": int(tot_pin[0].nbytes),
-           "copies": "queued each step on the pool's stream (gc_pool_upload_async, "
-                     "gc_read_totals_async), one host wait at the end",
+           "copies": "queued each step (gc_pool_upload_async, gc_read_totals_async) on "
+                     "the pool's host-to-device and device-to-host copy streams, in "
+                     "order with its device work by events; one host wait at the end",
            "last_totals_equal_sync_read": last_ok}
     if ws > 1:
         e2e_max, _ = reduce_over_ranks(e2e_s, 0, "cuda")

@@ -163,8 +163,11 @@ int gc_pool_upload(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
 
 /* As gc_pool_upload, in stream order: returns once the copies are queued.
  * The host arrays must stay unchanged until the pool's stream has passed
- * this point (gc_join, then a wait on the joined stream); with pinned host
- * memory the copies overlap the pool's device work.  Ids are checked on the
+ * this point (gc_join, then a wait on the joined stream).  The copies run
+ * on a host-to-device stream of the pool's own and wait only for the
+ * previous asynchronous upload to be applied, so with pinned host memory they
+ * overlap the batches still running; the upload itself is applied in the
+ * pool's stream order.  Ids are checked on the
  * device, as by gc_pool_upload_device: an id >= id_capacity is skipped and
  * makes the next flush fail with GC_ERR_UNKNOWN_ID.  Errors: GC_ERR_ARG
  * (null arrays), GC_ERR_OOM, GC_ERR_CUDA. */
@@ -290,7 +293,9 @@ int gc_read_totals(gc_pool_t *pool, const uint32_t *ids, uint64_t n,
 /* As gc_read_totals, in stream order: the totals as of every batch flushed
  * so far are copied to acc4 once the pool's stream passes this point
  * (gc_join, then a wait on the joined stream); ids and acc4 must stay valid
- * until then (pinned host memory lets the copies overlap device work).
+ * until then.  The totals are gathered in the pool's stream order; the copy
+ * to acc4 runs on a device-to-host stream of the pool's own, so with pinned
+ * host memory it overlaps the work queued after it (gc_join waits for it).
  * Errors: GC_ERR_ARG, GC_ERR_OOM, GC_ERR_CUDA. */
 int gc_read_totals_async(gc_pool_t *pool, const uint32_t *ids, uint64_t n, double *acc4);
 

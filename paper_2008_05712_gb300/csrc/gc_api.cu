@@ -134,6 +134,8 @@ void free_ctx(FlushCtx &c)
 static void free_pool(gc_pool *p)
 {
     if (!p) return;
+    for (cudaStream_t cs : {p->cs_in, p->cs_out})
+        if (cs) cudaStreamSynchronize(cs);
     cudaFree(p->d_pool);
     cudaFree(p->d_slot_of_id);
     cudaFree(p->d_id_of_slot);
@@ -161,8 +163,10 @@ static void free_pool(gc_pool *p)
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t &e : p->nb.ev)
         if (e) cudaEventDestroy(e);
-    if (p->ev_au) cudaEventDestroy(p->ev_au);
-    if (p->ev_at) cudaEventDestroy(p->ev_at);
+    for (cudaEvent_t e : {p->ev_au, p->ev_au_in, p->ev_at_in, p->ev_at_g, p->ev_at})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t cs : {p->cs_in, p->cs_out})
+        if (cs) cudaStreamDestroy(cs);
     for (int i = 0; i < 2; ++i) free_ctx(p->ctx[i]);
     delete p;
 }
@@ -423,19 +427,33 @@ int gc_pool_upload(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_
     return rc;
 }
 
+// Copy streams and events of the stream-ordered upload and totals read.
+static int async_init(gc_pool *p)
+{
+    for (cudaStream_t *cs : {&p->cs_in, &p->cs_out})
+        if (!*cs) GC_CUDA_TRY(cudaStreamCreateWithFlags(cs, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&p->ev_au, &p->ev_au_in, &p->ev_at_in, &p->ev_at_g, &p->ev_at})
+        if (!*e) GC_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return GC_OK;
+}
+
 int gc_pool_upload_async(gc_pool_t *p, const uint32_t *ids, const float *xyzm, uint64_t n)
 {
     if (!p || (n && (!ids || !xyzm))) return GC_ERR_ARG;
     if (n == 0) return GC_OK;
-    if (!p->ev_au) GC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_au, cudaEventDisableTiming));
-    // the previous asynchronous upload has read its device copies
-    if (p->au_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_au, 0));
+    GC_TRY(async_init(p));
+    // a reallocation frees the old buffers, which waits for the device
     GC_TRY(grow_keep(p->au_ids, n * sizeof(uint32_t) + 16, 0, p->s));
     GC_TRY(grow_keep(p->au_vals, n * sizeof(float4) + 16, 0, p->s));
+    // the copies wait only for the previous upload kernel to have read the
+    // buffers, not for the batches queued on the pool's stream
+    if (p->au_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_au, 0));
     GC_CUDA_TRY(cudaMemcpyAsync(p->au_ids.p, ids, n * sizeof(uint32_t), cudaMemcpyHostToDevice,
-                                p->s));
+                                p->cs_in));
     GC_CUDA_TRY(cudaMemcpyAsync(p->au_vals.p, xyzm, n * sizeof(float4), cudaMemcpyHostToDevice,
-                                p->s));
+                                p->cs_in));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_au_in, p->cs_in));
+    GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_au_in, 0));
     GC_TRY(gc_launch_upload(p, p->au_ids.as<uint32_t>(), p->au_vals.as<float4>(), n, 1));
     GC_CUDA_TRY(cudaEventRecord(p->ev_au, p->s));
     p->au_used = true;
@@ -835,6 +853,8 @@ int gc_join(gc_pool_t *p, void *stream)
     for (int i = 0; i < 2; ++i)
         if (p->ctx[i].ev_done && p->ctx[i].s != s)
             GC_CUDA_TRY(cudaStreamWaitEvent(s, p->ctx[i].ev_done, 0));
+    // the last stream-ordered totals read's copy out
+    if (p->at_used) GC_CUDA_TRY(cudaStreamWaitEvent(s, p->ev_at, 0));
     if (p->s != s) {
         // work issued on the pool's stream after the last flush (uploads,
         // task builds, graph replays)
@@ -1002,23 +1022,32 @@ int gc_read_totals_async(gc_pool_t *p, const uint32_t *ids, uint64_t n, double *
 {
     if (!p || (n && (!ids || !acc4))) return GC_ERR_ARG;
     if (n == 0) return GC_OK;
+    GC_TRY(async_init(p));
     GC_TRY(order_after_scatters(p));
     GC_TRY(gc_apply_totals_reset(p, p->s));
-    if (!p->ev_at) GC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_at, cudaEventDisableTiming));
-    // the previous asynchronous read has copied its results out
-    if (p->at_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_at, 0));
     GC_TRY(grow_keep(p->at_ids, n * 4 + 16, 0, p->s));
     GC_TRY(grow_keep(p->at_out, n * sizeof(gcd4) + 32, 0, p->s));
-    GC_CUDA_TRY(cudaMemcpyAsync(p->at_ids.p, ids, n * 4, cudaMemcpyHostToDevice, p->s));
+    // ids in: after the previous gather has read at_ids
+    if (p->at_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_at_g, 0));
+    GC_CUDA_TRY(cudaMemcpyAsync(p->at_ids.p, ids, n * 4, cudaMemcpyHostToDevice, p->cs_in));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_at_in, p->cs_in));
+    // gather on the pool's stream (after every scatter queued so far, before
+    // any later one): after the ids are in and the previous totals copied out
+    GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_at_in, 0));
+    if (p->at_used) GC_CUDA_TRY(cudaStreamWaitEvent(p->s, p->ev_at, 0));
     unsigned g = (unsigned)((n + 255) / 256);
     if (g > 65535u * 8) g = 65535u * 8;
     ++p->stats.kernel_launches;
     k_gather_totals<<<g, 256, 0, p->s>>>(p->d_totals, p->at_ids.as<uint32_t>(), n,
                                          p->cfg.id_capacity, p->at_out.as<gcd4>());
     GC_CUDA_TRY(cudaGetLastError());
+    GC_CUDA_TRY(cudaEventRecord(p->ev_at_g, p->s));
+    // totals out on their own stream: the work queued next on the pool's
+    // stream does not wait for this copy
+    GC_CUDA_TRY(cudaStreamWaitEvent(p->cs_out, p->ev_at_g, 0));
     GC_CUDA_TRY(cudaMemcpyAsync(acc4, p->at_out.p, n * sizeof(gcd4), cudaMemcpyDeviceToHost,
-                                p->s));
-    GC_CUDA_TRY(cudaEventRecord(p->ev_at, p->s));
+                                p->cs_out));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_at, p->cs_out));
     p->at_used = true;
     return GC_OK;
 }

@@ -206,10 +206,17 @@ struct gc_pool {
     DBuf uniq, miss, miss_sorted, freel, tiles, ekeys, ekeys2, evicted, cub_tmp;
     DBuf io_a, io_b;                  // host <-> device staging of uploads and reads
     // stream-ordered uploads and totals reads (gc_pool_upload_async,
-    // gc_read_totals_async): own device buffers, and the event after each
-    // one's last use, which the next one's stream waits for
+    // gc_read_totals_async): own device buffers, and one copy stream per
+    // direction, so that a step's input copies overlap the batch before it
+    // and its totals copy the tree build after it; events order each copy
+    // or kernel after the last use of the buffer it overwrites
     DBuf au_ids, au_vals, at_ids, at_out;
-    cudaEvent_t ev_au = nullptr, ev_at = nullptr;
+    cudaStream_t cs_in = nullptr, cs_out = nullptr;
+    cudaEvent_t ev_au = nullptr;      // upload kernel has read au_*
+    cudaEvent_t ev_au_in = nullptr;   // au_* copied in
+    cudaEvent_t ev_at_in = nullptr;   // at_ids copied in
+    cudaEvent_t ev_at_g = nullptr;    // gather has read at_ids and written at_out
+    cudaEvent_t ev_at = nullptr;      // at_out copied out
     bool au_used = false, at_used = false;
     uint64_t n_evicted_last = 0;
     uint32_t epoch = 0;
