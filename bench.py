@@ -722,7 +722,10 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=Tr
                 "mean_us": rep["lat_mean_us"] if lat_ok else None,
                 "interactions_per_s": rep["interactions_per_s"], "wall_s": rep["wall_s"],
                 "batches": rep["batches"], "mean_batch": rep["mean_batch"],
-                "max_size": rep["max_size"], "busy_s": rep["busy_s"]})
+                "max_size": rep["max_size"], "busy_s": rep["busy_s"],
+                "host_s": {"submit": rep["submit_s"], "flush": rep["flush_s"],
+                           "retire": rep["retire_s"]},
+                "pinned_bytes": rep["pinned_bytes"]})
     pool.close()
     return uneven, serving
 

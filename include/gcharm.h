@@ -550,6 +550,11 @@ typedef struct {
                                  slot (both flush contexts busy)              */
     uint64_t measured;        /* tasks in the latency statistics               */
     uint64_t unserved;        /* arrivals not served within the drain limit    */
+    uint64_t pinned_bytes;    /* bytes of tgt_ids and src_ids page-locked for
+                                 the call (already, or registered by it)      */
+    double submit_s;          /* host time in gc_submit_csr                    */
+    double flush_s;           /* host time in gc_flush                         */
+    double retire_s;          /* host time retiring completed batches          */
 } gc_serve_report;
 
 /* Replay an open-loop arrival schedule in real time on this thread: task t

@@ -83,18 +83,23 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     // are): the per-batch host-to-device copies then run as direct DMA
     // instead of through the driver's pageable staging
     std::vector<void *> pinned;
+    uint64_t pinned_bytes = 0;
     auto pin = [&](const void *ptr, uint64_t bytes) {
         if (!ptr || !bytes) return;
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, ptr) == cudaSuccess &&
-            at.type != cudaMemoryTypeUnregistered)
+            at.type != cudaMemoryTypeUnregistered) {
+            pinned_bytes += bytes;
             return;
+        }
         cudaGetLastError();
         if (cudaHostRegister(const_cast<void *>(ptr), bytes, cudaHostRegisterDefault) ==
-            cudaSuccess)
+            cudaSuccess) {
             pinned.push_back(const_cast<void *>(ptr));
-        else
+            pinned_bytes += bytes;
+        } else {
             cudaGetLastError();   // stays pageable: slower copies, same results
+        }
     };
     pin(tgt_ids, tgt_off[m] * sizeof(uint32_t));
     pin(src_ids, src_off[m] * sizeof(uint32_t));
@@ -105,6 +110,7 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     std::deque<InFlight> inflight;
     uint64_t next = 0, head = 0, done = 0;   // arrivals [0,next) queued from `head`
     uint64_t batches = 0, taken_total = 0, busy_ns = 0, last_iter = 0;
+    uint64_t submit_ns = 0, flush_ns = 0, retire_ns = 0;
     const uint64_t limit = cfg->timeout_ns ? cfg->timeout_ns : 60000000000ull;
     const uint64_t last_arrival = arrival_ns[n - 1];
     gc_stats_t s0;
@@ -122,6 +128,7 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
             ++next;
         }
         // retire completed batches, oldest first
+        const uint64_t r0 = now_ns();
         while (!inflight.empty()) {
             int fin = 0;
             rc = gc_batch_done(p, inflight.front().batch, &fin);
@@ -139,6 +146,7 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
             done += f.t1 - f.t0;
             inflight.pop_front();
         }
+        retire_ns += now_ns() - r0;
         if (rc != GC_OK) break;
         // past the drain limit: start nothing more, finish what runs
         const bool closed = cfg->drain_ns && next == n && now > last_arrival + cfg->drain_ns;
@@ -165,6 +173,7 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
                 }
                 // arrivals head .. t1-1: contiguous runs of the task arrays
                 uint64_t b_idx = 0;
+                const uint64_t s0_ns = now_ns();
                 for (uint64_t k = head; k < t1 && rc == GC_OK;) {
                     const uint64_t q0 = task_of(k);
                     const uint64_t len = std::min(t1 - k, m - q0);
@@ -180,7 +189,10 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
                                        0, 0, 0, &b_idx);
                     k += len;
                 }
+                const uint64_t f0_ns = now_ns();
+                submit_ns += f0_ns - s0_ns;
                 if (rc == GC_OK) rc = gc_flush(p);
+                flush_ns += now_ns() - f0_ns;
                 if (rc != GC_OK) break;
                 inflight.push_back(InFlight{b_idx, head, t1, now_ns() - start});
                 taken_total += t1 - head;
@@ -234,6 +246,10 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
     report->mean_batch = batches ? (double)taken_total / (double)batches : 0.0;
     report->busy_s = (double)busy_ns * 1e-9;
     report->max_size = max_size;
+    report->pinned_bytes = pinned_bytes;
+    report->submit_s = (double)submit_ns * 1e-9;
+    report->flush_s = (double)flush_ns * 1e-9;
+    report->retire_s = (double)retire_ns * 1e-9;
     if (latency_ns_out) std::memcpy(latency_ns_out, lat.data(), n * sizeof(uint64_t));
     return GC_OK;
 }

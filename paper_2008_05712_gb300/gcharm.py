@@ -84,13 +84,15 @@ class GcServeConfig(C.Structure):
 _SERVE_FIELDS = ["tasks", "batches", "interactions", "max_size"]
 _SERVE_DFIELDS = ["wall_s", "interactions_per_s", "lat_mean_us", "lat_p50_us", "lat_p99_us",
                   "lat_max_us", "mean_batch", "busy_s"]
-_SERVE_TAIL = ["measured", "unserved"]
+_SERVE_TAIL = ["measured", "unserved", "pinned_bytes"]
+_SERVE_HOST = ["submit_s", "flush_s", "retire_s"]
 
 
 class GcServeReport(C.Structure):
     _fields_ = ([(f, C.c_uint64) for f in _SERVE_FIELDS]
                 + [(f, C.c_double) for f in _SERVE_DFIELDS]
-                + [(f, C.c_uint64) for f in _SERVE_TAIL])
+                + [(f, C.c_uint64) for f in _SERVE_TAIL]
+                + [(f, C.c_double) for f in _SERVE_HOST])
 
 
 _NBODY_FIELDS = ["builds", "seeded_builds", "last_resorted", "timed_builds"]
@@ -425,7 +427,8 @@ class Pool:
         _check(self.lib.gc_serve(self.h, n, _p(arr), _p(kinds), _p(sh), _p(to), _p(tg), _p(so),
                                  _p(sr), C.byref(cfg), _p(lat), _p(rows), C.byref(rep)),
                "gc_serve")
-        d = {f: getattr(rep, f) for f in _SERVE_FIELDS + _SERVE_DFIELDS + _SERVE_TAIL}
+        d = {f: getattr(rep, f) for f in _SERVE_FIELDS + _SERVE_DFIELDS + _SERVE_TAIL
+             + _SERVE_HOST}
         return d, lat, rows
 
     def read_results(self, task_ids, n_rows):
