@@ -526,6 +526,9 @@ typedef struct {
     uint64_t static_n;        /* GC_COMBINE_STATIC: arrivals per combine       */
     uint64_t window;          /* GC_COMBINE_ADAPTIVE_WINDOW: intervals kept    */
     uint32_t max_in_flight;   /* batches on the device at once: 1 or 2         */
+    uint32_t keep_pageable;   /* 0: page-lock tgt_ids and src_ids for the call
+                                 (cudaHostRegister) unless they already are;
+                                 1: copy them from pageable memory as given   */
     uint64_t poll_ns;         /* longest idle sleep while nothing is queued    */
     uint64_t timeout_ns;      /* a batch not complete after this long fails the
                                  call with GC_ERR_TIMEOUT; 0 = 60 s           */
@@ -576,7 +579,8 @@ typedef struct {
  * the task arrays), so a long schedule needs no more than one task set.  An
  * offered load the engine cannot sustain leaves a queue behind: drain_ns
  * bounds the time spent after the schedule, and what is still queued then
- * is reported as unserved instead of delaying the call without end.  tgt_ids and src_ids are page-locked for the
+ * is reported as unserved instead of delaying the call without end.  Unless
+ * keep_pageable is set, tgt_ids and src_ids are page-locked for the
  * duration of the call (cudaHostRegister) unless they already are, so that
  * the per-batch copies run as direct DMA.  The pool must have no pending tasks; per-id
  * totals accumulate as for any flush.  Errors: GC_ERR_ARG (bad pointers,

@@ -128,13 +128,20 @@ void free_ctx(FlushCtx &c)
     if (c.ev_scattered) cudaEventDestroy(c.ev_scattered);
     if (c.d_ctr) cudaFree(c.d_ctr);
     if (c.h_ctr) cudaFreeHost(c.h_ctr);
+    for (cudaEvent_t e : c.pev)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t q : c.ps)
+        if (q) {
+            cudaStreamSynchronize(q);
+            cudaStreamDestroy(q);
+        }
     if (c.owns_stream && c.s) cudaStreamDestroy(c.s);
 }
 
 static void free_pool(gc_pool *p)
 {
     if (!p) return;
-    for (cudaStream_t cs : {p->cs_in, p->cs_out})
+    for (cudaStream_t cs : {p->cs_in, p->cs_out, p->cs_sub})
         if (cs) cudaStreamSynchronize(cs);
     cudaFree(p->d_pool);
     cudaFree(p->d_slot_of_id);
@@ -156,16 +163,18 @@ static void free_pool(gc_pool *p)
                     &p->nb.list_off, &p->nb.list_len, &p->nb.list, &p->nb.bounds,
                     &p->nb.cub_tmp, &p->nb.mono, &p->nb.hostcopy, &p->nb.wnode, &p->nb.seed_tiles,
                     &p->nb.seed_a, &p->nb.seed_m, &p->nb.seed_key, &p->au_ids, &p->au_vals,
-                    &p->at_ids, &p->at_out, &p->md.hostcopy,
+                    &p->at_ids, &p->at_out, &p->sub_desc, &p->md.hostcopy,
                     &p->md.keys,
                     &p->md.keys2, &p->md.ids, &p->md.ids2, &p->md.cell_start, &p->md.cnt_t,
                     &p->md.cnt_s, &p->md.cub_tmp};
     for (DBuf *b : bufs) b->release();
     for (cudaEvent_t &e : p->nb.ev)
         if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : {p->ev_au, p->ev_au_in, p->ev_at_in, p->ev_at_g, p->ev_at})
+    for (cudaEvent_t e : {p->ev_au, p->ev_au_in, p->ev_at_in, p->ev_at_g, p->ev_at,
+                          p->ev_pend_free, p->ev_sub_copied, p->ev_sub_done})
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t cs : {p->cs_in, p->cs_out})
+    if (p->h_sub) cudaFreeHost(p->h_sub);
+    for (cudaStream_t cs : {p->cs_in, p->cs_out, p->cs_sub})
         if (cs) cudaStreamDestroy(cs);
     for (int i = 0; i < 2; ++i) free_ctx(p->ctx[i]);
     delete p;
@@ -191,6 +200,12 @@ int init_ctx(FlushCtx &c, cudaStream_t given)
         cudaEventCreateWithFlags(&c.ev_packed, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c.ev_scattered, cudaEventDisableTiming) != cudaSuccess)
         return GC_ERR_CUDA;
+    for (cudaStream_t &q : c.ps)
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess)
+            return GC_ERR_CUDA;
+    for (cudaEvent_t &e : c.pev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return GC_ERR_CUDA;
     if (cudaMemsetAsync(c.d_ctr, 0, sizeof(unsigned long long) * FC_COUNT, c.s) != cudaSuccess)
         return GC_ERR_CUDA;
     return GC_OK;
@@ -471,6 +486,87 @@ int gc_pool_upload_device(gc_pool_t *p, const uint32_t *ids_dev, const float *xy
 
 // ---- submission ---------------------------------------------------------------
 
+// Host arrays of one submission: descriptors packed into the pinned host
+// staging (with the ids too when they are few), copied on the submission
+// stream, task records built there; returns once the caller's arrays have
+// been read.
+static const uint64_t SUB_PACK_IDS = 1u << 18;   // ids packed with the descriptors
+
+static int submit_host(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
+                       const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
+                       const uint32_t *tgt_ids, const uint64_t *src_off,
+                       const uint32_t *src_ids, uint64_t n_tgt, uint64_t n_src, uint32_t *dt,
+                       uint32_t *ds, uint64_t id_base, TaskRec *recs)
+{
+    if (!p->cs_sub) GC_CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_sub, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&p->ev_pend_free, &p->ev_sub_copied, &p->ev_sub_done})
+        if (!*e) GC_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    const size_t b_ids = task_ids ? n_tasks * 8 : 0, b_k = n_tasks * 4,
+                 b_sh = shifts ? n_tasks * 3 : 0, b_off = (n_tasks + 1) * 8;
+    const size_t o_ids = 0, o_k = al(o_ids + b_ids), o_sh = al(o_k + b_k), o_to = al(o_sh + b_sh),
+                 o_so = al(o_to + b_off), desc = o_so + b_off;
+    const bool pack_ids = n_tgt + n_src <= SUB_PACK_IDS;
+    const size_t o_tg = al(desc), o_sr = al(o_tg + n_tgt * 4),
+                 host_bytes = pack_ids ? o_sr + n_src * 4 : desc;
+    GC_TRY(grow_keep(p->sub_desc, desc + 16, 0, p->s));
+    if (host_bytes > p->h_sub_cap) {
+        if (p->h_sub) cudaFreeHost(p->h_sub);
+        p->h_sub = nullptr;
+        p->h_sub_cap = 0;
+        const size_t want = host_bytes + host_bytes / 2 + 4096;
+        if (cudaHostAlloc(&p->h_sub, want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p->h_sub = nullptr;
+            return GC_ERR_OOM;
+        }
+        p->h_sub_cap = want;
+    }
+    char *h = (char *)p->h_sub;
+    if (b_ids) std::memcpy(h + o_ids, task_ids, b_ids);
+    std::memcpy(h + o_k, kinds, b_k);
+    if (b_sh) std::memcpy(h + o_sh, shifts, b_sh);
+    std::memcpy(h + o_to, tgt_off, b_off);
+    std::memcpy(h + o_so, src_off, b_off);
+    if (pack_ids) {
+        if (n_tgt) std::memcpy(h + o_tg, tgt_ids, n_tgt * 4);
+        if (n_src) std::memcpy(h + o_sr, src_ids, n_src * 4);
+    }
+    // the pending arrays' last readers (the batch that held them before the
+    // flush handed them over); the previous submission's task records ran
+    // earlier on this stream, so the descriptor buffer is free
+    const cudaStream_t cs = p->cs_sub;
+    char *d = (char *)p->sub_desc.p;
+    int rc = GC_OK;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        if (rc == GC_OK && bytes &&
+            cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            rc = GC_ERR_CUDA;
+    };
+    if (cudaStreamWaitEvent(cs, p->ev_pend_free, 0) != cudaSuccess) rc = GC_ERR_CUDA;
+    cp(d, h, desc);
+    cp(dt, pack_ids ? (const void *)(h + o_tg) : (const void *)tgt_ids, n_tgt * 4);
+    cp(ds, pack_ids ? (const void *)(h + o_sr) : (const void *)src_ids, n_src * 4);
+    if (rc == GC_OK && cudaEventRecord(p->ev_sub_copied, cs) != cudaSuccess) rc = GC_ERR_CUDA;
+    if (rc == GC_OK)
+        rc = gc_make_task_recs(p, n_tasks, task_ids ? (uint64_t *)(d + o_ids) : nullptr,
+                               (uint32_t *)(d + o_k), shifts ? (int8_t *)(d + o_sh) : nullptr,
+                               (uint64_t *)(d + o_to), (uint64_t *)(d + o_so), p->nb_tgt,
+                               p->nb_src, id_base, recs, cs);
+    if (rc == GC_OK && (cudaEventRecord(p->ev_sub_done, cs) != cudaSuccess ||
+                        cudaStreamWaitEvent(p->s, p->ev_sub_done, 0) != cudaSuccess))
+        rc = GC_ERR_CUDA;
+    // the caller's arrays and the host staging have been read once the
+    // copies are done (a bad task is reported by the flush)
+    if (rc == GC_OK && cudaEventSynchronize(p->ev_sub_copied) != cudaSuccess) rc = GC_ERR_CUDA;
+    if (rc != GC_OK) {
+        cudaStreamSynchronize(cs);
+        return rc;
+    }
+    p->stats.h2d_bytes += desc + 4 * (n_tgt + n_src);
+    return GC_OK;
+}
+
 static int gc_submit_csr_impl(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
                        const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
                        const uint32_t *tgt_ids, const uint64_t *src_off,
@@ -510,47 +606,10 @@ static int gc_submit_csr_impl(gc_pool *p, uint64_t n_tasks, const uint64_t *task
             GC_CUDA_TRY(cudaMemcpyAsync(ds, src_ids, n_src_total * sizeof(uint32_t),
                                         cudaMemcpyDeviceToDevice, p->s));
         GC_TRY(gc_make_task_recs(p, n_tasks, task_ids, kinds, shifts, tgt_off, src_off,
-                                 p->nb_tgt, p->nb_src, id_base, recs));
+                                 p->nb_tgt, p->nb_src, id_base, recs, p->s));
     } else {
-        // stage the descriptor arrays on the device
-        size_t b_ids = task_ids ? n_tasks * 8 : 0, b_k = n_tasks * 4,
-               b_sh = shifts ? n_tasks * 3 : 0, b_off = (n_tasks + 1) * 8;
-        size_t o_ids = 0, o_k = (o_ids + b_ids + 15) & ~15ull, o_sh = (o_k + b_k + 15) & ~15ull,
-               o_to = (o_sh + b_sh + 15) & ~15ull, o_so = (o_to + b_off + 15) & ~15ull,
-               total = o_so + b_off;
-        GC_TRY(grow_keep(p->io_a, total + 16, 0, p->s));
-        char *base = (char *)p->io_a.p;
-        int rc = GC_OK;
-        if (task_ids && cudaMemcpyAsync(base + o_ids, task_ids, b_ids, cudaMemcpyHostToDevice,
-                                        p->s) != cudaSuccess)
-            rc = GC_ERR_CUDA;
-        if (cudaMemcpyAsync(base + o_k, kinds, b_k, cudaMemcpyHostToDevice, p->s) != cudaSuccess)
-            rc = GC_ERR_CUDA;
-        if (shifts && cudaMemcpyAsync(base + o_sh, shifts, b_sh, cudaMemcpyHostToDevice, p->s) !=
-                          cudaSuccess)
-            rc = GC_ERR_CUDA;
-        if (cudaMemcpyAsync(base + o_to, tgt_off, b_off, cudaMemcpyHostToDevice, p->s) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(base + o_so, src_off, b_off, cudaMemcpyHostToDevice, p->s) !=
-                cudaSuccess)
-            rc = GC_ERR_CUDA;
-        if (rc == GC_OK && n_tgt_total &&
-            cudaMemcpyAsync(dt, tgt_ids, n_tgt_total * 4, cudaMemcpyHostToDevice, p->s) !=
-                cudaSuccess)
-            rc = GC_ERR_CUDA;
-        if (rc == GC_OK && n_src_total &&
-            cudaMemcpyAsync(ds, src_ids, n_src_total * 4, cudaMemcpyHostToDevice, p->s) !=
-                cudaSuccess)
-            rc = GC_ERR_CUDA;
-        if (rc == GC_OK)
-            rc = gc_make_task_recs(p, n_tasks, task_ids ? (uint64_t *)(base + o_ids) : nullptr,
-                                   (uint32_t *)(base + o_k),
-                                   shifts ? (int8_t *)(base + o_sh) : nullptr,
-                                   (uint64_t *)(base + o_to), (uint64_t *)(base + o_so),
-                                   p->nb_tgt, p->nb_src, id_base, recs);
-        if (cudaStreamSynchronize(p->s) != cudaSuccess) rc = GC_ERR_CUDA;
-        if (rc != GC_OK) return rc;
-        p->stats.h2d_bytes += total + 4 * (n_tgt_total + n_src_total);
+        GC_TRY(submit_host(p, n_tasks, task_ids, kinds, shifts, tgt_off, tgt_ids, src_off,
+                           src_ids, n_tgt_total, n_src_total, dt, ds, id_base, recs));
     }
     p->nb_tasks += n_tasks;
     p->nb_tgt += n_tgt_total;
@@ -614,7 +673,12 @@ static int flush_impl(gc_pool *p, int per_task)
     count_timing(p, c, true);   // the context's previous batch (two batches ago)
     // the batch becomes this context's batch; the context's previous batch
     // arrays become the next pending arrays (every later write to them is
-    // ordered after this context's stream passes the point below)
+    // ordered after this context's stream passes the point below, or, for
+    // the copies of a host submission, after the previous batch's work on
+    // this stream: ev_pend_free)
+    if (!p->ev_pend_free)
+        GC_CUDA_TRY(cudaEventCreateWithFlags(&p->ev_pend_free, cudaEventDisableTiming));
+    GC_CUDA_TRY(cudaEventRecord(p->ev_pend_free, c.s));
     std::swap(p->tasks, c.tasks);
     std::swap(p->tgt_ids, c.tgt_ids);
     std::swap(p->src_ids, c.src_ids);

@@ -137,6 +137,9 @@ struct WaveRange {
 struct FlushCtx {
     cudaStream_t s = nullptr;
     bool owns_stream = false;
+    // side streams of the pack's size classes and their fork / join events
+    cudaStream_t ps[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     unsigned long long *d_ctr = nullptr;   // [FC_COUNT]
     unsigned long long *h_ctr = nullptr;   // pinned copy
     DBuf tasks, tgt_ids, src_ids;          // the executed batch
@@ -218,6 +221,18 @@ struct gc_pool {
     cudaEvent_t ev_at_g = nullptr;    // gather has read at_ids and written at_out
     cudaEvent_t ev_at = nullptr;      // at_out copied out
     bool au_used = false, at_used = false;
+    // host-array submissions: descriptors (and the ids of a small
+    // submission) packed into a pinned host buffer, copied and turned into
+    // task records on a stream of their own.  The copies wait only for the
+    // last readers of the pending arrays (ev_pend_free, recorded by the flush
+    // that handed them over) -- not for the batch in flight -- and the host
+    // waits for the copies alone (ev_sub_copied); the pool's stream waits
+    // for the task records (ev_sub_done)
+    cudaStream_t cs_sub = nullptr;
+    cudaEvent_t ev_pend_free = nullptr, ev_sub_copied = nullptr, ev_sub_done = nullptr;
+    DBuf sub_desc;                    // device copy of the descriptors
+    void *h_sub = nullptr;            // pinned host staging
+    size_t h_sub_cap = 0;
     uint64_t n_evicted_last = 0;
     uint32_t epoch = 0;
 
@@ -315,7 +330,7 @@ int gc_md_reduce(gc_pool *p, FlushCtx &c);
 int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
                       const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
                       const uint64_t *src_off, uint64_t tgt_base, uint64_t src_base,
-                      uint64_t task_id_base, TaskRec *out);
+                      uint64_t task_id_base, TaskRec *out, cudaStream_t s);
 
 // ---- compaction helper (gc_residency.cu) ---------------------------------------
 // Writes, in ascending order, every i in [0, n) with flags-kind predicate.

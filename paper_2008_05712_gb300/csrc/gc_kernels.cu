@@ -1650,11 +1650,11 @@ __global__ void __launch_bounds__(1024) k_scatter_small(uint32_t n_rows, const u
 int gc_make_task_recs(gc_pool *p, uint64_t n_tasks, const uint64_t *task_ids,
                       const uint32_t *kinds, const int8_t *shifts, const uint64_t *tgt_off,
                       const uint64_t *src_off, uint64_t tgt_base, uint64_t src_base,
-                      uint64_t task_id_base, TaskRec *out)
+                      uint64_t task_id_base, TaskRec *out, cudaStream_t s)
 {
     if (n_tasks == 0) return GC_OK;
     ++p->stats.kernel_launches;
-    k_task_recs<<<grid_for(n_tasks, 256, p->num_sms * 16), 256, 0, p->s>>>(
+    k_task_recs<<<grid_for(n_tasks, 256, p->num_sms * 16), 256, 0, s>>>(
         n_tasks, task_ids, kinds, shifts, tgt_off, src_off, tgt_base, src_base, task_id_base,
         out, p->d_ctr, p->n_ewald_h > 0 ? 1 : 0);
     GC_CUDA_TRY(cudaGetLastError());
@@ -1798,31 +1798,54 @@ int gc_pack(gc_pool *p, FlushCtx &c, uint64_t t0, uint64_t t1, uint64_t tgt_base
     ++p->stats.kernel_launches;
     a.work = c.d_ctr + FC_PACK_WORK;
     GC_CUDA_TRY(cudaMemsetAsync(a.work, 0, 4 * sizeof(unsigned long long), c.s));
-    k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, c.s>>>(a);
+    // The size classes pack disjoint lists, each with a claim counter of its
+    // own.  The block-per-list classes of more than 1024 entries a batch
+    // needs run on side streams beside the context's stream (longest lists
+    // first), so that a small batch's pack takes about its longest class's
+    // time instead of the sum over its classes; the context's stream joins
+    // them before the interaction.
+    int forked = 0;
+    cudaError_t ferr = cudaSuccess;
+    auto side = [&](int i) -> cudaStream_t {
+        if (!forked++ && ferr == cudaSuccess) ferr = cudaEventRecord(c.pev[3], c.s);
+        if (ferr == cudaSuccess) ferr = cudaStreamWaitEvent(c.ps[i], c.pev[3], 0);
+        return c.ps[i];
+    };
+    bool joined[3] = {false, false, false};
+    if (c.max_list > PK_CAP) {
+        ++p->stats.kernel_launches;
+        constexpr int nw = PackLargeWarps<PK_CAP_HUGE>::value;
+        k_pack_large<PK_CAP_HUGE><<<grid_for(a.n_lists, 1, p->num_sms), nw * 32,
+                                    sizeof(PackSmemLarge<PK_CAP_HUGE>), side(0)>>>(a);
+        joined[0] = true;
+    }
+    if (c.max_list > PM_CAP) {
+        ++p->stats.kernel_launches;
+        constexpr int nw = PackLargeWarps<PK_CAP>::value;
+        k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), nw * 32,
+                               sizeof(PackSmemLarge<PK_CAP>), side(1)>>>(a);
+        joined[1] = true;
+    }
+    if (c.max_list > PM_CAP / 2) {
+        ++p->stats.kernel_launches;
+        k_pack_mid<PM_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 6), PM_THREADS,
+                             sizeof(PackSmemMid<PM_CAP>), side(2)>>>(a);
+        joined[2] = true;
+    }
     // the block-per-list classes only when the batch has lists of their sizes
     if (c.max_list > 32) {
         ++p->stats.kernel_launches;
         k_pack_mid<PM_CAP / 2><<<grid_for(a.n_lists, 1, p->num_sms * 9), PM_THREADS,
                                  sizeof(PackSmemMid<PM_CAP / 2>), c.s>>>(a);
     }
-    if (c.max_list > PM_CAP / 2) {
-        ++p->stats.kernel_launches;
-        k_pack_mid<PM_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 6), PM_THREADS,
-                             sizeof(PackSmemMid<PM_CAP>), c.s>>>(a);
-    }
-    if (c.max_list > PM_CAP) {
-        ++p->stats.kernel_launches;
-        constexpr int nw = PackLargeWarps<PK_CAP>::value;
-        k_pack_large<PK_CAP><<<grid_for(a.n_lists, 1, p->num_sms * 3), nw * 32,
-                               sizeof(PackSmemLarge<PK_CAP>), c.s>>>(a);
-    }
-    if (c.max_list > PK_CAP) {
-        ++p->stats.kernel_launches;
-        constexpr int nw = PackLargeWarps<PK_CAP_HUGE>::value;
-        k_pack_large<PK_CAP_HUGE><<<grid_for(a.n_lists, 1, p->num_sms), nw * 32,
-                                    sizeof(PackSmemLarge<PK_CAP_HUGE>), c.s>>>(a);
-    }
+    k_pack_small<<<grid_for(a.n_lists * 32, 256, p->num_sms * 32), 256, 0, c.s>>>(a);
+    GC_CUDA_TRY(ferr);
     GC_CUDA_TRY(cudaGetLastError());
+    for (int i = 0; i < 3; ++i)
+        if (joined[i]) {
+            GC_CUDA_TRY(cudaEventRecord(c.pev[i], c.ps[i]));
+            GC_CUDA_TRY(cudaStreamWaitEvent(c.s, c.pev[i], 0));
+        }
     return GC_OK;
 }
 

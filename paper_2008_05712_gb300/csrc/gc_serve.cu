@@ -101,8 +101,10 @@ extern "C" int gc_serve(gc_pool_t *p, uint64_t n, const uint64_t *arrival_ns,
             cudaGetLastError();   // stays pageable: slower copies, same results
         }
     };
-    pin(tgt_ids, tgt_off[m] * sizeof(uint32_t));
-    pin(src_ids, src_off[m] * sizeof(uint32_t));
+    if (!cfg->keep_pageable) {
+        pin(tgt_ids, tgt_off[m] * sizeof(uint32_t));
+        pin(src_ids, src_off[m] * sizeof(uint32_t));
+    }
     const uint64_t budget = p->cfg.staging_budget_bytes;
     const uint64_t none = ~0ull;
     std::vector<uint64_t> lat(n, none);

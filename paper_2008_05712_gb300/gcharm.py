@@ -77,7 +77,7 @@ class GcStats(C.Structure):
 class GcServeConfig(C.Structure):
     _fields_ = [("policy", C.c_int), ("max_size", C.c_uint64), ("static_n", C.c_uint64),
                 ("window", C.c_uint64), ("max_in_flight", C.c_uint32),
-                ("poll_ns", C.c_uint64), ("timeout_ns", C.c_uint64),
+                ("keep_pageable", C.c_uint32), ("poll_ns", C.c_uint64), ("timeout_ns", C.c_uint64),
                 ("task_set", C.c_uint64), ("warmup_ns", C.c_uint64), ("drain_ns", C.c_uint64)]
 
 
@@ -401,7 +401,7 @@ class Pool:
     def serve(self, arrival_ns, kinds, tgt_off, tgt_ids, src_off, src_ids, shifts=None,
               policy=GC_COMBINE_GREEDY, max_size=0, static_n=100, window=1024,
               max_in_flight=2, poll_ns=50_000, timeout_ns=0, want_results=False,
-              task_set=0, warmup_ns=0, drain_ns=0):
+              task_set=0, warmup_ns=0, drain_ns=0, keep_pageable=False):
         """Replay an arrival schedule through the serving loop (gc_serve).
 
         Returns (report dict, latency_ns array, rows or None); rows are the
@@ -417,7 +417,8 @@ class Pool:
         n = arr.shape[0]
         cfg = GcServeConfig(policy=policy, max_size=max_size, static_n=static_n, window=window,
                             max_in_flight=max_in_flight, poll_ns=poll_ns, timeout_ns=timeout_ns,
-                            task_set=task_set, warmup_ns=warmup_ns, drain_ns=drain_ns)
+                            task_set=task_set, warmup_ns=warmup_ns, drain_ns=drain_ns,
+                            keep_pageable=1 if keep_pageable else 0)
         lat = np.zeros(n, np.uint64)
         rows = None
         if want_results:
