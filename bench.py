@@ -651,6 +651,7 @@ def uneven_and_serving(gcharm, torch, seed, stream, batch_reps=3, with_oracle=Tr
                          "schedule": "lpt" if tuning["schedule"] else "fifo",
                          "tile_pairs": tuning["tile_pairs"],
                          "comp_block": tuning["comp_block"],
+                         "targets_per_lane": tuning["targets_per_lane"],
                          "autotune_ms": tune_ms or tuning.get("times_ms")}}
     if with_oracle:
         # parity on 300 seeded tasks of the batch against the FP64 oracle
@@ -1056,6 +1057,7 @@ def main():
                        "schedule": "lpt" if tuning["schedule"] else "fifo",
                        "tile_pairs": tuning["tile_pairs"],
                        "comp_block": tuning["comp_block"],
+                       "targets_per_lane": tuning["targets_per_lane"],
                        "autotune_ms": tune_ms or tuning.get("times_ms"),
                        "cache": os.path.relpath(TUNE_CACHE, ROOT)},
             "reuse": {"last_hits": hits, "last_unique": uniq},

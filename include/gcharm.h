@@ -644,10 +644,14 @@ typedef struct {
                                  the resident blocks per SM)                   */
     uint32_t comp_block;      /* source pairs summed in plain FP32 before each
                                  compensated add: 8, 16 or 32                  */
+    uint32_t targets_per_lane; /* targets each lane accumulates, sharing every
+                                 source pair it reads: 1 or 2 (a unit of T
+                                 targets then runs ceil(T / 2) target lanes x
+                                 32 / ceil(T / 2) source lanes)              */
 } gc_tuning;
 
 /* Set / read the interaction schedule and tile shape used by later flushes
- * (default 16, FIFO, 128, 8).  The results change only by FP32 summation
+ * (default 16, FIFO, 128, 8, 1).  The results change only by FP32 summation
  * order (within the per-result tolerance).  Errors: GC_ERR_ARG (other
  * values). */
 int gc_set_tuning(gc_pool_t *pool, const gc_tuning *t);
@@ -656,15 +660,15 @@ int gc_get_tuning(gc_pool_t *pool, gc_tuning *t);
 /* Autotuner: re-run the interaction stage of the last flushed batch (one
  * wave, gravity tasks) under every schedule and tile shape, work-unit size
  * {8, 16, 32} x {FIFO, LPT} x tile pairs {64, 128, 256} x compensation block
- * {8, 16, 32}, timing each with CUDA events (best of `reps`), and keep the
- * fastest for later flushes.  ms_out (may be NULL) receives the
- * GC_TUNE_COUNT times, entry ((w * 2 + s) * 3 + t) * 3 + k for the w-th
- * work-unit size, schedule s, t-th tile size and k-th block; *best_out (may
- * be NULL) the choice.  The batch's result rows are rewritten by the re-runs
+ * {8, 16, 32} x targets per lane {1, 2}, timing each with CUDA events (best
+ * of `reps`), and keep the fastest for later flushes.  ms_out (may be NULL)
+ * receives the GC_TUNE_COUNT times, entry (((w * 2 + s) * 3 + t) * 3 + k) *
+ * 2 + l - 1 for the w-th work-unit size, schedule s, t-th tile size, k-th
+ * block and l targets per lane; *best_out (may be NULL) the choice.  The batch's result rows are rewritten by the re-runs
  * (same values up to summation order); per-id totals are not touched.
  * Errors: GC_ERR_NOT_READY (no batch), GC_ERR_STATE (the batch ran in more
  * than one wave, or has no gravity task), GC_ERR_CUDA. */
-#define GC_TUNE_COUNT 54
+#define GC_TUNE_COUNT 108
 int gc_autotune(gc_pool_t *pool, int reps, gc_tuning *best_out, float ms_out[GC_TUNE_COUNT]);
 
 /* ---- reuse ablation (Section 3.2, Fig. 3) --------------------------------- */

@@ -242,6 +242,7 @@ struct gc_pool {
     uint32_t wu_schedule = GC_SCHED_FIFO;
     uint32_t wu_tile = 128;            // gravity tile shape: source pairs per staged tile
     uint32_t wu_kb = 8;                // and pairs per plain partial sum
+    uint32_t wu_tpl = 1;               // and targets per lane
     uint64_t table_version = 0;        // bumped whenever a slot is assigned or freed
     // Ewald correction (GC_EWALD tasks): half of the reciprocal vectors
     // (hx, hy, hz, 2 exp(-pi^2 h^2 / (alpha L)^2) / h^2)

@@ -973,20 +973,42 @@ __device__ __forceinline__ void comp_add(float &s, float &c, float s2, float c2)
         bp = __ffma2_rn(mr, m1, bp);                                      \
     } while (0)
 
+// The same against the lane's target k (k a compile-time index into the
+// per-target arrays of the kernel below).
+#define GRAV_PAIR_K(A, B, k)                                              \
+    do {                                                                  \
+        float2 dx = __fadd2_rn(make_float2((A).x, (A).y), nx[k]);         \
+        float2 dy = __fadd2_rn(make_float2((A).z, (A).w), ny[k]);         \
+        float2 dz = __fadd2_rn(make_float2((B).x, (B).y), nz[k]);         \
+        float2 r2 = __ffma2_rn(dx, dx, e2);                               \
+        r2 = __ffma2_rn(dy, dy, r2);                                      \
+        r2 = __ffma2_rn(dz, dz, r2);                                      \
+        float2 ri = make_float2(gc_rsqrt(r2.x), gc_rsqrt(r2.y));          \
+        float2 mr = __fmul2_rn(make_float2((B).z, (B).w), ri);            \
+        float2 mr3 = __fmul2_rn(mr, __fmul2_rn(ri, ri));                  \
+        bx[k] = __ffma2_rn(mr3, dx, bx[k]);                               \
+        by[k] = __ffma2_rn(mr3, dy, by[k]);                               \
+        bz[k] = __ffma2_rn(mr3, dz, bz[k]);                               \
+        bp[k] = __ffma2_rn(mr, m1, bp[k]);                                \
+    } while (0)
+
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
 
 // TP source pairs per staged tile (32 TP bytes): shared memory of a block is
-// 512 TP bytes of tiles plus 8 KB, which sets the resident blocks per SM.
-template <int TP>
+// 512 TP bytes of tiles plus 8 KB per target a lane holds, which sets the
+// resident blocks per SM.
+template <int TP, int TPL>
 struct GravSmem {
     float4 buf[GRAV_WARPS][2][2 * TP];  // per warp: two tiles of source pairs
     uint64_t bar[GRAV_WARPS][2];        // one mbarrier per tile buffer
-    float4 red[GRAV_WARPS][32][2];      // cross-lane combine: (sum, compensation)
+    float4 red[GRAV_WARPS][32][2 * TPL];  // cross-lane combine: (sum, compensation)
 };
 
-// One warp per work unit (task, block of <= 16 targets).  With T targets in
-// the block, the warp splits into S = 32 / T source lanes per target: lane
-// (t, s) accumulates target t over source pairs s, s + S, ... of each tile.
+// One warp per work unit (task, block of <= 32 targets).  With T targets in
+// the block and TPL targets per lane, the warp splits into TL = ceil(T / TPL)
+// target lanes times S = 32 / TL source lanes: lane (t, s) accumulates
+// targets t, t + TL, ... over source pairs s, s + S, ... of each tile, so
+// each source pair read from shared memory serves TPL targets.
 // Source pairs stream through two shared-memory tile buffers per warp,
 // filled by 1-D bulk copies (TMA) that complete on mbarriers, one tile
 // ahead of the compute.  Every source pair is evaluated with paired FP32
@@ -998,12 +1020,14 @@ struct GravSmem {
 // polling limit sets GC_FLAG_TIMEOUT and the warp stops; the lanes poll
 // together and take that decision as one, so no lane is left waiting at a
 // later warp-wide shuffle.
-// The tile size TP and the block KB are the autotuner's tile shape.
-template <int TP, int KB>
+// The tile size TP, the block KB and the targets per lane TPL are the
+// autotuner's tile shape; a lane's target slot beyond the block's targets
+// (odd T) repeats the last target and is not written.
+template <int TP, int KB, int TPL>
 __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GravSmem<TP> &sm = *reinterpret_cast<GravSmem<TP> *>(smem_raw);
+    GravSmem<TP, TPL> &sm = *reinterpret_cast<GravSmem<TP, TPL> *>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const uint64_t gwarp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1028,19 +1052,26 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
         const GravWU u = a.wu[w];
         const TaskRec r = a.tasks[u.task];
         const int T = (int)u.tn;
-        const int S = 32 / T;
-        const int t = lane % T;
-        const int sl = lane / T;
+        const int TL = (T + TPL - 1) / TPL;
+        const int S = 32 / TL;
+        const int t = lane % TL;
+        const int sl = lane / TL;
         const bool active = sl < S;
         const float4 *P = a.stg_s + (r.src_off - a.src_base) + (u.task - a.task_base);
         const uint32_t np = (r.ns + 1u) >> 1;
         const uint32_t ntiles = (np + TP - 1) / TP;
-        const float4 xi = a.stg_t[r.tgt_off - a.tgt_base + u.t0 + t];
-        const float2 nx = make_float2(-xi.x, -xi.x);
-        const float2 ny = make_float2(-xi.y, -xi.y);
-        const float2 nz = make_float2(-xi.z, -xi.z);
-        float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
-        float2 cx = sx, cy = sx, cz = sx, cp = sx;
+        float2 nx[TPL], ny[TPL], nz[TPL];
+        float2 sx[TPL], sy[TPL], sz[TPL], sp[TPL], cx[TPL], cy[TPL], cz[TPL], cp[TPL];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            const int tk = min(t + k * TL, T - 1);
+            const float4 xi = a.stg_t[r.tgt_off - a.tgt_base + u.t0 + tk];
+            nx[k] = make_float2(-xi.x, -xi.x);
+            ny[k] = make_float2(-xi.y, -xi.y);
+            nz[k] = make_float2(-xi.z, -xi.z);
+            sx[k] = sy[k] = sz[k] = sp[k] = make_float2(0.f, 0.f);
+            cx[k] = cy[k] = cz[k] = cp[k] = make_float2(0.f, 0.f);
+        }
         if (lane == 0) {
             for (uint32_t b = 0; b < 2 && b < ntiles; ++b) {
                 const uint32_t bytes = min((uint32_t)TP, np - b * TP) * 32u;
@@ -1064,31 +1095,43 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
             const uint32_t stride = 2u * (uint32_t)S;
             uint32_t j = 0;
             for (; j + KB <= nq; j += KB) {
-                float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
+                float2 bx[TPL], by[TPL], bz[TPL], bp[TPL];
 #pragma unroll
-                for (int k = 0; k < KB; ++k) {
+                for (int k = 0; k < TPL; ++k) bx[k] = by[k] = bz[k] = bp[k] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < KB; ++kk) {
                     const float4 A = q[0];
                     const float4 B = q[1];
                     q += stride;
-                    GRAV_PAIR(A, B);
+#pragma unroll
+                    for (int k = 0; k < TPL; ++k) GRAV_PAIR_K(A, B, k);
                 }
-                kahan_add2(sx, cx, bx, m1);
-                kahan_add2(sy, cy, by, m1);
-                kahan_add2(sz, cz, bz, m1);
-                kahan_add2(sp, cp, bp, m1);
+#pragma unroll
+                for (int k = 0; k < TPL; ++k) {
+                    kahan_add2(sx[k], cx[k], bx[k], m1);
+                    kahan_add2(sy[k], cy[k], by[k], m1);
+                    kahan_add2(sz[k], cz[k], bz[k], m1);
+                    kahan_add2(sp[k], cp[k], bp[k], m1);
+                }
             }
             if (j < nq) {
-                float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
+                float2 bx[TPL], by[TPL], bz[TPL], bp[TPL];
+#pragma unroll
+                for (int k = 0; k < TPL; ++k) bx[k] = by[k] = bz[k] = bp[k] = make_float2(0.f, 0.f);
                 for (; j < nq; ++j) {
                     const float4 A = q[0];
                     const float4 B = q[1];
                     q += stride;
-                    GRAV_PAIR(A, B);
+#pragma unroll
+                    for (int k = 0; k < TPL; ++k) GRAV_PAIR_K(A, B, k);
                 }
-                kahan_add2(sx, cx, bx, m1);
-                kahan_add2(sy, cy, by, m1);
-                kahan_add2(sz, cz, bz, m1);
-                kahan_add2(sp, cp, bp, m1);
+#pragma unroll
+                for (int k = 0; k < TPL; ++k) {
+                    kahan_add2(sx[k], cx[k], bx[k], m1);
+                    kahan_add2(sy[k], cy[k], by[k], m1);
+                    kahan_add2(sz[k], cz[k], bz[k], m1);
+                    kahan_add2(sp[k], cp[k], bp[k], m1);
+                }
             }
             gc_fence_proxy_async_smem();
             __syncwarp();
@@ -1110,29 +1153,37 @@ __global__ void __launch_bounds__(GRAV_THREADS) k_gravity(InterArgs a)
         }
         // the two halves of each lane, then the S lanes of a target in lane
         // order, all as compensated FP32 pairs
-        comp_add(sx.x, cx.x, sx.y, cx.y);
-        comp_add(sy.x, cy.x, sy.y, cy.y);
-        comp_add(sz.x, cz.x, sz.y, cz.y);
-        comp_add(sp.x, cp.x, sp.y, cp.y);
-        sm.red[wib][lane][0] = make_float4(sx.x, sy.x, sz.x, sp.x);
-        sm.red[wib][lane][1] = make_float4(cx.x, cy.x, cz.x, cp.x);
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            comp_add(sx[k].x, cx[k].x, sx[k].y, cx[k].y);
+            comp_add(sy[k].x, cy[k].x, sy[k].y, cy[k].y);
+            comp_add(sz[k].x, cz[k].x, sz[k].y, cz[k].y);
+            comp_add(sp[k].x, cp[k].x, sp[k].y, cp[k].y);
+            sm.red[wib][lane][2 * k] = make_float4(sx[k].x, sy[k].x, sz[k].x, sp[k].x);
+            sm.red[wib][lane][2 * k + 1] = make_float4(cx[k].x, cy[k].x, cz[k].x, cp[k].x);
+        }
         __syncwarp();
         if (sl == 0) {
-            float4 vs = sm.red[wib][t][0], vc = sm.red[wib][t][1];
-            for (int s = 1; s < S; ++s) {
-                const int l = s * T + t;
-                const float4 ws = sm.red[wib][l][0], wc = sm.red[wib][l][1];
-                comp_add(vs.x, vc.x, ws.x, wc.x);
-                comp_add(vs.y, vc.y, ws.y, wc.y);
-                comp_add(vs.z, vc.z, ws.z, wc.z);
-                comp_add(vs.w, vc.w, ws.w, wc.w);
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) {
+                const int tk = t + k * TL;
+                if (tk >= T) break;
+                float4 vs = sm.red[wib][t][2 * k], vc = sm.red[wib][t][2 * k + 1];
+                for (int s = 1; s < S; ++s) {
+                    const int l = s * TL + t;
+                    const float4 ws = sm.red[wib][l][2 * k], wc = sm.red[wib][l][2 * k + 1];
+                    comp_add(vs.x, vc.x, ws.x, wc.x);
+                    comp_add(vs.y, vc.y, ws.y, wc.y);
+                    comp_add(vs.z, vc.z, ws.z, wc.z);
+                    comp_add(vs.w, vc.w, ws.w, wc.w);
+                }
+                const uint64_t e = r.tgt_off + u.t0 + tk;
+                const uint32_t pos = a.perm_t[e];
+                const uint64_t row = r.row_off + pos;
+                a.res[2 * row] = vs;
+                a.res[2 * row + 1] = vc;
+                a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
             }
-            const uint64_t e = r.tgt_off + u.t0 + t;
-            const uint32_t pos = a.perm_t[e];
-            const uint64_t row = r.row_off + pos;
-            a.res[2 * row] = vs;
-            a.res[2 * row + 1] = vc;
-            a.row_id[row] = a.tgt_ids[r.tgt_off + pos];
         }
         __syncwarp();
     }
@@ -1879,34 +1930,42 @@ static void fill_inter_args(gc_pool *p, FlushCtx &c, uint64_t tgt_base, uint64_t
 }
 
 // Tile shapes of the gravity kernel: TP in {64, 128, 256} source pairs per
-// staged tile, KB in {8, 16, 32} pairs per plain partial sum.
+// staged tile, KB in {8, 16, 32} pairs per plain partial sum, TPL in {1, 2}
+// targets per lane.
 struct GravVariant {
     void (*fn)(InterArgs);
-    uint32_t tp, kb;
+    uint32_t tp, kb, tpl;
     size_t smem;
     int ready;    // shared-memory limit raised
     int per_sm;   // resident blocks per SM (0: not yet asked)
 };
 
-#define GRAV_V(tp, kb) {k_gravity<tp, kb>, tp, kb, sizeof(GravSmem<tp>), 0, 0}
-static GravVariant g_grav[9] = {GRAV_V(64, 8),  GRAV_V(64, 16),  GRAV_V(64, 32),
-                                GRAV_V(128, 8), GRAV_V(128, 16), GRAV_V(128, 32),
-                                GRAV_V(256, 8), GRAV_V(256, 16), GRAV_V(256, 32)};
+#define GRAV_V(tp, kb, tpl) {k_gravity<tp, kb, tpl>, tp, kb, tpl, sizeof(GravSmem<tp, tpl>), 0, 0}
+static GravVariant g_grav[18] = {
+    GRAV_V(64, 8, 1),  GRAV_V(64, 16, 1),  GRAV_V(64, 32, 1),
+    GRAV_V(128, 8, 1), GRAV_V(128, 16, 1), GRAV_V(128, 32, 1),
+    GRAV_V(256, 8, 1), GRAV_V(256, 16, 1), GRAV_V(256, 32, 1),
+    GRAV_V(64, 8, 2),  GRAV_V(64, 16, 2),  GRAV_V(64, 32, 2),
+    GRAV_V(128, 8, 2), GRAV_V(128, 16, 2), GRAV_V(128, 32, 2),
+    GRAV_V(256, 8, 2), GRAV_V(256, 16, 2), GRAV_V(256, 32, 2)};
 #undef GRAV_V
 
-static GravVariant *grav_variant(uint32_t tp, uint32_t kb)
+static GravVariant *grav_variant(uint32_t tp, uint32_t kb, uint32_t tpl)
 {
     for (GravVariant &v : g_grav)
-        if (v.tp == tp && v.kb == kb) return &v;
+        if (v.tp == tp && v.kb == kb && v.tpl == tpl) return &v;
     return nullptr;
 }
 
-static bool grav_shape_ok(uint32_t tp, uint32_t kb) { return grav_variant(tp, kb) != nullptr; }
+static bool grav_shape_ok(uint32_t tp, uint32_t kb, uint32_t tpl)
+{
+    return grav_variant(tp, kb, tpl) != nullptr;
+}
 
 // The pool's variant, its shared-memory limit raised.
 static int grav_setup(gc_pool *p, GravVariant **out)
 {
-    GravVariant *v = grav_variant(p->wu_tile, p->wu_kb);
+    GravVariant *v = grav_variant(p->wu_tile, p->wu_kb, p->wu_tpl);
     if (!v) return GC_ERR_STATE;
     if (!v->ready) {
         if (cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2142,11 +2201,12 @@ extern "C" int gc_set_tuning(gc_pool_t *p, const gc_tuning *t)
     if (t->wu_max_targets != 8 && t->wu_max_targets != 16 && t->wu_max_targets != 32)
         return GC_ERR_ARG;
     if (t->schedule != GC_SCHED_FIFO && t->schedule != GC_SCHED_LPT) return GC_ERR_ARG;
-    if (!grav_shape_ok(t->tile_pairs, t->comp_block)) return GC_ERR_ARG;
+    if (!grav_shape_ok(t->tile_pairs, t->comp_block, t->targets_per_lane)) return GC_ERR_ARG;
     p->wu_max_targets = t->wu_max_targets;
     p->wu_schedule = t->schedule;
     p->wu_tile = t->tile_pairs;
     p->wu_kb = t->comp_block;
+    p->wu_tpl = t->targets_per_lane;
     return GC_OK;
 }
 
@@ -2157,6 +2217,7 @@ extern "C" int gc_get_tuning(gc_pool_t *p, gc_tuning *t)
     t->schedule = p->wu_schedule;
     t->tile_pairs = p->wu_tile;
     t->comp_block = p->wu_kb;
+    t->targets_per_lane = p->wu_tpl;
     return GC_OK;
 }
 
@@ -2200,7 +2261,7 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
     FlushCtx &c = p->ctx[p->last];
     GC_CUDA_TRY(cudaEventSynchronize(c.ev_done));
     if (c.n_waves != 1) return GC_ERR_STATE;
-    const gc_tuning saved{p->wu_max_targets, p->wu_schedule, p->wu_tile, p->wu_kb};
+    const gc_tuning saved{p->wu_max_targets, p->wu_schedule, p->wu_tile, p->wu_kb, p->wu_tpl};
     const uint32_t wus[3] = {8, 16, 32}, tps[3] = {64, 128, 256}, kbs[3] = {8, 16, 32};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -2210,14 +2271,15 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
     float best = 1e30f;
     gc_tuning choice = saved;
     int rc = GC_OK;
-    // index = ((wu * 2 + schedule) * 3 + tile) * 3 + block
+    // index = (((wu * 2 + schedule) * 3 + tile) * 3 + block) * 2 + targets per lane - 1
     for (int idx = 0; idx < GC_TUNE_COUNT && rc == GC_OK; ++idx) {
-        const gc_tuning t{wus[idx / 18], (uint32_t)((idx / 9) % 2), tps[(idx / 3) % 3],
-                          kbs[idx % 3]};
+        const gc_tuning t{wus[idx / 36], (uint32_t)((idx / 18) % 2), tps[(idx / 6) % 3],
+                          kbs[(idx / 2) % 3], (uint32_t)(idx % 2) + 1u};
         p->wu_max_targets = t.wu_max_targets;
         p->wu_schedule = t.schedule;
         p->wu_tile = t.tile_pairs;
         p->wu_kb = t.comp_block;
+        p->wu_tpl = t.targets_per_lane;
         float tbest = 1e30f;
         for (int r = 0; r < reps && rc == GC_OK; ++r) {
             uint64_t W = 0;
@@ -2254,6 +2316,7 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
     p->wu_schedule = keep.schedule;
     p->wu_tile = keep.tile_pairs;
     p->wu_kb = keep.comp_block;
+    p->wu_tpl = keep.targets_per_lane;
     if (rc != GC_OK) return rc;
     uint64_t W = 0;
     GC_TRY(rebuild_wus(p, c, choice.wu_max_targets, &W));   // context matches the choice

@@ -106,23 +106,26 @@ class GcNbodyStats(C.Structure):
 
 class GcTuning(C.Structure):
     _fields_ = [("wu_max_targets", C.c_uint32), ("schedule", C.c_uint32),
-                ("tile_pairs", C.c_uint32), ("comp_block", C.c_uint32)]
+                ("tile_pairs", C.c_uint32), ("comp_block", C.c_uint32),
+                ("targets_per_lane", C.c_uint32)]
 
 
-GC_TUNE_COUNT = 54
-_TUNE_FIELDS = ["wu_max_targets", "schedule", "tile_pairs", "comp_block"]
+GC_TUNE_COUNT = 108
+_TUNE_FIELDS = ["wu_max_targets", "schedule", "tile_pairs", "comp_block", "targets_per_lane"]
 
 
 def tune_key(t):
-    """Name of a tuning in the autotuner's times: 'wu,fifo|lpt,tile,block'."""
+    """Name of a tuning in the autotuner's times:
+    'wu,fifo|lpt,tile,block,targets per lane'."""
     return (f"{t['wu_max_targets']},{'lpt' if t['schedule'] else 'fifo'},"
-            f"{t['tile_pairs']},{t['comp_block']}")
+            f"{t['tile_pairs']},{t['comp_block']},{t['targets_per_lane']}")
 
 
 def tune_order():
     """The autotuner's tunings in the order of its times (gc_autotune)."""
-    return [dict(wu_max_targets=w, schedule=s, tile_pairs=tp, comp_block=kb)
-            for w in (8, 16, 32) for s in (0, 1) for tp in (64, 128, 256) for kb in (8, 16, 32)]
+    return [dict(wu_max_targets=w, schedule=s, tile_pairs=tp, comp_block=kb, targets_per_lane=l)
+            for w in (8, 16, 32) for s in (0, 1) for tp in (64, 128, 256) for kb in (8, 16, 32)
+            for l in (1, 2)]
 
 
 class GcError(RuntimeError):
@@ -485,9 +488,9 @@ class Pool:
         return d
 
     def set_tuning(self, wu_max_targets=16, schedule=GC_SCHED_FIFO, tile_pairs=128,
-                   comp_block=8):
+                   comp_block=8, targets_per_lane=1):
         t = GcTuning(wu_max_targets=wu_max_targets, schedule=schedule, tile_pairs=tile_pairs,
-                     comp_block=comp_block)
+                     comp_block=comp_block, targets_per_lane=targets_per_lane)
         _check(self.lib.gc_set_tuning(self.h, C.byref(t)), "gc_set_tuning")
 
     def tuning(self):

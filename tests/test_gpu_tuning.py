@@ -1,6 +1,7 @@
 """GPU tests of the interaction schedule (work-unit size 8 / 16 / 32 targets,
 admission-order or longest-first hand-out) and tile shape (64 / 128 / 256
-source pairs per staged tile, 8 / 16 / 32 pairs per plain partial sum), and
+source pairs per staged tile, 8 / 16 / 32 pairs per plain partial sum, one
+or two targets per lane; odd work units leave a lane's second slot idle), and
 of the autotuner over all of them: every schedule and shape matches the FP64
 oracle within the per-result tolerance, the work-unit order alone leaves
 every result bit-identical, and the autotuner keeps its fastest measured
@@ -77,13 +78,14 @@ def test_bad_tuning_rejected(gc, batch):
     pool = make_pool(gc, torch, x.shape[0], x.shape[0])
     for bad in [dict(wu_max_targets=12), dict(wu_max_targets=64), dict(schedule=2),
                 dict(tile_pairs=96), dict(tile_pairs=512), dict(comp_block=4),
-                dict(comp_block=64)]:
-        t = dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8)
+                dict(comp_block=64), dict(targets_per_lane=0), dict(targets_per_lane=3)]:
+        t = dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8, targets_per_lane=1)
         t.update(bad)
         with pytest.raises(gc.GcError) as e:
             pool.set_tuning(**t)
         assert e.value.code == gc.GC_ERR_ARG
-    assert pool.tuning() == dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8)
+    assert pool.tuning() == dict(wu_max_targets=16, schedule=0, tile_pairs=128, comp_block=8,
+                                 targets_per_lane=1)
     with pytest.raises(gc.GcError) as e:
         pool.autotune()                      # nothing flushed yet
     assert e.value.code == gc.GC_ERR_NOT_READY
