@@ -661,7 +661,10 @@ int gc_get_tuning(gc_pool_t *pool, gc_tuning *t);
  * wave, gravity tasks) under every schedule and tile shape, work-unit size
  * {8, 16, 32} x {FIFO, LPT} x tile pairs {64, 128, 256} x compensation block
  * {8, 16, 32} x targets per lane {1, 2}, timing each with CUDA events (best
- * of `reps`), and keep the fastest for later flushes.  ms_out (may be NULL)
+ * of `reps`), and keep the fastest for later flushes -- a two-targets-per-
+ * lane shape only when more than 3 % faster than the fastest one-target
+ * shape, since it holds fewer warps per SM (a smaller gc_max_combine_size,
+ * slower small batches).  ms_out (may be NULL)
  * receives the GC_TUNE_COUNT times, entry (((w * 2 + s) * 3 + t) * 3 + k) *
  * 2 + l - 1 for the w-th work-unit size, schedule s, t-th tile size, k-th
  * block and l targets per lane; *best_out (may be NULL) the choice.  The batch's result rows are rewritten by the re-runs

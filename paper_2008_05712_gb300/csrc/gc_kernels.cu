@@ -2268,8 +2268,8 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
         if (e0) cudaEventDestroy(e0);
         return GC_ERR_CUDA;
     }
-    float best = 1e30f;
-    gc_tuning choice = saved;
+    float best = 1e30f, best1 = 1e30f;
+    gc_tuning choice = saved, choice1 = saved;
     int rc = GC_OK;
     // index = (((wu * 2 + schedule) * 3 + tile) * 3 + block) * 2 + targets per lane - 1
     for (int idx = 0; idx < GC_TUNE_COUNT && rc == GC_OK; ++idx) {
@@ -2308,6 +2308,17 @@ extern "C" int gc_autotune(gc_pool_t *p, int reps, gc_tuning *best_out,
             best = tbest;
             choice = t;
         }
+        if (t.targets_per_lane == 1 && tbest < best1) {
+            best1 = tbest;
+            choice1 = t;
+        }
+    }
+    // Two targets per lane hold fewer warps per SM, which lowers the
+    // combine size (resident warps) and slows small batches: taken only
+    // when more than 3 % faster than the best one-target shape
+    if (choice.targets_per_lane != 1 && best1 <= best * 1.03f) {
+        best = best1;
+        choice = choice1;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -258,14 +258,28 @@ __global__ void k_classify(const uint32_t *uniq, const unsigned long long *count
     if (threadIdx.x < 8) hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) hits = 0;
     __syncthreads();
+    // counts kept per thread and summed per warp at the end: one shared-
+    // memory add per id made every thread of a block wait on the same few
+    // words
+    uint32_t h[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    uint32_t nh = 0;
     uint64_t U = *count_dev;
     for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < U;
          k += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t id = uniq[k];
         uint32_t c = ref_count[id];
         ref_count[id] = 0;
-        atomicAdd(&hist[hist_bin(c)], 1u);
-        if (slot_of_id[id] != GC_NONE) atomicAdd(&hits, 1u);
+        const int bin = hist_bin(c);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] += bin == q ? 1u : 0u;
+        nh += slot_of_id[id] != GC_NONE ? 1u : 0u;
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        uint32_t v = q < 8 ? h[q] : nh;
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(q < 8 ? &hist[q] : &hits, v);
     }
     __syncthreads();
     if (threadIdx.x < 8 && hist[threadIdx.x])

@@ -97,7 +97,15 @@ def test_autotune_keeps_fastest_and_caches(gc, orc, batch, tmp_path):
     pool, _ = run(gc, x, to, tg, so, sr, 16, gc.GC_SCHED_FIFO)
     choice, times = pool.autotune(reps=2)
     assert len(times) == gc.GC_TUNE_COUNT and all(v > 0 for v in times.values())
-    assert times[gc.tune_key(choice)] == min(times.values())
+    # the fastest shape, or the fastest with one target per lane when a two-
+    # target shape is at most 3 % faster
+    fastest = min(times.values())
+    one = min(v for k, v in times.items() if k.endswith(",1"))
+    if choice["targets_per_lane"] == 1:
+        assert times[gc.tune_key(choice)] == one
+        assert one == fastest or one <= fastest * 1.03 * (1 + 1e-5)
+    else:
+        assert times[gc.tune_key(choice)] == fastest and one > fastest * 1.03 * (1 - 1e-5)
     assert pool.tuning() == choice
     # the re-run rows of the tuned batch still match the oracle
     ref = orc.gravity_batch(x, to, tg, so, sr, EPS2)
