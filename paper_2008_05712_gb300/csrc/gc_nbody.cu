@@ -867,11 +867,14 @@ struct WalkThresholds {
 };
 
 // The walk's view of node k, 16 bytes: W[k] = {subtree size | leaf << 31,
-// centre x | level << 22, centre y, centre z} (centre in doubled grid units,
-// below 2^22), and for a leaf LF[k] = {first particle, count}.  W[nn] is a
-// sentinel.  Whether a node contains a bucket is a preorder test against the
+// centre x | level << 22, centre y | leaf count << 22, centre z} (centre in
+// doubled grid units, below 2^22; the leaf count, WALK_LEAF_FAR when it does
+// not fit in 10 bits, lets the count pass skip LF), and for a leaf LF[k] =
+// {first particle, count}.  W[nn] is a sentinel.  Whether a node contains a bucket is a preorder test against the
 // bucket's own leaf (k <= leaf < k + size), so the per-node record needs no
 // particle range; the acceptance thresholds come per level from a table.
+constexpr uint32_t WALK_LEAF_FAR = 1023u;   // leaf count field: read LF instead
+
 __global__ void k_walk_nodes(const uint4 *node_a, const uint4 *node_b, uint32_t nn, uint4 *W,
                              uint2 *LF)
 {
@@ -883,8 +886,9 @@ __global__ void k_walk_nodes(const uint4 *node_a, const uint4 *node_b, uint32_t 
         const uint4 A = node_a[k], C = node_b[k];
         const uint32_t lvl = A.w & 255u;
         const uint32_t s = 1u << (22 - lvl), h = s >> 1;
-        W[k] = make_uint4(A.z | ((A.w & 256u) << 23), (C.x * s + h) | (lvl << 22), C.y * s + h,
-                          C.z * s + h);
+        const uint32_t ln = (A.w & 256u) ? min(A.y, WALK_LEAF_FAR) : 0u;
+        W[k] = make_uint4(A.z | ((A.w & 256u) << 23), (C.x * s + h) | (lvl << 22),
+                          (C.y * s + h) | (ln << 22), C.z * s + h);
         LF[k] = make_uint2(A.x, A.y);
     }
 }
@@ -926,7 +930,7 @@ __device__ __forceinline__ bool walk_accepts(uint32_t k, const uint4 &R, uint32_
 {
     const uint32_t size = R.x & 0x7FFFFFFFu;
     if (k <= lf && lf < k + size) return false;
-    const int cx = (int)(R.y & 0x3FFFFFu), cy = (int)R.z, cz = (int)R.w;
+    const int cx = (int)(R.y & 0x3FFFFFu), cy = (int)(R.z & 0x3FFFFFu), cz = (int)R.w;
     const uint32_t dx = (uint32_t)max(0, max(lo.x - cx, cx - hi.x));
     const uint32_t dy = (uint32_t)max(0, max(lo.y - cy, cy - hi.y));
     const uint32_t dz = (uint32_t)max(0, max(lo.z - cz, cz - hi.z));
@@ -1018,6 +1022,11 @@ __global__ void __launch_bounds__(128, 8) k_walk(const uint4 *W, const uint2 *LF
                     }
                 }
                 ++cnt;
+                k += size;
+            } else if (R.x >> 31 && !FILL) {   // leaf: its particle count
+                uint32_t ln = R.z >> 22;
+                if (ln == WALK_LEAF_FAR) ln = LF[k].y;
+                cnt += ln;
                 k += size;
             } else if (R.x >> 31) {      // leaf: its particles
                 const uint2 L = LF[k];
