@@ -116,6 +116,8 @@ __global__ void k_row_values(const float4 *res, uint64_t n, gcd4 *out)
 
 void free_ctx(FlushCtx &c)
 {
+    for (cudaStream_t q : c.ps)   // the pack's side streams read the buffers below
+        if (q) cudaStreamSynchronize(q);
     DBuf *bufs[] = {&c.tasks, &c.tgt_ids, &c.src_ids, &c.tgt_perm, &c.src_perm, &c.stg_tgt,
                     &c.stg_src, &c.wu, &c.wu_cnt, &c.wu_off, &c.rowcnt, &c.lj_list, &c.res,
                     &c.row_id, &c.rid_sorted, &c.row_sorted, &c.rows_tmp, &c.runs, &c.tiles,
@@ -128,13 +130,10 @@ void free_ctx(FlushCtx &c)
     if (c.ev_scattered) cudaEventDestroy(c.ev_scattered);
     if (c.d_ctr) cudaFree(c.d_ctr);
     if (c.h_ctr) cudaFreeHost(c.h_ctr);
+    for (cudaStream_t q : c.ps)
+        if (q) cudaStreamDestroy(q);
     for (cudaEvent_t e : c.pev)
         if (e) cudaEventDestroy(e);
-    for (cudaStream_t q : c.ps)
-        if (q) {
-            cudaStreamSynchronize(q);
-            cudaStreamDestroy(q);
-        }
     if (c.owns_stream && c.s) cudaStreamDestroy(c.s);
 }
 
