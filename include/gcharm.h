@@ -161,7 +161,8 @@ int gc_pool_destroy(gc_pool_t *pool);
 int gc_pool_upload(gc_pool_t *pool, const uint32_t *ids, const float *xyzm,
                    uint64_t n);
 
-/* As gc_pool_upload, in stream order: returns once the copies are queued.
+/* As gc_pool_upload (Section 3.2: the chares' data regions on the GPU), in
+ * stream order: returns once the copies are queued.
  * The host arrays must stay unchanged until the pool's stream has passed
  * this point (gc_join, then a wait on the joined stream).  The copies run
  * on a host-to-device stream of the pool's own and wait only for the
@@ -290,7 +291,8 @@ int gc_read_results(gc_pool_t *pool, const uint64_t *task_ids, uint64_t n,
 int gc_read_totals(gc_pool_t *pool, const uint32_t *ids, uint64_t n,
                    double *acc4);
 
-/* As gc_read_totals, in stream order: the totals as of every batch flushed
+/* As gc_read_totals (Section 2.2: results returned to the chares), in stream
+ * order: the totals as of every batch flushed
  * so far are copied to acc4 once the pool's stream passes this point
  * (gc_join, then a wait on the joined stream); ids and acc4 must stay valid
  * until then.  The totals are gathered in the pool's stream order; the copy
@@ -372,7 +374,8 @@ int gc_build_nbody_tasks(gc_pool_t *pool, const float *xyzm_dev, uint64_t n,
                          int bucket_max, int theta_num, int theta_den,
                          uint64_t task_id_base, uint64_t info_out[4]);
 
-/* Morton order of the next N-body builds: GC_ORDER_FULL sorts every build's
+/* Morton order of the next N-body builds (Section 4.1: the tree is rebuilt
+ * every step): GC_ORDER_FULL sorts every build's
  * keys from scratch; GC_ORDER_SEEDED (default) starts from the previous
  * build's order when it had the same n.  Both give identical trees.
  * Errors: GC_ERR_ARG (unknown mode). */
@@ -394,8 +397,9 @@ typedef struct {
     double tree_ms_sum;
 } gc_nbody_stats_t;
 
-/* Statistics of this pool's N-body builds (waits for the last build's end
- * event).  Errors: GC_ERR_ARG, GC_ERR_CUDA. */
+/* Statistics of this pool's N-body builds (Section 4.1's per-step tree
+ * build; waits for the last build's end event).  Errors: GC_ERR_ARG,
+ * GC_ERR_CUDA. */
 int gc_nbody_stats(gc_pool_t *pool, gc_nbody_stats_t *out);
 
 /* As gc_build_nbody_tasks, with the positions of particles 0..n-1 taken
@@ -627,6 +631,10 @@ int gc_graph_results(gc_graph_t *g, uint64_t first_row, uint64_t n_rows, float *
 int gc_graph_destroy(gc_graph_t *g);
 
 /* ---- interaction schedule and its autotuner ------------------------------ */
+/* How the combined kernel of a batch (Section 3.1: one launch for many work
+ * requests) hands its work to warps and stages its sources; the paper fixes
+ * one thread block per work request, so these choices have no counterpart
+ * there beyond that design. */
 
 #define GC_SCHED_FIFO 0u   /* work units handed out in admission order          */
 #define GC_SCHED_LPT 1u    /* longest first (targets x sources, descending;
