@@ -61,6 +61,10 @@ int main(void) {
          offsetof(gc_config, cuda_stream), sizeof(gc_task), offsetof(gc_task, target_ids),
          offsetof(gc_task, shift), sizeof(gc_stats_t), offsetof(gc_stats_t, stage_ms_sum),
          sizeof(gc_serve_config), sizeof(gc_serve_report), offsetof(gc_serve_report, wall_s));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gc_serve_config, keep_pageable),
+         offsetof(gc_serve_config, poll_ns), offsetof(gc_serve_report, pinned_bytes),
+         offsetof(gc_serve_report, retire_s), sizeof(gc_tuning),
+         offsetof(gc_tuning, targets_per_lane), sizeof(gc_nbody_stats_t));
   return 0;
 }
 """)
@@ -73,7 +77,11 @@ int main(void) {
             ctypes.sizeof(gcharm.GcTask), gcharm.GcTask.target_ids.offset,
             gcharm.GcTask.shift.offset, ctypes.sizeof(gcharm.GcStats),
             gcharm.GcStats.stage_ms_sum.offset, ctypes.sizeof(gcharm.GcServeConfig),
-            ctypes.sizeof(gcharm.GcServeReport), gcharm.GcServeReport.wall_s.offset]
+            ctypes.sizeof(gcharm.GcServeReport), gcharm.GcServeReport.wall_s.offset,
+            gcharm.GcServeConfig.keep_pageable.offset, gcharm.GcServeConfig.poll_ns.offset,
+            gcharm.GcServeReport.pinned_bytes.offset, gcharm.GcServeReport.retire_s.offset,
+            ctypes.sizeof(gcharm.GcTuning), gcharm.GcTuning.targets_per_lane.offset,
+            ctypes.sizeof(gcharm.GcNbodyStats)]
     assert got == want
 
 
