@@ -110,3 +110,19 @@ def test_row_values_on_the_host():
     assert v[0].tolist() == [1.0 - 2.0 ** -30, -2.0, 0.75, 0.0]
     assert v[1].tolist() == [0.0, 0.0, 0.0, 0.0]
     assert gcharm.value(np.zeros((0, 8), np.float32)).shape == (0, 4)
+
+
+def test_tuning_order_matches_header():
+    # the binding's autotuner times are read by index: its order must be the
+    # header's (((w * 2 + s) * 3 + t) * 3 + k) * 2 + l - 1 over GC_TUNE_COUNT
+    from paper_2008_05712_gb300 import gcharm
+    with open(os.path.join(ROOT, "include", "gcharm.h")) as f:
+        count = int(re.search(r"#define GC_TUNE_COUNT (\d+)", f.read()).group(1))
+    order = gcharm.tune_order()
+    assert count == gcharm.GC_TUNE_COUNT == len(order)
+    assert len({gcharm.tune_key(t) for t in order}) == count
+    for idx, t in enumerate(order):
+        w = (8, 16, 32).index(t["wu_max_targets"])
+        tp = (64, 128, 256).index(t["tile_pairs"])
+        kb = (8, 16, 32).index(t["comp_block"])
+        assert idx == (((w * 2 + t["schedule"]) * 3 + tp) * 3 + kb) * 2 + t["targets_per_lane"] - 1
