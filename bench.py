@@ -51,8 +51,9 @@ PACK_BYTES_PER_ENTRY = 40
 # kernels (None until captured again after a kernel change):
 # k_gravity per interaction, the pack kernels per list entry.
 # profiles/k_gravity_nbody262k.md: 502.6 MB for 2.949e8 interactions (262,144-particle
-# step, k_gravity<128, 32>, the tuned tile shape)
-GRAVITY_DRAM_BYTES_PER_INTERACTION = 502.6e6 / 2.949e8
+# step, k_gravity<128, 32>, the tuned tile shape) -- taken before the kernel
+# gained its targets-per-lane parameter, so not reported for the current one
+GRAVITY_DRAM_BYTES_PER_INTERACTION = None
 # profiles/k_pack_mid_nbody262k.md: 629.6 MB for 3.07e7 entries (262,144-particle step,
 # the chunked block sort)
 PACK_DRAM_BYTES_PER_ENTRY = 629.6e6 / 3.07e7
